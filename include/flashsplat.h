@@ -1,0 +1,219 @@
+/*
+ * flashsplat.h -- C ABI of the GB300 FlashSplat library (libflashsplat.so).
+ *
+ * FlashSplat (arXiv 2409.08270) segments a reconstructed 3D Gaussian Splatting
+ * scene from 2D label masks in one pass: every mask pixel of every view is
+ * alpha-composited through the scene (Sec. 3.1, Eq. 1), each Gaussian's
+ * alpha_i*T_i is accumulated into the column of the pixel's label (Sec. 3.2,
+ * Eq. 6; Sec. 3.3, Eq. 7; Supp. Sec. 6: the table A in R^{E x N}), and the
+ * optimal label per Gaussian is the closed-form biased argmax of its row
+ * (Sec. 3.2 "Regularized ILP for Noise Reduction"; Sec. 3.3, Eq. 7).
+ *
+ * Conventions (fixed where the paper is silent):
+ *   - Gaussian i: mean m_i (3), unit quaternion q_i = (w, x, y, z) (any
+ *     non-zero norm; normalised inside), linear scales s_i (3, > 0),
+ *     activated opacity o_i in [0, 1].  Sigma3D = R(q) diag(s^2) R(q)^T.
+ *   - Camera: world->camera rotation R (row-major 3x3) and translation t,
+ *     OpenCV axes (x right, y down, z forward), pinhole fx, fy, cx, cy.
+ *     Pixel (u, v) is sampled at (u + 0.5, v + 0.5).
+ *   - EWA projection, +0.3 px^2 on the 2D covariance diagonal; Gaussians with
+ *     view depth <= 0.2 or opacity < 1/255 are culled.
+ *   - alpha = min(0.99, o exp(-0.5 d^T Sigma2D^-1 d)); alpha < 1/255 is
+ *     skipped; a pixel stops before a Gaussian that would take T below 1e-4.
+ *   - Depth order: view-space z of the mean, ties by lower Gaussian index.
+ *   - Table layout: Gaussian-major, element (i, e) at index i*E + e.
+ *
+ * Threading and streams: a context is bound to one device.  Calls on one
+ * context must not run concurrently from several host threads.  Work is
+ * enqueued on the caller's CUDA stream (cudaStream_t passed as void*; NULL =
+ * legacy default stream) and is asynchronous unless stated otherwise;
+ * fs_synchronize() waits for it and reports device-side errors.
+ *
+ * Errors: every call returns an fs_status; no C++ exception crosses the ABI.
+ * fs_last_error() returns a message for the calling thread's last failure.
+ */
+#ifndef FLASHSPLAT_H
+#define FLASHSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FS_VERSION_MAJOR 0
+#define FS_VERSION_MINOR 1
+
+typedef enum fs_status {
+  FS_OK = 0,
+  FS_INVALID_ARGUMENT = 1, /* bad pointer, size, dtype, zero quaternion, ... */
+  FS_OUT_OF_MEMORY = 2,    /* a device or pinned-host allocation failed */
+  FS_CUDA_ERROR = 3,       /* a CUDA runtime call or kernel failed */
+  FS_TIMEOUT = 4,          /* a bounded device-side wait gave up */
+  FS_UNSUPPORTED = 5,      /* valid request outside what this build handles */
+  FS_CANCELLED = 6
+} fs_status;
+
+typedef enum fs_dtype {
+  FS_F32 = 0,
+  FS_F64 = 1,
+  FS_BF16 = 2,
+  FS_F16 = 3,
+  FS_U8 = 4,
+  FS_I32 = 5
+} fs_dtype;
+
+typedef enum fs_memory {
+  FS_MEM_HOST = 0,   /* host memory (pinned memory makes copies asynchronous) */
+  FS_MEM_DEVICE = 1  /* device memory on the context's device */
+} fs_memory;
+
+typedef struct fs_ctx fs_ctx;
+typedef struct fs_scene fs_scene;
+
+/* Context options.  Zero-initialise and set what you need; 0 = default. */
+typedef struct fs_options {
+  int32_t views_per_batch;  /* views binned and blended per launch group (default 8) */
+  int32_t reserved[15];
+} fs_options;
+
+/* A Gaussian scene (Sec. 3.1: G_i = {m_i, q_i, s_i, o_i}; colour unused). */
+typedef struct fs_gaussians {
+  int64_t n;             /* number of Gaussians, 0 <= n < 2^31 */
+  const void* mean;      /* [n][3] FS_F32 */
+  const void* quat;      /* [n][4] (w, x, y, z), FS_F32 or FS_BF16 */
+  const void* scale;     /* [n][3] linear scales, FS_F32 or FS_BF16 */
+  const void* opacity;   /* [n] activated opacity, FS_F32 or FS_F16 */
+  int32_t quat_dtype;
+  int32_t scale_dtype;
+  int32_t opacity_dtype;
+  int32_t memory;        /* fs_memory of all four arrays */
+} fs_gaussians;
+
+/* A pinhole camera (world -> camera). */
+typedef struct fs_camera {
+  double R[9];           /* row-major rotation */
+  double t[3];
+  double fx, fy, cx, cy;
+  int32_t width, height; /* mask size in pixels, each in [1, 65535] */
+} fs_camera;
+
+/* Counters of the last fs_accumulate / fs_solve on a context. */
+typedef struct fs_stats {
+  int64_t views;          /* views processed */
+  int64_t pixels;         /* mask pixels walked */
+  int64_t list_entries;   /* (tile, Gaussian) pairs binned, summed over views */
+  int64_t bad_labels;     /* pixels whose label was outside [0, E) (skipped) */
+  int64_t reserved[4];
+} fs_stats;
+
+/* Outputs of fs_solve.  Any pointer may be NULL to skip that output. */
+typedef struct fs_result {
+  int32_t memory;         /* fs_memory of every output below */
+  int32_t table_dtype;    /* FS_F32 or FS_F64: element type of `table` */
+  void* table;            /* [n][E] contribution table A (Gaussian-major) */
+  uint64_t* member_bits;  /* [n] bit e set iff S[e, i] = 1 (needs E <= 64) */
+  int32_t* label;         /* [n] the unique e with S[e, i] = 1, else -1 */
+  float* margin;          /* [n] min over e of the relative decision margin */
+} fs_result;
+
+/* Version as MAJOR*1000 + MINOR. */
+int32_t fs_version(void);
+
+/* Message for the calling thread's most recent failed call ("" if none).
+ * The pointer stays valid until the next failing call on the same thread. */
+const char* fs_last_error(void);
+
+/* Create a context on CUDA device `device`.  opt may be NULL.  The library
+ * owns the context and its device workspace; release with fs_destroy.
+ * Errors: FS_INVALID_ARGUMENT (out NULL, device out of range),
+ * FS_UNSUPPORTED (device is not compute capability 10.3), FS_CUDA_ERROR. */
+fs_status fs_create(fs_ctx** out, int32_t device, const fs_options* opt);
+
+/* Destroy a context (waits for its outstanding work).  NULL is a no-op.
+ * Scenes created on it must be destroyed first. */
+fs_status fs_destroy(fs_ctx* ctx);
+
+/* Make a scene resident on the context's device (Sec. 3.1, Sec. 4.2: only
+ * {m, q, s, o} are used).  The library copies the arrays into its own device
+ * storage (quaternions normalised, the 3D covariance precomputed in FP64);
+ * the caller may free its buffers when the call returns (the call is
+ * synchronous).  Errors: FS_INVALID_ARGUMENT (NULL pointers, n out of
+ * range, dtype not allowed for the field, a zero quaternion, a non-finite
+ * value), FS_OUT_OF_MEMORY, FS_CUDA_ERROR. */
+fs_status fs_scene_create(fs_ctx* ctx, const fs_gaussians* g, fs_scene** out);
+
+/* Free a scene's device storage (waits for work that uses it).  NULL is a
+ * no-op. */
+fs_status fs_scene_destroy(fs_scene* scene);
+
+/* Number of Gaussians in a scene (0 for NULL). */
+int64_t fs_scene_size(const fs_scene* scene);
+
+/*
+ * fs_accumulate -- add the contributions of n_views masks to a table
+ * (Sec. 3.2 Eq. 6, Sec. 3.3 Eq. 7, Sec. 4.2, Supp. Sec. 6):
+ *
+ *   table[i*E + e] += sum_{v, pixels p with M^v_p = e} alpha_i(p) T_i(p)
+ *
+ * cams[n_views]: host array.  masks[n_views]: host array of pointers, view
+ * v's labels row-major [cams[v].height][cams[v].width], element type
+ * mask_dtype (FS_U8 or FS_I32), in mask_memory (FS_MEM_HOST or
+ * FS_MEM_DEVICE).  Pixels whose label is outside [0, E) are skipped and
+ * counted in fs_stats.bad_labels.  E in [1, 4096].
+ * table: device memory [n][E] of table_dtype (FS_F32, or FS_F64 for the
+ * FP64 cross-view reduction), NOT cleared: contributions are added, so a
+ * solve can be split over several calls (view subsets) and resumed.
+ * Host masks are copied on `stream` and must stay valid until the stream
+ * reaches the end of the call.  Asynchronous.
+ * Errors: FS_INVALID_ARGUMENT, FS_OUT_OF_MEMORY (workspace growth),
+ * FS_CUDA_ERROR.
+ */
+fs_status fs_accumulate(fs_ctx* ctx, const fs_scene* scene, const fs_camera* cams,
+                        int32_t n_views, const void* const* masks, int32_t mask_dtype,
+                        int32_t mask_memory, int32_t E, void* table, int32_t table_dtype,
+                        void* stream);
+
+/*
+ * fs_assign -- closed-form optimal labels from a contribution table
+ * (Sec. 3.2: L1-normalise, add the background bias gamma to the background
+ * entry, argmax; Sec. 3.3 Eq. 7: object e against "others" = sum of every
+ * other column; Supp. Sec. 6: segmentation matrix S in {0,1}^{E x N}).
+ *
+ * For every Gaussian i and label e, with S_i = sum_e A[i, e]:
+ *   member(e, i)  <=>  A[i,e]/n_i  >  (S_i - A[i,e])/n_i + gamma,
+ *   n_i = max(|S_i - A[i,e]| + |A[i,e]|, 1e-12)   (a tie is not a member).
+ * gamma in [-1, 1].  table: device [n][E] of table_dtype (FS_F32 / FS_F64).
+ * Outputs (device, each may be NULL): member_bits[n] (needs E <= 64),
+ * label[n] (the unique member e, else -1), margin[n]
+ * (min_e |(1-gamma) A[i,e] - (1+gamma)(S_i - A[i,e])| / S_i; +inf if
+ * S_i = 0).  Asynchronous.  Errors: FS_INVALID_ARGUMENT, FS_UNSUPPORTED
+ * (member_bits with E > 64), FS_CUDA_ERROR.
+ */
+fs_status fs_assign(fs_ctx* ctx, const void* table, int32_t table_dtype, int64_t n, int32_t E,
+                    float gamma, uint64_t* member_bits, int32_t* label, float* margin,
+                    void* stream);
+
+/*
+ * fs_solve -- the whole path: clear a table, fs_accumulate all views, then
+ * fs_assign with gamma (Sec. 3.2-3.3).  Outputs go where `out` says
+ * (out->memory: device buffers, or host buffers filled by asynchronous
+ * copies on `stream` -- pinned host memory keeps them asynchronous).  When
+ * out->table is NULL the table lives in the context's workspace.
+ * Asynchronous; call fs_synchronize before reading host outputs.
+ * Errors: as fs_accumulate and fs_assign.
+ */
+fs_status fs_solve(fs_ctx* ctx, const fs_scene* scene, const fs_camera* cams, int32_t n_views,
+                   const void* const* masks, int32_t mask_dtype, int32_t mask_memory, int32_t E,
+                   float gamma, const fs_result* out, void* stream);
+
+/* Wait for the context's work on `stream` and report errors recorded by its
+ * kernels (FS_CUDA_ERROR with a message).  Fills *stats if non-NULL. */
+fs_status fs_synchronize(fs_ctx* ctx, void* stream, fs_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLASHSPLAT_H */

@@ -1,0 +1,216 @@
+"""FlashSplat FP64 CPU oracle -- test infrastructure only.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA path:
+the renderer/accumulator is plain C (``fs_oracle.c``), the assignment step is
+numpy (``assign.py``).
+
+Paper: FlashSplat (arXiv 2409.08270).  Sec. 3.1 Eq. 1 (alpha blending),
+Sec. 3.2 Eq. 2-6 (binary ILP and its closed form), Sec. 3.2 "Regularized ILP"
+(background bias), Sec. 3.3 Eq. 7 (multi-instance), Supp. Sec. 6 (contribution
+table A in R^{E x N} and segmentation matrix S).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+from .assign import assign, assign_margin  # noqa: F401
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libfs_oracle.so")
+_lib = None
+
+FLAG_ALPHA_EDGE = 1
+FLAG_T_EDGE = 2
+FLAG_DEPTH_TIE = 4
+FLAG_DOWNSTREAM = 8
+
+
+class Camera(ctypes.Structure):
+    """Mirror of ``fso_camera``: world->camera R (row-major), t, intrinsics."""
+
+    _fields_ = [
+        ("R", ctypes.c_double * 9),
+        ("t", ctypes.c_double * 3),
+        ("fx", ctypes.c_double),
+        ("fy", ctypes.c_double),
+        ("cx", ctypes.c_double),
+        ("cy", ctypes.c_double),
+        ("width", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+        ("pad", ctypes.c_int32 * 2),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/libfs_oracle.so`` (gcc, -O2)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    i64, i32, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
+    lib.fso_accumulate.restype = ctypes.c_int
+    lib.fso_accumulate.argtypes = [i64, vp, vp, vp, vp, i32, vp, vp, vp, i32, vp, i64, i32, i32,
+                                   vp, vp, vp, vp, vp]
+    lib.fso_pixel_lists.restype = ctypes.c_int64
+    lib.fso_pixel_lists.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, i64, vp, vp, vp, vp]
+    lib.fso_project_view.restype = ctypes.c_int
+    lib.fso_project_view.argtypes = [i64, vp, vp, vp, vp, vp, vp]
+    _lib = lib
+    return lib
+
+
+def _f32(a, shape_last=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if shape_last is not None and a.ndim != 2:
+        a = a.reshape(-1, shape_last)
+    return a
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_cameras(cams) -> ctypes.Array:
+    """cams: iterable of dicts with R (3x3), t (3), fx, fy, cx, cy, width, height."""
+    cams = list(cams)
+    arr = (Camera * max(len(cams), 1))()
+    for k, c in enumerate(cams):
+        R = np.asarray(c["R"], dtype=np.float64).reshape(9)
+        t = np.asarray(c["t"], dtype=np.float64).reshape(3)
+        arr[k].R[:] = list(R)
+        arr[k].t[:] = list(t)
+        arr[k].fx, arr[k].fy = float(c["fx"]), float(c["fy"])
+        arr[k].cx, arr[k].cy = float(c["cx"]), float(c["cy"])
+        arr[k].width, arr[k].height = int(c["width"]), int(c["height"])
+    return arr
+
+
+@dataclass
+class Accumulation:
+    table: np.ndarray   # [rows, E] float64
+    risk: np.ndarray    # [rows, E] float64: bound on |change| if marginal decisions flip
+    flags: np.ndarray   # [rows] uint8, FLAG_* bits
+    t_final: np.ndarray | None
+    n_eval: int         # evaluated (pixel, Gaussian) pairs
+    n_hit: int          # contributing pairs (alpha*T > 0) on tracked rows
+    n_bad_label: int    # pixels whose label is outside [0, E)
+    n_unseen: int       # tracked Gaussians valid in no view
+
+
+def accumulate(gaussians, cams, masks, E: int, sel=None, cull_mode: int = 0,
+               nthreads: int | None = None, want_t_final: bool = False) -> Accumulation:
+    """Contribution table of Eq. 6 / Eq. 7 in FP64.
+
+    gaussians: dict with mean [N,3], quat [N,4] (w,x,y,z), scale [N,3] (linear),
+    opacity [N] (activated).  cams: list of camera dicts.  masks: list of V
+    integer arrays [H, W].  sel: optional sorted Gaussian indices to track.
+    """
+    lib = _load()
+    mean = _f32(gaussians["mean"], 3)
+    quat = _f32(gaussians["quat"], 4)
+    scale = _f32(gaussians["scale"], 3)
+    opac = np.ascontiguousarray(np.asarray(gaussians["opacity"], dtype=np.float32).reshape(-1))
+    N = mean.shape[0]
+    cams = list(cams)
+    V = len(cams)
+    carr = make_cameras(cams)
+    flat = [np.ascontiguousarray(np.asarray(m).reshape(-1).astype(np.int32)) for m in masks]
+    offs = np.zeros(max(V, 1), dtype=np.int64)
+    acc = 0
+    for v in range(V):
+        c = cams[v]
+        if flat[v].size != int(c["width"]) * int(c["height"]):
+            raise ValueError(f"mask {v} has {flat[v].size} pixels, camera wants "
+                             f"{int(c['width'])}x{int(c['height'])}")
+        offs[v] = acc
+        acc += flat[v].size
+    allm = np.concatenate(flat) if flat else np.zeros(1, np.int32)
+    if sel is not None:
+        sel = np.ascontiguousarray(np.asarray(sel, dtype=np.int64))
+        if sel.size and np.any(np.diff(sel) <= 0):
+            raise ValueError("sel must be strictly increasing")
+        rows = sel.size
+    else:
+        rows = N
+    table = np.zeros((rows, E), dtype=np.float64)
+    risk = np.zeros((rows, E), dtype=np.float64)
+    flags = np.zeros(max(rows, 1), dtype=np.uint8)
+    tf = np.zeros(max(acc, 1), dtype=np.float64) if want_t_final else None
+    stats = np.zeros(4, dtype=np.int64)
+    if nthreads is None:
+        nthreads = max(1, len(os.sched_getaffinity(0)))
+    rc = lib.fso_accumulate(N, _ptr(mean), _ptr(quat), _ptr(scale), _ptr(opac), V, carr,
+                            _ptr(allm), _ptr(offs), E, _ptr(sel),
+                            0 if sel is None else sel.size, cull_mode, nthreads,
+                            _ptr(table), _ptr(risk), _ptr(flags), _ptr(tf), _ptr(stats))
+    if rc != 0:
+        raise ValueError(f"fso_accumulate failed with code {rc}")
+    return Accumulation(table, risk, flags[:rows], None if tf is None else tf[:acc],
+                        int(stats[0]), int(stats[1]), int(stats[2]), int(stats[3]))
+
+
+def pixel_lists(gaussians, cams, cull_mode: int = 0):
+    """Per-pixel ordered (Gaussian, alpha*T) terms of Eq. 1, CSR over all pixels.
+
+    Returns (offsets [P+1], gidx, contrib, t_final [P]); pixels are listed view
+    by view, row-major.
+    """
+    lib = _load()
+    mean = _f32(gaussians["mean"], 3)
+    quat = _f32(gaussians["quat"], 4)
+    scale = _f32(gaussians["scale"], 3)
+    opac = np.ascontiguousarray(np.asarray(gaussians["opacity"], dtype=np.float32).reshape(-1))
+    N = mean.shape[0]
+    cams = list(cams)
+    carr = make_cameras(cams)
+    P = sum(int(c["width"]) * int(c["height"]) for c in cams)
+    offs = np.zeros(P + 1, dtype=np.int64)
+    tf = np.zeros(max(P, 1), dtype=np.float64)
+    cap = 1 << 16
+    while True:
+        gidx = np.zeros(cap, dtype=np.int32)
+        con = np.zeros(cap, dtype=np.float64)
+        n = lib.fso_pixel_lists(N, _ptr(mean), _ptr(quat), _ptr(scale), _ptr(opac), len(cams),
+                                carr, cull_mode, cap, _ptr(offs), _ptr(gidx), _ptr(con), _ptr(tf))
+        if n < 0:
+            raise ValueError("fso_pixel_lists failed")
+        if n <= cap:
+            return offs, gidx[:n], con[:n], tf[:P]
+        cap = int(n)
+
+
+def project_view(gaussians, cam):
+    """Projected quantities of one view: [N, 10] = valid, depth, mx, my,
+    conic a, b, c, opacity, bbox width, bbox height."""
+    lib = _load()
+    mean = _f32(gaussians["mean"], 3)
+    quat = _f32(gaussians["quat"], 4)
+    scale = _f32(gaussians["scale"], 3)
+    opac = np.ascontiguousarray(np.asarray(gaussians["opacity"], dtype=np.float32).reshape(-1))
+    N = mean.shape[0]
+    out = np.zeros((max(N, 1), 10), dtype=np.float64)
+    rc = lib.fso_project_view(N, _ptr(mean), _ptr(quat), _ptr(scale), _ptr(opac),
+                              make_cameras([cam]), _ptr(out))
+    if rc != 0:
+        raise ValueError("fso_project_view failed (zero quaternion?)")
+    return out[:N]

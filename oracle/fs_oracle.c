@@ -1,0 +1,648 @@
+/*
+ * FlashSplat FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, obviously-correct restatement of what the GPU path computes,
+ * written from the paper (FlashSplat, arXiv 2409.08270):
+ *
+ *   Sec. 3.1, Eq. 1   front-to-back alpha blending  X = sum_i x_i alpha_i T_i,
+ *                     T_i = prod_{j<i} (1 - alpha_j), Gaussians taken in depth
+ *                     order, alpha_i = o_i * (2D Gaussian value at the pixel).
+ *   Sec. 3.2, Eq. 6   A_n^i = sum_{v,j,k} alpha_i T_i * [M^v_jk == n].
+ *   Sec. 3.3, Eq. 7   the same table with one column per label e = 0..E-1.
+ *   Sec. 4.2 / Supp. Sec. 6   the table is filled by walking every mask pixel
+ *                     with the rasteriser's alpha compositing, adding
+ *                     alpha_i*T_i into the column of the pixel's label.
+ *
+ * Everything is double precision.  Conventions the paper leaves open are fixed
+ * here and listed, with the reasons, in the repository's design notes:
+ *   - 3D covariance  Sigma = R(q) diag(s^2) R(q)^T, q = (w,x,y,z) normalised.
+ *   - EWA projection with a 0.3 px^2 low-pass on the 2D covariance diagonal;
+ *     the Jacobian is evaluated with tx/tz, ty/tz clamped to 1.3*tan(half-FoV).
+ *   - Cull: tz <= 0.2, det(Sigma2D) <= 0, o < 1/255.
+ *   - Pixel (u,v) is sampled at (u+0.5, v+0.5); mean2D = (fx tx/tz + cx, ...).
+ *   - alpha = min(0.99, o * exp(-0.5 d^T Sigma2D^-1 d)); a Gaussian with
+ *     alpha < 1/255 is skipped; if T*(1-alpha) < 1e-4 the pixel stops before
+ *     adding that Gaussian.
+ *   - Depth order: view-space tz of the mean, ties by lower Gaussian index.
+ *
+ * The candidate set of a pixel is found through a spatial index (8x8 pixel
+ * bins holding every Gaussian whose exact alpha >= 1/255 ellipse bound, plus a
+ * one-pixel margin, touches the bin).  With cull_mode = 1 every pixel instead
+ * walks every projected Gaussian; both must give the same table, which the
+ * tests check.
+ *
+ * This file shares no code with the CUDA path and must only be called from
+ * tests, the smoke check and the CPU-baseline leg of the benchmark.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define FSO_ALPHA_MIN (1.0 / 255.0)
+#define FSO_ALPHA_MAX 0.99
+#define FSO_T_MIN 1e-4
+#define FSO_NEAR_PLANE 0.2
+#define FSO_LOWPASS 0.3
+#define FSO_BIN 8
+
+/* Near-threshold windows (relative) used to flag discrete decisions that a
+ * lower-precision implementation may legitimately take the other way. */
+#define FSO_EVENT_REL 1e-5
+#define FSO_T_EVENT_REL 1e-4
+#define FSO_DEPTH_TIE_REL 1e-6
+
+/* flag bits per Gaussian */
+#define FSO_FLAG_ALPHA_EDGE 1u   /* alpha within 1e-5 rel. of 1/255 */
+#define FSO_FLAG_T_EDGE 2u       /* T(1-alpha) within 1e-4 rel. of 1e-4 */
+#define FSO_FLAG_DEPTH_TIE 4u    /* depth within 1e-6 rel. of a neighbour */
+#define FSO_FLAG_DOWNSTREAM 8u   /* after an event in the same pixel */
+
+typedef struct {
+  double R[9]; /* world -> camera rotation, row-major */
+  double t[3]; /* world -> camera translation */
+  double fx, fy, cx, cy;
+  int32_t width, height;
+  int32_t pad[2];
+} fso_camera;
+
+typedef struct {
+  int valid;
+  double depth;        /* view-space z of the mean */
+  double mx, my;       /* projected mean, pixel units */
+  double ca, cb, cc;   /* conic = inverse 2D covariance [[ca cb][cb cc]] */
+  double opacity;
+  int x0, x1, y0, y1;  /* inclusive pixel bounding box of the alpha>=1/255 ellipse */
+} fso_proj;
+
+/* ------------------------------------------------------------------------ */
+/* Projection (Sec. 3.1: 3D Gaussians are projected to 2D Gaussians          */
+/* (m^2D, Sigma^2D) and rendered with the tile rasteriser)                   */
+/* ------------------------------------------------------------------------ */
+
+static int project_one(const fso_camera* cam, const float* m, const float* q4,
+                       const float* s3, float opac, fso_proj* p) {
+  p->valid = 0;
+  const double mx = m[0], my = m[1], mz = m[2];
+  const double* R = cam->R;
+  const double tx = R[0] * mx + R[1] * my + R[2] * mz + cam->t[0];
+  const double ty = R[3] * mx + R[4] * my + R[5] * mz + cam->t[1];
+  const double tz = R[6] * mx + R[7] * my + R[8] * mz + cam->t[2];
+  if (!(tz > FSO_NEAR_PLANE)) return 0;
+  const double o = opac;
+  if (!(o >= FSO_ALPHA_MIN)) return 0; /* alpha <= o can never reach 1/255 */
+
+  /* rotation matrix of the unit quaternion (w, x, y, z) */
+  double qw = q4[0], qx = q4[1], qy = q4[2], qz = q4[3];
+  const double qn = sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
+  if (!(qn > 0.0)) return -1;
+  qw /= qn; qx /= qn; qy /= qn; qz /= qn;
+  double Rq[3][3];
+  Rq[0][0] = 1.0 - 2.0 * (qy * qy + qz * qz);
+  Rq[0][1] = 2.0 * (qx * qy - qw * qz);
+  Rq[0][2] = 2.0 * (qx * qz + qw * qy);
+  Rq[1][0] = 2.0 * (qx * qy + qw * qz);
+  Rq[1][1] = 1.0 - 2.0 * (qx * qx + qz * qz);
+  Rq[1][2] = 2.0 * (qy * qz - qw * qx);
+  Rq[2][0] = 2.0 * (qx * qz - qw * qy);
+  Rq[2][1] = 2.0 * (qy * qz + qw * qx);
+  Rq[2][2] = 1.0 - 2.0 * (qx * qx + qy * qy);
+
+  /* Sigma3D = Rq diag(s^2) Rq^T */
+  const double s2[3] = {(double)s3[0] * s3[0], (double)s3[1] * s3[1], (double)s3[2] * s3[2]};
+  double S3[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k) acc += Rq[a][k] * s2[k] * Rq[b][k];
+      S3[a][b] = acc;
+    }
+
+  /* EWA: Sigma2D = J W Sigma3D W^T J^T, W = camera rotation */
+  const double limx = 1.3 * (0.5 * cam->width / cam->fx);
+  const double limy = 1.3 * (0.5 * cam->height / cam->fy);
+  double ux = tx / tz, uy = ty / tz;
+  if (ux < -limx) ux = -limx;
+  if (ux > limx) ux = limx;
+  if (uy < -limy) uy = -limy;
+  if (uy > limy) uy = limy;
+  const double J[2][3] = {{cam->fx / tz, 0.0, -cam->fx * ux / tz},
+                          {0.0, cam->fy / tz, -cam->fy * uy / tz}};
+  double T[2][3]; /* T = J W */
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k) acc += J[a][k] * R[3 * k + b];
+      T[a][b] = acc;
+    }
+  double S2[2][2];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) acc += T[a][k] * S3[k][l] * T[b][l];
+      S2[a][b] = acc;
+    }
+  const double sa = S2[0][0] + FSO_LOWPASS;
+  const double sb = 0.5 * (S2[0][1] + S2[1][0]);
+  const double sc = S2[1][1] + FSO_LOWPASS;
+  const double det = sa * sc - sb * sb;
+  if (!(det > 0.0)) return 0;
+
+  p->depth = tz;
+  p->mx = cam->fx * tx / tz + cam->cx;
+  p->my = cam->fy * ty / tz + cam->cy;
+  p->ca = sc / det;
+  p->cb = -sb / det;
+  p->cc = sa / det;
+  p->opacity = o;
+
+  /* alpha >= 1/255 requires d^T C d <= 2 ln(255 o); the ellipse
+   * {d : d^T Sigma^-1 d <= r2} has half extents sqrt(Sigma_xx r2),
+   * sqrt(Sigma_yy r2).  One pixel of margin. */
+  const double r2 = 2.0 * log(255.0 * o);
+  const double hx = sqrt(sa * (r2 > 0 ? r2 : 0.0));
+  const double hy = sqrt(sc * (r2 > 0 ? r2 : 0.0));
+  /* pixel u is sampled at u + 0.5 */
+  double fx0 = ceil(p->mx - hx - 0.5 - 1.0), fx1 = floor(p->mx + hx - 0.5 + 1.0);
+  double fy0 = ceil(p->my - hy - 0.5 - 1.0), fy1 = floor(p->my + hy - 0.5 + 1.0);
+  if (fx0 < 0) fx0 = 0;
+  if (fy0 < 0) fy0 = 0;
+  if (fx1 > cam->width - 1) fx1 = cam->width - 1;
+  if (fy1 > cam->height - 1) fy1 = cam->height - 1;
+  if (fx0 > fx1 || fy0 > fy1) return 0;
+  p->x0 = (int)fx0; p->x1 = (int)fx1; p->y0 = (int)fy0; p->y1 = (int)fy1;
+  p->valid = 1;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One pixel: front-to-back compositing (Eq. 1)                              */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t g;       /* Gaussian index */
+  double c;        /* alpha * T added by the oracle (0 if not added) */
+  double risk;     /* bound on |change of c| if a marginal decision flips */
+  uint8_t flag;    /* event flags raised at this pixel for g */
+} fso_hit;
+
+/* Walk the candidate list `cand` (length n, already in (depth, index) order)
+ * for the pixel centred at (px, py), Eq. 1 term by term.  Writes every
+ * contribution into `hits` (capacity >= n) and returns how many; *t_final
+ * receives the transmittance left when the walk ends.
+ *
+ * Discrete decisions that sit within a small relative window of their
+ * threshold (alpha vs 1/255, T(1-alpha) vs 1e-4, equal depths) are ones an
+ * implementation with other rounding may take the other way.  For them the
+ * walk records, per Gaussian, `risk`: an upper bound on how much that
+ * Gaussian's alpha*T at this pixel changes if the decision flips.  Gaussians
+ * the oracle does not add but another walk could are listed with c = 0.
+ * `use_bbox` skips candidates whose pixel bounding box excludes the pixel. */
+static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use_bbox,
+                      int px_i, int py_i, fso_hit* hits, double* t_final,
+                      int64_t* n_eval) {
+  const double px = px_i + 0.5, py = py_i + 0.5;
+  double T = 1.0;
+  int nh = 0;
+  double down = 0.0;      /* relative uncertainty of T from earlier marginal events */
+  int all_risky = 0;      /* a marginal stop was passed: every later term may change */
+  int stopped = 0;        /* the oracle stopped on a marginal test; T_shadow continues */
+  double T_shadow = 0.0;
+  int last_hit = -1;
+  for (int64_t k = 0; k < n; ++k) {
+    const int32_t g = cand[k];
+    const fso_proj* p = &P[g];
+    if (use_bbox && (px_i < p->x0 || px_i > p->x1 || py_i < p->y0 || py_i > p->y1)) continue;
+    ++*n_eval;
+    const double dx = px - p->mx, dy = py - p->my;
+    const double power = -0.5 * (p->ca * dx * dx + p->cc * dy * dy) - p->cb * dx * dy;
+    double alpha = p->opacity * exp(power);
+    if (alpha > FSO_ALPHA_MAX) alpha = FSO_ALPHA_MAX;
+    const int a_edge = fabs(alpha - FSO_ALPHA_MIN) <= FSO_EVENT_REL * FSO_ALPHA_MIN;
+    if (stopped) {
+      /* Beyond a marginal stop: another walk may keep adding terms. */
+      if (alpha >= FSO_ALPHA_MIN * (1.0 - FSO_EVENT_REL)) {
+        hits[nh].g = g; hits[nh].c = 0.0;
+        hits[nh].risk = alpha * T_shadow * (1.0 + down) + 1e-300;
+        hits[nh].flag = FSO_FLAG_DOWNSTREAM | (a_edge ? FSO_FLAG_ALPHA_EDGE : 0);
+        ++nh;
+        T_shadow *= 1.0 - alpha;
+      }
+      continue;
+    }
+    if (alpha < FSO_ALPHA_MIN) {
+      if (a_edge) { /* skipped here, but on the threshold: another walk may add it */
+        hits[nh].g = g; hits[nh].c = 0.0;
+        hits[nh].risk = alpha * T * (1.0 + down);
+        hits[nh].flag = FSO_FLAG_ALPHA_EDGE;
+        ++nh;
+        down += alpha / (1.0 - alpha);
+      }
+      continue;
+    }
+    const double test_T = T * (1.0 - alpha);
+    const int t_edge = fabs(test_T - FSO_T_MIN) <= FSO_T_EVENT_REL * FSO_T_MIN;
+    if (test_T < FSO_T_MIN) {
+      if (t_edge || down > 0.0 || all_risky) {
+        /* the stop may not happen in another walk: this term and all
+         * later ones are at risk */
+        hits[nh].g = g; hits[nh].c = 0.0;
+        hits[nh].risk = alpha * T * (1.0 + down);
+        hits[nh].flag = FSO_FLAG_T_EDGE;
+        ++nh;
+        stopped = 1;
+        T_shadow = test_T;
+        continue;
+      }
+      break;
+    }
+    const double c = alpha * T;
+    double risk = c * down;
+    uint8_t fl = down > 0.0 ? FSO_FLAG_DOWNSTREAM : 0;
+    if (a_edge) { risk = c * (1.0 + down); fl |= FSO_FLAG_ALPHA_EDGE; }
+    if (t_edge || all_risky) { risk = c * (1.0 + down); fl |= FSO_FLAG_T_EDGE; all_risky = 1; }
+    if (last_hit >= 0 &&
+        fabs(p->depth - P[hits[last_hit].g].depth) <= FSO_DEPTH_TIE_REL * p->depth) {
+      /* swapping two neighbours changes each term by alpha_a*alpha_b*T */
+      const double swap = hits[last_hit].c * alpha; /* alpha_a alpha_b T_before */
+      risk += swap;
+      hits[last_hit].risk += swap;
+      fl |= FSO_FLAG_DEPTH_TIE;
+      hits[last_hit].flag |= FSO_FLAG_DEPTH_TIE;
+    }
+    hits[nh].g = g; hits[nh].c = c; hits[nh].risk = risk; hits[nh].flag = fl;
+    last_hit = nh;
+    ++nh;
+    if (a_edge) down += alpha / (1.0 - alpha);
+    T = test_T;
+  }
+  *t_final = T;
+  return nh;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-view setup: projection, depth order, spatial bins                     */
+/* ------------------------------------------------------------------------ */
+
+static const fso_proj* g_sort_P; /* qsort has no context argument in C99 */
+
+static int cmp_depth(const void* a, const void* b) {
+  const int32_t ia = *(const int32_t*)a, ib = *(const int32_t*)b;
+  const double da = g_sort_P[ia].depth, db = g_sort_P[ib].depth;
+  if (da < db) return -1;
+  if (da > db) return 1;
+  return (ia > ib) - (ia < ib);
+}
+
+typedef struct {
+  int64_t N;
+  const float *mean, *quat, *scale, *opacity;
+  const fso_camera* cam;
+  fso_proj* P;
+  int64_t begin, end;
+  int status;
+} proj_job;
+
+static void* proj_worker(void* arg) {
+  proj_job* j = (proj_job*)arg;
+  for (int64_t i = j->begin; i < j->end; ++i) {
+    if (project_one(j->cam, j->mean + 3 * i, j->quat + 4 * i, j->scale + 3 * i, j->opacity[i],
+                    &j->P[i]) < 0)
+      j->status = -1;
+  }
+  return NULL;
+}
+
+typedef struct {
+  int32_t* order;  /* valid Gaussians in (depth, index) order */
+  int64_t n_valid;
+  int bins_x, bins_y;
+  int64_t* bin_start; /* [bins+1] */
+  int32_t* bin_list;  /* Gaussians per bin, each bin in depth order */
+} view_index;
+
+static int build_view(int64_t N, const float* mean, const float* quat, const float* scale,
+                      const float* opacity, const fso_camera* cam, int nthreads, fso_proj* P,
+                      int build_bins, view_index* vi) {
+  memset(vi, 0, sizeof(*vi));
+  if (nthreads < 1) nthreads = 1;
+  proj_job* jobs = (proj_job*)calloc((size_t)nthreads, sizeof(proj_job));
+  pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+  for (int t = 0; t < nthreads; ++t) {
+    jobs[t] = (proj_job){N, mean, quat, scale, opacity, cam, P, N * t / nthreads,
+                         N * (t + 1) / nthreads, 0};
+    pthread_create(&th[t], NULL, proj_worker, &jobs[t]);
+  }
+  int status = 0;
+  for (int t = 0; t < nthreads; ++t) {
+    pthread_join(th[t], NULL);
+    if (jobs[t].status) status = jobs[t].status;
+  }
+  free(jobs);
+  free(th);
+  if (status) return status;
+
+  int64_t nv = 0;
+  for (int64_t i = 0; i < N; ++i) nv += P[i].valid;
+  vi->order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
+  nv = 0;
+  for (int64_t i = 0; i < N; ++i)
+    if (P[i].valid) vi->order[nv++] = (int32_t)i;
+  vi->n_valid = nv;
+  g_sort_P = P;
+  qsort(vi->order, (size_t)nv, sizeof(int32_t), cmp_depth);
+
+  if (!build_bins) return 0;
+  const int bx = (cam->width + FSO_BIN - 1) / FSO_BIN, by = (cam->height + FSO_BIN - 1) / FSO_BIN;
+  vi->bins_x = bx;
+  vi->bins_y = by;
+  int64_t nb = (int64_t)bx * by;
+  vi->bin_start = (int64_t*)calloc((size_t)nb + 1, sizeof(int64_t));
+  for (int64_t k = 0; k < nv; ++k) {
+    const fso_proj* p = &P[vi->order[k]];
+    for (int y = p->y0 / FSO_BIN; y <= p->y1 / FSO_BIN; ++y)
+      for (int x = p->x0 / FSO_BIN; x <= p->x1 / FSO_BIN; ++x) vi->bin_start[(int64_t)y * bx + x + 1]++;
+  }
+  for (int64_t b = 0; b < nb; ++b) vi->bin_start[b + 1] += vi->bin_start[b];
+  vi->bin_list = (int32_t*)malloc(sizeof(int32_t) * (size_t)(vi->bin_start[nb] > 0 ? vi->bin_start[nb] : 1));
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nb > 0 ? nb : 1));
+  memcpy(fill, vi->bin_start, sizeof(int64_t) * (size_t)nb);
+  for (int64_t k = 0; k < nv; ++k) { /* depth order is kept inside each bin */
+    const int32_t g = vi->order[k];
+    const fso_proj* p = &P[g];
+    for (int y = p->y0 / FSO_BIN; y <= p->y1 / FSO_BIN; ++y)
+      for (int x = p->x0 / FSO_BIN; x <= p->x1 / FSO_BIN; ++x) vi->bin_list[fill[(int64_t)y * bx + x]++] = g;
+  }
+  free(fill);
+  return 0;
+}
+
+static void free_view(view_index* vi) {
+  free(vi->order);
+  free(vi->bin_start);
+  free(vi->bin_list);
+  memset(vi, 0, sizeof(*vi));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Accumulation of the contribution table (Eq. 6 / Eq. 7)                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  /* shared, read-only */
+  const fso_proj* P;
+  const view_index* vi;
+  const fso_camera* cam;
+  const int32_t* mask;      /* this view's labels, row-major H x W */
+  const int64_t* slot;      /* Gaussian -> table row, -1 = not tracked */
+  const uint8_t* pix_sel;   /* NULL or per-pixel "walk this pixel" */
+  int32_t E;
+  int cull_mode;
+  int nthreads, tid;
+  double* t_final;          /* this view's slice or NULL */
+  /* per thread */
+  double* table;            /* [rows][E] */
+  double* risk;             /* [rows][E] */
+  uint8_t* flags;           /* [rows] */
+  fso_hit* hits;            /* scratch, capacity max candidates */
+  int64_t n_eval, n_hit, n_bad;
+} acc_job;
+
+static void* acc_worker(void* arg) {
+  acc_job* j = (acc_job*)arg;
+  const int W = j->cam->width, H = j->cam->height;
+  for (int y = j->tid; y < H; y += j->nthreads) {
+    for (int x = 0; x < W; ++x) {
+      const int64_t pix = (int64_t)y * W + x;
+      if (j->pix_sel && !j->pix_sel[pix]) continue;
+      const int32_t* cand;
+      int64_t n;
+      if (j->cull_mode == 1) {
+        cand = j->vi->order;
+        n = j->vi->n_valid;
+      } else {
+        const int64_t b = (int64_t)(y / FSO_BIN) * j->vi->bins_x + x / FSO_BIN;
+        cand = j->vi->bin_list + j->vi->bin_start[b];
+        n = j->vi->bin_start[b + 1] - j->vi->bin_start[b];
+      }
+      double tf;
+      const int nh = walk_pixel(j->P, cand, n, j->cull_mode != 1, x, y, j->hits, &tf, &j->n_eval);
+      if (j->t_final) j->t_final[pix] = tf;
+      const int32_t lab = j->mask[pix];
+      const int lab_ok = (lab >= 0 && lab < j->E);
+      if (!lab_ok) j->n_bad++;
+      for (int h = 0; h < nh; ++h) {
+        const int64_t r = j->slot ? j->slot[j->hits[h].g] : j->hits[h].g;
+        if (r < 0) continue;
+        if (j->hits[h].c > 0.0) j->n_hit++;
+        j->flags[r] |= j->hits[h].flag;
+        if (lab_ok) {
+          j->table[r * j->E + lab] += j->hits[h].c;
+          j->risk[r * j->E + lab] += j->hits[h].risk;
+        }
+      }
+    }
+  }
+  return NULL;
+}
+
+/*
+ * fso_accumulate: fill table[rows][E] (FP64) with the per-label contribution
+ * sums of Eq. 6/7 over all V views, and risk[rows][E] with the summed bounds
+ * on how much each entry moves if marginal decisions flip (see walk_pixel).
+ *
+ *   mean[N*3], quat[N*4] (w,x,y,z), scale[N*3] (linear), opacity[N] (activated)
+ *   cams[V]; masks: view v's int32 labels at masks + mask_offsets[v] (H*W)
+ *   sel: NULL -> rows = N, row i = Gaussian i; otherwise n_sel sorted Gaussian
+ *        indices and only those rows are tracked (pixels outside the union of
+ *        their bounding boxes are not walked, which does not change the rows)
+ *   cull_mode: 0 = spatial bins, 1 = every pixel walks every Gaussian
+ *   t_final: NULL or [sum_v H*W] transmittance left at each pixel (-1 where
+ *        the pixel was not walked)
+ *   stats[4]: evaluated pairs, contributing pairs, pixels with bad labels,
+ *        tracked Gaussians that were never valid in any view
+ * Returns 0, or -1 on a zero quaternion, -2 on bad arguments.
+ */
+int fso_accumulate(int64_t N, const float* mean, const float* quat, const float* scale,
+                   const float* opacity, int32_t V, const fso_camera* cams,
+                   const int32_t* masks, const int64_t* mask_offsets, int32_t E,
+                   const int64_t* sel, int64_t n_sel, int32_t cull_mode, int32_t nthreads,
+                   double* table, double* risk, uint8_t* flags, double* t_final,
+                   int64_t* stats) {
+  if (N < 0 || V < 0 || E < 1 || (sel && n_sel < 0)) return -2;
+  if (nthreads < 1) nthreads = 1;
+  const int64_t rows = sel ? n_sel : N;
+  int64_t* slot = NULL;
+  if (sel) {
+    slot = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    for (int64_t i = 0; i < N; ++i) slot[i] = -1;
+    for (int64_t r = 0; r < n_sel; ++r) {
+      if (sel[r] < 0 || sel[r] >= N) { free(slot); return -2; }
+      slot[sel[r]] = r;
+    }
+  }
+  memset(table, 0, sizeof(double) * (size_t)(rows * E));
+  memset(risk, 0, sizeof(double) * (size_t)(rows * E));
+  memset(flags, 0, (size_t)rows);
+  int64_t st[4] = {0, 0, 0, 0};
+
+  fso_proj* P = (fso_proj*)malloc(sizeof(fso_proj) * (size_t)(N > 0 ? N : 1));
+  acc_job* jobs = (acc_job*)calloc((size_t)nthreads, sizeof(acc_job));
+  pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+  for (int t = 0; t < nthreads; ++t) {
+    jobs[t].table = (double*)calloc((size_t)(rows * E > 0 ? rows * E : 1), sizeof(double));
+    jobs[t].risk = (double*)calloc((size_t)(rows * E > 0 ? rows * E : 1), sizeof(double));
+    jobs[t].flags = (uint8_t*)calloc((size_t)(rows > 0 ? rows : 1), 1);
+  }
+  uint8_t* seen = (uint8_t*)calloc((size_t)(rows > 0 ? rows : 1), 1);
+  int status = 0;
+  int64_t pix_base = 0;
+  for (int32_t v = 0; v < V && !status; ++v) {
+    const fso_camera* cam = &cams[v];
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    view_index vi;
+    status = build_view(N, mean, quat, scale, opacity, cam, nthreads, P, cull_mode != 1, &vi);
+    if (status) { free_view(&vi); break; }
+    for (int64_t i = 0; i < N; ++i)
+      if (P[i].valid) {
+        const int64_t r = slot ? slot[i] : i;
+        if (r >= 0) seen[r] = 1;
+      }
+    uint8_t* pix_sel = NULL;
+    if (sel) { /* union of the tracked Gaussians' bounding boxes */
+      pix_sel = (uint8_t*)calloc((size_t)(npix > 0 ? npix : 1), 1);
+      for (int64_t r = 0; r < n_sel; ++r) {
+        const fso_proj* p = &P[sel[r]];
+        if (!p->valid) continue;
+        for (int y = p->y0; y <= p->y1; ++y) memset(pix_sel + (int64_t)y * cam->width + p->x0, 1, (size_t)(p->x1 - p->x0 + 1));
+      }
+    }
+    if (t_final) {
+      for (int64_t k = 0; k < npix; ++k) t_final[pix_base + k] = -1.0;
+    }
+    /* the longest candidate list bounds the hits of one pixel */
+    int64_t max_cand = vi.n_valid;
+    if (cull_mode != 1) {
+      max_cand = 0;
+      const int64_t nb = (int64_t)vi.bins_x * vi.bins_y;
+      for (int64_t b = 0; b < nb; ++b) {
+        const int64_t c = vi.bin_start[b + 1] - vi.bin_start[b];
+        if (c > max_cand) max_cand = c;
+      }
+    }
+    for (int t = 0; t < nthreads; ++t) {
+      acc_job* j = &jobs[t];
+      j->P = P; j->vi = &vi; j->cam = cam; j->mask = masks + mask_offsets[v];
+      j->slot = slot; j->pix_sel = pix_sel; j->E = E; j->cull_mode = cull_mode;
+      j->nthreads = nthreads; j->tid = t;
+      j->t_final = t_final ? t_final + pix_base : NULL;
+      j->hits = (fso_hit*)malloc(sizeof(fso_hit) * (size_t)(max_cand > 0 ? max_cand : 1));
+      pthread_create(&th[t], NULL, acc_worker, j);
+    }
+    for (int t = 0; t < nthreads; ++t) {
+      pthread_join(th[t], NULL);
+      free(jobs[t].hits);
+      jobs[t].hits = NULL;
+    }
+    free(pix_sel);
+    free_view(&vi);
+    pix_base += npix;
+  }
+  /* fixed-order merge of the per-thread partial tables */
+  for (int t = 0; t < nthreads; ++t) {
+    for (int64_t k = 0; k < rows * E; ++k) table[k] += jobs[t].table[k];
+    for (int64_t k = 0; k < rows * E; ++k) risk[k] += jobs[t].risk[k];
+    for (int64_t r = 0; r < rows; ++r) flags[r] |= jobs[t].flags[r];
+    st[0] += jobs[t].n_eval;
+    st[1] += jobs[t].n_hit;
+    st[2] += jobs[t].n_bad;
+    free(jobs[t].table);
+    free(jobs[t].risk);
+    free(jobs[t].flags);
+  }
+  for (int64_t r = 0; r < rows; ++r) st[3] += !seen[r];
+  if (stats) memcpy(stats, st, sizeof(st));
+  free(seen);
+  free(jobs);
+  free(th);
+  free(P);
+  free(slot);
+  return status;
+}
+
+/*
+ * fso_pixel_lists: every pixel's ordered list of (Gaussian, alpha*T) -- the
+ * terms of Eq. 1 -- for small scenes (brute-force and linearity tests).
+ *   pix_offsets[P+1] (CSR over all pixels of all views, views in order,
+ *   row-major), gidx/contrib[capacity], t_final[P].
+ * Only contributions with alpha*T > 0 are listed.  Returns the number of
+ * pairs; when it exceeds `capacity` nothing beyond capacity is written and
+ * the caller repeats with a larger buffer.  Negative on error.
+ */
+int64_t fso_pixel_lists(int64_t N, const float* mean, const float* quat, const float* scale,
+                        const float* opacity, int32_t V, const fso_camera* cams,
+                        int32_t cull_mode, int64_t capacity, int64_t* pix_offsets,
+                        int32_t* gidx, double* contrib, double* t_final) {
+  fso_proj* P = (fso_proj*)malloc(sizeof(fso_proj) * (size_t)(N > 0 ? N : 1));
+  fso_hit* hits = (fso_hit*)malloc(sizeof(fso_hit) * (size_t)(N > 0 ? N : 1));
+  int64_t total = 0, pix = 0, n_eval = 0;
+  for (int32_t v = 0; v < V; ++v) {
+    const fso_camera* cam = &cams[v];
+    view_index vi;
+    const int st = build_view(N, mean, quat, scale, opacity, cam, 1, P, cull_mode != 1, &vi);
+    if (st) { free_view(&vi); free(P); free(hits); return -1; }
+    for (int y = 0; y < cam->height; ++y)
+      for (int x = 0; x < cam->width; ++x) {
+        const int32_t* cand;
+        int64_t n;
+        if (cull_mode == 1) {
+          cand = vi.order; n = vi.n_valid;
+        } else {
+          const int64_t b = (int64_t)(y / FSO_BIN) * vi.bins_x + x / FSO_BIN;
+          cand = vi.bin_list + vi.bin_start[b];
+          n = vi.bin_start[b + 1] - vi.bin_start[b];
+        }
+        double tf;
+        const int nh = walk_pixel(P, cand, n, cull_mode != 1, x, y, hits, &tf, &n_eval);
+        pix_offsets[pix] = total;
+        if (t_final) t_final[pix] = tf;
+        for (int h = 0; h < nh; ++h) {
+          if (!(hits[h].c > 0.0)) continue;
+          if (total < capacity) {
+            gidx[total] = hits[h].g;
+            contrib[total] = hits[h].c;
+          }
+          ++total;
+        }
+        ++pix;
+      }
+    free_view(&vi);
+  }
+  pix_offsets[pix] = total;
+  free(P);
+  free(hits);
+  return total;
+}
+
+/*
+ * fso_project_view: the projected quantities of one view, for closed-form
+ * tests of the projection.  out[N*10] per Gaussian: valid, depth, mx, my,
+ * conic a, b, c, opacity, bbox width, bbox height (0 when invalid).
+ */
+int fso_project_view(int64_t N, const float* mean, const float* quat, const float* scale,
+                     const float* opacity, const fso_camera* cam, double* out) {
+  for (int64_t i = 0; i < N; ++i) {
+    fso_proj p;
+    memset(&p, 0, sizeof(p));
+    if (project_one(cam, mean + 3 * i, quat + 4 * i, scale + 3 * i, opacity[i], &p) < 0) return -1;
+    double* o = out + 10 * i;
+    o[0] = p.valid;
+    o[1] = p.depth; o[2] = p.mx; o[3] = p.my;
+    o[4] = p.ca; o[5] = p.cb; o[6] = p.cc; o[7] = p.opacity;
+    o[8] = p.valid ? (double)(p.x1 - p.x0 + 1) : 0.0;
+    o[9] = p.valid ? (double)(p.y1 - p.y0 + 1) : 0.0;
+  }
+  return 0;
+}

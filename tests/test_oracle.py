@@ -1,0 +1,407 @@
+"""Pins for the FP64 oracle (CPU only).
+
+Each test checks the oracle against something other than itself: closed forms
+derived by hand (tests/golden/closed_forms.json), independent library routines
+(scipy's quaternion rotation and Gaussian density, finite-difference
+Jacobians), brute force over every label assignment of the paper's integer
+program, and invariants of alpha compositing.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.assign import assign, assign_margin, labels_from_membership
+from paper_2409_08270_gb300 import synth
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))
+
+
+def _cam(width=32, height=32, fx=40.0, fy=None, cx=None, cy=None, R=None, t=None):
+    return {"R": np.eye(3) if R is None else R, "t": np.zeros(3) if t is None else t,
+            "fx": fx, "fy": fx if fy is None else fy,
+            "cx": width / 2 if cx is None else cx, "cy": height / 2 if cy is None else cy,
+            "width": width, "height": height}
+
+
+def _gauss(means, quats=None, scales=None, opac=None):
+    means = np.asarray(means, np.float32).reshape(-1, 3)
+    n = means.shape[0]
+    quats = np.tile([1, 0, 0, 0], (n, 1)) if quats is None else quats
+    scales = np.full((n, 3), 0.1) if scales is None else scales
+    opac = np.full(n, 0.5) if opac is None else opac
+    return {"mean": means, "quat": np.asarray(quats, np.float32).reshape(-1, 4),
+            "scale": np.asarray(scales, np.float32).reshape(-1, 3),
+            "opacity": np.asarray(opac, np.float32).reshape(-1)}
+
+
+def _conic_to_cov(row):
+    a, b, c = row[4], row[5], row[6]
+    C = np.array([[a, b], [b, c]])
+    return np.linalg.inv(C)
+
+
+# --------------------------------------------------------------------------
+# projection (Sec. 3.1: 3D Gaussians projected to 2D Gaussians)
+# --------------------------------------------------------------------------
+
+def test_projection_isotropic_on_axis():
+    """Isotropic Gaussian on the optical axis: Sigma2D = diag((fx s/z)^2, (fy s/z)^2) + 0.3."""
+    z, s = 2.5, 0.07
+    cam = _cam(64, 48, fx=55.0, fy=71.0, cx=30.0, cy=20.0)
+    g = _gauss([[0, 0, z]], quats=[[0.3, -0.5, 0.2, 0.7]], scales=[[s, s, s]], opac=[0.8])
+    row = oracle.project_view(g, cam)[0]
+    assert row[0] == 1
+    z32, s32 = float(np.float32(z)), float(np.float32(s))
+    assert row[1] == pytest.approx(z32, rel=1e-15)
+    assert row[2] == pytest.approx(30.0, abs=1e-12) and row[3] == pytest.approx(20.0, abs=1e-12)
+    cov = _conic_to_cov(row)
+    exp = np.diag([(55.0 * s32 / z32) ** 2 + 0.3, (71.0 * s32 / z32) ** 2 + 0.3])
+    np.testing.assert_allclose(cov, exp, rtol=1e-12, atol=1e-14)
+
+
+def _rot_scipy(q_wxyz):
+    from scipy.spatial.transform import Rotation
+    w, x, y, z = q_wxyz
+    return Rotation.from_quat([x, y, z, w]).as_matrix()      # scipy is scalar-last
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_projection_matches_finite_difference_jacobian(seed):
+    """Sigma2D = J W Sigma3D W^T J^T + 0.3 I with J the Jacobian of the pinhole
+    map, here taken by central differences, and Sigma3D built with scipy's
+    quaternion->matrix (scalar-last convention, converted)."""
+    rng = np.random.default_rng(seed)
+    cam = synth.camera(rng.uniform(-1, 1, 3) + np.array([0, 0, -4.0]), 200, 150, 180.0,
+                       target=rng.uniform(-0.2, 0.2, 3))
+    m = rng.uniform(-0.5, 0.5, 3)
+    q = rng.standard_normal(4)
+    s = np.exp(rng.normal(-2.5, 0.6, 3))
+    g = _gauss([m], quats=[q], scales=[s], opac=[0.9])
+    row = oracle.project_view(g, cam)[0]
+    assert row[0] == 1
+    m64, q64, s64 = (np.asarray(g[k][0], np.float64) for k in ("mean", "quat", "scale"))
+    R, t = np.asarray(cam["R"]), np.asarray(cam["t"])
+    X = R @ m64 + t
+
+    def pin(P):
+        return np.array([cam["fx"] * P[0] / P[2] + cam["cx"], cam["fy"] * P[1] / P[2] + cam["cy"]])
+
+    h = 1e-6
+    J = np.stack([(pin(X + h * e) - pin(X - h * e)) / (2 * h) for e in np.eye(3)], axis=1)
+    Rq = _rot_scipy(q64 / np.linalg.norm(q64))
+    S3 = Rq @ np.diag(s64 ** 2) @ Rq.T
+    S2 = J @ R @ S3 @ R.T @ J.T + 0.3 * np.eye(2)
+    np.testing.assert_allclose(_conic_to_cov(row), S2, rtol=2e-7)
+    np.testing.assert_allclose(row[2:4], pin(X), rtol=1e-12)
+    assert row[1] == pytest.approx(X[2], rel=1e-14)
+
+
+def test_identity_and_quarter_turn_quaternion():
+    """q = identity keeps the scale axes; a quarter turn about z swaps x and y."""
+    z = 3.0
+    cam = _cam(64, 64, fx=50.0, fy=50.0)
+    a, b, c = 0.05, 0.12, 0.2
+    h = math.sqrt(0.5)
+    g = _gauss([[0, 0, z], [0, 0, z]], quats=[[1, 0, 0, 0], [h, 0, 0, h]],
+               scales=[[a, b, c], [a, b, c]], opac=[0.5, 0.5])
+    rows = oracle.project_view(g, cam)
+    a32, b32 = float(np.float32(a)), float(np.float32(b))
+    exp0 = np.diag([(50 * a32 / z) ** 2 + 0.3, (50 * b32 / z) ** 2 + 0.3])
+    exp1 = np.diag([(50 * b32 / z) ** 2 + 0.3, (50 * a32 / z) ** 2 + 0.3])
+    np.testing.assert_allclose(_conic_to_cov(rows[0]), exp0, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(_conic_to_cov(rows[1]), exp1, rtol=1e-6, atol=1e-9)
+
+
+def test_projection_culls():
+    cam = _cam()
+    g = _gauss([[0, 0, 0.1], [0, 0, 2.0], [0, 0, 2.0], [50, 0, 2.0]],
+               opac=[0.5, 0.5, 1.0 / 256.0, 0.5])
+    rows = oracle.project_view(g, cam)
+    assert rows[:, 0].tolist() == [0, 1, 0, 0]   # near plane, kept, opacity < 1/255, off-screen
+    with pytest.raises(ValueError):
+        oracle.project_view(_gauss([[0, 0, 2]], quats=[[0, 0, 0, 0]]), cam)
+
+
+# --------------------------------------------------------------------------
+# alpha compositing (Sec. 3.1 Eq. 1)
+# --------------------------------------------------------------------------
+
+def test_single_gaussian_alpha_is_unnormalised_density():
+    """alpha = min(0.99, o * 2 pi sqrt(det Sigma) * N(d; 0, Sigma)) with scipy's density;
+    pixels below 1/255 contribute nothing."""
+    from scipy.stats import multivariate_normal
+    cam = _cam(40, 36, fx=60.0, fy=48.0, cx=19.5, cy=17.5)   # mean on pixel (19, 17)'s centre
+    g = _gauss([[0.0, 0.0, 2.0]], quats=[[0.9, 0.1, -0.3, 0.2]], scales=[[0.12, 0.03, 0.07]],
+               opac=[0.995])
+    row = oracle.project_view(g, cam)[0]
+    cov = _conic_to_cov(row)
+    offs, gidx, con, tf = oracle.pixel_lists(g, [cam])
+    H, W = 36, 40
+    yy, xx = np.mgrid[0:H, 0:W]
+    pts = np.stack([xx.ravel() + 0.5, yy.ravel() + 0.5], axis=1)
+    dens = multivariate_normal(mean=row[2:4], cov=cov).pdf(pts) * 2 * np.pi * np.sqrt(np.linalg.det(cov))
+    alpha = np.minimum(0.99, float(np.float32(0.995)) * dens)
+    exp = np.where(alpha >= 1 / 255, alpha, 0.0)
+    got = np.zeros(H * W)
+    counts = np.diff(offs)
+    assert counts.max() <= 1
+    got[counts == 1] = con
+    np.testing.assert_allclose(got, exp, rtol=1e-12, atol=0)
+    assert (got > 0).sum() > 50 and (got == 0.99).sum() > 0   # both the clamp and the cut occur
+    np.testing.assert_allclose(tf, 1 - got, rtol=0, atol=1e-15)
+
+
+def test_opaque_stack_golden():
+    gd = GOLDEN["opaque_stack"]
+    cam = _cam(17, 17, fx=40.0, cx=8.5, cy=8.5)       # the mean lands on pixel (8, 8)'s centre
+    g = _gauss([[0, 0, 2.0]] * gd["count"], scales=np.full((3, 3), 0.05),
+               opac=[gd["opacity"]] * gd["count"])
+    offs, gidx, con, tf = oracle.pixel_lists(g, [cam])
+    p = 8 * 17 + 8
+    assert con[offs[p]:offs[p + 1]].tolist() == gd["contributions"]
+    assert gidx[offs[p]:offs[p + 1]].tolist() == [0, 1]      # equal depth: lower index first
+    assert tf[p] == gd["t_final"]
+
+
+def test_two_layer_golden_and_depth_order():
+    gd = GOLDEN["two_layer"]
+    cam = _cam(17, 17, fx=40.0, cx=8.5, cy=8.5)
+    # index 0 is the BACK Gaussian: depth, not index, decides the order
+    g = _gauss([[0, 0, 3.0], [0, 0, 2.0]], scales=np.full((2, 3), 0.05),
+               opac=[gd["opacity_back"], gd["opacity_front"]])
+    offs, gidx, con, tf = oracle.pixel_lists(g, [cam])
+    p = 8 * 17 + 8
+    assert gidx[offs[p]:offs[p + 1]].tolist() == [1, 0]
+    assert con[offs[p]:offs[p + 1]].tolist() == gd["contributions"]
+    assert tf[p] == gd["t_final"]
+
+
+def test_compositing_invariant_and_table_consistency(tiny):
+    """sum_i alpha_i T_i + T_final = 1 at every pixel; the table equals the
+    per-pixel terms binned by label; table total = sum_p (1 - T_final)."""
+    cams, masks = tiny.cams[:3], tiny.masks[:3]
+    offs, gidx, con, tf = oracle.pixel_lists(tiny.gaussians, cams)
+    per_pix = np.add.reduceat(np.append(con, 0.0), offs[:-1]) * (np.diff(offs) > 0)
+    np.testing.assert_allclose(per_pix + tf, 1.0, rtol=0, atol=1e-12)
+    acc = oracle.accumulate(tiny.gaussians, cams, masks, tiny.E, want_t_final=True)
+    np.testing.assert_array_equal(acc.t_final, tf)
+    labels = np.concatenate([m.reshape(-1) for m in masks]).astype(np.int64)
+    pix_of = np.repeat(np.arange(labels.size), np.diff(offs))
+    exp = np.zeros((tiny.n, tiny.E))
+    np.add.at(exp, (gidx, labels[pix_of]), con)
+    np.testing.assert_allclose(acc.table, exp, rtol=1e-12, atol=1e-15)
+    assert acc.table.sum() == pytest.approx((1 - tf).sum(), rel=1e-12)
+
+
+def test_spatial_index_equals_brute_force(tiny):
+    """cull_mode=1 walks every projected Gaussian at every pixel (no spatial
+    index); the table, flags and transmittance must be identical."""
+    a = oracle.accumulate(tiny.gaussians, tiny.cams[:4], tiny.masks[:4], tiny.E, want_t_final=True)
+    b = oracle.accumulate(tiny.gaussians, tiny.cams[:4], tiny.masks[:4], tiny.E, cull_mode=1,
+                          want_t_final=True)
+    np.testing.assert_array_equal(a.table, b.table)
+    np.testing.assert_array_equal(a.t_final, b.t_final)
+    assert b.n_eval > 5 * a.n_eval
+
+
+def test_brute_force_clustered_scene():
+    w = synth.binary_scene(n=3000, views=2, width=96, height=72, n_clusters=4)
+    a = oracle.accumulate(w.gaussians, w.cams, w.masks, w.E)
+    b = oracle.accumulate(w.gaussians, w.cams, w.masks, w.E, cull_mode=1)
+    np.testing.assert_array_equal(a.table, b.table)
+
+
+def test_thread_count_and_selection(tiny):
+    a = oracle.accumulate(tiny.gaussians, tiny.cams, tiny.masks, tiny.E, nthreads=1)
+    b = oracle.accumulate(tiny.gaussians, tiny.cams, tiny.masks, tiny.E, nthreads=5)
+    np.testing.assert_allclose(a.table, b.table, rtol=1e-13, atol=1e-16)
+    sel = np.array([3, 17, 400, 1999])
+    c = oracle.accumulate(tiny.gaussians, tiny.cams, tiny.masks, tiny.E, sel=sel)
+    np.testing.assert_allclose(c.table, a.table[sel], rtol=1e-13, atol=1e-16)
+
+
+def test_column_sums_independent_of_labels(tiny):
+    """sum_e A[i, e] depends on the scene and cameras only; relabelling the
+    masks permutes the columns."""
+    E = 3
+    rng = np.random.default_rng(5)
+    m1 = [rng.integers(0, E, size=m.shape) for m in tiny.masks]
+    m2 = [np.zeros_like(m) for m in tiny.masks]
+    perm = np.array([2, 0, 1])
+    m3 = [perm[m] for m in m1]
+    a1 = oracle.accumulate(tiny.gaussians, tiny.cams, m1, E).table
+    a2 = oracle.accumulate(tiny.gaussians, tiny.cams, m2, E).table
+    a3 = oracle.accumulate(tiny.gaussians, tiny.cams, m3, E).table
+    np.testing.assert_allclose(a1.sum(1), a2.sum(1), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(a3[:, perm], a1, rtol=1e-12, atol=1e-15)
+
+
+def test_bad_labels_are_skipped(tiny):
+    masks = [m.astype(np.int32) for m in tiny.masks[:2]]
+    masks[0] = masks[0].copy()
+    masks[0][:4, :] = 7
+    masks[1] = masks[1].copy()
+    masks[1][:, :2] = -1
+    acc = oracle.accumulate(tiny.gaussians, tiny.cams[:2], masks, 2)
+    assert acc.n_bad_label == 4 * 128 + 2 * 128
+    ref = oracle.accumulate(tiny.gaussians, tiny.cams[:2], [m.clip(0, 1) for m in masks], 2)
+    assert acc.table.sum() < ref.table.sum()
+
+
+# --------------------------------------------------------------------------
+# the integer program (Sec. 3.2 Eq. 2-6) and its closed form
+# --------------------------------------------------------------------------
+
+def _small_scene(seed, n, views, size, E):
+    rng = np.random.default_rng(seed)
+    g = {
+        "mean": rng.uniform(-0.35, 0.35, (n, 3)).astype(np.float32),
+        "quat": rng.standard_normal((n, 4)).astype(np.float32),
+        "scale": np.exp(rng.normal(-2.0, 0.4, (n, 3))).astype(np.float32),
+        "opacity": rng.uniform(0.2, 0.99, n).astype(np.float32),
+    }
+    cams = []
+    for v in range(views):
+        az = 2 * math.pi * v / views + 0.3
+        cams.append(synth.camera((2.0 * math.sin(az), 0.4, -2.0 * math.cos(az)), size, size,
+                                 size * 1.1))
+    masks = [rng.integers(0, E, size=(size, size)) for _ in range(views)]
+    # blobs make the vote non-trivial: most pixels agree locally
+    for m in masks:
+        yy, xx = np.mgrid[0:size, 0:size]
+        m[(xx - size / 2) ** 2 + (yy - size / 2.5) ** 2 < (size / 4) ** 2] = E - 1
+    return g, cams, masks
+
+
+def _dense_terms(g, cams):
+    offs, gidx, con, tf = oracle.pixel_lists(g, cams)
+    n = g["mean"].shape[0]
+    P = offs.size - 1
+    C = np.zeros((n, P))
+    pix = np.repeat(np.arange(P), np.diff(offs))
+    np.add.at(C, (gidx, pix), con)
+    return C
+
+
+@pytest.mark.parametrize("seed,n,views,size,E", [
+    (11, 10, 2, 24, 2), (12, 12, 3, 16, 2), (13, 9, 4, 20, 3), (14, 12, 1, 48, 3), (15, 11, 2, 32, 2),
+])
+def test_closed_form_reaches_ilp_optimum(seed, n, views, size, E):
+    """Brute force over all 2^N assignments.  For label e, with y_p = [M_p = e]
+    and x_p = sum_i P_i alpha_i T_i rendered per pixel (Eq. 1 with x_i = P_i),
+    the objective of Eq. 2 (gamma = 0) and its background-biased form
+    F_gamma = sum_p w_p |x_p - y_p|, w_p = (1 - gamma) if y_p else (1 + gamma),
+    is minimised by the closed-form membership S[e] (Eq. 6/7 with the bias)."""
+    g, cams, masks = _small_scene(seed, n, views, size, E)
+    C = _dense_terms(g, cams)                                 # [N, P]
+    lab = np.concatenate([m.reshape(-1) for m in masks])
+    A = oracle.accumulate(g, cams, masks, E).table
+    Pall = np.array(list(itertools.product([0, 1], repeat=n)), dtype=np.float64)   # [2^N, N]
+    X = Pall @ C                                               # rendered masks, [2^N, P]
+    assert X.max() <= 1 + 1e-12 and X.min() >= 0                # Lemma 1
+    for gamma in GOLDEN["gamma_grid"]["values"]:
+        S = assign(A, gamma)
+        for e in range(E):
+            y = (lab == e).astype(np.float64)
+            wts = np.where(y > 0, 1 - gamma, 1 + gamma)
+            F = (np.abs(X - y[None, :]) * wts[None, :]).sum(1)
+            k = int(np.dot(S[e].astype(np.int64), 1 << np.arange(n - 1, -1, -1)))
+            assert F[k] <= F.min() * (1 + 1e-12) + 1e-12, (gamma, e, F[k], F.min())
+            # unique minimiser when every coefficient is clearly non-zero
+            coef = (1 + gamma) * (A.sum(1) - A[:, e]) - (1 - gamma) * A[:, e]
+            if np.all(np.abs(coef) > 1e-9):
+                assert int(np.argmin(F)) == k
+
+
+@pytest.mark.parametrize("seed", [21, 22, 23])
+def test_linearisation_eq3_to_eq5(seed):
+    """F(P) evaluated per pixel equals C + sum_i P_i (A_0^i - A_1^i) (Eq. 3-5),
+    and the rendered total equals sum_i P_i sum_e A[i, e]."""
+    g, cams, masks = _small_scene(seed, 12, 3, 24, 2)
+    C = _dense_terms(g, cams)
+    lab = np.concatenate([m.reshape(-1) for m in masks]).astype(np.float64)
+    A = oracle.accumulate(g, cams, masks, 2).table
+    rng = np.random.default_rng(seed)
+    for _ in range(20):
+        P = rng.integers(0, 2, 12).astype(np.float64)
+        x = P @ C
+        F = np.abs(x - lab).sum()
+        np.testing.assert_allclose(F, lab.sum() + P @ (A[:, 0] - A[:, 1]), rtol=1e-12)
+        np.testing.assert_allclose(x.sum(), P @ A.sum(1), rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# the assignment (Sec. 3.2 regularised ILP, Sec. 3.3 Eq. 7, Listing 1)
+# --------------------------------------------------------------------------
+
+def test_assign_golden_ties():
+    for case in GOLDEN["assign_ties"]["cases"]:
+        S = assign(np.array([case["A"]]), case["gamma"])
+        assert bool(S[1, 0]) == case["member_label1"], case
+
+
+@pytest.mark.parametrize("gamma", GOLDEN["gamma_grid"]["values"] + GOLDEN["gamma_grid"]["ends"])
+def test_assign_threshold_law(gamma):
+    """Membership of e  <=>  A_e > (1 + gamma)/2 * sum_e A  (sum > 0), and
+    <=> gamma < 0 for a Gaussian nobody saw; exclusive for gamma >= 0."""
+    rng = np.random.default_rng(7)
+    A = rng.exponential(1.0, (5000, 6)) * (rng.random((5000, 6)) < 0.6)
+    A[:50] = 0.0
+    S = assign(A, gamma)
+    s = A.sum(1)
+    for e in range(6):
+        exp = np.where(s > 0, A[:, e] > (1 + gamma) / 2 * s, gamma < 0)
+        # only exact ties could differ in rounding; the random table has none
+        np.testing.assert_array_equal(S[e], exp)
+    if gamma >= 0:
+        assert S.sum(0).max() <= 1
+    if gamma == 1.0:
+        assert not S.any()
+    if gamma == -1.0:
+        np.testing.assert_array_equal(S, (A > 0).T | (s == 0)[None, :])
+
+
+def test_assign_overlap_only_below_zero():
+    A = np.array([[1.0, 1.0, 1.0], [2.0, 1.0, 1.0]])
+    assert assign(A, -0.5)[:, 0].sum() == 3       # Sec. 3.3: subsets overlap for gamma < 0
+    assert assign(A, 0.0)[:, 0].sum() == 0
+    assert assign(A, 0.0)[:, 1].tolist() == [False, False, False]
+    assert assign(A, -0.2)[:, 1].tolist() == [True, False, False]
+
+
+def test_assign_margin_and_labels():
+    A = np.array([[1.0, 3.0], [3.0, 1.0], [0.0, 0.0], [1.0, 1.0]])
+    m = assign_margin(A, 0.5)
+    # (1-g)A_e - (1+g)(S-A_e) over S: label 1 of row 0: (0.5*3 - 1.5*1)/4 = 0
+    assert m[0, 1] == 0.0 and m[0, 0] == pytest.approx((1.5 * 3 - 0.5 * 1) / 4)
+    assert np.isinf(m[2]).all()
+    lab = labels_from_membership(assign(A, 0.0))
+    assert lab.tolist() == [1, 0, -1, -1]
+
+
+def test_special_masks(tiny):
+    """All-foreground masks: every seen Gaussian joins label 1 (gamma < 1);
+    all-background: none does."""
+    cams = tiny.cams[:3]
+    fg = oracle.accumulate(tiny.gaussians, cams, [np.ones_like(m) for m in tiny.masks[:3]], 2)
+    bg = oracle.accumulate(tiny.gaussians, cams, [np.zeros_like(m) for m in tiny.masks[:3]], 2)
+    seen = fg.table.sum(1) > 0
+    assert seen.sum() > 100
+    for gamma in (-0.8, 0.0, 0.9):
+        assert assign(fg.table, gamma)[1][seen].all()
+        assert not assign(bg.table, gamma)[1][seen].any()
+
+
+def test_risk_bounds_are_local(tiny):
+    """The near-threshold bookkeeping stays small: most Gaussians carry no
+    risk, and the rest carry little relative to their contributions."""
+    acc = oracle.accumulate(tiny.gaussians, tiny.cams, tiny.masks, tiny.E)
+    s = acc.table.sum(1)
+    r = acc.risk.sum(1)
+    assert (r > 0).mean() < 0.5
+    assert np.median(r[r > 0] / s[r > 0]) < 1e-4
