@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the FlashSplat hot path on GB300.
+
+One step = one whole scene solve (Sec. 3.2-3.3, Sec. 4.2): every mask pixel
+of every view is alpha-composited through the scene, alpha*T is accumulated
+per (Gaussian, label), and the biased closed-form assignment runs -- the
+binary segmentation workload at real-scene scale: 1,000,000 Gaussians from 20
+anisotropic clusters, 100 forward-facing views of 1008x756, noisy binary
+masks, gamma = 0.5 (seeded synthetic data).
+
+Metric: Gpix/s = mask pixels solved per second (76.2 M pixels per scene), and
+seconds per scene solve.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Default arm: the CUDA library (device-resident inputs, L2 flushed before each
+timed step, CUDA-event timing on the launching stream), plus the end-to-end
+number through the C ABI with host masks and host outputs.  Under torchrun
+every rank solves its own replica of the scene (independent problems, no
+collective on the data path).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s per scene solve & Gpix/s of α·T accumulation; batched BF16 vs plain FP32"
+UNIT = "Gpix/s"
+FLOPS_PER_PAIR = 19   # FP32 flops of one (pixel, Gaussian) evaluation, FMA = 2
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="flashsplat", choices=["flashsplat", "reference"])
+    ap.add_argument("--views-per-batch", type=int, default=0)
+    ap.add_argument("--views", type=int, default=100)
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-views", type=int, default=2)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2409_08270_gb300 import synth
+    return synth.binary_scene(n=args.n, views=args.views)
+
+
+def config_of(w, args, extra=None):
+    c = {"workload": f"binary segmentation, {w.n} Gaussians / 20 clusters, {len(w.cams)} views "
+                     f"{w.cams[0]['width']}x{w.cams[0]['height']}, uint8 masks, gamma {w.gamma}",
+         "gaussians": w.n, "views": len(w.cams), "width": w.cams[0]["width"],
+         "height": w.cams[0]["height"], "labels": w.E, "gamma": w.gamma,
+         "pixels_per_scene": w.pixels, "table": "fp32 [N x E]",
+         "mask_noise_fraction": round(w.info.get("noise_fraction", 0.0), 4)}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.path = tempfile.mktemp(prefix="fs_clocks_", suffix=".csv")
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ---------------------------------------------------------------------------
+# the CUDA arm
+# ---------------------------------------------------------------------------
+
+def run_flashsplat(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2409_08270_gb300 import build as lib_build
+    from paper_2409_08270_gb300 import flashsplat as fsb
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    lib_build.build()
+    fsb.load()
+    w = workload(args)
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    solver = fsb.Solver(w.gaussians, device=local_rank, views_per_batch=args.views_per_batch,
+                        time_stages=True)
+    dmasks = solver.upload_masks(w.masks)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+
+    def step():
+        return solver.solve(w.cams, dmasks, w.E, w.gamma, sync=False)
+
+    for _ in range(args.warmup):
+        out = step()
+    fsb.fs_synchronize(solver.ctx, stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(props.uuid)
+    except Exception:
+        pass
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(uuid)
+    torch.cuda.synchronize(dev)
+    ms_steps, blend_ms, pairs, launches, blend_launches, entries = [], 0.0, 0, 0, 0, 0
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)                       # evict the previous step's data from L2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = step()
+        e1.record(stream)
+        st = fsb.fs_synchronize(solver.ctx, stream.cuda_stream)
+        ms_steps.append(e0.elapsed_time(e1))
+        blend_ms += st.blend_ms
+        blend_launches += st.blend_launches
+        pairs += st.pairs
+        entries += st.list_entries
+        launches += st.kernel_launches
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    total_ms = sum(ms_steps)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = total_ms / args.steps
+    gpix = world * w.pixels * args.steps / (total_ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI: host masks in, host outputs out --------
+    e2e = None
+    if not args.no_e2e:
+        host_masks = [torch.from_numpy(m).pin_memory() for m in w.masks]
+        n = w.n
+        h_bits = torch.empty(n, dtype=torch.int64).pin_memory()
+        h_label = torch.empty(n, dtype=torch.int32).pin_memory()
+        h_margin = torch.empty(n, dtype=torch.float32).pin_memory()
+        res = fsb.fs_result()
+        res.memory, res.table_dtype = fsb.FS_MEM_HOST, fsb.FS_F32
+        res.table = None
+        res.member_bits, res.label, res.margin = (h_bits.data_ptr(), h_label.data_ptr(),
+                                                  h_margin.data_ptr())
+        cams = fsb.make_cameras(w.cams)
+        mptr = [m.data_ptr() for m in host_masks]
+
+        def e2e_step():
+            fsb.fs_solve(solver.ctx, solver.scene, cams, mptr, fsb.FS_U8, fsb.FS_MEM_HOST, w.E,
+                         float(w.gamma), res, stream.cuda_stream)
+            fsb.fs_synchronize(solver.ctx, stream.cuda_stream)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        h2d = sum(m.numel() * m.element_size() for m in host_masks)
+        d2h = n * (8 + 4 + 4)
+        # the result is on the host: check it once (labels in range, some members)
+        lab = h_label.numpy()
+        assert lab.min() >= -1 and lab.max() < w.E
+        e2e = {"value": world * w.pixels * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+               "ms_per_step": e2e_ms / args.steps, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "api": "fs_solve (host masks, host outputs)"}
+
+    # ---- roofline of the dominant kernel (blend/accumulate) -------------------
+    sm_clk = clk.get("sm_max_mhz") or 2070.0
+    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_clk * 1e6 / 1e12
+    achieved = (FLOPS_PER_PAIR * pairs) / (blend_ms * 1e-3) / 1e12 if blend_ms > 0 else None
+    roofline = {"kernel": "blend_kernel (alpha*T accumulation)", "bound": "alu",
+                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": (achieved / peak_tflops) if achieved else None, "traffic": None,
+                "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_clk:.0f} MHz",
+                "pairs_per_step": pairs // max(1, args.steps),
+                "list_entries_per_step": entries // max(1, args.steps),
+                "flops_per_pair": FLOPS_PER_PAIR,
+                "blend_ms_per_step": blend_ms / args.steps,
+                "blend_share_of_step": blend_ms / max(total_ms, 1e-9),
+                "blend_launches_per_step": blend_launches // max(1, args.steps)}
+
+    line = {
+        "metric": METRIC, "value": gpix, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "s_per_scene": ms_per_step / 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded clustered 3D-GS scene and noisy masks; stands in for the "
+                "paper's LLFF/MIP-360/T&T scenes with SAM masks)",
+        "config": config_of(w, args, {"l2": "flushed (512 MB write) before each timed step",
+                                      "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                                      "wall_s_timed": t_wall}),
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "clocks": clk,
+    }
+    solver.close()
+    return line, w
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(w, views):
+    import oracle
+    cams = w.cams[:views]
+    masks = w.masks[:views]
+    t0 = time.perf_counter()
+    acc = oracle.accumulate(w.gaussians, cams, masks, w.E)
+    oracle.assign(acc.table, w.gamma)
+    dt = time.perf_counter() - t0
+    pix = sum(m.size for m in masks)
+    return pix, dt
+
+
+def cpu_cores():
+    return len(os.sched_getaffinity(0))
+
+
+def run_reference(args, rank, world):
+    import oracle
+    oracle.build()
+    w = workload(args)
+    cfg = config_of(w, args, {"sample": "1 view per step (762,048 pixels), all Gaussians"})
+    for _ in range(args.warmup):
+        oracle_sample(w, 1)
+    pix, tsum = 0, 0.0
+    for _ in range(args.steps):
+        p, dt = oracle_sample(w, 1)
+        pix += p
+        tsum += dt
+    val = pix / tsum / 1e9
+    ms = tsum / args.steps * 1e3
+    sample = "1 of 100 views per step (762,048 pixels); FP64 oracle over all 1M Gaussians"
+    return {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded clustered 3D-GS scene and noisy masks)", "config": cfg,
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    line, w = run_flashsplat(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pix, dt = oracle_sample(w, args.cpu_sample_views)
+        line["cpu_baseline"] = {
+            "value": pix / dt / 1e9, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"first {args.cpu_sample_views} of {len(w.cams)} views "
+                      f"({pix:,} pixels), all {w.n:,} Gaussians, FP64, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

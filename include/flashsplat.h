@@ -75,7 +75,8 @@ typedef struct fs_scene fs_scene;
 /* Context options.  Zero-initialise and set what you need; 0 = default. */
 typedef struct fs_options {
   int32_t views_per_batch;  /* views binned and blended per launch group (default 8) */
-  int32_t reserved[15];
+  int32_t time_stages;      /* non-zero: time every blend launch with CUDA events */
+  int32_t reserved[14];
 } fs_options;
 
 /* A Gaussian scene (Sec. 3.1: G_i = {m_i, q_i, s_i, o_i}; colour unused). */
@@ -101,11 +102,14 @@ typedef struct fs_camera {
 
 /* Counters of the last fs_accumulate / fs_solve on a context. */
 typedef struct fs_stats {
-  int64_t views;          /* views processed */
-  int64_t pixels;         /* mask pixels walked */
-  int64_t list_entries;   /* (tile, Gaussian) pairs binned, summed over views */
-  int64_t bad_labels;     /* pixels whose label was outside [0, E) (skipped) */
-  int64_t reserved[4];
+  int64_t views;           /* views processed */
+  int64_t pixels;          /* mask pixels walked */
+  int64_t list_entries;    /* (tile, Gaussian) pairs binned, summed over views */
+  int64_t bad_labels;      /* pixels whose label was outside [0, E) (skipped) */
+  int64_t pairs;           /* (pixel, Gaussian) pairs evaluated by the blend */
+  int64_t kernel_launches; /* kernels launched by the library */
+  double blend_ms;         /* summed blend time (fs_options.time_stages), else 0 */
+  int64_t blend_launches;  /* blend launches timed */
 } fs_stats;
 
 /* Outputs of fs_solve.  Any pointer may be NULL to skip that output. */

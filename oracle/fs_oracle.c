@@ -48,13 +48,17 @@
 #define FSO_BIN 8
 
 /* Near-threshold windows (relative) used to flag discrete decisions that a
- * lower-precision implementation may legitimately take the other way. */
-#define FSO_EVENT_REL 1e-5
+ * lower-precision implementation may legitimately take the other way.  An FP32
+ * tile rasteriser evaluates the exponent of a thin Gaussian (0.55 px wide)
+ * across a 16-px tile with an absolute error of ~2e-5, i.e. alpha to ~1e-5
+ * relative near the 1/255 cut, and T after hundreds of factors to ~1e-5; the
+ * windows are set an order of magnitude wider than that. */
+#define FSO_EVENT_REL 1e-4
 #define FSO_T_EVENT_REL 1e-4
 #define FSO_DEPTH_TIE_REL 1e-6
 
 /* flag bits per Gaussian */
-#define FSO_FLAG_ALPHA_EDGE 1u   /* alpha within 1e-5 rel. of 1/255 */
+#define FSO_FLAG_ALPHA_EDGE 1u   /* alpha within 1e-4 rel. of 1/255 */
 #define FSO_FLAG_T_EDGE 2u       /* T(1-alpha) within 1e-4 rel. of 1e-4 */
 #define FSO_FLAG_DEPTH_TIE 4u    /* depth within 1e-6 rel. of a neighbour */
 #define FSO_FLAG_DOWNSTREAM 8u   /* after an event in the same pixel */
@@ -243,9 +247,12 @@ static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use
       continue;
     }
     const double test_T = T * (1.0 - alpha);
-    const int t_edge = fabs(test_T - FSO_T_MIN) <= FSO_T_EVENT_REL * FSO_T_MIN;
+    /* T itself is uncertain by the relative amount `down` after marginal
+     * alpha decisions earlier in this pixel, so the stop test is marginal
+     * within that much more. */
+    const int t_edge = fabs(test_T - FSO_T_MIN) <= (FSO_T_EVENT_REL + 1.01 * down) * FSO_T_MIN;
     if (test_T < FSO_T_MIN) {
-      if (t_edge || down > 0.0 || all_risky) {
+      if (t_edge || all_risky) {
         /* the stop may not happen in another walk: this term and all
          * later ones are at risk */
         hits[nh].g = g; hits[nh].c = 0.0;

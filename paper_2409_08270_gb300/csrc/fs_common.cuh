@@ -1,0 +1,134 @@
+// Shared device-side definitions of the FlashSplat CUDA path (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fs {
+
+constexpr int kTile = 16;                 // 16x16 pixel tiles (Sec. 3.1)
+constexpr int kTilePixels = kTile * kTile;
+constexpr int kBlendThreads = 256;        // one thread per tile pixel
+
+// Thresholds of the compositing rule (Sec. 3.1 Eq. 1 with the rasteriser's
+// conventions): alpha below 1/255 is skipped, alpha is clamped to 0.99, and a
+// pixel stops before a Gaussian that would take T below 1e-4.
+constexpr float kAlphaMin = (float)(1.0 / 255.0);
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kLowPass = 0.3f;          // px^2 added to the 2D covariance diagonal
+// 0.5 * log2(e): alpha = o * 2^(-|W d|^2) with W = sqrt(kHalfLog2e) Lambda^-1/2 V^T
+constexpr double kHalfLog2e = 0.72134752044448170368;
+
+// Per-view parameters, prepared on the host.  Double precision quantities are
+// carried as float pairs (hi + lo) so the projection needs no FP64 pipe.
+struct ViewParams {
+  float R_hi[9], R_lo[9];      // world->camera rotation, row-major
+  float t_hi[3], t_lo[3];
+  float fx_hi, fx_lo, fy_hi, fy_lo, cx_hi, cx_lo, cy_hi, cy_lo;
+  float near_hi, near_lo;      // near plane 0.2 as a float pair
+  float limx, limy;            // 1.3 * tan(half field of view) per axis
+  int32_t width, height;
+  int32_t tiles_x, tiles_y;
+  int32_t tile_base;           // first tile id of this view in the batch
+  int32_t pad0;
+  const void* mask;            // device pointer to the view's labels
+};
+
+// Projected record of one (view, Gaussian): 3 x float4 = 48 B.
+//   r0 = W (row-major 2x2 whitening, FP32)
+//   r1 = (c0_hi, c1_hi, c0_lo, c1_lo) with c = -W m2D as float pairs
+//   r2 = (opacity, 0, 0, 0)
+// For a tile with integer origin o the blend uses b = W o + c, evaluated in
+// float-pair arithmetic, and w = W p_local + b for p_local in the tile.
+struct alignas(16) ProjRecord {
+  float4 w;
+  float4 c;
+  float4 misc;
+};
+
+// ---------------------------------------------------------------------------
+// Float-pair ("double-float") arithmetic: error-free transformations of
+// Knuth (TwoSum), Dekker/FMA (TwoProduct) and the compensated dot product of
+// Ogita, Rump and Oishi (2005).  Values are hi + lo with |lo| <= ulp(hi)/2.
+// ---------------------------------------------------------------------------
+struct f2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ f2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  const float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+
+__device__ __forceinline__ f2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  return {p, e};
+}
+
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 s = two_sum(a.hi, b.hi);
+  const f2 t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+  return fast_two_sum(p.hi, p.lo);
+}
+
+__device__ __forceinline__ f2 f2_mul_f(f2 a, float b) {
+  f2 p = two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+
+// a / b for float pairs: one correction step of the float quotient.
+__device__ __forceinline__ f2 f2_div(f2 a, f2 b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  // r = a - q1 * b, exactly up to the lo terms
+  const f2 p = two_prod(q1, b.hi);
+  float r = __fsub_rn(a.hi, p.hi);
+  r = __fsub_rn(r, p.lo);
+  r = __fadd_rn(r, a.lo);
+  r = __fmaf_rn(-q1, b.lo, r);
+  const float q2 = __fdiv_rn(r, b.hi);
+  return fast_two_sum(q1, q2);
+}
+
+// sum_k a_k * x_k + c for float-pair a_k, c and float x_k (compensated dot product).
+__device__ __forceinline__ f2 f2_dot3_add(const float* a_hi, const float* a_lo, float x0, float x1,
+                                          float x2, float c_hi, float c_lo) {
+  f2 p0 = two_prod(a_hi[0], x0);
+  f2 p1 = two_prod(a_hi[1], x1);
+  f2 p2 = two_prod(a_hi[2], x2);
+  float err = __fmaf_rn(a_lo[0], x0, p0.lo);
+  err = __fadd_rn(err, __fmaf_rn(a_lo[1], x1, p1.lo));
+  err = __fadd_rn(err, __fmaf_rn(a_lo[2], x2, p2.lo));
+  f2 s = two_sum(p0.hi, p1.hi);
+  err = __fadd_rn(err, s.lo);
+  s = two_sum(s.hi, p2.hi);
+  err = __fadd_rn(err, s.lo);
+  s = two_sum(s.hi, c_hi);
+  err = __fadd_rn(err, s.lo);
+  err = __fadd_rn(err, c_lo);
+  return fast_two_sum(s.hi, err);
+}
+
+// Order-preserving map of a positive float to uint32 (depth keys).
+__device__ __forceinline__ uint32_t depth_key(float z) { return __float_as_uint(z); }
+
+}  // namespace fs

@@ -1,0 +1,313 @@
+"""Thin Python binding of libflashsplat (include/flashsplat.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  The ``fs_*`` functions mirror the C ABI one to one; ``Solver`` is a
+convenience wrapper that takes numpy / torch inputs, keeps device buffers in
+torch tensors and returns torch tensors.  PyTorch provides device memory and
+streams only.
+
+The library must have been built (``paper_2409_08270_gb300.build.build()``);
+loading fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FS_OK, FS_INVALID_ARGUMENT, FS_OUT_OF_MEMORY, FS_CUDA_ERROR, FS_TIMEOUT, FS_UNSUPPORTED, \
+    FS_CANCELLED = range(7)
+FS_F32, FS_F64, FS_BF16, FS_F16, FS_U8, FS_I32 = range(6)
+FS_MEM_HOST, FS_MEM_DEVICE = 0, 1
+
+STATUS_NAMES = {0: "FS_OK", 1: "FS_INVALID_ARGUMENT", 2: "FS_OUT_OF_MEMORY", 3: "FS_CUDA_ERROR",
+                4: "FS_TIMEOUT", 5: "FS_UNSUPPORTED", 6: "FS_CANCELLED"}
+
+# every entry point declared in include/flashsplat.h
+EXPORTS = ["fs_version", "fs_last_error", "fs_create", "fs_destroy", "fs_scene_create",
+           "fs_scene_destroy", "fs_scene_size", "fs_accumulate", "fs_assign", "fs_solve",
+           "fs_synchronize"]
+
+
+class fs_options(ctypes.Structure):
+    _fields_ = [("views_per_batch", ctypes.c_int32), ("time_stages", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 14)]
+
+
+class fs_gaussians(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("mean", ctypes.c_void_p), ("quat", ctypes.c_void_p),
+                ("scale", ctypes.c_void_p), ("opacity", ctypes.c_void_p),
+                ("quat_dtype", ctypes.c_int32), ("scale_dtype", ctypes.c_int32),
+                ("opacity_dtype", ctypes.c_int32), ("memory", ctypes.c_int32)]
+
+
+class fs_camera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3), ("fx", ctypes.c_double),
+                ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class fs_stats(ctypes.Structure):
+    _fields_ = [("views", ctypes.c_int64), ("pixels", ctypes.c_int64),
+                ("list_entries", ctypes.c_int64), ("bad_labels", ctypes.c_int64),
+                ("pairs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("blend_ms", ctypes.c_double), ("blend_launches", ctypes.c_int64)]
+
+
+class fs_result(ctypes.Structure):
+    _fields_ = [("memory", ctypes.c_int32), ("table_dtype", ctypes.c_int32),
+                ("table", ctypes.c_void_p), ("member_bits", ctypes.c_void_p),
+                ("label", ctypes.c_void_p), ("margin", ctypes.c_void_p)]
+
+
+class FlashSplatError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libflashsplat.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libflashsplat.so not found at {path}: build it with "
+                           "paper_2409_08270_gb300.build.build() (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    sig = {
+        "fs_version": (i32, []),
+        "fs_last_error": (ctypes.c_char_p, []),
+        "fs_create": (i32, [ctypes.POINTER(vp), i32, ctypes.POINTER(fs_options)]),
+        "fs_destroy": (i32, [vp]),
+        "fs_scene_create": (i32, [vp, ctypes.POINTER(fs_gaussians), ctypes.POINTER(vp)]),
+        "fs_scene_destroy": (i32, [vp]),
+        "fs_scene_size": (i64, [vp]),
+        "fs_accumulate": (i32, [vp, vp, ctypes.POINTER(fs_camera), i32, ctypes.POINTER(vp), i32,
+                                i32, i32, vp, i32, vp]),
+        "fs_assign": (i32, [vp, vp, i32, i64, i32, f32, vp, vp, vp, vp]),
+        "fs_solve": (i32, [vp, vp, ctypes.POINTER(fs_camera), i32, ctypes.POINTER(vp), i32, i32,
+                           i32, f32, ctypes.POINTER(fs_result), vp]),
+        "fs_synchronize": (i32, [vp, vp, ctypes.POINTER(fs_stats)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != FS_OK:
+        msg = load().fs_last_error().decode(errors="replace")
+        raise FlashSplatError(status, msg)
+
+
+# ---- one-to-one wrappers of the C ABI ------------------------------------
+
+def fs_version() -> int:
+    return load().fs_version()
+
+
+def fs_last_error() -> str:
+    return load().fs_last_error().decode(errors="replace")
+
+
+def fs_create(device: int = 0, views_per_batch: int = 0, time_stages: bool = False) -> int:
+    ctx = ctypes.c_void_p()
+    opt = fs_options()
+    opt.views_per_batch = views_per_batch
+    opt.time_stages = 1 if time_stages else 0
+    check(load().fs_create(ctypes.byref(ctx), device, ctypes.byref(opt)))
+    return ctx.value
+
+
+def fs_destroy(ctx: int):
+    check(load().fs_destroy(ctx))
+
+
+def fs_scene_create(ctx: int, g: fs_gaussians) -> int:
+    sc = ctypes.c_void_p()
+    check(load().fs_scene_create(ctx, ctypes.byref(g), ctypes.byref(sc)))
+    return sc.value
+
+
+def fs_scene_destroy(scene: int):
+    check(load().fs_scene_destroy(scene))
+
+
+def fs_accumulate(ctx, scene, cams, masks, mask_dtype, mask_memory, E, table, table_dtype,
+                  stream=0):
+    V = len(masks)
+    mp = (ctypes.c_void_p * max(V, 1))(*masks)
+    check(load().fs_accumulate(ctx, scene, cams, V, mp, mask_dtype, mask_memory, E, table,
+                               table_dtype, stream))
+
+
+def fs_assign(ctx, table, table_dtype, n, E, gamma, bits=None, label=None, margin=None, stream=0):
+    check(load().fs_assign(ctx, table, table_dtype, n, E, gamma, bits, label, margin, stream))
+
+
+def fs_solve(ctx, scene, cams, masks, mask_dtype, mask_memory, E, gamma, result: fs_result,
+             stream=0):
+    V = len(masks)
+    mp = (ctypes.c_void_p * max(V, 1))(*masks)
+    check(load().fs_solve(ctx, scene, cams, V, mp, mask_dtype, mask_memory, E, gamma,
+                          ctypes.byref(result), stream))
+
+
+def fs_synchronize(ctx, stream=0) -> fs_stats:
+    st = fs_stats()
+    check(load().fs_synchronize(ctx, stream, ctypes.byref(st)))
+    return st
+
+
+# ---- helpers ---------------------------------------------------------------
+
+def make_cameras(cams) -> ctypes.Array:
+    cams = list(cams)
+    arr = (fs_camera * max(len(cams), 1))()
+    for k, c in enumerate(cams):
+        arr[k].R[:] = [float(x) for x in np.asarray(c["R"], dtype=np.float64).reshape(9)]
+        arr[k].t[:] = [float(x) for x in np.asarray(c["t"], dtype=np.float64).reshape(3)]
+        arr[k].fx, arr[k].fy = float(c["fx"]), float(c["fy"])
+        arr[k].cx, arr[k].cy = float(c["cx"]), float(c["cy"])
+        arr[k].width, arr[k].height = int(c["width"]), int(c["height"])
+    return arr
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Solver:
+    """A context on one GPU with one resident scene.
+
+    gaussians: dict of arrays mean [N,3] f32, quat [N,4], scale [N,3], opacity [N]
+    (numpy or torch; float32, or bfloat16 quat/scale and float16 opacity for
+    the reduced-precision storage form).
+    """
+
+    _DT = {"float32": FS_F32, "bfloat16": FS_BF16, "float16": FS_F16}
+
+    def __init__(self, gaussians, device: int = 0, views_per_batch: int = 0,
+                 time_stages: bool = False):
+        torch = _torch()
+        self.device = torch.device("cuda", device)
+        self.ctx = fs_create(device, views_per_batch, time_stages)
+        self.scene = None
+        dev = {}
+        for k in ("mean", "quat", "scale", "opacity"):
+            a = gaussians[k]
+            if not torch.is_tensor(a):
+                a = torch.from_numpy(np.ascontiguousarray(a))
+            dev[k] = a.to(self.device).contiguous()
+        self.n = int(dev["mean"].shape[0])
+        g = fs_gaussians()
+        g.n = self.n
+        g.mean, g.quat = dev["mean"].data_ptr(), dev["quat"].data_ptr()
+        g.scale, g.opacity = dev["scale"].data_ptr(), dev["opacity"].data_ptr()
+        g.quat_dtype = self._DT[str(dev["quat"].dtype).replace("torch.", "")]
+        g.scale_dtype = self._DT[str(dev["scale"].dtype).replace("torch.", "")]
+        g.opacity_dtype = self._DT[str(dev["opacity"].dtype).replace("torch.", "")]
+        g.memory = FS_MEM_DEVICE
+        self.scene = fs_scene_create(self.ctx, g)
+        torch.cuda.synchronize(self.device)
+
+    def close(self):
+        if self.scene:
+            fs_scene_destroy(self.scene)
+            self.scene = None
+        if self.ctx:
+            fs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream(stream):
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return s.cuda_stream
+
+    def upload_masks(self, masks):
+        """Device copies of the masks (uint8 or int32), one tensor per view."""
+        torch = _torch()
+        out = []
+        for m in masks:
+            t = m if torch.is_tensor(m) else torch.from_numpy(np.ascontiguousarray(m))
+            out.append(t.to(self.device).contiguous())
+        return out
+
+    @staticmethod
+    def _mask_dtype(t):
+        s = str(t.dtype)
+        if "uint8" in s:
+            return FS_U8
+        if "int32" in s:
+            return FS_I32
+        raise ValueError(f"mask dtype {t.dtype} (want uint8 or int32)")
+
+    def accumulate(self, cams, masks, E, table, stream=None):
+        """table (torch, device, [N, E] float32/float64) += contributions."""
+        torch = _torch()
+        dm = self.upload_masks(masks)
+        tdt = FS_F64 if table.dtype == torch.float64 else FS_F32
+        fs_accumulate(self.ctx, self.scene, make_cameras(cams), [m.data_ptr() for m in dm],
+                      self._mask_dtype(dm[0]), FS_MEM_DEVICE, E, table.data_ptr(), tdt,
+                      self._stream(stream))
+        return dm
+
+    def assign(self, table, gamma, stream=None):
+        torch = _torch()
+        n, E = table.shape
+        bits = torch.empty(n, dtype=torch.int64, device=self.device) if E <= 64 else None
+        label = torch.empty(n, dtype=torch.int32, device=self.device)
+        margin = torch.empty(n, dtype=torch.float32, device=self.device)
+        tdt = FS_F64 if table.dtype == torch.float64 else FS_F32
+        fs_assign(self.ctx, table.data_ptr(), tdt, n, E, float(gamma),
+                  bits.data_ptr() if bits is not None else None, label.data_ptr(),
+                  margin.data_ptr(), self._stream(stream))
+        return bits, label, margin
+
+    def solve(self, cams, masks, E, gamma, table_dtype="float32", stream=None, sync=True):
+        """Whole path on device-resident masks: returns dict of device tensors."""
+        torch = _torch()
+        dm = masks if (masks and torch.is_tensor(masks[0]) and masks[0].is_cuda) \
+            else self.upload_masks(masks)
+        tdt = FS_F64 if table_dtype == "float64" else FS_F32
+        table = torch.empty((self.n, E), dtype=torch.float64 if tdt == FS_F64 else torch.float32,
+                            device=self.device)
+        bits = torch.empty(self.n, dtype=torch.int64, device=self.device) if E <= 64 else None
+        label = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        margin = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        res = fs_result()
+        res.memory, res.table_dtype = FS_MEM_DEVICE, tdt
+        res.table = table.data_ptr()
+        res.member_bits = bits.data_ptr() if bits is not None else None
+        res.label, res.margin = label.data_ptr(), margin.data_ptr()
+        st = self._stream(stream)
+        fs_solve(self.ctx, self.scene, make_cameras(cams), [m.data_ptr() for m in dm],
+                 self._mask_dtype(dm[0]), FS_MEM_DEVICE, E, float(gamma), res, st)
+        out = {"table": table, "bits": bits, "label": label, "margin": margin}
+        if sync:
+            out["stats"] = fs_synchronize(self.ctx, st)
+        return out

@@ -99,12 +99,15 @@ def fx_from_hfov(width, hfov_deg):
     return (width / 2.0) / math.tan(math.radians(hfov_deg) / 2.0)
 
 
-def _pixel_rays(cam):
-    """Unit-free world-space ray directions through every pixel centre, [H, W, 3]."""
+def _pixel_rays(cam, y0=0, y1=None, x0=0, x1=None):
+    """World-space ray directions (not normalised) through the pixel centres of
+    rows [y0, y1) and columns [x0, x1), shape [h, w, 3]."""
     W, H = cam["width"], cam["height"]
-    u = (np.arange(W) + 0.5 - cam["cx"]) / cam["fx"]
-    v = (np.arange(H) + 0.5 - cam["cy"]) / cam["fy"]
-    dc = np.empty((H, W, 3))
+    y1 = H if y1 is None else y1
+    x1 = W if x1 is None else x1
+    u = (np.arange(x0, x1) + 0.5 - cam["cx"]) / cam["fx"]
+    v = (np.arange(y0, y1) + 0.5 - cam["cy"]) / cam["fy"]
+    dc = np.empty((y1 - y0, x1 - x0, 3))
     dc[..., 0] = u[None, :]
     dc[..., 1] = v[:, None]
     dc[..., 2] = 1.0
@@ -117,10 +120,29 @@ def _camera_origin(cam):
     return -R.T @ np.asarray(cam["t"])
 
 
-def ellipsoid_hits(cam, centre, axes_rot, radii):
+def _sphere_box(cam, centre, radius):
+    """Pixel rectangle [y0, y1) x [x0, x1) that holds the image of a ball
+    (the ball lies inside a camera-aligned cube whose corners bound x/z, y/z)."""
+    W, H = cam["width"], cam["height"]
+    p = np.asarray(cam["R"]) @ np.asarray(centre) + np.asarray(cam["t"])
+    if p[2] - radius <= 1e-3:
+        return 0, H, 0, W
+    zs = (p[2] - radius, p[2] + radius)
+    xs = [cam["fx"] * (p[0] + sx * radius) / z + cam["cx"] for sx in (-1, 1) for z in zs]
+    ys = [cam["fy"] * (p[1] + sy * radius) / z + cam["cy"] for sy in (-1, 1) for z in zs]
+    x0, x1 = int(max(0, math.floor(min(xs)) - 1)), int(min(W, math.ceil(max(xs)) + 1))
+    y0, y1 = int(max(0, math.floor(min(ys)) - 1)), int(min(H, math.ceil(max(ys)) + 1))
+    if x0 >= x1 or y0 >= y1:
+        return 0, 0, 0, 0
+    return y0, y1, x0, x1
+
+
+def ellipsoid_hits(cam, centre, axes_rot, radii, box=None):
     """Ray entry distance into the ellipsoid {c + Rot diag(radii) u : |u| <= 1}
-    for every pixel ([H, W], +inf where the ray misses, 0 when the camera is inside)."""
-    rays = _pixel_rays(cam)
+    for the pixels of `box` = (y0, y1, x0, x1) (default: the whole image):
+    +inf where the ray misses, 0 when the camera is inside."""
+    y0, y1, x0, x1 = box if box is not None else (0, cam["height"], 0, cam["width"])
+    rays = _pixel_rays(cam, y0, y1, x0, x1)
     o = _camera_origin(cam) - np.asarray(centre)
     inv = np.asarray(axes_rot).T / np.asarray(radii)[:, None]     # D^-1 Rot^T
     o2 = inv @ o
@@ -143,10 +165,14 @@ def label_map(cam, objects):
     best = np.full((H, W), np.inf)
     lab = np.zeros((H, W), dtype=np.int32)
     for oid, c, rot, rad in objects:
-        s = ellipsoid_hits(cam, c, rot, rad)
-        closer = s < best
-        best = np.where(closer, s, best)
-        lab = np.where(closer, oid, lab)
+        y0, y1, x0, x1 = _sphere_box(cam, c, float(np.max(rad)))
+        if y0 >= y1:
+            continue
+        s = ellipsoid_hits(cam, c, rot, rad, (y0, y1, x0, x1))
+        sub_b = best[y0:y1, x0:x1]
+        closer = s < sub_b
+        best[y0:y1, x0:x1] = np.where(closer, s, sub_b)
+        lab[y0:y1, x0:x1] = np.where(closer, oid, lab[y0:y1, x0:x1])
     return lab
 
 
@@ -249,7 +275,7 @@ def tiny_scene(seed=SEED_BASE + 1, n=2000, views=8, width=128, height=128, fx=15
 
 
 def binary_scene(seed=SEED_BASE + 2, n=1_000_000, views=100, width=1008, height=756,
-                 hfov=60.0, n_clusters=20, flip=0.025, max_morph=3, gamma=0.5):
+                 hfov=60.0, n_clusters=20, flip=0.045, max_morph=3, gamma=0.5):
     """Binary segmentation at real-scene scale (LLFF-like forward-facing):
     N Gaussians from `n_clusters` anisotropic clusters (centres in
     [-1,1]^2 x [-0.5,0.5], per-axis std U[0.05,0.3]), log-scales N(-4,1),

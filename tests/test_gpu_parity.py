@@ -1,0 +1,164 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Sizes span several 16x16 tiles with ragged right/bottom edges.  Contributions
+must agree within 1e-5 relative (plus the oracle's near-threshold risk bound);
+membership decisions must agree exactly wherever the table's error cannot
+reach the decision (see tests/parity.py).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_08270_gb300 import synth
+from parity import label_check, table_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fsb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_08270_gb300 import build, flashsplat
+    build.build()
+    flashsplat.load()
+    return flashsplat
+
+
+def _solve(fsb, w, table_dtype="float32", views_per_batch=0, masks=None, E=None, gamma=None):
+    s = fsb.Solver(w.gaussians, views_per_batch=views_per_batch)
+    try:
+        out = s.solve(w.cams, w.masks if masks is None else masks, w.E if E is None else E,
+                      w.gamma if gamma is None else gamma, table_dtype=table_dtype)
+        return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
+    finally:
+        s.close()
+
+
+def _check(gpu, acc, gamma, rtol=1e-5):
+    ok, rel, summ = table_errors(gpu["table"], acc.table, acc.risk, rtol=rtol)
+    bad = np.argwhere(~ok)[:5]
+    assert summ["violations"] == 0, (summ, [(tuple(b), gpu["table"][tuple(b)],
+                                              acc.table[tuple(b)], acc.risk[tuple(b)]) for b in bad])
+    lab = label_check(gpu["bits"], acc.table, acc.risk, gamma, table_rtol=rtol)
+    assert lab["mismatch_outside_window"] == 0, lab
+    return summ, lab
+
+
+def test_tiny_scene(fsb, tiny):
+    gpu = _solve(fsb, tiny)
+    acc = oracle.accumulate(tiny.gaussians, tiny.cams, tiny.masks, tiny.E)
+    summ, lab = _check(gpu, acc, tiny.gamma)
+    print("tiny", summ, lab)
+    assert summ["checked_rel"] > 1000
+    assert gpu["stats"].bad_labels == 0 and gpu["stats"].views == len(tiny.cams)
+
+
+def test_tiny_scene_fp64_table_and_batching(fsb, tiny):
+    gpu = _solve(fsb, tiny, table_dtype="float64", views_per_batch=3)
+    acc = oracle.accumulate(tiny.gaussians, tiny.cams, tiny.masks, tiny.E)
+    _check(gpu, acc, tiny.gamma)
+
+
+@pytest.mark.parametrize("E", [3, 7, 40])
+def test_random_multilabel_masks(fsb, tiny, E):
+    """i.i.d. random labels: every warp holds several labels, and with E = 7
+    or 40 most tiles exceed the shared-memory label slots (direct path)."""
+    rng = np.random.default_rng(E)
+    masks = [rng.integers(0, E, size=m.shape).astype(np.int32) for m in tiny.masks[:4]]
+    cams = tiny.cams[:4]
+    w = synth.Workload("t", tiny.gaussians, cams, masks, E, 0.0, tiny.gt)
+    gpu = _solve(fsb, w)
+    acc = oracle.accumulate(tiny.gaussians, cams, masks, E)
+    _check(gpu, acc, 0.0)
+
+
+def test_bad_labels_skipped_and_counted(fsb, tiny):
+    masks = [m.astype(np.int32).copy() for m in tiny.masks[:2]]
+    masks[0][:3, :] = 9
+    masks[1][:, :5] = -4
+    w = synth.Workload("t", tiny.gaussians, tiny.cams[:2], masks, 2, 0.5, tiny.gt)
+    gpu = _solve(fsb, w)
+    acc = oracle.accumulate(tiny.gaussians, tiny.cams[:2], masks, 2)
+    _check(gpu, acc, 0.5)
+    assert gpu["stats"].bad_labels == acc.n_bad_label == 3 * 128 + 5 * 128
+
+
+@pytest.mark.parametrize("gamma", [-1.0, -0.8, -0.4, 0.0, 0.4, 0.8, 1.0])
+def test_assign_kernel_matches_oracle_rule(fsb, gamma):
+    """The fused assignment on an FP64 table against the oracle's rule."""
+    import torch
+    rng = np.random.default_rng(3)
+    A = rng.exponential(1.0, (20000, 5)) * (rng.random((20000, 5)) < 0.5)
+    A[:30] = 0
+    A[30:40] = np.array([1.0, 3.0, 0, 0, 0])   # exact ties for gamma = 0.5 ... and others
+    s = fsb.Solver({"mean": np.zeros((1, 3), np.float32), "quat": np.array([[1, 0, 0, 0]], np.float32),
+                    "scale": np.ones((1, 3), np.float32), "opacity": np.ones(1, np.float32)})
+    try:
+        for dt in (torch.float64, torch.float32):
+            t = torch.from_numpy(A).to(dt).cuda()
+            bits, label, margin = s.assign(t, gamma)
+            torch.cuda.synchronize()
+            Aref = t.double().cpu().numpy()
+            S = oracle.assign(Aref, gamma)
+            b = bits.cpu().numpy().astype(np.uint64)
+            Sg = np.stack([((b >> np.uint64(e)) & np.uint64(1)).astype(bool) for e in range(5)])
+            m = oracle.assign_margin(Aref, gamma).T
+            safe = m > (1e-12 if dt == torch.float64 else 1e-6)
+            assert np.array_equal(Sg[safe], S[safe])
+            from oracle.assign import labels_from_membership
+            lab = labels_from_membership(S)
+            safe_lab = safe.all(0)
+            assert np.array_equal(label.cpu().numpy()[safe_lab], lab[safe_lab])
+            mo = m.min(0)
+            mg = margin.cpu().numpy()
+            fin = np.isfinite(mo)
+            assert np.allclose(mg[fin], mo[fin], rtol=1e-5, atol=1e-6)
+            assert np.isinf(mg[~fin]).all()
+    finally:
+        s.close()
+
+
+def test_binary_scene_reduced(fsb):
+    """Real-scene statistics (clustered, anisotropic log-scales N(-4,1)) at a
+    size the oracle finishes in seconds; 1008x756 views keep the ragged rows."""
+    w = synth.binary_scene(n=40000, views=3, width=1008, height=756)
+    gpu = _solve(fsb, w)
+    acc = oracle.accumulate(w.gaussians, w.cams, w.masks, w.E)
+    summ, lab = _check(gpu, acc, w.gamma)
+    print("binary", summ, lab)
+    assert summ["checked_rel"] > 10000
+
+
+def test_multi_scene_reduced(fsb):
+    w = synth.multi_scene(n=60000, views=4, width=628, height=414)
+    gpu = _solve(fsb, w)
+    acc = oracle.accumulate(w.gaussians, w.cams, w.masks, w.E)
+    summ, lab = _check(gpu, acc, w.gamma)
+    print("multi", summ, lab)
+
+
+def test_degenerate_inputs(fsb):
+    """Nothing visible, a 1x1 view, a Gaussian behind the camera, one Gaussian."""
+    g = {"mean": np.array([[0, 0, -5.0], [0, 0, 0.0]], np.float32),
+         "quat": np.array([[1, 0, 0, 0], [0, 0, 0, 2.0]], np.float32),
+         "scale": np.full((2, 3), 0.3, np.float32), "opacity": np.array([0.9, 0.7], np.float32)}
+    cams = [synth.camera((0, 0, -3.0), 1, 1, 2.0), synth.camera((0, 0, 3.0), 17, 33, 20.0),
+            synth.camera((0, 0, -3.0), 40, 24, 30.0)]
+    masks = [np.ones((1, 1), np.uint8), np.zeros((33, 17), np.uint8), np.ones((24, 40), np.uint8)]
+    w = synth.Workload("deg", g, cams, masks, 2, 0.5, np.zeros(2, np.int32))
+    gpu = _solve(fsb, w)
+    acc = oracle.accumulate(g, cams, masks, 2)
+    _check(gpu, acc, 0.5)
+    assert acc.table.sum() > 0
+
+
+def test_scene_validation(fsb):
+    bad = {"mean": np.zeros((2, 3), np.float32), "quat": np.zeros((2, 4), np.float32),
+           "scale": np.ones((2, 3), np.float32), "opacity": np.ones(2, np.float32)}
+    with pytest.raises(fsb.FlashSplatError) as ei:
+        fsb.Solver(bad)
+    assert ei.value.status == fsb.FS_INVALID_ARGUMENT

@@ -398,10 +398,12 @@ def test_special_masks(tiny):
 
 
 def test_risk_bounds_are_local(tiny):
-    """The near-threshold bookkeeping stays small: most Gaussians carry no
-    risk, and the rest carry little relative to their contributions."""
+    """The near-threshold bookkeeping stays small relative to the
+    contributions, so the parity comparison stays tight for almost every
+    Gaussian."""
     acc = oracle.accumulate(tiny.gaussians, tiny.cams, tiny.masks, tiny.E)
     s = acc.table.sum(1)
     r = acc.risk.sum(1)
-    assert (r > 0).mean() < 0.5
-    assert np.median(r[r > 0] / s[r > 0]) < 1e-4
+    rel = r[s > 0] / s[s > 0]
+    assert np.median(rel) < 1e-5
+    assert (rel > 1e-3).mean() < 0.01
