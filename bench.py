@@ -167,7 +167,7 @@ def run_flashsplat(args, rank, world, local_rank):
         torch.distributed.barrier()
     clocks = ClockSampler(uuid)
     torch.cuda.synchronize(dev)
-    ms_steps, blend_ms, pairs, launches, blend_launches, entries = [], 0.0, 0, 0, 0, 0
+    ms_steps, blend_ms, pairs, launches, blend_launches, entries, staged = [], 0.0, 0, 0, 0, 0, 0
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
         flush.fill_(1)                       # evict the previous step's data from L2
@@ -182,6 +182,7 @@ def run_flashsplat(args, rank, world, local_rank):
         blend_launches += st.blend_launches
         pairs += st.pairs
         entries += st.list_entries
+        staged += st.staged_entries
         launches += st.kernel_launches
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter() - t_wall0
@@ -252,6 +253,7 @@ def run_flashsplat(args, rank, world, local_rank):
                 "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_clk:.0f} MHz",
                 "pairs_per_step": pairs // max(1, args.steps),
                 "list_entries_per_step": entries // max(1, args.steps),
+                "staged_entries_per_step": staged // max(1, args.steps),
                 "flops_per_pair": FLOPS_PER_PAIR,
                 "blend_ms_per_step": blend_ms / args.steps,
                 "blend_share_of_step": blend_ms / max(total_ms, 1e-9),

@@ -76,7 +76,8 @@ typedef struct fs_scene fs_scene;
 typedef struct fs_options {
   int32_t views_per_batch;  /* views binned and blended per launch group (default 8) */
   int32_t time_stages;      /* non-zero: time every blend launch with CUDA events */
-  int32_t reserved[14];
+  int32_t depth_chunks;     /* front-to-back binning chunks per batch (default 6, 1 = off) */
+  int32_t reserved[13];
 } fs_options;
 
 /* A Gaussian scene (Sec. 3.1: G_i = {m_i, q_i, s_i, o_i}; colour unused). */
@@ -110,6 +111,8 @@ typedef struct fs_stats {
   int64_t kernel_launches; /* kernels launched by the library */
   double blend_ms;         /* summed blend time (fs_options.time_stages), else 0 */
   int64_t blend_launches;  /* blend launches timed */
+  int64_t staged_entries;  /* list entries the blend staged before its tiles saturated */
+  int64_t reserved[3];
 } fs_stats;
 
 /* Outputs of fs_solve.  Any pointer may be NULL to skip that output. */

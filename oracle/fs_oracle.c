@@ -55,12 +55,15 @@
  * windows are set an order of magnitude wider than that. */
 #define FSO_EVENT_REL 1e-4
 #define FSO_T_EVENT_REL 1e-4
-#define FSO_DEPTH_TIE_REL 1e-6
+/* Depths are view-space z in double precision; two Gaussians whose depths
+ * agree to 1e-12 relative may be ordered either way by an implementation that
+ * computes z with other rounding. */
+#define FSO_DEPTH_TIE_REL 1e-12
 
 /* flag bits per Gaussian */
 #define FSO_FLAG_ALPHA_EDGE 1u   /* alpha within 1e-4 rel. of 1/255 */
 #define FSO_FLAG_T_EDGE 2u       /* T(1-alpha) within 1e-4 rel. of 1e-4 */
-#define FSO_FLAG_DEPTH_TIE 4u    /* depth within 1e-6 rel. of a neighbour */
+#define FSO_FLAG_DEPTH_TIE 4u    /* depth within 1e-12 rel. of a neighbour */
 #define FSO_FLAG_DOWNSTREAM 8u   /* after an event in the same pixel */
 
 typedef struct {

@@ -157,12 +157,13 @@ int64_t radix_launches(int64_t n, int bits) {
 struct fs_ctx {
   int device = 0;
   int views_per_batch = 8;
+  int depth_chunks = 6;  // front-to-back chunks per batch (sizes 1/32 .. 1/2 of the batch)
   int n_sm = 0;
   bool time_stages = false;
   std::vector<cudaEvent_t> events;  // (start, stop) pairs around blend launches
   size_t events_used = 0;
   // workspace
-  DevBuf views, rec, rect, cnt, key_a, val_a, key_b, val_b, offs;
+  DevBuf views, rec, foot, cnt, key_a, val_a, key_b, val_b, offs, ccnt, dlo, state, sat;
   DevBuf lk_a, lv_a, lk_b, lv_b, ranges, sort_tmp, scan_tmp, total, counters;
   DevBuf mask_stage, table_tmp, bits_tmp, label_tmp, margin_tmp;
   HostBuf views_host, total_host, counters_host;
@@ -173,7 +174,7 @@ struct fs_ctx {
 struct fs_scene {
   fs_ctx* ctx = nullptr;
   int64_t n = 0;
-  DevBuf pos_op, quat, scale;
+  DevBuf pos_op, cov;  // (m, o) and Sigma3D as float pairs
 };
 
 extern "C" {
@@ -202,6 +203,7 @@ fs_status fs_create(fs_ctx** out, int32_t device, const fs_options* opt) {
   if (opt && opt->views_per_batch > 0)
     c->views_per_batch = std::min(opt->views_per_batch, fs::kMaxViewsPerBatch);
   c->time_stages = opt && opt->time_stages;
+  if (opt && opt->depth_chunks > 0) c->depth_chunks = std::min(opt->depth_chunks, 16);
   DeviceGuard g(device);
   fs_status st;
   if ((st = c->views.ensure(sizeof(fs::ViewParams) * fs::kMaxViewsPerBatch, "views")) != FS_OK ||
@@ -224,7 +226,7 @@ fs_status fs_destroy(fs_ctx* c) {
     return fail(FS_INVALID_ARGUMENT, "fs_destroy: %d scene(s) still alive", c->scenes);
   DeviceGuard g(c->device);
   cudaDeviceSynchronize();
-  DevBuf* bufs[] = {&c->views, &c->rec, &c->rect, &c->cnt, &c->key_a, &c->val_a, &c->key_b,
+  DevBuf* bufs[] = {&c->ccnt, &c->dlo, &c->state, &c->sat, &c->views, &c->rec, &c->foot, &c->cnt, &c->key_a, &c->val_a, &c->key_b,
                     &c->val_b, &c->offs, &c->lk_a, &c->lv_a, &c->lk_b, &c->lv_b, &c->ranges,
                     &c->sort_tmp, &c->scan_tmp, &c->total, &c->counters, &c->mask_stage,
                     &c->table_tmp, &c->bits_tmp, &c->label_tmp, &c->margin_tmp};
@@ -259,9 +261,8 @@ fs_status fs_scene_create(fs_ctx* c, const fs_gaussians* g, fs_scene** out) {
   const size_t nn = static_cast<size_t>(n > 0 ? n : 1);
   fs_status st;
   if ((st = s->pos_op.ensure(nn * 16, "scene")) != FS_OK ||
-      (st = s->quat.ensure(nn * 16, "scene")) != FS_OK ||
-      (st = s->scale.ensure(nn * 16, "scene")) != FS_OK) {
-    s->pos_op.release(); s->quat.release(); s->scale.release();
+      (st = s->cov.ensure(nn * 48, "scene")) != FS_OK) {
+    s->pos_op.release(); s->cov.release();
     delete s;
     return st;
   }
@@ -274,7 +275,7 @@ fs_status fs_scene_create(fs_ctx* c, const fs_gaussians* g, fs_scene** out) {
   if (n > 0 && g->memory == FS_MEM_HOST) {
     st = stage.ensure(b_mean + b_quat + b_scale + b_op + 64 * 4, "scene staging");
     if (st != FS_OK) {
-      s->pos_op.release(); s->quat.release(); s->scale.release();
+      s->pos_op.release(); s->cov.release();
       delete s;
       return st;
     }
@@ -292,17 +293,17 @@ fs_status fs_scene_create(fs_ctx* c, const fs_gaussians* g, fs_scene** out) {
   if (e == cudaSuccess)
     e = fs::launch_scene_prep(n, static_cast<const float*>(dm), dq, g->quat_dtype, ds,
                               g->scale_dtype, dop, g->opacity_dtype, s->pos_op.as<float4>(),
-                              s->quat.as<float4>(), s->scale.as<float4>(), d_err, nullptr);
+                              s->cov.as<float4>(), d_err, nullptr);
   unsigned int h_err = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&h_err, d_err, sizeof(h_err), cudaMemcpyDeviceToHost);
   stage.release();
   if (e != cudaSuccess) {
-    s->pos_op.release(); s->quat.release(); s->scale.release();
+    s->pos_op.release(); s->cov.release();
     delete s;
     return cuda_fail(e, "fs_scene_create");
   }
   if (h_err) {
-    s->pos_op.release(); s->quat.release(); s->scale.release();
+    s->pos_op.release(); s->cov.release();
     delete s;
     return fail(FS_INVALID_ARGUMENT,
                 "fs_scene_create: a Gaussian has a zero quaternion or a non-finite attribute");
@@ -317,8 +318,7 @@ fs_status fs_scene_destroy(fs_scene* s) {
   DeviceGuard g(s->ctx->device);
   cudaDeviceSynchronize();
   s->pos_op.release();
-  s->quat.release();
-  s->scale.release();
+  s->cov.release();
   s->ctx->scenes--;
   delete s;
   return FS_OK;
@@ -360,8 +360,8 @@ void fill_view(const fs_camera& cam, fs::ViewParams* vp) {
   split(cam.cx, &vp->cx_hi, &vp->cx_lo);
   split(cam.cy, &vp->cy_hi, &vp->cy_lo);
   split(0.2, &vp->near_hi, &vp->near_lo);
-  vp->limx = static_cast<float>(1.3 * (0.5 * cam.width / cam.fx));
-  vp->limy = static_cast<float>(1.3 * (0.5 * cam.height / cam.fy));
+  split(1.3 * (0.5 * cam.width / cam.fx), &vp->limx_hi, &vp->limx_lo);
+  split(1.3 * (0.5 * cam.height / cam.fy), &vp->limy_hi, &vp->limy_lo);
   vp->width = cam.width;
   vp->height = cam.height;
   vp->tiles_x = (cam.width + fs::kTile - 1) / fs::kTile;
@@ -381,7 +381,7 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
   const size_t msize = dtype_size(mask_dtype);
   const int64_t kcap = static_cast<int64_t>(vb) * n;
   FS_TRY(c->rec.ensure(static_cast<size_t>(kcap) * sizeof(fs::ProjRecord), "records"));
-  FS_TRY(c->rect.ensure(static_cast<size_t>(kcap) * 8, "rects"));
+  FS_TRY(c->foot.ensure(static_cast<size_t>(kcap) * sizeof(fs::Footprint), "footprints"));
   FS_TRY(c->cnt.ensure(static_cast<size_t>(kcap) * 4, "counts"));
   FS_TRY(c->key_a.ensure(static_cast<size_t>(kcap) * 4, "keys"));
   FS_TRY(c->val_a.ensure(static_cast<size_t>(kcap) * 4, "vals"));
@@ -391,11 +391,16 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
   FS_TRY(c->scan_tmp.ensure(fs::scan_temp_bytes(kcap), "scan temp"));
   FS_TRY(c->sort_tmp.ensure(fs::radix_temp_bytes(kcap), "sort temp"));
 
+  FS_TRY(c->ccnt.ensure(static_cast<size_t>(kcap) * 4, "chunk counts"));
+  FS_TRY(c->dlo.ensure(static_cast<size_t>(kcap) * 4, "depth low words"));
+
   fs::ViewParams* vh = c->views_host.as<fs::ViewParams>();
   uint32_t* total_h = c->total_host.as<uint32_t>();
+  unsigned long long* ctr = c->counters.as<unsigned long long>();
   for (int32_t v0 = 0; v0 < V; v0 += vb) {
     const int nb = std::min(vb, V - v0);
     int tile_base = 0, max_tiles = 0;
+    int64_t state_off = 0;
     size_t stage_bytes = 0;
     for (int k = 0; k < nb; ++k) {
       const fs_camera& cam = cams[v0 + k];
@@ -407,10 +412,13 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
       const fs_camera& cam = cams[v0 + k];
       fill_view(cam, &vh[k]);
       vh[k].tile_base = tile_base;
+      vh[k].state_off = state_off;
       const int nt = vh[k].tiles_x * vh[k].tiles_y;
       tile_base += nt;
       max_tiles = std::max(max_tiles, nt);
-      const size_t mbytes = static_cast<size_t>(cam.width) * cam.height * msize;
+      const size_t npix = static_cast<size_t>(cam.width) * cam.height;
+      state_off += static_cast<int64_t>(npix);
+      const size_t mbytes = npix * msize;
       if (mask_memory == FS_MEM_DEVICE) {
         vh[k].mask = masks[v0 + k];
       } else {
@@ -422,77 +430,106 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
       }
     }
     const int total_tiles = tile_base;
+    const int tile_bits = std::max(1, ceil_log2(total_tiles));
     const int64_t k_total = static_cast<int64_t>(nb) * n;
+    FS_TRY(c->state.ensure(static_cast<size_t>(state_off) * 4, "pixel state"));
+    FS_TRY(c->sat.ensure(static_cast<size_t>(total_tiles), "tile flags"));
+    FS_TRY(c->ranges.ensure(static_cast<size_t>(total_tiles) * 8, "tile ranges"));
     fs::ViewParams* vd = c->views.as<fs::ViewParams>();
+    float* state = c->state.as<float>();
+    uint8_t* sat = c->sat.as<uint8_t>();
     FS_CUDA(cudaMemcpyAsync(vd, vh, sizeof(fs::ViewParams) * nb, cudaMemcpyHostToDevice, stream),
             "view upload");
-    c->stats.kernel_launches += 1 + radix_launches(k_total, 32) + scan_launches(k_total);
-    FS_CUDA(fs::launch_project(n, nb, vd, s->pos_op.as<float4>(), s->quat.as<float4>(),
-                               s->scale.as<float4>(), c->rec.as<fs::ProjRecord>(),
-                               c->rect.as<uint2>(), c->cnt.as<uint32_t>(), c->key_a.as<uint32_t>(),
-                               c->val_a.as<uint32_t>(), stream),
+
+    // project every Gaussian into the batch's views, sort by depth
+    c->stats.kernel_launches += 3 + radix_launches(k_total, 32);
+    FS_CUDA(fs::launch_project(n, nb, vd, s->pos_op.as<float4>(), s->cov.as<float4>(),
+                               c->rec.as<fs::ProjRecord>(), c->foot.as<fs::Footprint>(),
+                               c->cnt.as<uint32_t>(), c->key_a.as<uint32_t>(),
+                               c->val_a.as<uint32_t>(), c->dlo.as<uint32_t>(), stream),
             "project");
     bool alt = false;
     FS_CUDA(fs::radix_sort_pairs(c->key_a.as<uint32_t>(), c->val_a.as<uint32_t>(),
                                  c->key_b.as<uint32_t>(), c->val_b.as<uint32_t>(), k_total, 32,
                                  c->sort_tmp.p, &alt, stream),
             "depth sort");
-    const uint32_t* sorted_val = alt ? c->val_b.as<uint32_t>() : c->val_a.as<uint32_t>();
-    uint32_t* total_d = c->total.as<uint32_t>();
-    FS_CUDA(fs::exclusive_scan(c->cnt.as<uint32_t>(), sorted_val, c->offs.as<uint32_t>(), k_total,
-                               total_d, c->scan_tmp.p, stream),
-            "count scan");
-    FS_CUDA(cudaMemcpyAsync(total_h, total_d, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream),
-            "count readback");
-    FS_CUDA(cudaStreamSynchronize(stream), "count readback");
-    const int64_t I = *total_h;
-    if (I >= (static_cast<int64_t>(1) << 31))
-      return fail(FS_UNSUPPORTED, "fs_accumulate: %lld list entries in one batch; use fewer "
-                  "views per batch", (long long)I);
-    c->stats.list_entries += I;
+    uint32_t* sorted_key = alt ? c->key_b.as<uint32_t>() : c->key_a.as<uint32_t>();
+    uint32_t* sorted_val = alt ? c->val_b.as<uint32_t>() : c->val_a.as<uint32_t>();
+    FS_CUDA(fs::launch_depth_tie_fix(k_total, sorted_key, sorted_val, c->dlo.as<uint32_t>(),
+                                     stream),
+            "depth ties");
+    FS_CUDA(fs::launch_state_init(vd, nb, max_tiles, E, mask_dtype, state, sat, ctr, stream),
+            "pixel state");
     c->stats.views += nb;
-    for (int k = 0; k < nb; ++k)
-      c->stats.pixels += static_cast<int64_t>(cams[v0 + k].width) * cams[v0 + k].height;
-    if (I == 0) continue;
-    FS_TRY(c->lk_a.ensure(static_cast<size_t>(I) * 4, "list keys"));
-    FS_TRY(c->lv_a.ensure(static_cast<size_t>(I) * 4, "list values"));
-    FS_TRY(c->lk_b.ensure(static_cast<size_t>(I) * 4, "list keys"));
-    FS_TRY(c->lv_b.ensure(static_cast<size_t>(I) * 4, "list values"));
-    FS_TRY(c->sort_tmp.ensure(fs::radix_temp_bytes(std::max<int64_t>(I, kcap)), "sort temp"));
-    FS_TRY(c->ranges.ensure(static_cast<size_t>(total_tiles) * 8, "tile ranges"));
-    const int tile_bits = std::max(1, ceil_log2(total_tiles));
-    c->stats.kernel_launches += 3 + radix_launches(I, tile_bits);
-    FS_CUDA(fs::launch_emit(k_total, n, vd, sorted_val, c->offs.as<uint32_t>(),
-                            c->cnt.as<uint32_t>(), c->rect.as<uint2>(), c->lk_a.as<uint32_t>(),
-                            c->lv_a.as<uint32_t>(), stream),
-            "emit");
-    bool alt2 = false;
-    FS_CUDA(fs::radix_sort_pairs(c->lk_a.as<uint32_t>(), c->lv_a.as<uint32_t>(),
-                                 c->lk_b.as<uint32_t>(), c->lv_b.as<uint32_t>(), I, tile_bits,
-                                 c->sort_tmp.p, &alt2, stream),
-            "tile sort");
-    const uint32_t* lkey = alt2 ? c->lk_b.as<uint32_t>() : c->lk_a.as<uint32_t>();
-    const uint32_t* lval = alt2 ? c->lv_b.as<uint32_t>() : c->lv_a.as<uint32_t>();
-    FS_CUDA(cudaMemsetAsync(c->ranges.p, 0, static_cast<size_t>(total_tiles) * 8, stream),
-            "ranges clear");
-    FS_CUDA(fs::launch_ranges(I, lkey, c->ranges.as<uint2>(), stream), "ranges");
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    if (c->time_stages) {
-      while (c->events.size() < c->events_used + 2) {
-        cudaEvent_t e;
-        FS_CUDA(cudaEventCreate(&e), "cudaEventCreate");
-        c->events.push_back(e);
+    c->stats.pixels += state_off;
+
+    // front-to-back depth chunks: a chunk lists only tiles not yet saturated
+    const int chunks = std::max(1, c->depth_chunks);
+    int64_t p0 = 0;
+    for (int ci = 0; ci < chunks; ++ci) {
+      const int64_t p1 = (ci == chunks - 1) ? k_total : (k_total >> (chunks - 1 - ci));
+      const int64_t n_pos = p1 - p0;
+      if (n_pos <= 0) continue;
+      uint32_t* total_d = c->total.as<uint32_t>();
+      c->stats.kernel_launches += 1 + scan_launches(n_pos);
+      FS_CUDA(fs::launch_chunk_count(p0, n_pos, n, vd, sorted_val, c->cnt.as<uint32_t>(),
+                                     c->foot.as<fs::Footprint>(), sat, c->ccnt.as<uint32_t>(),
+                                     stream),
+              "chunk count");
+      FS_CUDA(fs::exclusive_scan(c->ccnt.as<uint32_t>(), nullptr, c->offs.as<uint32_t>(), n_pos,
+                                 total_d, c->scan_tmp.p, stream),
+              "count scan");
+      FS_CUDA(cudaMemcpyAsync(total_h, total_d, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream),
+              "count readback");
+      FS_CUDA(cudaStreamSynchronize(stream), "count readback");
+      const int64_t I = *total_h;
+      if (I >= (static_cast<int64_t>(1) << 31))
+        return fail(FS_UNSUPPORTED, "fs_accumulate: %lld list entries in one chunk; use fewer "
+                    "views per batch", (long long)I);
+      c->stats.list_entries += I;
+      if (I == 0) {
+        p0 = p1;
+        continue;
       }
-      ev0 = c->events[c->events_used];
-      ev1 = c->events[c->events_used + 1];
-      c->events_used += 2;
-      FS_CUDA(cudaEventRecord(ev0, stream), "cudaEventRecord");
+      FS_TRY(c->lk_a.ensure(static_cast<size_t>(I) * 4, "list keys"));
+      FS_TRY(c->lv_a.ensure(static_cast<size_t>(I) * 4, "list values"));
+      FS_TRY(c->lk_b.ensure(static_cast<size_t>(I) * 4, "list keys"));
+      FS_TRY(c->lv_b.ensure(static_cast<size_t>(I) * 4, "list values"));
+      FS_TRY(c->sort_tmp.ensure(fs::radix_temp_bytes(std::max<int64_t>(I, kcap)), "sort temp"));
+      c->stats.kernel_launches += 3 + radix_launches(I, tile_bits);
+      FS_CUDA(fs::launch_emit(p0, n_pos, n, vd, sorted_val, c->offs.as<uint32_t>(),
+                              c->ccnt.as<uint32_t>(), c->foot.as<fs::Footprint>(), sat,
+                              c->lk_a.as<uint32_t>(), c->lv_a.as<uint32_t>(), ctr, stream),
+              "emit");
+      bool alt2 = false;
+      FS_CUDA(fs::radix_sort_pairs(c->lk_a.as<uint32_t>(), c->lv_a.as<uint32_t>(),
+                                   c->lk_b.as<uint32_t>(), c->lv_b.as<uint32_t>(), I, tile_bits,
+                                   c->sort_tmp.p, &alt2, stream),
+              "tile sort");
+      const uint32_t* lkey = alt2 ? c->lk_b.as<uint32_t>() : c->lk_a.as<uint32_t>();
+      const uint32_t* lval = alt2 ? c->lv_b.as<uint32_t>() : c->lv_a.as<uint32_t>();
+      FS_CUDA(cudaMemsetAsync(c->ranges.p, 0, static_cast<size_t>(total_tiles) * 8, stream),
+              "ranges clear");
+      FS_CUDA(fs::launch_ranges(I, lkey, c->ranges.as<uint2>(), stream), "ranges");
+      cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+      if (c->time_stages) {
+        while (c->events.size() < c->events_used + 2) {
+          cudaEvent_t e;
+          FS_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+          c->events.push_back(e);
+        }
+        ev0 = c->events[c->events_used];
+        ev1 = c->events[c->events_used + 1];
+        c->events_used += 2;
+        FS_CUDA(cudaEventRecord(ev0, stream), "cudaEventRecord");
+      }
+      FS_CUDA(fs::launch_blend(vd, nb, max_tiles, c->ranges.as<uint2>(), lval,
+                               c->rec.as<fs::ProjRecord>(), n, E, mask_dtype, table, table_dtype,
+                               state, sat, ctr, stream),
+              "blend");
+      if (ev1) FS_CUDA(cudaEventRecord(ev1, stream), "cudaEventRecord");
+      p0 = p1;
     }
-    FS_CUDA(fs::launch_blend(vd, nb, max_tiles, c->ranges.as<uint2>(), lval,
-                             c->rec.as<fs::ProjRecord>(), n, E, mask_dtype, table, table_dtype,
-                             c->counters.as<unsigned long long>(), stream),
-            "blend");
-    if (ev1) FS_CUDA(cudaEventRecord(ev1, stream), "cudaEventRecord");
   }
   return FS_OK;
 }
@@ -621,6 +658,10 @@ fs_status fs_synchronize(fs_ctx* c, void* stream, fs_stats* stats) {
   FS_CUDA(cudaGetLastError(), "fs_synchronize");
   c->stats.bad_labels = static_cast<int64_t>(ch[fs::kBadLabels]);
   c->stats.pairs = static_cast<int64_t>(ch[fs::kPairs]);
+  c->stats.staged_entries = static_cast<int64_t>(ch[fs::kStaged]);
+  if (ch[fs::kBinningMismatch])
+    return fail(FS_CUDA_ERROR, "internal error: tile binning count and emission disagreed for "
+                "%llu Gaussian(s)", ch[fs::kBinningMismatch]);
   double ms = 0.0;
   for (size_t k = 0; k + 1 < c->events_used; k += 2) {
     float t = 0.f;

@@ -80,11 +80,42 @@ __device__ __forceinline__ void table_add(TableT* p, float v) {
   atomicAdd(p, static_cast<TableT>(v));
 }
 
+// Per-pixel state of a batch before its first depth chunk: T = 1 for pixels
+// with a label in [0, E), 0 ("stopped") for the others; a tile with no
+// labelled pixel starts saturated.  Counts the pixels with bad labels.
+template <typename LabelT>
+__global__ void __launch_bounds__(kBlendThreads) state_init_kernel(
+    const ViewParams* __restrict__ views, int E, float* __restrict__ state,
+    uint8_t* __restrict__ sat, unsigned long long* __restrict__ counters) {
+  const int v = blockIdx.y;
+  const int tiles_x = views[v].tiles_x;
+  const int tile = blockIdx.x;
+  if (tile >= tiles_x * views[v].tiles_y) return;  // whole block
+  const int W = views[v].width, H = views[v].height;
+  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  const int px = tx * kTile + (threadIdx.x & 15), py = ty * kTile + (threadIdx.x >> 4);
+  const bool inside = px < W && py < H;
+  bool valid = false;
+  if (inside) {
+    const int64_t p = static_cast<int64_t>(py) * W + px;
+    const int label = static_cast<int>(static_cast<const LabelT*>(views[v].mask)[p]);
+    valid = label >= 0 && label < E;
+    state[views[v].state_off + p] = valid ? 1.f : 0.f;
+  }
+  const int n_bad = __syncthreads_count(inside && !valid);
+  const int any = __syncthreads_or(valid);
+  if (threadIdx.x == 0) {
+    if (n_bad) atomicAdd(&counters[kBadLabels], static_cast<unsigned long long>(n_bad));
+    sat[views[v].tile_base + tile] = any ? 0 : 1;
+  }
+}
+
 template <typename LabelT, typename TableT>
 __global__ void __launch_bounds__(kBlendThreads, 4) blend_kernel(
     const ViewParams* __restrict__ views, const uint2* __restrict__ ranges,
     const uint32_t* __restrict__ list_val, const ProjRecord* __restrict__ rec, int64_t n, int E,
-    TableT* __restrict__ table, unsigned long long* __restrict__ counters) {
+    TableT* __restrict__ table, float* __restrict__ state, uint8_t* __restrict__ sat,
+    unsigned long long* __restrict__ counters) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlendSmem& S = *reinterpret_cast<BlendSmem*>(smem_raw);
 
@@ -109,9 +140,8 @@ __global__ void __launch_bounds__(kBlendThreads, 4) blend_kernel(
     if (inside) label = static_cast<int>(mask[static_cast<int64_t>(py) * W + px]);
     valid = inside && label >= 0 && label < E;
   }
-  const int n_bad = __syncthreads_count(inside && !valid);
-  if (tid == 0 && n_bad) atomicAdd(&counters[kBadLabels], static_cast<unsigned long long>(n_bad));
-  if (rg.y <= rg.x) return;  // no Gaussian touches this tile: whole block
+  (void)inside;
+  if (rg.y <= rg.x) return;  // no list entry for this tile in this chunk: whole block
 
   // ---- assign pixels to threads in label order ------------------------
   if (tid == 0) S.label0 = label;
@@ -142,8 +172,9 @@ __global__ void __launch_bounds__(kBlendThreads, 4) blend_kernel(
   const int pix = key & 255;
   const int lab = key >> 8;
   valid = lab != kNoLabel;
-  const float xl = static_cast<float>(pix & 15) + 0.5f;
-  const float yl = static_cast<float>(pix >> 4) + 0.5f;
+  // pixel centre relative to the tile centre, in [-7.5, 7.5]
+  const float xl = static_cast<float>(pix & 15) - 7.5f;
+  const float yl = static_cast<float>(pix >> 4) - 7.5f;
 
   // ---- label slots of the tile (distinct labels, in order) -------------
   const int prev_lab = tid > 0 ? (S.sortkey[tid - 1] >> 8) : -1;
@@ -164,22 +195,33 @@ __global__ void __launch_bounds__(kBlendThreads, 4) blend_kernel(
   __syncthreads();
 
   // ---- walk the tile's list front to back ------------------------------
-  float T = 1.f;
-  bool done = !valid;
+  // T resumes from the previous depth chunk; T == 0 marks a stopped pixel.
+  const int64_t spix = views[v].state_off +
+                       static_cast<int64_t>(ty * kTile + (pix >> 4)) * W + tx * kTile + (pix & 15);
+  float T = valid ? state[spix] : 0.f;
+  bool done = !(T > 0.f);
   uint32_t n_eval = 0;  // pairs this thread evaluated
-  const float ox = static_cast<float>(tx * kTile), oy = static_cast<float>(ty * kTile);
+  const float ox = static_cast<float>(tx * kTile + 8), oy = static_cast<float>(ty * kTile + 8);
+  uint32_t n_staged = 0;  // list entries staged by this block (thread 0 counts)
   const uint32_t gbase = static_cast<uint32_t>(static_cast<int64_t>(v) * n);
   float* const row = &S.buf[warp][lane][0];
 
   for (uint32_t base = rg.x; base < rg.y; base += kBatch) {
     if (__syncthreads_count(!done) == 0) break;
     const int nin = static_cast<int>(min(static_cast<uint32_t>(kBatch), rg.y - base));
+    n_staged += static_cast<uint32_t>(nin);
     if (tid < nin) {
+      // b = W o + c for the tile centre o, with W = W_hi + W_lo and c as float
+      // pairs: W_hi o exactly (TwoProduct), W_lo o in FP32 (a 2^-24 correction)
       const uint32_t g = list_val[base + tid];
       const ProjRecord r = rec[g];
-      const f2 b0 = f2_add(f2_add(two_prod(r.w.x, ox), two_prod(r.w.y, oy)), f2{r.c.x, r.c.z});
-      const f2 b1 = f2_add(f2_add(two_prod(r.w.z, ox), two_prod(r.w.w, oy)), f2{r.c.y, r.c.w});
-      S.w[tid] = r.w;
+      f2 b0 = f2_add(two_prod(r.w_hi.x, ox), two_prod(r.w_hi.y, oy));
+      f2 b1 = f2_add(two_prod(r.w_hi.z, ox), two_prod(r.w_hi.w, oy));
+      b0 = f2_add(b0, f2{r.c.x, r.c.z});
+      b1 = f2_add(b1, f2{r.c.y, r.c.w});
+      b0 = f2_add(b0, f2_from(fmaf(r.w_lo.x, ox, r.w_lo.y * oy)));
+      b1 = f2_add(b1, f2_from(fmaf(r.w_lo.z, ox, r.w_lo.w * oy)));
+      S.w[tid] = r.w_hi;
       S.bo[tid] = make_float4(b0.hi + b0.lo, b1.hi + b1.lo, r.misc.x, 0.f);
       S.gid[tid] = static_cast<int32_t>(g - gbase);
     }
@@ -265,15 +307,20 @@ __global__ void __launch_bounds__(kBlendThreads, 4) blend_kernel(
       }
     }
   }
+  if (valid) state[spix] = done ? 0.f : T;
+  const int all_done = __syncthreads_and(done);
+  if (tid == 0 && all_done) sat[views[v].tile_base + tile] = 1;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) n_eval += __shfl_xor_sync(0xffffffffu, n_eval, o);
   if (lane == 0 && n_eval) atomicAdd(&counters[kPairs], static_cast<unsigned long long>(n_eval));
+  if (tid == 0 && n_staged) atomicAdd(&counters[kStaged], static_cast<unsigned long long>(n_staged));
 }
 
 template <typename LabelT, typename TableT>
 cudaError_t launch_typed(const ViewParams* views, int n_views, int max_tiles, const uint2* ranges,
                          const uint32_t* list_val, const ProjRecord* rec, int64_t n, int E,
-                         void* table, unsigned long long* counters, cudaStream_t stream) {
+                         void* table, float* state, uint8_t* sat, unsigned long long* counters,
+                         cudaStream_t stream) {
   const size_t smem = sizeof(BlendSmem);
   cudaError_t e = cudaFuncSetAttribute(blend_kernel<LabelT, TableT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -281,29 +328,43 @@ cudaError_t launch_typed(const ViewParams* views, int n_views, int max_tiles, co
   if (e != cudaSuccess) return e;
   dim3 grid(static_cast<unsigned>(max_tiles), static_cast<unsigned>(n_views));
   blend_kernel<LabelT, TableT><<<grid, kBlendThreads, smem, stream>>>(
-      views, ranges, list_val, rec, n, E, static_cast<TableT*>(table), counters);
+      views, ranges, list_val, rec, n, E, static_cast<TableT*>(table), state, sat, counters);
   return cudaGetLastError();
 }
 
 }  // namespace
 
+cudaError_t launch_state_init(const ViewParams* views, int n_views, int max_tiles_per_view, int E,
+                              int mask_dtype, float* state, uint8_t* sat,
+                              unsigned long long* counters, cudaStream_t stream) {
+  if (n_views == 0 || max_tiles_per_view == 0) return cudaSuccess;
+  dim3 grid(static_cast<unsigned>(max_tiles_per_view), static_cast<unsigned>(n_views));
+  if (mask_dtype == 4)
+    state_init_kernel<uint8_t><<<grid, kBlendThreads, 0, stream>>>(views, E, state, sat, counters);
+  else
+    state_init_kernel<int32_t><<<grid, kBlendThreads, 0, stream>>>(views, E, state, sat, counters);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_blend(const ViewParams* views, int n_views, int max_tiles_per_view,
                          const uint2* ranges, const uint32_t* list_val, const ProjRecord* rec,
                          int64_t n, int E, int mask_dtype, void* table, int table_dtype,
-                         unsigned long long* counters, cudaStream_t stream) {
+                         float* state, uint8_t* sat, unsigned long long* counters,
+                         cudaStream_t stream) {
   if (n_views == 0 || max_tiles_per_view == 0) return cudaSuccess;
+  const int mt = max_tiles_per_view;
   if (mask_dtype == 4) {
     if (table_dtype == 0)
-      return launch_typed<uint8_t, float>(views, n_views, max_tiles_per_view, ranges, list_val, rec,
-                                          n, E, table, counters, stream);
-    return launch_typed<uint8_t, double>(views, n_views, max_tiles_per_view, ranges, list_val, rec,
-                                         n, E, table, counters, stream);
+      return launch_typed<uint8_t, float>(views, n_views, mt, ranges, list_val, rec, n, E, table,
+                                          state, sat, counters, stream);
+    return launch_typed<uint8_t, double>(views, n_views, mt, ranges, list_val, rec, n, E, table,
+                                         state, sat, counters, stream);
   }
   if (table_dtype == 0)
-    return launch_typed<int32_t, float>(views, n_views, max_tiles_per_view, ranges, list_val, rec, n,
-                                        E, table, counters, stream);
-  return launch_typed<int32_t, double>(views, n_views, max_tiles_per_view, ranges, list_val, rec, n,
-                                       E, table, counters, stream);
+    return launch_typed<int32_t, float>(views, n_views, mt, ranges, list_val, rec, n, E, table,
+                                        state, sat, counters, stream);
+  return launch_typed<int32_t, double>(views, n_views, mt, ranges, list_val, rec, n, E, table,
+                                       state, sat, counters, stream);
 }
 
 }  // namespace fs

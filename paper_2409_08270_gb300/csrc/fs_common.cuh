@@ -27,24 +27,39 @@ struct ViewParams {
   float t_hi[3], t_lo[3];
   float fx_hi, fx_lo, fy_hi, fy_lo, cx_hi, cx_lo, cy_hi, cy_lo;
   float near_hi, near_lo;      // near plane 0.2 as a float pair
-  float limx, limy;            // 1.3 * tan(half field of view) per axis
+  float limx_hi, limx_lo;      // 1.3 * tan(half field of view), x
+  float limy_hi, limy_lo;      // 1.3 * tan(half field of view), y
   int32_t width, height;
   int32_t tiles_x, tiles_y;
   int32_t tile_base;           // first tile id of this view in the batch
   int32_t pad0;
+  int64_t state_off;           // first pixel of this view in the batch's pixel state
   const void* mask;            // device pointer to the view's labels
 };
 
-// Projected record of one (view, Gaussian): 3 x float4 = 48 B.
-//   r0 = W (row-major 2x2 whitening, FP32)
-//   r1 = (c0_hi, c1_hi, c0_lo, c1_lo) with c = -W m2D as float pairs
-//   r2 = (opacity, 0, 0, 0)
-// For a tile with integer origin o the blend uses b = W o + c, evaluated in
-// float-pair arithmetic, and w = W p_local + b for p_local in the tile.
+// Projected record of one (view, Gaussian): 4 x float4 = 64 B.
+//   w_hi, w_lo = whitening matrix W (row-major 2x2) as float pairs, with
+//                |W d|^2 = 0.5 log2(e) d^T Sigma2D^-1 d
+//   c          = (c0_hi, c1_hi, c0_lo, c1_lo), c = -W m2D as float pairs
+//   misc       = (opacity, -, -, -)
+// For a tile whose centre is o the blend forms b = W o + c (float pairs) and
+// evaluates w = W_hi (p - o) + b for the pixel centre p, |p - o| <= 7.5 px.
 struct alignas(16) ProjRecord {
-  float4 w;
+  float4 w_hi;
+  float4 w_lo;
   float4 c;
   float4 misc;
+};
+
+// Footprint of one (view, Gaussian) for the tile binning: the alpha >= 1/255
+// ellipse {d : d^T Sigma2D^-1 d <= r2} around the projected mean, in FP32
+// (the binning is conservative: it widens r2 and adds a pixel of margin).
+struct alignas(16) Footprint {
+  float mx, my;            // projected mean (pixels)
+  float sxx, sxy, syy;     // Sigma2D
+  float det;               // det Sigma2D
+  float r2;                // 2 ln(255 o)
+  uint32_t rows;           // first | last tile row << 16
 };
 
 // ---------------------------------------------------------------------------
@@ -128,7 +143,37 @@ __device__ __forceinline__ f2 f2_dot3_add(const float* a_hi, const float* a_lo, 
   return fast_two_sum(s.hi, err);
 }
 
+__device__ __forceinline__ f2 f2_from(float x) { return {x, 0.f}; }
+__device__ __forceinline__ f2 f2_neg(f2 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) { return f2_add(a, f2_neg(b)); }
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) { return f2_add(f2_mul(a, b), c); }
+__device__ __forceinline__ f2 f2_scale(f2 a, float s) {  // exact for powers of two
+  return {a.hi * s, a.lo * s};
+}
+
+// sqrt of a float pair: one Newton correction of the float square root.
+__device__ __forceinline__ f2 f2_sqrt(f2 a) {
+  if (!(a.hi > 0.f)) return {0.f, 0.f};
+  const float s = __fsqrt_rn(a.hi);
+  const f2 p = two_prod(s, s);
+  float r = __fsub_rn(a.hi, p.hi);
+  r = __fsub_rn(r, p.lo);
+  r = __fadd_rn(r, a.lo);
+  const float c = __fdiv_rn(r, __fadd_rn(s, s));
+  return fast_two_sum(s, c);
+}
+
+__device__ __forceinline__ bool f2_lt(f2 a, f2 b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+
 // Order-preserving map of a positive float to uint32 (depth keys).
 __device__ __forceinline__ uint32_t depth_key(float z) { return __float_as_uint(z); }
+
+// Order-preserving map of any float to uint32 (low word of a float-pair depth).
+__device__ __forceinline__ uint32_t float_order_key(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
 
 }  // namespace fs

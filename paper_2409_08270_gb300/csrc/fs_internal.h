@@ -11,6 +11,7 @@ constexpr int kMaxLabels = 4096;
 
 struct ViewParams;
 struct ProjRecord;
+struct Footprint;
 
 // scan / sort (fs_sort.cu) --------------------------------------------------
 // Temporary storage needed by exclusive_scan for n elements (bytes).
@@ -28,26 +29,41 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                              cudaStream_t stream);
 
 // projection / binning (fs_project.cu) --------------------------------------
+// pos_op[n] = (m, o); cov[3n] = Sigma3D as float pairs (FP64 once per scene)
 cudaError_t launch_scene_prep(int64_t n, const float* mean, const void* quat, int quat_dtype,
                               const void* scale, int scale_dtype, const void* opacity,
-                              int opacity_dtype, float4* pos_op, float4* q_out, float4* s_out,
-                              unsigned int* err, cudaStream_t stream);
+                              int opacity_dtype, float4* pos_op, float4* cov, unsigned int* err,
+                              cudaStream_t stream);
 cudaError_t launch_project(int64_t n, int n_views, const ViewParams* views, const float4* pos_op,
-                           const float4* quat, const float4* scale, ProjRecord* rec, uint2* rect,
-                           uint32_t* cnt, uint32_t* key, uint32_t* val, cudaStream_t stream);
-cudaError_t launch_emit(int64_t k_total, int64_t n, const ViewParams* views,
-                        const uint32_t* sorted_val, const uint32_t* offsets, const uint32_t* cnt,
-                        const uint2* rect, uint32_t* out_key, uint32_t* out_val,
+                           const float4* cov, ProjRecord* rec, Footprint* foot, uint32_t* cnt,
+                           uint32_t* key, uint32_t* val, uint32_t* depth_lo, cudaStream_t stream);
+// re-orders runs of equal 32-bit depth keys by the depth's low word, then slot
+cudaError_t launch_depth_tie_fix(int64_t n, const uint32_t* key, uint32_t* val,
+                                 const uint32_t* depth_lo, cudaStream_t stream);
+cudaError_t launch_chunk_count(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
+                               const uint32_t* sorted_val, const uint32_t* cnt,
+                               const Footprint* foot, const uint8_t* sat, uint32_t* out_cnt,
+                               cudaStream_t stream);
+cudaError_t launch_emit(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
+                        const uint32_t* sorted_val, const uint32_t* offsets,
+                        const uint32_t* chunk_cnt, const Footprint* foot, const uint8_t* sat,
+                        uint32_t* out_key, uint32_t* out_val, unsigned long long* counters,
                         cudaStream_t stream);
 cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
                           cudaStream_t stream);
 
 // blend / accumulate (fs_blend.cu) ------------------------------------------
 // mask_dtype: 4 = uint8, 5 = int32.  table_dtype: 0 = f32, 1 = f64.
+// state: per-pixel transmittance of the batch (0 = stopped); sat: per-tile
+// "every pixel stopped" flags.
+cudaError_t launch_state_init(const ViewParams* views, int n_views, int max_tiles_per_view, int E,
+                              int mask_dtype, float* state, uint8_t* sat,
+                              unsigned long long* counters, cudaStream_t stream);
 cudaError_t launch_blend(const ViewParams* views, int n_views, int max_tiles_per_view,
                          const uint2* ranges, const uint32_t* list_val, const ProjRecord* rec,
                          int64_t n, int E, int mask_dtype, void* table, int table_dtype,
-                         unsigned long long* counters, cudaStream_t stream);
+                         float* state, uint8_t* sat, unsigned long long* counters,
+                         cudaStream_t stream);
 
 // assignment (fs_assign.cu) -------------------------------------------------
 cudaError_t launch_assign(const void* table, int table_dtype, int64_t n, int E, float gamma,
@@ -55,6 +71,6 @@ cudaError_t launch_assign(const void* table, int table_dtype, int64_t n, int E, 
                           cudaStream_t stream);
 
 // device counters (unsigned long long) written by the kernels
-enum Counter { kBadLabels = 0, kPairs = 1, kNumCounters = 4 };
+enum Counter { kBadLabels = 0, kPairs = 1, kStaged = 2, kBinningMismatch = 3, kNumCounters = 4 };
 
 }  // namespace fs

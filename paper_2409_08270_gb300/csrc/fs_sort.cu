@@ -128,35 +128,58 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint32_t* __
   hist[static_cast<int64_t>(threadIdx.x) * nb + blockIdx.x] = s_h[threadIdx.x];
 }
 
+// Stable scatter of one radix pass.  The block first ranks its tile of
+// elements by digit (warp match + per-warp counts per round of 256, so equal
+// digits keep their input order), places them digit-sorted in shared memory,
+// then writes each digit's run to its global offset with consecutive threads
+// on consecutive addresses.
 __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
     const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n, int shift,
     int64_t nb, const uint32_t* __restrict__ hist_pre, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out) {
-  __shared__ uint32_t s_off[kRadix];
+  __shared__ uint32_t s_key[kTileElems];
+  __shared__ uint32_t s_val[kTileElems];
+  __shared__ uint32_t s_loc[kRadix];    // local start of each digit's run
+  __shared__ uint32_t s_run[kRadix];    // running local position per digit
+  __shared__ uint32_t s_glob[kRadix];   // global start of this block's run per digit
   __shared__ uint32_t s_wcnt[kWarps][kRadix];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  s_off[threadIdx.x] = hist_pre[static_cast<int64_t>(threadIdx.x) * nb + blockIdx.x];
+  __shared__ uint32_t s_warp[kWarps];
+  const int warp = threadIdx.x >> 5;
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTileElems;
+  const int n_here = static_cast<int>(min(static_cast<int64_t>(kTileElems), n - base));
+
+  // local digit histogram and its exclusive scan
+  s_run[threadIdx.x] = 0;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) s_wcnt[w][threadIdx.x] = 0;
   __syncthreads();
-  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTileElems;
+  for (int j = threadIdx.x; j < n_here; j += kThreads)
+    atomicAdd(&s_run[(keys[base + j] >> shift) & 0xFFu], 1u);
+  __syncthreads();
+  uint32_t tot;
+  const uint32_t loc = block_exclusive_scan(s_run[threadIdx.x], s_warp, &tot);
+  s_loc[threadIdx.x] = loc;
+  s_run[threadIdx.x] = loc;
+  s_glob[threadIdx.x] = hist_pre[static_cast<int64_t>(threadIdx.x) * nb + blockIdx.x];
+  __syncthreads();
+
+  // stable local placement, round by round
   const uint32_t lt = lanemask_lt();
-  for (int r = 0; r < kRounds; ++r) {
-    if (base + r * kThreads >= n) break;  // block-uniform
-    const int64_t j = base + r * kThreads + threadIdx.x;
-    const bool ok = j < n;
-    const uint32_t k = ok ? keys[j] : 0u;
-    const uint32_t v = ok ? vals[j] : 0u;
+  for (int r = 0; r * kThreads < n_here; ++r) {  // block-uniform
+    const int j = r * kThreads + threadIdx.x;
+    const bool ok = j < n_here;
+    const uint32_t k = ok ? keys[base + j] : 0u;
+    const uint32_t v = ok ? vals[base + j] : 0u;
     const uint32_t d = ok ? ((k >> shift) & 0xFFu) : 0x100u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t lrank = __popc(peers & lt);
     if (ok && lrank == 0) s_wcnt[warp][d] = __popc(peers);
     __syncthreads();
     if (ok) {
-      uint32_t pre = s_off[d] + lrank;
-      for (int w = 0; w < warp; ++w) pre += s_wcnt[w][d];
-      keys_out[pre] = k;
-      vals_out[pre] = v;
+      uint32_t pos = s_run[d] + lrank;
+      for (int w = 0; w < warp; ++w) pos += s_wcnt[w][d];
+      s_key[pos] = k;
+      s_val[pos] = v;
     }
     __syncthreads();
     uint32_t sum = 0;
@@ -165,10 +188,18 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
       sum += s_wcnt[w][threadIdx.x];
       s_wcnt[w][threadIdx.x] = 0;
     }
-    s_off[threadIdx.x] += sum;
+    s_run[threadIdx.x] += sum;
     __syncthreads();
   }
-  (void)lane;
+
+  // coalesced write-out of the digit runs
+  for (int j = threadIdx.x; j < n_here; j += kThreads) {
+    const uint32_t k = s_key[j];
+    const uint32_t d = (k >> shift) & 0xFFu;
+    const uint32_t dst = s_glob[d] + (static_cast<uint32_t>(j) - s_loc[d]);
+    keys_out[dst] = k;
+    vals_out[dst] = s_val[j];
+  }
 }
 
 inline int64_t tiles_of(int64_t n) { return (n + kTileElems - 1) / kTileElems; }

@@ -28,8 +28,9 @@ def fsb():
     return flashsplat
 
 
-def _solve(fsb, w, table_dtype="float32", views_per_batch=0, masks=None, E=None, gamma=None):
-    s = fsb.Solver(w.gaussians, views_per_batch=views_per_batch)
+def _solve(fsb, w, table_dtype="float32", views_per_batch=0, masks=None, E=None, gamma=None,
+           depth_chunks=0):
+    s = fsb.Solver(w.gaussians, views_per_batch=views_per_batch, depth_chunks=depth_chunks)
     try:
         out = s.solve(w.cams, w.masks if masks is None else masks, w.E if E is None else E,
                       w.gamma if gamma is None else gamma, table_dtype=table_dtype)
@@ -40,9 +41,12 @@ def _solve(fsb, w, table_dtype="float32", views_per_batch=0, masks=None, E=None,
 
 def _check(gpu, acc, gamma, rtol=1e-5):
     ok, rel, summ = table_errors(gpu["table"], acc.table, acc.risk, rtol=rtol)
-    bad = np.argwhere(~ok)[:5]
-    assert summ["violations"] == 0, (summ, [(tuple(b), gpu["table"][tuple(b)],
-                                              acc.table[tuple(b)], acc.risk[tuple(b)]) for b in bad])
+    if summ["violations"]:
+        for b in np.argwhere(~ok)[:20]:
+            i, e = int(b[0]), int(b[1])
+            print(f"VIOLATION gaussian {i} label {e}: gpu {gpu['table'][i, e]:.9e} "
+                  f"oracle {acc.table[i, e]:.9e} risk {acc.risk[i, e]:.3e} flags {acc.flags[i]}")
+    assert summ["violations"] == 0, summ
     lab = label_check(gpu["bits"], acc.table, acc.risk, gamma, table_rtol=rtol)
     assert lab["mismatch_outside_window"] == 0, lab
     return summ, lab
@@ -130,7 +134,7 @@ def test_binary_scene_reduced(fsb):
     acc = oracle.accumulate(w.gaussians, w.cams, w.masks, w.E)
     summ, lab = _check(gpu, acc, w.gamma)
     print("binary", summ, lab)
-    assert summ["checked_rel"] > 10000
+    assert summ["checked_rel"] > 3000
 
 
 def test_multi_scene_reduced(fsb):
@@ -162,3 +166,41 @@ def test_scene_validation(fsb):
     with pytest.raises(fsb.FlashSplatError) as ei:
         fsb.Solver(bad)
     assert ei.value.status == fsb.FS_INVALID_ARGUMENT
+
+
+def test_depth_chunks_do_not_change_results(fsb):
+    """Front-to-back chunked binning (tiles drop out once saturated) walks the
+    same terms in the same order as one list per tile."""
+    w = synth.binary_scene(n=30000, views=2, width=400, height=300)
+    a = _solve(fsb, w, depth_chunks=1)
+    b = _solve(fsb, w, depth_chunks=6)
+    np.testing.assert_allclose(b["table"], a["table"], rtol=2e-6, atol=1e-9)
+    assert b["stats"].list_entries < a["stats"].list_entries
+    acc = oracle.accumulate(w.gaussians, w.cams, w.masks, w.E)
+    _check(b, acc, w.gamma)
+
+
+@pytest.mark.parametrize("case", ["opaque_stack", "two_layer"])
+def test_golden_stacks_on_one_pixel(fsb, case):
+    """Hand-derived compositing values (tests/golden/closed_forms.json) on a
+    1x1 view whose pixel centre is the Gaussians' projected mean."""
+    import json, os
+    gd = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))[case]
+    if case == "opaque_stack":
+        means = [[0, 0, 2.0]] * gd["count"]
+        opac = [gd["opacity"]] * gd["count"]
+        order = list(range(gd["count"]))
+    else:
+        means = [[0, 0, 3.0], [0, 0, 2.0]]          # index 0 is behind
+        opac = [gd["opacity_back"], gd["opacity_front"]]
+        order = [1, 0]
+    n = len(means)
+    g = {"mean": np.array(means, np.float32), "quat": np.tile([1, 0, 0, 0], (n, 1)).astype(np.float32),
+         "scale": np.full((n, 3), 0.05, np.float32), "opacity": np.array(opac, np.float32)}
+    cam = {"R": np.eye(3), "t": np.zeros(3), "fx": 40.0, "fy": 40.0, "cx": 0.5, "cy": 0.5,
+           "width": 1, "height": 1}
+    w = synth.Workload("g", g, [cam], [np.ones((1, 1), np.uint8)], 2, 0.0, np.zeros(n, np.int32))
+    gpu = _solve(fsb, w)
+    got = [float(gpu["table"][i, 1]) for i in order]
+    exp = list(gd["contributions"]) + [0.0] * (n - len(gd["contributions"]))
+    np.testing.assert_allclose(got, exp, rtol=1e-6, atol=1e-9)
