@@ -219,6 +219,41 @@ fs_status fs_solve(fs_ctx* ctx, const fs_scene* scene, const fs_camera* cams, in
  * kernels (FS_CUDA_ERROR with a message).  Fills *stats if non-NULL. */
 fs_status fs_synchronize(fs_ctx* ctx, void* stream, fs_stats* stats);
 
+/* ---- solve without allocating ----------------------------------------------
+ * The paper has no counterpart of this call; it exists for callers that may
+ * not allocate device memory -- e.g. a plugin inside an application that owns
+ * all device memory through its own pool, or a latency-critical loop that
+ * cannot afford cudaMalloc/cudaFree, which may synchronise the whole device.
+ *
+ * fs_solve_noalloc computes what fs_solve computes (FP32 table), for small
+ * scenes, without a context and without allocating anything: its working
+ * memory is a fixed array of about 13 MB in the library's device memory that
+ * every GPU loading the library holds until the process exits.  Limits:
+ * 1..FS_NOALLOC_MAX_GAUSSIANS Gaussians, views of at most FS_NOALLOC_MAX_SIDE
+ * pixels per side, at most FS_NOALLOC_MAX_LIST_ENTRIES (tile, Gaussian) pairs
+ * per view and depth chunk; larger inputs are rejected (FS_INVALID_ARGUMENT,
+ * or FS_UNSUPPORTED when the pair count is exceeded mid-solve, after which the
+ * table is incomplete).
+ *   device: CUDA device to run on.  g: FS_F32 attributes in device memory.
+ *   cams[n_views], masks[n_views]: host arrays; masks point to device
+ *   memory (FS_U8 or FS_I32).  table: device [n][E] FP32, overwritten.
+ *   member_bits / label / margin: device outputs as in fs_assign (each may
+ *   be NULL).  stream: the caller's stream (NULL = legacy default stream).
+ * The first call on a device looks up the array's device address once (make
+ * that first call before any stream capture).  The call returns after the
+ * work has completed (it reads counts back between steps).  All calls share
+ * the one array, which keeps the previous call's contents (what must start
+ * at zero is cleared on every call); calls whose work overlaps on the GPU --
+ * from several host threads or on several streams -- race and must not be
+ * made.  Errors are reported like every other call (fs_last_error). */
+#define FS_NOALLOC_MAX_GAUSSIANS 16384
+#define FS_NOALLOC_MAX_SIDE 512
+#define FS_NOALLOC_MAX_LIST_ENTRIES (1 << 19)
+fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, const fs_camera* cams,
+                           int32_t n_views, const void* const* masks, int32_t mask_dtype,
+                           int32_t E, float gamma, float* table, uint64_t* member_bits,
+                           int32_t* label, float* margin, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -154,6 +154,10 @@ int64_t radix_launches(int64_t n, int bits) {
 
 }  // namespace
 
+void fs::set_last_error(const char* msg) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+}
+
 struct fs_ctx {
   int device = 0;
   int views_per_batch = 8;

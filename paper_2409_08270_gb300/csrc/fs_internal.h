@@ -70,6 +70,9 @@ cudaError_t launch_assign(const void* table, int table_dtype, int64_t n, int E, 
                           uint64_t* member_bits, int32_t* label, float* margin,
                           cudaStream_t stream);
 
+// Sets the calling thread's fs_last_error() message (fs_api.cu).
+void set_last_error(const char* msg);
+
 // device counters (unsigned long long) written by the kernels
 enum Counter { kBadLabels = 0, kPairs = 1, kStaged = 2, kBinningMismatch = 3, kNumCounters = 4 };
 

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "FS_OK", 1: "FS_INVALID_ARGUMENT", 2: "FS_OUT_OF_MEMORY", 3: 
 # every entry point declared in include/flashsplat.h
 EXPORTS = ["fs_version", "fs_last_error", "fs_create", "fs_destroy", "fs_scene_create",
            "fs_scene_destroy", "fs_scene_size", "fs_accumulate", "fs_assign", "fs_solve",
-           "fs_synchronize"]
+           "fs_synchronize", "fs_solve_noalloc"]
 
 
 class fs_options(ctypes.Structure):
@@ -102,6 +102,8 @@ def load(path: str | None = None):
         "fs_solve": (i32, [vp, vp, ctypes.POINTER(fs_camera), i32, ctypes.POINTER(vp), i32, i32,
                            i32, f32, ctypes.POINTER(fs_result), vp]),
         "fs_synchronize": (i32, [vp, vp, ctypes.POINTER(fs_stats)]),
+        "fs_solve_noalloc": (i32, [i32, ctypes.POINTER(fs_gaussians), ctypes.POINTER(fs_camera),
+                                   i32, ctypes.POINTER(vp), i32, i32, f32, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -176,6 +178,15 @@ def fs_synchronize(ctx, stream=0) -> fs_stats:
     st = fs_stats()
     check(load().fs_synchronize(ctx, stream, ctypes.byref(st)))
     return st
+
+
+def fs_solve_noalloc(device, g: fs_gaussians, cams, masks, mask_dtype, E, gamma, table,
+                     bits=None, label=None, margin=None, stream=0):
+    """Allocation-free small-scene solve (see include/flashsplat.h)."""
+    V = len(masks)
+    mp = (ctypes.c_void_p * max(V, 1))(*masks)
+    check(load().fs_solve_noalloc(device, ctypes.byref(g), cams, V, mp, mask_dtype, E, gamma,
+                                  table, bits, label, margin, stream))
 
 
 # ---- helpers ---------------------------------------------------------------
