@@ -74,9 +74,9 @@ typedef struct fs_scene fs_scene;
 
 /* Context options.  Zero-initialise and set what you need; 0 = default. */
 typedef struct fs_options {
-  int32_t views_per_batch;  /* views binned and blended per launch group (default 8) */
+  int32_t views_per_batch;  /* views binned and blended per launch group (default 16) */
   int32_t time_stages;      /* non-zero: time every blend launch with CUDA events */
-  int32_t depth_chunks;     /* front-to-back binning chunks per batch (default 6, 1 = off) */
+  int32_t depth_chunks;     /* front-to-back binning chunks per batch (default 4, 1 = off) */
   int32_t reserved[13];
 } fs_options;
 

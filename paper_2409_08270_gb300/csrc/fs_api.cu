@@ -160,14 +160,14 @@ void fs::set_last_error(const char* msg) {
 
 struct fs_ctx {
   int device = 0;
-  int views_per_batch = 8;
-  int depth_chunks = 6;  // front-to-back chunks per batch (sizes 1/32 .. 1/2 of the batch)
+  int views_per_batch = 16;
+  int depth_chunks = 4;  // front-to-back chunks per batch (sizes 1/8, 1/8, 1/4, 1/2)
   int n_sm = 0;
   bool time_stages = false;
   std::vector<cudaEvent_t> events;  // (start, stop) pairs around blend launches
   size_t events_used = 0;
   // workspace
-  DevBuf views, rec, foot, cnt, key_a, val_a, key_b, val_b, offs, ccnt, dlo, state, sat;
+  DevBuf views, rec, foot, cnt, key_a, val_a, key_b, val_b, offs, ccnt, dlo, state, sat, subsat;
   DevBuf lk_a, lv_a, lk_b, lv_b, ranges, sort_tmp, scan_tmp, total, counters;
   DevBuf mask_stage, table_tmp, bits_tmp, label_tmp, margin_tmp;
   HostBuf views_host, total_host, counters_host;
@@ -230,7 +230,7 @@ fs_status fs_destroy(fs_ctx* c) {
     return fail(FS_INVALID_ARGUMENT, "fs_destroy: %d scene(s) still alive", c->scenes);
   DeviceGuard g(c->device);
   cudaDeviceSynchronize();
-  DevBuf* bufs[] = {&c->ccnt, &c->dlo, &c->state, &c->sat, &c->views, &c->rec, &c->foot, &c->cnt, &c->key_a, &c->val_a, &c->key_b,
+  DevBuf* bufs[] = {&c->subsat, &c->ccnt, &c->dlo, &c->state, &c->sat, &c->views, &c->rec, &c->foot, &c->cnt, &c->key_a, &c->val_a, &c->key_b,
                     &c->val_b, &c->offs, &c->lk_a, &c->lv_a, &c->lk_b, &c->lv_b, &c->ranges,
                     &c->sort_tmp, &c->scan_tmp, &c->total, &c->counters, &c->mask_stage,
                     &c->table_tmp, &c->bits_tmp, &c->label_tmp, &c->margin_tmp};
@@ -437,11 +437,14 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     const int tile_bits = std::max(1, ceil_log2(total_tiles));
     const int64_t k_total = static_cast<int64_t>(nb) * n;
     FS_TRY(c->state.ensure(static_cast<size_t>(state_off) * 4, "pixel state"));
-    FS_TRY(c->sat.ensure(static_cast<size_t>(total_tiles), "tile flags"));
+    const size_t sat_bytes = static_cast<size_t>((total_tiles + 63) / 64) * 8;
+    FS_TRY(c->sat.ensure(sat_bytes, "tile flags"));
+    const size_t subsat_bytes = static_cast<size_t>((4 * total_tiles + 63) / 64) * 8;
+    FS_TRY(c->subsat.ensure(subsat_bytes, "sub-tile flags"));
     FS_TRY(c->ranges.ensure(static_cast<size_t>(total_tiles) * 8, "tile ranges"));
     fs::ViewParams* vd = c->views.as<fs::ViewParams>();
     float* state = c->state.as<float>();
-    uint8_t* sat = c->sat.as<uint8_t>();
+    uint64_t* sat = c->sat.as<uint64_t>();
     FS_CUDA(cudaMemcpyAsync(vd, vh, sizeof(fs::ViewParams) * nb, cudaMemcpyHostToDevice, stream),
             "view upload");
 
@@ -459,10 +462,14 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
             "depth sort");
     uint32_t* sorted_key = alt ? c->key_b.as<uint32_t>() : c->key_a.as<uint32_t>();
     uint32_t* sorted_val = alt ? c->val_b.as<uint32_t>() : c->val_a.as<uint32_t>();
-    FS_CUDA(fs::launch_depth_tie_fix(k_total, sorted_key, sorted_val, c->dlo.as<uint32_t>(),
+    FS_CUDA(fs::launch_depth_tie_fix(k_total, n, sorted_key, sorted_val, c->dlo.as<uint32_t>(),
                                      stream),
             "depth ties");
-    FS_CUDA(fs::launch_state_init(vd, nb, max_tiles, E, mask_dtype, state, sat, ctr, stream),
+    uint64_t* subsat = c->subsat.as<uint64_t>();
+    FS_CUDA(cudaMemsetAsync(sat, 0, sat_bytes, stream), "tile flags clear");
+    FS_CUDA(cudaMemsetAsync(subsat, 0, subsat_bytes, stream), "sub-tile flags clear");
+    FS_CUDA(fs::launch_state_init(vd, nb, max_tiles, E, mask_dtype, state, sat, subsat, ctr,
+                                  stream),
             "pixel state");
     c->stats.views += nb;
     c->stats.pixels += state_off;
@@ -529,7 +536,7 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
       }
       FS_CUDA(fs::launch_blend(vd, nb, max_tiles, c->ranges.as<uint2>(), lval,
                                c->rec.as<fs::ProjRecord>(), n, E, mask_dtype, table, table_dtype,
-                               state, sat, ctr, stream),
+                               state, sat, subsat, ctr, stream),
               "blend");
       if (ev1) FS_CUDA(cudaEventRecord(ev1, stream), "cudaEventRecord");
       p0 = p1;

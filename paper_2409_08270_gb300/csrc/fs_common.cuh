@@ -41,9 +41,10 @@ struct ViewParams {
 //   w_hi, w_lo = whitening matrix W (row-major 2x2) as float pairs, with
 //                |W d|^2 = 0.5 log2(e) d^T Sigma2D^-1 d
 //   c          = (c0_hi, c1_hi, c0_lo, c1_lo), c = -W m2D as float pairs
-//   misc       = (opacity, -, -, -)
-// For a tile whose centre is o the blend forms b = W o + c (float pairs) and
-// evaluates w = W_hi (p - o) + b for the pixel centre p, |p - o| <= 7.5 px.
+//   misc       = (opacity, q_cut, -, -), q_cut ~ log2(255 o): alpha = o 2^-|w|^2
+//                reaches 1/255 at |w|^2 = log2(255 o) (stored slightly widened)
+// For a sub-tile whose centre is o the blend forms b = W o + c (float pairs)
+// and evaluates w = W_hi (p - o) + b for the pixel centre p, |p - o| <= 5 px.
 struct alignas(16) ProjRecord {
   float4 w_hi;
   float4 w_lo;
@@ -52,13 +53,17 @@ struct alignas(16) ProjRecord {
 };
 
 // Footprint of one (view, Gaussian) for the tile binning: the alpha >= 1/255
-// ellipse {d : d^T Sigma2D^-1 d <= r2} around the projected mean, in FP32
-// (the binning is conservative: it widens r2 and adds a pixel of margin).
+// ellipse {d : d^T Sigma2D^-1 d <= r2} around the projected mean, r2 slightly
+// inflated, in FP32 (the binning is conservative: it also adds a pixel of
+// margin).  With S = Sigma2D, the ellipse's x-range at height dy is
+//   x(dy) = mx + a dy +- sqrt(b2 (syr - dy^2)),  a = Sxy/Syy, b2 = det S / Syy^2,
+//   syr = Syy r2  (|dy| <= hy = sqrt(syr)),
+// and its rightmost point lies at dy* = Sxy sqrt(r2 / Sxx).
 struct alignas(16) Footprint {
   float mx, my;            // projected mean (pixels)
-  float sxx, sxy, syy;     // Sigma2D
-  float det;               // det Sigma2D
-  float r2;                // 2 ln(255 o)
+  float hy, syr;           // half height of the ellipse, and its square
+  float dys;               // dy of the rightmost point
+  float a, b2;             // slope and width factor of x(dy)
   uint32_t rows;           // first | last tile row << 16
 };
 
@@ -90,13 +95,13 @@ __device__ __forceinline__ f2 two_prod(float a, float b) {
   return {p, e};
 }
 
+// Sum of float pairs (Dekker's addition): error below ~2^-44 (|a| + |b|),
+// i.e. about 1e-11 relative to the result even when a and b cancel to three
+// orders of magnitude -- far more than any quantity here needs.
 __device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
-  f2 s = two_sum(a.hi, b.hi);
-  const f2 t = two_sum(a.lo, b.lo);
-  s.lo = __fadd_rn(s.lo, t.hi);
-  s = fast_two_sum(s.hi, s.lo);
-  s.lo = __fadd_rn(s.lo, t.lo);
-  return fast_two_sum(s.hi, s.lo);
+  const f2 s = two_sum(a.hi, b.hi);
+  const float e = __fadd_rn(__fadd_rn(s.lo, a.lo), b.lo);
+  return fast_two_sum(s.hi, e);
 }
 
 __device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {

@@ -38,15 +38,16 @@ cudaError_t launch_project(int64_t n, int n_views, const ViewParams* views, cons
                            const float4* cov, ProjRecord* rec, Footprint* foot, uint32_t* cnt,
                            uint32_t* key, uint32_t* val, uint32_t* depth_lo, cudaStream_t stream);
 // re-orders runs of equal 32-bit depth keys by the depth's low word, then slot
-cudaError_t launch_depth_tie_fix(int64_t n, const uint32_t* key, uint32_t* val,
+// (n_total elements; slot / n is the view of a slot)
+cudaError_t launch_depth_tie_fix(int64_t n_total, int64_t n, const uint32_t* key, uint32_t* val,
                                  const uint32_t* depth_lo, cudaStream_t stream);
 cudaError_t launch_chunk_count(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
                                const uint32_t* sorted_val, const uint32_t* cnt,
-                               const Footprint* foot, const uint8_t* sat, uint32_t* out_cnt,
+                               const Footprint* foot, const uint64_t* sat, uint32_t* out_cnt,
                                cudaStream_t stream);
 cudaError_t launch_emit(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
                         const uint32_t* sorted_val, const uint32_t* offsets,
-                        const uint32_t* chunk_cnt, const Footprint* foot, const uint8_t* sat,
+                        const uint32_t* chunk_cnt, const Footprint* foot, const uint64_t* sat,
                         uint32_t* out_key, uint32_t* out_val, unsigned long long* counters,
                         cudaStream_t stream);
 cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
@@ -54,16 +55,18 @@ cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
 
 // blend / accumulate (fs_blend.cu) ------------------------------------------
 // mask_dtype: 4 = uint8, 5 = int32.  table_dtype: 0 = f32, 1 = f64.
-// state: per-pixel transmittance of the batch (0 = stopped); sat: per-tile
-// "every pixel stopped" flags.
+// state: per-pixel transmittance of the batch (0 = stopped).  sat / subsat:
+// bit arrays over the batch's tile ids / 4 * tile id + sub-tile: set = every
+// pixel of the tile / 8x8 sub-tile stopped (cleared by the caller before
+// state_init).
 cudaError_t launch_state_init(const ViewParams* views, int n_views, int max_tiles_per_view, int E,
-                              int mask_dtype, float* state, uint8_t* sat,
+                              int mask_dtype, float* state, uint64_t* sat, uint64_t* subsat,
                               unsigned long long* counters, cudaStream_t stream);
 cudaError_t launch_blend(const ViewParams* views, int n_views, int max_tiles_per_view,
                          const uint2* ranges, const uint32_t* list_val, const ProjRecord* rec,
                          int64_t n, int E, int mask_dtype, void* table, int table_dtype,
-                         float* state, uint8_t* sat, unsigned long long* counters,
-                         cudaStream_t stream);
+                         float* state, uint64_t* sat, uint64_t* subsat,
+                         unsigned long long* counters, cudaStream_t stream);
 
 // assignment (fs_assign.cu) -------------------------------------------------
 cudaError_t launch_assign(const void* table, int table_dtype, int64_t n, int E, float gamma,

@@ -61,7 +61,8 @@ constexpr size_t oLvB = oLkB + al(kNA_Entries * 4);
 constexpr size_t oRanges = oLvB + al(kNA_Entries * 4);
 constexpr size_t oState = oRanges + al(kNA_Tiles * 8);
 constexpr size_t oSat = oState + al(static_cast<size_t>(kNA_Side) * kNA_Side * 4);
-constexpr size_t oSortTmp = oSat + al(kNA_Tiles);
+constexpr size_t oSubsat = oSat + al(kNA_Tiles);
+constexpr size_t oSortTmp = oSubsat + al(4 * kNA_Tiles);
 constexpr size_t oScanTmp = oSortTmp + al(kNA_SortTmp);
 constexpr size_t oWords = oScanTmp + al(kNA_ScanTmp);  // total (u32), error word (u32)
 constexpr size_t oCounters = oWords + 256;
@@ -202,7 +203,8 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
   uint32_t* lv_b = reinterpret_cast<uint32_t*>(S + oLvB);
   uint2* ranges = reinterpret_cast<uint2*>(S + oRanges);
   float* state = reinterpret_cast<float*>(S + oState);
-  uint8_t* sat = reinterpret_cast<uint8_t*>(S + oSat);
+  uint64_t* sat = reinterpret_cast<uint64_t*>(S + oSat);
+  uint64_t* subsat = reinterpret_cast<uint64_t*>(S + oSubsat);
   void* sort_tmp = S + oSortTmp;
   void* scan_tmp = S + oScanTmp;
   uint32_t* total_d = reinterpret_cast<uint32_t*>(S + oWords);
@@ -252,8 +254,11 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
     NA_CUDA(radix_sort_pairs(key_a, val_a, key_b, val_b, n, 32, sort_tmp, &alt, strm), "sort");
     uint32_t* skey = alt ? key_b : key_a;
     uint32_t* sval = alt ? val_b : val_a;
-    NA_CUDA(launch_depth_tie_fix(n, skey, sval, dlo, strm), "ties");
-    NA_CUDA(launch_state_init(vd, 1, tiles, E, mask_dtype, state, sat, ctr, strm), "state");
+    NA_CUDA(launch_depth_tie_fix(n, n, skey, sval, dlo, strm), "ties");
+    NA_CUDA(cudaMemsetAsync(sat, 0, static_cast<size_t>((tiles + 63) / 64) * 8, strm), "clear");
+    NA_CUDA(cudaMemsetAsync(subsat, 0, static_cast<size_t>((4 * tiles + 63) / 64) * 8, strm),
+            "clear");
+    NA_CUDA(launch_state_init(vd, 1, tiles, E, mask_dtype, state, sat, subsat, ctr, strm), "state");
     const int chunks = 6;
     int64_t p0 = 0;
     for (int ci = 0; ci < chunks; ++ci) {
@@ -280,7 +285,7 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
         NA_CUDA(cudaMemsetAsync(ranges, 0, static_cast<size_t>(tiles) * 8, strm), "clear");
         NA_CUDA(launch_ranges(I, lkey, ranges, strm), "ranges");
         NA_CUDA(launch_blend(vd, 1, tiles, ranges, lval, rec, n, E, mask_dtype, table, FS_F32,
-                             state, sat, ctr, strm),
+                             state, sat, subsat, ctr, strm),
                 "blend");
       }
       p0 = p1;

@@ -113,28 +113,37 @@ __device__ __forceinline__ void footprint_rows(const Footprint& f, int* ty0, int
   *ty1 = static_cast<int>(f.rows >> 16);
 }
 
+// Saturated tiles are bits of a bit array over the batch's tile ids.
+// Number of unsaturated tiles among ids [a, b].
+__device__ __forceinline__ uint32_t count_free(const uint64_t* __restrict__ sat, int a, int b) {
+  uint32_t c = 0;
+  const int wa = a >> 6, wb = b >> 6;
+  for (int w = wa; w <= wb; ++w) {
+    uint64_t m = ~0ull;
+    if (w == wa) m &= ~0ull << (a & 63);
+    if (w == wb) m &= ~0ull >> (63 - (b & 63));
+    c += static_cast<uint32_t>(__popcll(~sat[w] & m));
+  }
+  return c;
+}
+
 // Tiles [tx0, tx1] of tile row ty touched by the footprint (false if none).
 // The band of pixel-centre rows of the tile, widened by one pixel, is
-// intersected with the ellipse; its x-extent over the band comes from the
-// boundary x_R(dy) = (sxy dy + sqrt(det (syy r2 - dy^2))) / syy, which is
-// concave (maximal at the ellipse's rightmost point, dy* = sxy sqrt(r2/sxx),
-// clamped to the band), and the mirror image on the left.
+// intersected with the ellipse; over the band the right boundary x(dy) is
+// concave, so its maximum is at the rightmost point dy* clamped to the band
+// (and the left boundary's minimum at -dy*, clamped).
 __device__ __forceinline__ bool row_span(const Footprint& f, int ty, int width, int* tx0,
                                          int* tx1) {
-  const float r2 = binning_r2(f.r2);
   const float yt = static_cast<float>(ty * kTile);
   const float y0 = __fsub_rn(__fadd_rn(yt, -0.5f), f.my);   // band widened by one pixel
   const float y1 = __fsub_rn(__fadd_rn(yt, 16.5f), f.my);
-  const float hy = __fsqrt_rn(__fmul_rn(f.syy, r2));
-  const float u0 = fmaxf(y0, -hy), u1 = fminf(y1, hy);
+  const float u0 = fmaxf(y0, -f.hy), u1 = fminf(y1, f.hy);
   if (!(u0 <= u1)) return false;
-  const float dys = __fmul_rn(f.sxy, __fsqrt_rn(__fdiv_rn(r2, f.sxx)));
-  const float dr = fminf(fmaxf(dys, u0), u1), dl = fminf(fmaxf(-dys, u0), u1);
-  const float syr = __fmul_rn(f.syy, r2);
-  const float sr = __fsqrt_rn(__fmul_rn(f.det, fmaxf(0.f, __fsub_rn(syr, __fmul_rn(dr, dr)))));
-  const float sl = __fsqrt_rn(__fmul_rn(f.det, fmaxf(0.f, __fsub_rn(syr, __fmul_rn(dl, dl)))));
-  const float xr = __fadd_rn(f.mx, __fdiv_rn(__fadd_rn(__fmul_rn(f.sxy, dr), sr), f.syy));
-  const float xl = __fadd_rn(f.mx, __fdiv_rn(__fsub_rn(__fmul_rn(f.sxy, dl), sl), f.syy));
+  const float dr = fminf(fmaxf(f.dys, u0), u1), dl = fminf(fmaxf(-f.dys, u0), u1);
+  const float sr = __fsqrt_rn(__fmul_rn(f.b2, fmaxf(0.f, __fsub_rn(f.syr, __fmul_rn(dr, dr)))));
+  const float sl = __fsqrt_rn(__fmul_rn(f.b2, fmaxf(0.f, __fsub_rn(f.syr, __fmul_rn(dl, dl)))));
+  const float xr = __fadd_rn(__fadd_rn(f.mx, __fmul_rn(f.a, dr)), sr);
+  const float xl = __fsub_rn(__fadd_rn(f.mx, __fmul_rn(f.a, dl)), sl);
   float px0 = ceilf(__fsub_rn(xl, 1.5f)), px1 = floorf(__fadd_rn(xr, 0.5f));
   px0 = fmaxf(px0, 0.f);
   px1 = fminf(px1, static_cast<float>(width - 1));
@@ -193,10 +202,12 @@ __global__ void __launch_bounds__(256) project_kernel(
     float depth = 0.f, depth_l = 0.f;
     ProjRecord R;
     R.w_hi = R.w_lo = R.c = make_float4(0.f, 0.f, 0.f, 0.f);
-    R.misc = make_float4(o, 0.f, 0.f, 0.f);
+    // misc.y: |w|^2 at which alpha falls to 1/255, log2(255 o), widened by
+    // 0.1% + 1e-3 so the blend's sub-tile test stays conservative in FP32
+    const float qcut = opaque_enough ? fmaxf(log2f(255.f * o), 0.f) * 1.001f + 1e-3f : 0.f;
+    R.misc = make_float4(o, qcut, 0.f, 0.f);
     Footprint F;
-    F.mx = F.my = F.sxy = F.det = F.r2 = 0.f;
-    F.sxx = F.syy = 1.f;
+    F.mx = F.my = F.hy = F.syr = F.dys = F.a = F.b2 = 0.f;
     F.rows = 0;
     if (visible) {
       const f2 ux = f2_div(tx, tz), uy = f2_div(ty, tz);
@@ -265,28 +276,31 @@ __global__ void __launch_bounds__(256) project_kernel(
       R.w_hi = make_float4(W00.hi, W01.hi, W10.hi, W11.hi);
       R.w_lo = make_float4(W00.lo, W01.lo, W10.lo, W11.lo);
       R.c = make_float4(c0.hi, c1.hi, c0.lo, c1.lo);
-      // binning footprint
+      // binning footprint (FP32 is plenty: the binning keeps a pixel of margin)
+      const float r2b = binning_r2(r2);
+      const float sxx = a.hi, sxy = b.hi, syy = c.hi;
       F.mx = mx.hi;
       F.my = my.hi;
-      F.sxx = a.hi;
-      F.sxy = b.hi;
-      F.syy = c.hi;
-      F.det = det.hi;
-      F.r2 = r2;
-      const float hy = __fsqrt_rn(__fmul_rn(F.syy, binning_r2(r2)));
+      F.syr = syy * r2b;
+      F.hy = sqrtf(F.syr);
+      F.dys = sxy * sqrtf(r2b / sxx);
+      F.a = sxy / syy;
+      F.b2 = det.hi / (syy * syy);
+      const float hy = F.hy;
       const float py0 = ceilf(__fsub_rn(__fsub_rn(F.my, hy), 1.5f));
       const float py1 = floorf(__fadd_rn(__fadd_rn(F.my, hy), 0.5f));
-      if (!(py1 >= 0.f && py0 <= vp.height - 1)) {
+      // visible when the widened bounding box meets the image; the exact
+      // per-row tile spans are counted later, per depth chunk
+      const float hx = sqrtf(sxx * r2b);
+      const float px0 = ceilf(__fsub_rn(__fsub_rn(F.mx, hx), 1.5f));
+      const float px1 = floorf(__fadd_rn(__fadd_rn(F.mx, hx), 0.5f));
+      if (!(py1 >= 0.f && py0 <= vp.height - 1 && px1 >= 0.f && px0 <= vp.width - 1)) {
         visible = false;
       } else {
         const int ty0 = static_cast<int>(fmaxf(py0, 0.f)) / kTile;
         const int ty1 = static_cast<int>(fminf(py1, (float)(vp.height - 1))) / kTile;
         F.rows = static_cast<uint32_t>(ty0) | (static_cast<uint32_t>(ty1) << 16);
-        for (int t = ty0; t <= ty1; ++t) {
-          int a0, a1;
-          if (row_span(F, t, vp.width, &a0, &a1)) count += static_cast<uint32_t>(a1 - a0 + 1);
-        }
-        if (count == 0) visible = false;
+        count = 1;
       }
     }
     rec[slot] = R;
@@ -303,24 +317,35 @@ __global__ void __launch_bounds__(256) project_kernel(
 // then by slot), so the order is that of the full-precision depth with ties
 // by index -- the order the compositing of Eq. 1 walks.  Runs are short; one
 // thread sorts each run by insertion.
-__global__ void depth_tie_fix_kernel(int64_t n, const uint32_t* __restrict__ key,
+__global__ void depth_tie_fix_kernel(int64_t n_total, int64_t n, const uint32_t* __restrict__ key,
                                      uint32_t* __restrict__ val,
                                      const uint32_t* __restrict__ depth_lo) {
   const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k + 1 >= n) return;
+  if (k + 1 >= n_total) return;
   const uint32_t kk = key[k];
   if (kk == 0xFFFFFFFFu || key[k + 1] != kk) return;
   if (k > 0 && key[k - 1] == kk) return;  // not the start of the run
   int64_t e = k + 2;
-  while (e < n && key[e] == kk) ++e;
+  while (e < n_total && key[e] == kk) ++e;
+  // Only the order of the same view's elements matters (views are separated
+  // later by a stable sort); order by (view, low word, slot).
+  const uint32_t nn = static_cast<uint32_t>(n);
   for (int64_t a = k + 1; a < e; ++a) {
     const uint32_t va = val[a];
-    const uint64_t ka = (static_cast<uint64_t>(depth_lo[va]) << 32) | va;
+    const uint32_t view_a = va / nn;
     int64_t b = a - 1;
     while (b >= k) {
       const uint32_t vb = val[b];
-      const uint64_t kb = (static_cast<uint64_t>(depth_lo[vb]) << 32) | vb;
-      if (kb <= ka) break;
+      const uint32_t view_b = vb / nn;
+      bool greater;  // element b goes after element a
+      if (view_b != view_a) {
+        greater = view_b > view_a;
+      } else {
+        const uint64_t ka = (static_cast<uint64_t>(depth_lo[va]) << 32) | va;
+        const uint64_t kb = (static_cast<uint64_t>(depth_lo[vb]) << 32) | vb;
+        greater = kb > ka;
+      }
+      if (!greater) break;
       val[b + 1] = vb;
       --b;
     }
@@ -329,37 +354,87 @@ __global__ void depth_tie_fix_kernel(int64_t n, const uint32_t* __restrict__ key
 }
 
 // Number of list entries of sorted positions [p0, p0 + n_pos) that fall on
-// tiles not yet saturated (sat[t] != 0: every pixel of tile t has stopped).
+// tiles not yet saturated.  Footprints spanning many tile rows are counted by
+// the whole warp, one row per lane, so one large Gaussian does not hold up
+// the 31 others of its warp.
+constexpr int kBigRows = 12;
+
 __global__ void __launch_bounds__(256) chunk_count_kernel(
     int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
     const uint32_t* __restrict__ sorted_val, const uint32_t* __restrict__ cnt,
-    const Footprint* __restrict__ foot, const uint8_t* __restrict__ sat,
+    const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
     uint32_t* __restrict__ out_cnt) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= n_pos) return;
-  const uint32_t g = sorted_val[p0 + j];
-  uint32_t c = 0;
-  if (cnt[g] > 0) {
+  const int lane = threadIdx.x & 31;
+  uint32_t g = 0, c = 0;
+  int ty0 = 0, ty1 = -1;
+  Footprint f;
+  if (j < n_pos) {
+    g = sorted_val[p0 + j];
+    if (cnt[g] > 0) {
+      f = foot[g];
+      footprint_rows(f, &ty0, &ty1);
+    }
+  }
+  const bool big = ty1 - ty0 + 1 > kBigRows;
+  if (!big && ty1 >= ty0) {
     const int v = static_cast<int>(g / n);
-    const Footprint f = foot[g];
     const int tiles_x = views[v].tiles_x, width = views[v].width;
-    const uint8_t* st = sat + views[v].tile_base;
-    int ty0, ty1;
-    footprint_rows(f, &ty0, &ty1);
+    const int base = views[v].tile_base;
     for (int ty = ty0; ty <= ty1; ++ty) {
       int tx0, tx1;
       if (!row_span(f, ty, width, &tx0, &tx1)) continue;
-      for (int tx = tx0; tx <= tx1; ++tx) c += st[ty * tiles_x + tx] ? 0u : 1u;
+      c += count_free(sat, base + ty * tiles_x + tx0, base + ty * tiles_x + tx1);
     }
   }
-  out_cnt[j] = c;
+  uint32_t m = __ballot_sync(0xffffffffu, big);
+  while (m) {
+    const int src = __ffs(m) - 1;
+    m &= m - 1;
+    const uint32_t gb = __shfl_sync(0xffffffffu, g, src);
+    const int v = static_cast<int>(gb / n);
+    const Footprint fb = foot[gb];
+    const int tiles_x = views[v].tiles_x, width = views[v].width;
+    const int base = views[v].tile_base;
+    int r0, r1;
+    footprint_rows(fb, &r0, &r1);
+    uint32_t part = 0;
+    for (int ty = r0 + lane; ty <= r1; ty += 32) {
+      int tx0, tx1;
+      if (row_span(fb, ty, width, &tx0, &tx1))
+        part += count_free(sat, base + ty * tiles_x + tx0, base + ty * tiles_x + tx1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == src) c = part;
+  }
+  if (j < n_pos) out_cnt[j] = c;
 }
 
-// ---------------------------------------------------------------------------
-// emission of (tile, Gaussian) list entries in depth order
-// ---------------------------------------------------------------------------
-
 constexpr uint32_t kBigEmit = 64;  // longer lists are written by a whole warp
+
+// Writes (tile, g) for every unsaturated tile id in [a, b], from position o,
+// never at or past `end`; returns the next position.
+__device__ __forceinline__ uint32_t emit_free(const uint64_t* __restrict__ sat, int a, int b,
+                                              uint32_t g, uint32_t* __restrict__ out_key,
+                                              uint32_t* __restrict__ out_val, uint32_t o,
+                                              uint32_t end) {
+  const int wa = a >> 6, wb = b >> 6;
+  for (int w = wa; w <= wb; ++w) {
+    uint64_t m = ~0ull;
+    if (w == wa) m &= ~0ull << (a & 63);
+    if (w == wb) m &= ~0ull >> (63 - (b & 63));
+    uint64_t bits = ~sat[w] & m;
+    while (bits && o < end) {
+      const int bit = __ffsll(static_cast<long long>(bits)) - 1;
+      bits &= bits - 1;
+      out_key[o] = static_cast<uint32_t>(w * 64 + bit);
+      out_val[o] = g;
+      ++o;
+    }
+  }
+  return o;
+}
 
 // Writes the list entries of sorted positions [p0, p0 + n_pos): for each
 // Gaussian, in depth order, the (tile, Gaussian) pairs of its non-saturated
@@ -368,7 +443,7 @@ __global__ void __launch_bounds__(256) emit_kernel(
     int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
     const uint32_t* __restrict__ sorted_val, const uint32_t* __restrict__ offsets,
     const uint32_t* __restrict__ chunk_cnt, const Footprint* __restrict__ foot,
-    const uint8_t* __restrict__ sat, uint32_t* __restrict__ out_key,
+    const uint64_t* __restrict__ sat, uint32_t* __restrict__ out_key,
     uint32_t* __restrict__ out_val, unsigned long long* __restrict__ counters) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -385,20 +460,14 @@ __global__ void __launch_bounds__(256) emit_kernel(
     const int tiles_x = views[v].tiles_x, width = views[v].width;
     const uint32_t base = static_cast<uint32_t>(views[v].tile_base);
     const uint32_t end = off + c;  // never write past this Gaussian's allotment
-    const uint8_t* st = sat + base;
     uint32_t o = off;
     int ty0, ty1;
     footprint_rows(f, &ty0, &ty1);
     for (int ty = ty0; ty <= ty1; ++ty) {
       int tx0, tx1;
       if (!row_span(f, ty, width, &tx0, &tx1)) continue;
-      for (int tx = tx0; tx <= tx1 && o < end; ++tx) {
-        const int t = ty * tiles_x + tx;
-        if (st[t]) continue;
-        out_key[o] = base + static_cast<uint32_t>(t);
-        out_val[o] = g;
-        ++o;
-      }
+      o = emit_free(sat, static_cast<int>(base) + ty * tiles_x + tx0,
+                    static_cast<int>(base) + ty * tiles_x + tx1, g, out_key, out_val, o, end);
     }
     if (o != end) atomicAdd(&counters[kBinningMismatch], 1ull);
   }
@@ -416,7 +485,6 @@ __global__ void __launch_bounds__(256) emit_kernel(
     const uint32_t base = static_cast<uint32_t>(views[v].tile_base);
     int ty0, ty1;
     footprint_rows(f, &ty0, &ty1);
-    const uint8_t* st = sat + base;
     for (int r0 = ty0; r0 <= ty1; r0 += 32) {
       const int ty = r0 + lane;
       int tx0 = 0, tx1 = -1;
@@ -424,22 +492,16 @@ __global__ void __launch_bounds__(256) emit_kernel(
         tx0 = 0;
         tx1 = -1;
       }
-      uint32_t len = 0;
-      for (int tx = tx0; tx <= tx1; ++tx) len += st[ty * tiles_x + tx] ? 0u : 1u;
+      const int ga = static_cast<int>(base) + ty * tiles_x + tx0;
+      const int gb_ = static_cast<int>(base) + ty * tiles_x + tx1;
+      const uint32_t len = tx1 >= tx0 ? count_free(sat, ga, gb_) : 0u;
       uint32_t incl = len;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
       }
-      uint32_t w = ob + incl - len;
-      for (int tx = tx0; tx <= tx1 && w < end; ++tx) {
-        const int t = ty * tiles_x + tx;
-        if (st[t]) continue;
-        out_key[w] = base + static_cast<uint32_t>(t);
-        out_val[w] = gb;
-        ++w;
-      }
+      if (tx1 >= tx0) emit_free(sat, ga, gb_, gb, out_key, out_val, ob + incl - len, end);
       ob += __shfl_sync(0xffffffffu, incl, 31);
     }
     if (lane == 0 && ob != end) atomicAdd(&counters[kBinningMismatch], 1ull);
@@ -483,19 +545,19 @@ cudaError_t launch_project(int64_t n, int n_views, const ViewParams* views, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_depth_tie_fix(int64_t n, const uint32_t* key, uint32_t* val,
+cudaError_t launch_depth_tie_fix(int64_t n_total, int64_t n, const uint32_t* key, uint32_t* val,
                                  const uint32_t* depth_lo, cudaStream_t stream) {
-  if (n < 2) return cudaSuccess;
+  if (n_total < 2) return cudaSuccess;
   const int threads = 256;
-  const int64_t blocks = (n + threads - 1) / threads;
-  depth_tie_fix_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(n, key, val,
+  const int64_t blocks = (n_total + threads - 1) / threads;
+  depth_tie_fix_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(n_total, n, key, val,
                                                                               depth_lo);
   return cudaGetLastError();
 }
 
 cudaError_t launch_chunk_count(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
                                const uint32_t* sorted_val, const uint32_t* cnt,
-                               const Footprint* foot, const uint8_t* sat, uint32_t* out_cnt,
+                               const Footprint* foot, const uint64_t* sat, uint32_t* out_cnt,
                                cudaStream_t stream) {
   if (n_pos == 0) return cudaSuccess;
   const int threads = 256;
@@ -507,7 +569,7 @@ cudaError_t launch_chunk_count(int64_t p0, int64_t n_pos, int64_t n, const ViewP
 
 cudaError_t launch_emit(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
                         const uint32_t* sorted_val, const uint32_t* offsets,
-                        const uint32_t* chunk_cnt, const Footprint* foot, const uint8_t* sat,
+                        const uint32_t* chunk_cnt, const Footprint* foot, const uint64_t* sat,
                         uint32_t* out_key, uint32_t* out_val, unsigned long long* counters,
                         cudaStream_t stream) {
   if (n_pos == 0) return cudaSuccess;
