@@ -509,7 +509,8 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
       FS_TRY(c->sort_tmp.ensure(fs::radix_temp_bytes(std::max<int64_t>(I, kcap)), "sort temp"));
       c->stats.kernel_launches += 3 + radix_launches(I, tile_bits);
       FS_CUDA(fs::launch_emit(p0, n_pos, n, vd, sorted_val, c->offs.as<uint32_t>(),
-                              c->ccnt.as<uint32_t>(), c->foot.as<fs::Footprint>(), sat,
+                              c->ccnt.as<uint32_t>(), c->cnt.as<uint32_t>(),
+                              c->foot.as<fs::Footprint>(), sat,
                               c->lk_a.as<uint32_t>(), c->lv_a.as<uint32_t>(), ctr, stream),
               "emit");
       bool alt2 = false;

@@ -47,9 +47,9 @@ cudaError_t launch_chunk_count(int64_t p0, int64_t n_pos, int64_t n, const ViewP
                                cudaStream_t stream);
 cudaError_t launch_emit(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
                         const uint32_t* sorted_val, const uint32_t* offsets,
-                        const uint32_t* chunk_cnt, const Footprint* foot, const uint64_t* sat,
-                        uint32_t* out_key, uint32_t* out_val, unsigned long long* counters,
-                        cudaStream_t stream);
+                        const uint32_t* chunk_cnt, const uint32_t* cnt, const Footprint* foot,
+                        const uint64_t* sat, uint32_t* out_key, uint32_t* out_val,
+                        unsigned long long* counters, cudaStream_t stream);
 cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
                           cudaStream_t stream);
 

@@ -275,7 +275,8 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
                        "fs_solve_noalloc: a view needs more than FS_NOALLOC_MAX_LIST_ENTRIES "
                        "(tile, Gaussian) pairs in one depth chunk; the table is incomplete");
       if (I > 0) {
-        NA_CUDA(launch_emit(p0, n_pos, n, vd, sval, offs, ccnt, foot, sat, lk_a, lv_a, ctr, strm),
+        NA_CUDA(launch_emit(p0, n_pos, n, vd, sval, offs, ccnt, cnt, foot, sat, lk_a, lv_a, ctr,
+                            strm),
                 "emit");
         bool alt2 = false;
         NA_CUDA(radix_sort_pairs(lk_a, lv_a, lk_b, lv_b, I, bits_for(tiles), sort_tmp, &alt2, strm),

@@ -353,65 +353,114 @@ __global__ void depth_tie_fix_kernel(int64_t n_total, int64_t n, const uint32_t*
   }
 }
 
-// Number of list entries of sorted positions [p0, p0 + n_pos) that fall on
-// tiles not yet saturated.  Footprints spanning many tile rows are counted by
-// the whole warp, one row per lane, so one large Gaussian does not hold up
-// the 31 others of its warp.
-constexpr int kBigRows = 12;
+// ---------------------------------------------------------------------------
+// Per depth chunk: count and emit the (tile, Gaussian) entries of sorted
+// positions [p0, p0 + n_pos) on tiles not yet saturated.  A warp takes 32
+// consecutive positions and spreads all of their tile rows over its lanes,
+// one (Gaussian, row) per lane per round, so large footprints do not hold up
+// small ones.  The owner of row r is found by a binary search over the
+// lanes' inclusive row counts.
+// ---------------------------------------------------------------------------
+
+struct RowJob {
+  uint32_t g;      // slot of the owning Gaussian (view * n + index)
+  int row;         // tile row
+  int owner;       // lane that holds the owning Gaussian
+  bool ok;         // r < R
+};
+
+// Every lane of the warp must call this (it shuffles).
+__device__ __forceinline__ RowJob row_job(int r, int R, uint32_t incl_rows, uint32_t g_lane,
+                                          int ty0_lane) {
+  // owner = number of lanes whose inclusive row count is <= r
+  int lo = 0;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const uint32_t v = __shfl_sync(0xffffffffu, incl_rows, lo + s - 1);
+    if (v <= static_cast<uint32_t>(r)) lo += s;
+  }
+  const int owner = min(lo, 31);
+  const uint32_t pi = __shfl_sync(0xffffffffu, incl_rows, max(owner - 1, 0));
+  const uint32_t g = __shfl_sync(0xffffffffu, g_lane, owner);
+  const int ty0 = __shfl_sync(0xffffffffu, ty0_lane, owner);
+  RowJob j;
+  j.ok = r < R;
+  j.g = g;
+  j.owner = owner;
+  j.row = ty0 + (r - static_cast<int>(owner > 0 ? pi : 0u));
+  return j;
+}
+
+// Unsaturated tiles of one job's row: [a, b] (global ids) and their number.
+__device__ __forceinline__ uint32_t job_free(const RowJob& jb, int64_t n,
+                                             const ViewParams* __restrict__ views,
+                                             const Footprint* __restrict__ foot,
+                                             const uint64_t* __restrict__ sat, int* a, int* b) {
+  *a = 0;
+  *b = -1;
+  if (!jb.ok) return 0;
+  const int v = static_cast<int>(jb.g / static_cast<uint32_t>(n));
+  const Footprint f = foot[jb.g];
+  int tx0, tx1;
+  if (!row_span(f, jb.row, views[v].width, &tx0, &tx1)) return 0;
+  const int base = views[v].tile_base + jb.row * views[v].tiles_x;
+  *a = base + tx0;
+  *b = base + tx1;
+  return count_free(sat, *a, *b);
+}
+
+__device__ __forceinline__ void lane_rows(int64_t j, int64_t n_pos, int64_t p0,
+                                          const uint32_t* __restrict__ sorted_val,
+                                          const uint32_t* __restrict__ cnt,
+                                          const Footprint* __restrict__ foot, uint32_t* g,
+                                          int* ty0, uint32_t* nrows) {
+  *g = 0;
+  *ty0 = 0;
+  *nrows = 0;
+  if (j < n_pos) {
+    *g = sorted_val[p0 + j];
+    if (cnt[*g] > 0) {
+      int t0, t1;
+      footprint_rows(foot[*g], &t0, &t1);
+      *ty0 = t0;
+      *nrows = static_cast<uint32_t>(max(0, t1 - t0 + 1));
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
 
 __global__ void __launch_bounds__(256) chunk_count_kernel(
     int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
     const uint32_t* __restrict__ sorted_val, const uint32_t* __restrict__ cnt,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
     uint32_t* __restrict__ out_cnt) {
+  __shared__ uint32_t s_cnt[8][32];
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  uint32_t g = 0, c = 0;
-  int ty0 = 0, ty1 = -1;
-  Footprint f;
-  if (j < n_pos) {
-    g = sorted_val[p0 + j];
-    if (cnt[g] > 0) {
-      f = foot[g];
-      footprint_rows(f, &ty0, &ty1);
-    }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t g, nrows;
+  int ty0;
+  lane_rows(j, n_pos, p0, sorted_val, cnt, foot, &g, &ty0, &nrows);
+  const uint32_t incl = warp_incl_scan(nrows, lane);
+  const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
+  s_cnt[warp][lane] = 0;
+  __syncwarp();
+  for (int r0 = 0; r0 < R; r0 += 32) {
+    const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
+    int a, b;
+    const uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
+    if (jb.ok && fr) atomicAdd(&s_cnt[warp][jb.owner], fr);
   }
-  const bool big = ty1 - ty0 + 1 > kBigRows;
-  if (!big && ty1 >= ty0) {
-    const int v = static_cast<int>(g / n);
-    const int tiles_x = views[v].tiles_x, width = views[v].width;
-    const int base = views[v].tile_base;
-    for (int ty = ty0; ty <= ty1; ++ty) {
-      int tx0, tx1;
-      if (!row_span(f, ty, width, &tx0, &tx1)) continue;
-      c += count_free(sat, base + ty * tiles_x + tx0, base + ty * tiles_x + tx1);
-    }
-  }
-  uint32_t m = __ballot_sync(0xffffffffu, big);
-  while (m) {
-    const int src = __ffs(m) - 1;
-    m &= m - 1;
-    const uint32_t gb = __shfl_sync(0xffffffffu, g, src);
-    const int v = static_cast<int>(gb / n);
-    const Footprint fb = foot[gb];
-    const int tiles_x = views[v].tiles_x, width = views[v].width;
-    const int base = views[v].tile_base;
-    int r0, r1;
-    footprint_rows(fb, &r0, &r1);
-    uint32_t part = 0;
-    for (int ty = r0 + lane; ty <= r1; ty += 32) {
-      int tx0, tx1;
-      if (row_span(fb, ty, width, &tx0, &tx1))
-        part += count_free(sat, base + ty * tiles_x + tx0, base + ty * tiles_x + tx1);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (lane == src) c = part;
-  }
-  if (j < n_pos) out_cnt[j] = c;
+  __syncwarp();
+  if (j < n_pos) out_cnt[j] = s_cnt[warp][lane];
 }
-
-constexpr uint32_t kBigEmit = 64;  // longer lists are written by a whole warp
 
 // Writes (tile, g) for every unsaturated tile id in [a, b], from position o,
 // never at or past `end`; returns the next position.
@@ -436,76 +485,45 @@ __device__ __forceinline__ uint32_t emit_free(const uint64_t* __restrict__ sat, 
   return o;
 }
 
-// Writes the list entries of sorted positions [p0, p0 + n_pos): for each
-// Gaussian, in depth order, the (tile, Gaussian) pairs of its non-saturated
-// tiles, at offsets[j] (the exclusive scan of chunk_cnt).
+// Writes the list entries of sorted positions [p0, p0 + n_pos) in depth
+// order: the warp's 32 Gaussians own the contiguous output range starting at
+// offsets[first] (the exclusive scan of chunk_cnt); row r's entries start at
+// that base plus the free tiles of all earlier rows of the warp.
 __global__ void __launch_bounds__(256) emit_kernel(
     int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
     const uint32_t* __restrict__ sorted_val, const uint32_t* __restrict__ offsets,
-    const uint32_t* __restrict__ chunk_cnt, const Footprint* __restrict__ foot,
-    const uint64_t* __restrict__ sat, uint32_t* __restrict__ out_key,
-    uint32_t* __restrict__ out_val, unsigned long long* __restrict__ counters) {
+    const uint32_t* __restrict__ chunk_cnt, const uint32_t* __restrict__ cnt,
+    const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
+    uint32_t* __restrict__ out_key, uint32_t* __restrict__ out_val,
+    unsigned long long* __restrict__ counters) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  uint32_t g = 0, c = 0, off = 0;
-  if (j < n_pos) {
-    g = sorted_val[p0 + j];
-    c = chunk_cnt[j];
-    off = offsets[j];
+  uint32_t g, nrows;
+  int ty0;
+  lane_rows(j, n_pos, p0, sorted_val, cnt, foot, &g, &ty0, &nrows);
+  const uint32_t incl = warp_incl_scan(nrows, lane);
+  const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
+  // the warp's output range [wbeg, wend)
+  const int64_t jw = j - lane;  // first position of the warp
+  const int64_t jl = min(jw + 31, n_pos - 1);
+  uint32_t wbeg = 0, wend = 0;
+  if (lane == 0 && jw < n_pos) {
+    wbeg = offsets[jw];
+    wend = offsets[jl] + chunk_cnt[jl];
   }
-  const bool big = c > kBigEmit;
-  if (c > 0 && !big) {
-    const int v = static_cast<int>(g / n);
-    const Footprint f = foot[g];
-    const int tiles_x = views[v].tiles_x, width = views[v].width;
-    const uint32_t base = static_cast<uint32_t>(views[v].tile_base);
-    const uint32_t end = off + c;  // never write past this Gaussian's allotment
-    uint32_t o = off;
-    int ty0, ty1;
-    footprint_rows(f, &ty0, &ty1);
-    for (int ty = ty0; ty <= ty1; ++ty) {
-      int tx0, tx1;
-      if (!row_span(f, ty, width, &tx0, &tx1)) continue;
-      o = emit_free(sat, static_cast<int>(base) + ty * tiles_x + tx0,
-                    static_cast<int>(base) + ty * tiles_x + tx1, g, out_key, out_val, o, end);
-    }
-    if (o != end) atomicAdd(&counters[kBinningMismatch], 1ull);
+  wbeg = __shfl_sync(0xffffffffu, wbeg, 0);
+  wend = __shfl_sync(0xffffffffu, wend, 0);
+  uint32_t carry = 0;
+  for (int r0 = 0; r0 < R; r0 += 32) {
+    const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
+    int a, b;
+    const uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
+    const uint32_t sc = warp_incl_scan(fr, lane);
+    const uint32_t o = wbeg + carry + sc - fr;
+    if (fr) emit_free(sat, a, b, jb.g, out_key, out_val, o, min(o + fr, wend));
+    carry += __shfl_sync(0xffffffffu, sc, 31);
   }
-  // long lists: the warp takes them one at a time, one tile row per lane
-  uint32_t m = __ballot_sync(0xffffffffu, big);
-  while (m) {
-    const int src = __ffs(m) - 1;
-    m &= m - 1;
-    const uint32_t gb = __shfl_sync(0xffffffffu, g, src);
-    uint32_t ob = __shfl_sync(0xffffffffu, off, src);
-    const uint32_t end = ob + __shfl_sync(0xffffffffu, c, src);
-    const int v = static_cast<int>(gb / n);
-    const Footprint f = foot[gb];
-    const int tiles_x = views[v].tiles_x, width = views[v].width;
-    const uint32_t base = static_cast<uint32_t>(views[v].tile_base);
-    int ty0, ty1;
-    footprint_rows(f, &ty0, &ty1);
-    for (int r0 = ty0; r0 <= ty1; r0 += 32) {
-      const int ty = r0 + lane;
-      int tx0 = 0, tx1 = -1;
-      if (ty > ty1 || !row_span(f, ty, width, &tx0, &tx1)) {
-        tx0 = 0;
-        tx1 = -1;
-      }
-      const int ga = static_cast<int>(base) + ty * tiles_x + tx0;
-      const int gb_ = static_cast<int>(base) + ty * tiles_x + tx1;
-      const uint32_t len = tx1 >= tx0 ? count_free(sat, ga, gb_) : 0u;
-      uint32_t incl = len;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      if (tx1 >= tx0) emit_free(sat, ga, gb_, gb, out_key, out_val, ob + incl - len, end);
-      ob += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (lane == 0 && ob != end) atomicAdd(&counters[kBinningMismatch], 1ull);
-  }
+  if (lane == 0 && jw < n_pos && wbeg + carry != wend) atomicAdd(&counters[kBinningMismatch], 1ull);
 }
 
 // [start, end) of every tile's run in the tile-sorted list.
@@ -569,14 +587,15 @@ cudaError_t launch_chunk_count(int64_t p0, int64_t n_pos, int64_t n, const ViewP
 
 cudaError_t launch_emit(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
                         const uint32_t* sorted_val, const uint32_t* offsets,
-                        const uint32_t* chunk_cnt, const Footprint* foot, const uint64_t* sat,
-                        uint32_t* out_key, uint32_t* out_val, unsigned long long* counters,
-                        cudaStream_t stream) {
+                        const uint32_t* chunk_cnt, const uint32_t* cnt, const Footprint* foot,
+                        const uint64_t* sat, uint32_t* out_key, uint32_t* out_val,
+                        unsigned long long* counters, cudaStream_t stream) {
   if (n_pos == 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = (n_pos + threads - 1) / threads;
   emit_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-      p0, n_pos, n, views, sorted_val, offsets, chunk_cnt, foot, sat, out_key, out_val, counters);
+      p0, n_pos, n, views, sorted_val, offsets, chunk_cnt, cnt, foot, sat, out_key, out_val,
+      counters);
   return cudaGetLastError();
 }
 

@@ -1,12 +1,10 @@
 // Device exclusive scan and stable LSD radix sort of (uint32 key, uint32 value)
 // pairs, used for the depth order and the tile binning of Sec. 3.1.
 //
-// Both work on tiles of 4096 elements per 256-thread block, processed as 16
-// coalesced rounds of 256.  The radix sort is the classic three-step pass
-// (per-block digit histogram, scan of the histogram in digit-major order,
-// stable scatter); within a round, equal digits are ranked with a warp match
-// and per-warp counts, so equal keys keep their input order.  No step waits
-// on another block.
+// Both work on tiles of 4096 elements per 256-thread block.  The radix sort
+// is the classic three-step pass (per-block digit histogram, scan of the
+// histogram in digit-major order, stable scatter).  No step waits on another
+// block.
 #include "fs_internal.h"
 
 namespace fs {
@@ -128,70 +126,69 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint32_t* __
   hist[static_cast<int64_t>(threadIdx.x) * nb + blockIdx.x] = s_h[threadIdx.x];
 }
 
-// Stable scatter of one radix pass.  The block first ranks its tile of
-// elements by digit (warp match + per-warp counts per round of 256, so equal
-// digits keep their input order), places them digit-sorted in shared memory,
-// then writes each digit's run to its global offset with consecutive threads
-// on consecutive addresses.
+// Stable scatter of one radix pass.  Each warp ranks its 512 elements (16
+// coalesced columns of 32) by digit with a warp match per column and per-warp
+// digit counters, so equal digits keep their input order; the block then
+// turns (digit, warp) counts into local offsets, places its 4096 elements
+// digit-sorted in shared memory and writes each digit's run to its global
+// offset with consecutive threads on consecutive addresses.
 __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
     const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n, int shift,
     int64_t nb, const uint32_t* __restrict__ hist_pre, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out) {
   __shared__ uint32_t s_key[kTileElems];
   __shared__ uint32_t s_val[kTileElems];
-  __shared__ uint32_t s_loc[kRadix];    // local start of each digit's run
-  __shared__ uint32_t s_run[kRadix];    // running local position per digit
-  __shared__ uint32_t s_glob[kRadix];   // global start of this block's run per digit
-  __shared__ uint32_t s_wcnt[kWarps][kRadix];
+  __shared__ uint32_t s_wcnt[kWarps][kRadix];  // per-warp digit counts, then warp prefixes
+  __shared__ uint32_t s_loc[kRadix];           // local start of each digit's run
+  __shared__ uint32_t s_glob[kRadix];          // global start of this block's run per digit
   __shared__ uint32_t s_warp[kWarps];
-  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTileElems;
   const int n_here = static_cast<int>(min(static_cast<int64_t>(kTileElems), n - base));
-
-  // local digit histogram and its exclusive scan
-  s_run[threadIdx.x] = 0;
+  const int wbase = warp * (kTileElems / kWarps);  // 512 elements per warp
 #pragma unroll
-  for (int w = 0; w < kWarps; ++w) s_wcnt[w][threadIdx.x] = 0;
+  for (int k = 0; k < kRadix / 32; ++k) s_wcnt[warp][lane + 32 * k] = 0;
+  __syncwarp();
+
+  const uint32_t lt = lanemask_lt();
+  uint32_t key[kRounds], rank[kRounds];
+#pragma unroll
+  for (int i = 0; i < kRounds; ++i) {
+    const int j = wbase + i * 32 + lane;
+    const bool ok = j < n_here;
+    key[i] = ok ? keys[base + j] : 0u;
+    const uint32_t d = ok ? ((key[i] >> shift) & 0xFFu) : 0x100u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t before = ok ? s_wcnt[warp][d] : 0u;
+    rank[i] = before + __popc(peers & lt);
+    __syncwarp();
+    if (ok && (peers & lt) == 0) s_wcnt[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
   __syncthreads();
-  for (int j = threadIdx.x; j < n_here; j += kThreads)
-    atomicAdd(&s_run[(keys[base + j] >> shift) & 0xFFu], 1u);
-  __syncthreads();
+  // per digit (thread t): warp prefixes, then the block-wide digit offsets
+  uint32_t running = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const uint32_t c = s_wcnt[w][threadIdx.x];
+    s_wcnt[w][threadIdx.x] = running;
+    running += c;
+  }
   uint32_t tot;
-  const uint32_t loc = block_exclusive_scan(s_run[threadIdx.x], s_warp, &tot);
-  s_loc[threadIdx.x] = loc;
-  s_run[threadIdx.x] = loc;
+  s_loc[threadIdx.x] = block_exclusive_scan(running, s_warp, &tot);
   s_glob[threadIdx.x] = hist_pre[static_cast<int64_t>(threadIdx.x) * nb + blockIdx.x];
   __syncthreads();
-
-  // stable local placement, round by round
-  const uint32_t lt = lanemask_lt();
-  for (int r = 0; r * kThreads < n_here; ++r) {  // block-uniform
-    const int j = r * kThreads + threadIdx.x;
-    const bool ok = j < n_here;
-    const uint32_t k = ok ? keys[base + j] : 0u;
-    const uint32_t v = ok ? vals[base + j] : 0u;
-    const uint32_t d = ok ? ((k >> shift) & 0xFFu) : 0x100u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t lrank = __popc(peers & lt);
-    if (ok && lrank == 0) s_wcnt[warp][d] = __popc(peers);
-    __syncthreads();
-    if (ok) {
-      uint32_t pos = s_run[d] + lrank;
-      for (int w = 0; w < warp; ++w) pos += s_wcnt[w][d];
-      s_key[pos] = k;
-      s_val[pos] = v;
-    }
-    __syncthreads();
-    uint32_t sum = 0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      sum += s_wcnt[w][threadIdx.x];
-      s_wcnt[w][threadIdx.x] = 0;
+  for (int i = 0; i < kRounds; ++i) {
+    const int j = wbase + i * 32 + lane;
+    if (j < n_here) {
+      const uint32_t d = (key[i] >> shift) & 0xFFu;
+      const uint32_t pos = s_loc[d] + s_wcnt[warp][d] + rank[i];
+      s_key[pos] = key[i];
+      s_val[pos] = vals[base + j];
     }
-    s_run[threadIdx.x] += sum;
-    __syncthreads();
   }
-
+  __syncthreads();
   // coalesced write-out of the digit runs
   for (int j = threadIdx.x; j < n_here; j += kThreads) {
     const uint32_t k = s_key[j];
