@@ -51,7 +51,10 @@ def parse():
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample-views", type=int, default=2)
+    ap.add_argument("--cpu-sample-views", type=int, default=12)
+    ap.add_argument("--recheck-margin", type=float, default=0.0,
+                    help="FP64 re-check of decisions with a margin below this (0: library "
+                         "default 1e-4; negative: off)")
     return ap.parse_args()
 
 
@@ -145,7 +148,7 @@ def run_flashsplat(args, rank, world, local_rank):
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     solver = fsb.Solver(w.gaussians, device=local_rank, views_per_batch=args.views_per_batch,
-                        time_stages=True)
+                        time_stages=True, recheck_margin=args.recheck_margin)
     dmasks = solver.upload_masks(w.masks)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
@@ -168,6 +171,7 @@ def run_flashsplat(args, rank, world, local_rank):
     clocks = ClockSampler(uuid)
     torch.cuda.synchronize(dev)
     ms_steps, blend_ms, pairs, launches, blend_launches, entries, staged = [], 0.0, 0, 0, 0, 0, 0
+    rechecked, recheck_pairs = 0, 0
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
         flush.fill_(1)                       # evict the previous step's data from L2
@@ -183,6 +187,8 @@ def run_flashsplat(args, rank, world, local_rank):
         pairs += st.pairs
         entries += st.list_entries
         staged += st.staged_entries
+        rechecked += st.rechecked
+        recheck_pairs += st.recheck_pairs
         launches += st.kernel_launches
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter() - t_wall0
@@ -269,6 +275,10 @@ def run_flashsplat(args, rank, world, local_rank):
                                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                       "wall_s_timed": t_wall}),
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "clocks": clk,
+        "near_tie_recheck": {"margin_below": (args.recheck_margin if args.recheck_margin > 0 else
+                                              1e-4 if args.recheck_margin == 0 else None),
+                             "gaussians_per_step": rechecked // max(1, args.steps),
+                             "fp64_pairs_per_step": recheck_pairs // max(1, args.steps)},
     }
     solver.close()
     return line, w

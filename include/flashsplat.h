@@ -77,7 +77,18 @@ typedef struct fs_options {
   int32_t views_per_batch;  /* views binned and blended per launch group (default 16) */
   int32_t time_stages;      /* non-zero: time every blend launch with CUDA events */
   int32_t depth_chunks;     /* front-to-back binning chunks per batch (default 4, 1 = off) */
-  int32_t reserved[13];
+  /* fs_solve re-evaluates in FP64 every Gaussian whose FP32 decision margin
+   * (see fs_assign) is below this value (default 1e-4 when 0; negative = off).
+   * The FP32 table's entries are within ~1e-5 relative of exact, which moves
+   * a margin by at most ~2e-5; 1e-4 leaves a factor of five.
+   * Larger values re-check more Gaussians; a value above every margin
+   * re-renders every seen Gaussian's contributions in FP64. */
+  float recheck_margin;
+  /* 0: keep each view's projection resident for the re-check when device
+   * memory allows (about 108 B per Gaussian and view), else project again;
+   * 1: always project again. */
+  int32_t recheck_reproject;
+  int32_t reserved[11];
 } fs_options;
 
 /* A Gaussian scene (Sec. 3.1: G_i = {m_i, q_i, s_i, o_i}; colour unused). */
@@ -112,7 +123,9 @@ typedef struct fs_stats {
   double blend_ms;         /* summed blend time (fs_options.time_stages), else 0 */
   int64_t blend_launches;  /* blend launches timed */
   int64_t staged_entries;  /* list entries the blend staged before its tiles saturated */
-  int64_t reserved[3];
+  int64_t rechecked;       /* Gaussians re-evaluated in FP64 by fs_solve */
+  int64_t recheck_pairs;   /* (pixel, list entry) pairs the re-check evaluated */
+  int64_t recheck_rebinned;/* view batches the re-check binned anew (see fs_solve) */
 } fs_stats;
 
 /* Outputs of fs_solve.  Any pointer may be NULL to skip that output. */
@@ -204,12 +217,25 @@ fs_status fs_assign(fs_ctx* ctx, const void* table, int32_t table_dtype, int64_t
 
 /*
  * fs_solve -- the whole path: clear a table, fs_accumulate all views, then
- * fs_assign with gamma (Sec. 3.2-3.3).  Outputs go where `out` says
- * (out->memory: device buffers, or host buffers filled by asynchronous
- * copies on `stream` -- pinned host memory keeps them asynchronous).  When
- * out->table is NULL the table lives in the context's workspace.
- * Asynchronous; call fs_synchronize before reading host outputs.
- * Errors: as fs_accumulate and fs_assign.
+ * fs_assign with gamma (Sec. 3.2-3.3), then re-check near ties.  The blend
+ * runs in FP32, so a Gaussian whose decision margin is within the table's
+ * FP32 error of zero (relative error ~1e-5) could be labelled differently
+ * from an exact evaluation.  Every Gaussian whose margin is below
+ * fs_options.recheck_margin is therefore re-evaluated: every pixel its
+ * footprint reaches, in every view, is composited again front to back at
+ * about 1e-11 relative precision (float-pair arithmetic: alpha, T, the 1/255
+ * and 1e-4 decisions; FP64 sums), its table row is replaced by those sums
+ * (rounded to the table's type) and its bits/label/margin are decided again
+ * from them in FP64.  The depth-ordered tile lists of the main pass are kept
+ * for this when device memory allows (about 4 B per list entry); a view
+ * batch whose kept lists end before an exact walk does is binned anew
+ * (counted in fs_stats.recheck_rebinned).
+ * Outputs go where `out` says (out->memory: device buffers, or host buffers
+ * filled by asynchronous copies on `stream` -- pinned host memory keeps them
+ * asynchronous).  When out->table is NULL the table lives in the context's
+ * workspace.  The call reads counts back between steps and so returns after
+ * the device work is queued; call fs_synchronize before reading host
+ * outputs.  Errors: as fs_accumulate and fs_assign.
  */
 fs_status fs_solve(fs_ctx* ctx, const fs_scene* scene, const fs_camera* cams, int32_t n_views,
                    const void* const* masks, int32_t mask_dtype, int32_t mask_memory, int32_t E,

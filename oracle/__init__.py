@@ -70,7 +70,7 @@ def _load():
     i64, i32, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
     lib.fso_accumulate.restype = ctypes.c_int
     lib.fso_accumulate.argtypes = [i64, vp, vp, vp, vp, i32, vp, vp, vp, i32, vp, i64, i32, i32,
-                                   vp, vp, vp, vp, vp]
+                                   vp, vp, vp, vp, vp, ctypes.c_double]
     lib.fso_pixel_lists.restype = ctypes.c_int64
     lib.fso_pixel_lists.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, i64, vp, vp, vp, vp]
     lib.fso_project_view.restype = ctypes.c_int
@@ -118,12 +118,16 @@ class Accumulation:
 
 
 def accumulate(gaussians, cams, masks, E: int, sel=None, cull_mode: int = 0,
-               nthreads: int | None = None, want_t_final: bool = False) -> Accumulation:
+               nthreads: int | None = None, want_t_final: bool = False,
+               event_rel: float = 1e-4) -> Accumulation:
     """Contribution table of Eq. 6 / Eq. 7 in FP64.
 
     gaussians: dict with mean [N,3], quat [N,4] (w,x,y,z), scale [N,3] (linear),
     opacity [N] (activated).  cams: list of camera dicts.  masks: list of V
     integer arrays [H, W].  sel: optional sorted Gaussian indices to track.
+    event_rel: relative window around the 1/255 and 1e-4 thresholds inside
+    which a decision counts as marginal in `risk` (1e-4 suits an FP32
+    implementation; an FP64 one is compared with a far narrower window).
     """
     lib = _load()
     mean = _f32(gaussians["mean"], 3)
@@ -162,7 +166,8 @@ def accumulate(gaussians, cams, masks, E: int, sel=None, cull_mode: int = 0,
     rc = lib.fso_accumulate(N, _ptr(mean), _ptr(quat), _ptr(scale), _ptr(opac), V, carr,
                             _ptr(allm), _ptr(offs), E, _ptr(sel),
                             0 if sel is None else sel.size, cull_mode, nthreads,
-                            _ptr(table), _ptr(risk), _ptr(flags), _ptr(tf), _ptr(stats))
+                            _ptr(table), _ptr(risk), _ptr(flags), _ptr(tf), _ptr(stats),
+                            float(event_rel))
     if rc != 0:
         raise ValueError(f"fso_accumulate failed with code {rc}")
     return Accumulation(table, risk, flags[:rows], None if tf is None else tf[:acc],

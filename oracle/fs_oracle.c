@@ -47,14 +47,15 @@
 #define FSO_LOWPASS 0.3
 #define FSO_BIN 8
 
-/* Near-threshold windows (relative) used to flag discrete decisions that a
- * lower-precision implementation may legitimately take the other way.  An FP32
- * tile rasteriser evaluates the exponent of a thin Gaussian (0.55 px wide)
- * across a 16-px tile with an absolute error of ~2e-5, i.e. alpha to ~1e-5
- * relative near the 1/255 cut, and T after hundreds of factors to ~1e-5; the
- * windows are set an order of magnitude wider than that. */
+/* Default near-threshold window (relative) used to flag discrete decisions
+ * that a lower-precision implementation may legitimately take the other way.
+ * An FP32 tile rasteriser evaluates the exponent of a thin Gaussian (0.55 px
+ * wide) across a 16-px tile with an absolute error of ~2e-5, i.e. alpha to
+ * ~1e-5 relative near the 1/255 cut, and T after hundreds of factors to
+ * ~1e-5; the window is set an order of magnitude wider than that.  Callers
+ * comparing against an FP64 evaluation pass a much narrower window (the
+ * window only shapes the risk bookkeeping, never the table itself). */
 #define FSO_EVENT_REL 1e-4
-#define FSO_T_EVENT_REL 1e-4
 /* Depths are view-space z in double precision; two Gaussians whose depths
  * agree to 1e-12 relative may be ordered either way by an implementation that
  * computes z with other rounding. */
@@ -208,7 +209,7 @@ typedef struct {
  * the oracle does not add but another walk could are listed with c = 0.
  * `use_bbox` skips candidates whose pixel bounding box excludes the pixel. */
 static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use_bbox,
-                      int px_i, int py_i, fso_hit* hits, double* t_final,
+                      int px_i, int py_i, double ev_rel, fso_hit* hits, double* t_final,
                       int64_t* n_eval) {
   const double px = px_i + 0.5, py = py_i + 0.5;
   double T = 1.0;
@@ -227,10 +228,10 @@ static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use
     const double power = -0.5 * (p->ca * dx * dx + p->cc * dy * dy) - p->cb * dx * dy;
     double alpha = p->opacity * exp(power);
     if (alpha > FSO_ALPHA_MAX) alpha = FSO_ALPHA_MAX;
-    const int a_edge = fabs(alpha - FSO_ALPHA_MIN) <= FSO_EVENT_REL * FSO_ALPHA_MIN;
+    const int a_edge = fabs(alpha - FSO_ALPHA_MIN) <= ev_rel * FSO_ALPHA_MIN;
     if (stopped) {
       /* Beyond a marginal stop: another walk may keep adding terms. */
-      if (alpha >= FSO_ALPHA_MIN * (1.0 - FSO_EVENT_REL)) {
+      if (alpha >= FSO_ALPHA_MIN * (1.0 - ev_rel)) {
         hits[nh].g = g; hits[nh].c = 0.0;
         hits[nh].risk = alpha * T_shadow * (1.0 + down) + 1e-300;
         hits[nh].flag = FSO_FLAG_DOWNSTREAM | (a_edge ? FSO_FLAG_ALPHA_EDGE : 0);
@@ -253,7 +254,7 @@ static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use
     /* T itself is uncertain by the relative amount `down` after marginal
      * alpha decisions earlier in this pixel, so the stop test is marginal
      * within that much more. */
-    const int t_edge = fabs(test_T - FSO_T_MIN) <= (FSO_T_EVENT_REL + 1.01 * down) * FSO_T_MIN;
+    const int t_edge = fabs(test_T - FSO_T_MIN) <= (ev_rel + 1.01 * down) * FSO_T_MIN;
     if (test_T < FSO_T_MIN) {
       if (t_edge || all_risky) {
         /* the stop may not happen in another walk: this term and all
@@ -410,6 +411,7 @@ typedef struct {
   const uint8_t* pix_sel;   /* NULL or per-pixel "walk this pixel" */
   int32_t E;
   int cull_mode;
+  double ev_rel;            /* near-threshold window (relative) */
   int nthreads, tid;
   double* t_final;          /* this view's slice or NULL */
   /* per thread */
@@ -438,7 +440,8 @@ static void* acc_worker(void* arg) {
         n = j->vi->bin_start[b + 1] - j->vi->bin_start[b];
       }
       double tf;
-      const int nh = walk_pixel(j->P, cand, n, j->cull_mode != 1, x, y, j->hits, &tf, &j->n_eval);
+      const int nh = walk_pixel(j->P, cand, n, j->cull_mode != 1, x, y, j->ev_rel, j->hits, &tf,
+                                &j->n_eval);
       if (j->t_final) j->t_final[pix] = tf;
       const int32_t lab = j->mask[pix];
       const int lab_ok = (lab >= 0 && lab < j->E);
@@ -473,6 +476,8 @@ static void* acc_worker(void* arg) {
  *        the pixel was not walked)
  *   stats[4]: evaluated pairs, contributing pairs, pixels with bad labels,
  *        tracked Gaussians that were never valid in any view
+ *   event_rel: relative window around the 1/255 and 1e-4 thresholds inside
+ *        which a decision is counted as marginal in `risk` (<= 0: 1e-4)
  * Returns 0, or -1 on a zero quaternion, -2 on bad arguments.
  */
 int fso_accumulate(int64_t N, const float* mean, const float* quat, const float* scale,
@@ -480,8 +485,9 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
                    const int32_t* masks, const int64_t* mask_offsets, int32_t E,
                    const int64_t* sel, int64_t n_sel, int32_t cull_mode, int32_t nthreads,
                    double* table, double* risk, uint8_t* flags, double* t_final,
-                   int64_t* stats) {
+                   int64_t* stats, double event_rel) {
   if (N < 0 || V < 0 || E < 1 || (sel && n_sel < 0)) return -2;
+  if (!(event_rel > 0.0)) event_rel = FSO_EVENT_REL;
   if (nthreads < 1) nthreads = 1;
   const int64_t rows = sel ? n_sel : N;
   int64_t* slot = NULL;
@@ -546,6 +552,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
       acc_job* j = &jobs[t];
       j->P = P; j->vi = &vi; j->cam = cam; j->mask = masks + mask_offsets[v];
       j->slot = slot; j->pix_sel = pix_sel; j->E = E; j->cull_mode = cull_mode;
+      j->ev_rel = event_rel;
       j->nthreads = nthreads; j->tid = t;
       j->t_final = t_final ? t_final + pix_base : NULL;
       j->hits = (fso_hit*)malloc(sizeof(fso_hit) * (size_t)(max_cand > 0 ? max_cand : 1));
@@ -615,7 +622,8 @@ int64_t fso_pixel_lists(int64_t N, const float* mean, const float* quat, const f
           n = vi.bin_start[b + 1] - vi.bin_start[b];
         }
         double tf;
-        const int nh = walk_pixel(P, cand, n, cull_mode != 1, x, y, hits, &tf, &n_eval);
+        const int nh = walk_pixel(P, cand, n, cull_mode != 1, x, y, FSO_EVENT_REL, hits, &tf,
+                                &n_eval);
         pix_offsets[pix] = total;
         if (t_final) t_final[pix] = tf;
         for (int h = 0; h < nh; ++h) {

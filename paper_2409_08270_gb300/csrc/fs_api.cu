@@ -170,6 +170,17 @@ struct fs_ctx {
   DevBuf views, rec, foot, cnt, key_a, val_a, key_b, val_b, offs, ccnt, dlo, state, sat, subsat;
   DevBuf lk_a, lv_a, lk_b, lv_b, ranges, sort_tmp, scan_tmp, total, counters;
   DevBuf mask_stage, table_tmp, bits_tmp, label_tmp, margin_tmp;
+  // near-tie re-check: resident per-view depth keys, flagged set, FP64 rows
+  float recheck_margin = 1e-4f;  // <= 0: off
+  bool recheck_reproject = false;
+  DevBuf dkey, rk_flag, rk_offs, rk_F, rk_map, rk_R, rk_Rb;
+  // the main pass's tile lists, kept for the re-check (see kept_layout)
+  bool kl_valid = false;
+  int kl_chunks = 1;
+  std::vector<DevBuf> kl_val;
+  std::vector<int64_t> kl_tile_off;
+  DevBuf kl_ranges, kl_satc, kl_bound;
+  std::vector<const void*> mask_dev;  // device pointer of every view's mask (last solve)
   HostBuf views_host, total_host, counters_host;
   fs_stats stats{};
   int scenes = 0;
@@ -208,6 +219,11 @@ fs_status fs_create(fs_ctx** out, int32_t device, const fs_options* opt) {
     c->views_per_batch = std::min(opt->views_per_batch, fs::kMaxViewsPerBatch);
   c->time_stages = opt && opt->time_stages;
   if (opt && opt->depth_chunks > 0) c->depth_chunks = std::min(opt->depth_chunks, 16);
+  if (opt && opt->recheck_margin != 0.f)
+    c->recheck_margin = opt->recheck_margin > 0.f ? opt->recheck_margin : 0.f;
+  if (opt && !(opt->recheck_margin == opt->recheck_margin))
+    c->recheck_margin = 0.f;  // NaN: off
+  c->recheck_reproject = opt && opt->recheck_reproject;
   DeviceGuard g(device);
   fs_status st;
   if ((st = c->views.ensure(sizeof(fs::ViewParams) * fs::kMaxViewsPerBatch, "views")) != FS_OK ||
@@ -233,7 +249,10 @@ fs_status fs_destroy(fs_ctx* c) {
   DevBuf* bufs[] = {&c->subsat, &c->ccnt, &c->dlo, &c->state, &c->sat, &c->views, &c->rec, &c->foot, &c->cnt, &c->key_a, &c->val_a, &c->key_b,
                     &c->val_b, &c->offs, &c->lk_a, &c->lv_a, &c->lk_b, &c->lv_b, &c->ranges,
                     &c->sort_tmp, &c->scan_tmp, &c->total, &c->counters, &c->mask_stage,
-                    &c->table_tmp, &c->bits_tmp, &c->label_tmp, &c->margin_tmp};
+                    &c->table_tmp, &c->bits_tmp, &c->label_tmp, &c->margin_tmp,
+                    &c->dkey, &c->rk_flag, &c->rk_offs, &c->rk_F, &c->rk_map, &c->rk_R,
+                    &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_bound};
+  for (DevBuf& b : c->kl_val) b.release();
   for (DevBuf* b : bufs) b->release();
   c->views_host.release();
   c->total_host.release();
@@ -372,21 +391,86 @@ void fill_view(const fs_camera& cam, fs::ViewParams* vp) {
   vp->tiles_y = (cam.height + fs::kTile - 1) / fs::kTile;
 }
 
-fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t V,
-                          const void* const* masks, int32_t mask_dtype, int32_t mask_memory,
-                          int32_t E, void* table, int32_t table_dtype, cudaStream_t stream) {
-  const int64_t n = s->n;
-  if (n == 0 || V == 0) return FS_OK;
-  int vb = c->views_per_batch;
-  // (view, Gaussian) slots of one batch must fit in 31 bits
-  const int64_t max_vb = ((static_cast<int64_t>(1) << 31) - 1) / n;
-  if (max_vb < 1) return fail(FS_UNSUPPORTED, "fs_accumulate: scene too large");
-  vb = static_cast<int>(std::min<int64_t>(vb, max_vb));
+// Per-view mask device pointers for views [0, V).  Host masks are staged in
+// one buffer that holds every view, so a later pass can read them again.
+fs_status stage_masks(fs_ctx* c, const fs_camera* cams, int32_t V, const void* const* masks,
+                      int32_t mask_dtype, int32_t mask_memory, cudaStream_t stream) {
   const size_t msize = dtype_size(mask_dtype);
+  c->mask_dev.assign(V, nullptr);
+  if (mask_memory == FS_MEM_DEVICE) {
+    for (int v = 0; v < V; ++v) c->mask_dev[v] = masks[v];
+    return FS_OK;
+  }
+  size_t total = 0;
+  for (int v = 0; v < V; ++v)
+    total += ((static_cast<size_t>(cams[v].width) * cams[v].height * msize) + 255) & ~size_t(255);
+  FS_TRY(c->mask_stage.ensure(total > 0 ? total : 256, "mask staging"));
+  size_t off = 0;
+  for (int v = 0; v < V; ++v) {
+    const size_t mbytes = static_cast<size_t>(cams[v].width) * cams[v].height * msize;
+    char* dst = c->mask_stage.as<char>() + off;
+    FS_CUDA(cudaMemcpyAsync(dst, masks[v], mbytes, cudaMemcpyHostToDevice, stream), "mask upload");
+    c->mask_dev[v] = dst;
+    off += (mbytes + 255) & ~size_t(255);
+  }
+  return FS_OK;
+}
+
+// The view parameters of views [v0, v0 + nb) (host copy in c->views_host).
+struct BatchLayout {
+  int total_tiles = 0;
+  int max_tiles = 0;
+  int64_t pixels = 0;
+};
+
+BatchLayout layout_batch(fs_ctx* c, const fs_camera* cams, int32_t v0, int nb) {
+  fs::ViewParams* vh = c->views_host.as<fs::ViewParams>();
+  BatchLayout L;
+  for (int k = 0; k < nb; ++k) {
+    fill_view(cams[v0 + k], &vh[k]);
+    vh[k].tile_base = L.total_tiles;
+    vh[k].state_off = L.pixels;
+    vh[k].mask = c->mask_dev[v0 + k];
+    const int nt = vh[k].tiles_x * vh[k].tiles_y;
+    L.total_tiles += nt;
+    L.max_tiles = std::max(L.max_tiles, nt);
+    L.pixels += static_cast<int64_t>(cams[v0 + k].width) * cams[v0 + k].height;
+  }
+  return L;
+}
+
+// Views per batch: (view, Gaussian) slots of one batch must fit in 31 bits.
+int batch_views(const fs_ctx* c, int64_t n) {
+  const int64_t max_vb = ((static_cast<int64_t>(1) << 31) - 1) / n;
+  return static_cast<int>(std::min<int64_t>(c->views_per_batch, max_vb));
+}
+
+// Projection storage of a batch: either the batch window (slot = view in
+// batch * n + i) or, when `keep` is set, the slice of a buffer that holds
+// every view of the solve, so the near-tie re-check can read it again.
+struct ProjPtrs {
+  fs::ProjRecord* rec;
+  fs::Footprint* foot;
+  uint32_t* cnt;
+  uint32_t* dlo;
+  uint32_t* dkey;  // resident depth keys (keep only)
+};
+
+ProjPtrs proj_ptrs(fs_ctx* c, bool keep, int32_t v0, int64_t n) {
+  const int64_t off = keep ? static_cast<int64_t>(v0) * n : 0;
+  return {c->rec.as<fs::ProjRecord>() + off, c->foot.as<fs::Footprint>() + off,
+          c->cnt.as<uint32_t>() + off, c->dlo.as<uint32_t>() + off,
+          keep ? c->dkey.as<uint32_t>() + off : nullptr};
+}
+
+fs_status ensure_window(fs_ctx* c, int64_t n, int vb, int32_t V, bool keep) {
   const int64_t kcap = static_cast<int64_t>(vb) * n;
-  FS_TRY(c->rec.ensure(static_cast<size_t>(kcap) * sizeof(fs::ProjRecord), "records"));
-  FS_TRY(c->foot.ensure(static_cast<size_t>(kcap) * sizeof(fs::Footprint), "footprints"));
-  FS_TRY(c->cnt.ensure(static_cast<size_t>(kcap) * 4, "counts"));
+  const int64_t pcap = keep ? static_cast<int64_t>(V) * n : kcap;
+  FS_TRY(c->rec.ensure(static_cast<size_t>(pcap) * sizeof(fs::ProjRecord), "records"));
+  FS_TRY(c->foot.ensure(static_cast<size_t>(pcap) * sizeof(fs::Footprint), "footprints"));
+  FS_TRY(c->cnt.ensure(static_cast<size_t>(pcap) * 4, "counts"));
+  FS_TRY(c->dlo.ensure(static_cast<size_t>(pcap) * 4, "depth low words"));
+  if (keep) FS_TRY(c->dkey.ensure(static_cast<size_t>(pcap) * 4, "depth keys"));
   FS_TRY(c->key_a.ensure(static_cast<size_t>(kcap) * 4, "keys"));
   FS_TRY(c->val_a.ensure(static_cast<size_t>(kcap) * 4, "vals"));
   FS_TRY(c->key_b.ensure(static_cast<size_t>(kcap) * 4, "keys"));
@@ -394,49 +478,131 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
   FS_TRY(c->offs.ensure(static_cast<size_t>(kcap) * 4, "offsets"));
   FS_TRY(c->scan_tmp.ensure(fs::scan_temp_bytes(kcap), "scan temp"));
   FS_TRY(c->sort_tmp.ensure(fs::radix_temp_bytes(kcap), "sort temp"));
-
   FS_TRY(c->ccnt.ensure(static_cast<size_t>(kcap) * 4, "chunk counts"));
-  FS_TRY(c->dlo.ensure(static_cast<size_t>(kcap) * 4, "depth low words"));
+  return FS_OK;
+}
+
+// Reads a device uint32 total back (synchronises the stream).
+fs_status read_total(fs_ctx* c, cudaStream_t stream, int64_t* out) {
+  uint32_t* total_h = c->total_host.as<uint32_t>();
+  FS_CUDA(cudaMemcpyAsync(total_h, c->total.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream),
+          "count readback");
+  FS_CUDA(cudaStreamSynchronize(stream), "count readback");
+  *out = *total_h;
+  return FS_OK;
+}
+
+// Binning of sorted positions [p0, p0 + n_pos) into tile lists (count, scan,
+// emit, stable tile sort, ranges) on tiles whose `sat` bit is clear.  Returns
+// the entry count in *I and the sorted list values in *lval.
+// Binning of sorted positions [p0, p0 + n_pos) into tile lists (count, scan,
+// emit, stable tile sort, ranges) on tiles whose `sat` bit is clear.  The
+// sorted list values go to *val_dst (grown as needed) and the per-tile ranges
+// to ranges_dst.  Returns the entry count in *I_out.
+fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
+                        const fs::ViewParams* vd, const uint32_t* sorted_val, const ProjPtrs& P,
+                        const uint64_t* sat, int total_tiles, int tile_bits, int64_t kcap,
+                        bool count_entries, DevBuf* val_dst, uint2* ranges_dst,
+                        cudaStream_t stream, int64_t* I_out) {
+  unsigned long long* ctr = c->counters.as<unsigned long long>();
+  *I_out = 0;
+  FS_CUDA(cudaMemsetAsync(ranges_dst, 0, static_cast<size_t>(total_tiles) * 8, stream),
+          "ranges clear");
+  c->stats.kernel_launches += 1 + scan_launches(n_pos);
+  FS_CUDA(fs::launch_chunk_count(p0, n_pos, n, vd, sorted_val, P.cnt, P.foot, sat,
+                                 c->ccnt.as<uint32_t>(), stream),
+          "chunk count");
+  FS_CUDA(fs::exclusive_scan(c->ccnt.as<uint32_t>(), nullptr, c->offs.as<uint32_t>(), n_pos,
+                             c->total.as<uint32_t>(), c->scan_tmp.p, stream),
+          "count scan");
+  int64_t I = 0;
+  FS_TRY(read_total(c, stream, &I));
+  if (I >= (static_cast<int64_t>(1) << 31))
+    return fail(FS_UNSUPPORTED, "%lld list entries in one chunk; use fewer views per batch",
+                (long long)I);
+  if (count_entries) c->stats.list_entries += I;
+  *I_out = I;
+  if (I == 0) return FS_OK;
+  FS_TRY(c->lk_a.ensure(static_cast<size_t>(I) * 4, "list keys"));
+  FS_TRY(val_dst->ensure(static_cast<size_t>(I) * 4, "list values"));
+  FS_TRY(c->lk_b.ensure(static_cast<size_t>(I) * 4, "list keys"));
+  FS_TRY(c->lv_b.ensure(static_cast<size_t>(I) * 4, "list values"));
+  FS_TRY(c->sort_tmp.ensure(fs::radix_temp_bytes(std::max<int64_t>(I, kcap)), "sort temp"));
+  c->stats.kernel_launches += 2 + radix_launches(I, tile_bits);
+  FS_CUDA(fs::launch_emit(p0, n_pos, n, vd, sorted_val, c->offs.as<uint32_t>(),
+                          c->ccnt.as<uint32_t>(), P.cnt, P.foot, sat, c->lk_a.as<uint32_t>(),
+                          val_dst->as<uint32_t>(), ctr, stream),
+          "emit");
+  bool alt2 = false;
+  FS_CUDA(fs::radix_sort_pairs(c->lk_a.as<uint32_t>(), val_dst->as<uint32_t>(),
+                               c->lk_b.as<uint32_t>(), c->lv_b.as<uint32_t>(), I, tile_bits,
+                               c->sort_tmp.p, &alt2, stream),
+          "tile sort");
+  const uint32_t* lkey = alt2 ? c->lk_b.as<uint32_t>() : c->lk_a.as<uint32_t>();
+  if (alt2)
+    FS_CUDA(cudaMemcpyAsync(val_dst->p, c->lv_b.p, static_cast<size_t>(I) * 4,
+                            cudaMemcpyDeviceToDevice, stream),
+            "list copy");
+  FS_CUDA(fs::launch_ranges(I, lkey, ranges_dst, stream), "ranges");
+  return FS_OK;
+}
+
+// Front-to-back depth chunk boundaries of a batch of k_total sorted slots:
+// chunk ci covers positions [chunk_begin(ci), chunk_begin(ci + 1)).
+int64_t chunk_end(int64_t k_total, int chunks, int ci) {
+  return (ci == chunks - 1) ? k_total : (k_total >> (chunks - 1 - ci));
+}
+
+// Layout of the main pass's tile lists kept for the near-tie re-check: per
+// view batch and depth chunk, the list values and the ranges over the
+// batch's tiles; per batch tile, the chunk in which it saturated; per batch
+// and chunk, the last slot of the chunk.
+fs_status kept_layout(fs_ctx* c, const fs_camera* cams, int32_t V, int vb, int chunks) {
+  c->kl_tile_off.clear();
+  int64_t tiles = 0;
+  for (int32_t v0 = 0; v0 < V; v0 += vb) {
+    c->kl_tile_off.push_back(tiles);
+    const int nb = std::min(vb, V - v0);
+    for (int k = 0; k < nb; ++k) {
+      const int64_t tx = (cams[v0 + k].width + fs::kTile - 1) / fs::kTile;
+      const int64_t ty = (cams[v0 + k].height + fs::kTile - 1) / fs::kTile;
+      tiles += tx * ty;
+    }
+  }
+  c->kl_tile_off.push_back(tiles);
+  const size_t batches = c->kl_tile_off.size() - 1;
+  c->kl_chunks = chunks;
+  if (c->kl_val.size() < batches * chunks) c->kl_val.resize(batches * chunks);
+  FS_TRY(c->kl_ranges.ensure(static_cast<size_t>(tiles) * chunks * 8 + 8, "kept ranges"));
+  FS_TRY(c->kl_satc.ensure(static_cast<size_t>(tiles) + 8, "kept saturation chunks"));
+  FS_TRY(c->kl_bound.ensure(batches * chunks * 4 + 4, "kept chunk bounds"));
+  return FS_OK;
+}
+
+fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t V,
+                          const void* const* masks, int32_t mask_dtype, int32_t mask_memory,
+                          int32_t E, void* table, int32_t table_dtype, bool keep,
+                          cudaStream_t stream) {
+  const int64_t n = s->n;
+  c->kl_valid = false;
+  if (n == 0 || V == 0) return FS_OK;
+  const int vb = batch_views(c, n);
+  if (vb < 1) return fail(FS_UNSUPPORTED, "fs_accumulate: scene too large");
+  const int64_t kcap = static_cast<int64_t>(vb) * n;
+  const int chunks = std::max(1, std::min(c->depth_chunks, fs::kMaxChunks));
+  FS_TRY(ensure_window(c, n, vb, V, keep));
+  FS_TRY(stage_masks(c, cams, V, masks, mask_dtype, mask_memory, stream));
+  if (keep) FS_TRY(kept_layout(c, cams, V, vb, chunks));
 
   fs::ViewParams* vh = c->views_host.as<fs::ViewParams>();
-  uint32_t* total_h = c->total_host.as<uint32_t>();
   unsigned long long* ctr = c->counters.as<unsigned long long>();
-  for (int32_t v0 = 0; v0 < V; v0 += vb) {
+  for (int32_t v0 = 0, b = 0; v0 < V; v0 += vb, ++b) {
     const int nb = std::min(vb, V - v0);
-    int tile_base = 0, max_tiles = 0;
-    int64_t state_off = 0;
-    size_t stage_bytes = 0;
-    for (int k = 0; k < nb; ++k) {
-      const fs_camera& cam = cams[v0 + k];
-      stage_bytes += ((static_cast<size_t>(cam.width) * cam.height * msize) + 255) & ~size_t(255);
-    }
-    if (mask_memory == FS_MEM_HOST) FS_TRY(c->mask_stage.ensure(stage_bytes, "mask staging"));
-    size_t stage_off = 0;
-    for (int k = 0; k < nb; ++k) {
-      const fs_camera& cam = cams[v0 + k];
-      fill_view(cam, &vh[k]);
-      vh[k].tile_base = tile_base;
-      vh[k].state_off = state_off;
-      const int nt = vh[k].tiles_x * vh[k].tiles_y;
-      tile_base += nt;
-      max_tiles = std::max(max_tiles, nt);
-      const size_t npix = static_cast<size_t>(cam.width) * cam.height;
-      state_off += static_cast<int64_t>(npix);
-      const size_t mbytes = npix * msize;
-      if (mask_memory == FS_MEM_DEVICE) {
-        vh[k].mask = masks[v0 + k];
-      } else {
-        char* dst = c->mask_stage.as<char>() + stage_off;
-        FS_CUDA(cudaMemcpyAsync(dst, masks[v0 + k], mbytes, cudaMemcpyHostToDevice, stream),
-                "mask upload");
-        vh[k].mask = dst;
-        stage_off += (mbytes + 255) & ~size_t(255);
-      }
-    }
-    const int total_tiles = tile_base;
+    const BatchLayout L = layout_batch(c, cams, v0, nb);
+    const int total_tiles = L.total_tiles, max_tiles = L.max_tiles;
     const int tile_bits = std::max(1, ceil_log2(total_tiles));
     const int64_t k_total = static_cast<int64_t>(nb) * n;
-    FS_TRY(c->state.ensure(static_cast<size_t>(state_off) * 4, "pixel state"));
+    FS_TRY(c->state.ensure(static_cast<size_t>(L.pixels) * 4, "pixel state"));
     const size_t sat_bytes = static_cast<size_t>((total_tiles + 63) / 64) * 8;
     FS_TRY(c->sat.ensure(sat_bytes, "tile flags"));
     const size_t subsat_bytes = static_cast<size_t>((4 * total_tiles + 63) / 64) * 8;
@@ -447,14 +613,24 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     uint64_t* sat = c->sat.as<uint64_t>();
     FS_CUDA(cudaMemcpyAsync(vd, vh, sizeof(fs::ViewParams) * nb, cudaMemcpyHostToDevice, stream),
             "view upload");
+    const ProjPtrs P = proj_ptrs(c, keep, v0, n);
+    uint8_t* satc = nullptr;
+    if (keep) {
+      satc = c->kl_satc.as<uint8_t>() + c->kl_tile_off[b];
+      FS_CUDA(cudaMemsetAsync(satc, 0xFF, static_cast<size_t>(total_tiles), stream),
+              "saturation chunks");
+    }
 
     // project every Gaussian into the batch's views, sort by depth
     c->stats.kernel_launches += 3 + radix_launches(k_total, 32);
-    FS_CUDA(fs::launch_project(n, nb, vd, s->pos_op.as<float4>(), s->cov.as<float4>(),
-                               c->rec.as<fs::ProjRecord>(), c->foot.as<fs::Footprint>(),
-                               c->cnt.as<uint32_t>(), c->key_a.as<uint32_t>(),
-                               c->val_a.as<uint32_t>(), c->dlo.as<uint32_t>(), stream),
+    FS_CUDA(fs::launch_project(n, nb, vd, s->pos_op.as<float4>(), s->cov.as<float4>(), P.rec,
+                               P.foot, P.cnt, c->key_a.as<uint32_t>(), c->val_a.as<uint32_t>(),
+                               P.dlo, stream),
             "project");
+    if (P.dkey)
+      FS_CUDA(cudaMemcpyAsync(P.dkey, c->key_a.p, static_cast<size_t>(k_total) * 4,
+                              cudaMemcpyDeviceToDevice, stream),
+              "depth key copy");
     bool alt = false;
     FS_CUDA(fs::radix_sort_pairs(c->key_a.as<uint32_t>(), c->val_a.as<uint32_t>(),
                                  c->key_b.as<uint32_t>(), c->val_b.as<uint32_t>(), k_total, 32,
@@ -462,8 +638,7 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
             "depth sort");
     uint32_t* sorted_key = alt ? c->key_b.as<uint32_t>() : c->key_a.as<uint32_t>();
     uint32_t* sorted_val = alt ? c->val_b.as<uint32_t>() : c->val_a.as<uint32_t>();
-    FS_CUDA(fs::launch_depth_tie_fix(k_total, n, sorted_key, sorted_val, c->dlo.as<uint32_t>(),
-                                     stream),
+    FS_CUDA(fs::launch_depth_tie_fix(k_total, n, sorted_key, sorted_val, P.dlo, stream),
             "depth ties");
     uint64_t* subsat = c->subsat.as<uint64_t>();
     FS_CUDA(cudaMemsetAsync(sat, 0, sat_bytes, stream), "tile flags clear");
@@ -472,57 +647,41 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
                                   stream),
             "pixel state");
     c->stats.views += nb;
-    c->stats.pixels += state_off;
+    c->stats.pixels += L.pixels;
+    if (keep) {  // the last slot of every chunk but the last (0xFFFFFFFF: empty chunk)
+      uint32_t* bound = c->kl_bound.as<uint32_t>() + static_cast<int64_t>(b) * chunks;
+      FS_CUDA(cudaMemsetAsync(bound, 0xFF, static_cast<size_t>(chunks) * 4, stream), "bounds");
+      for (int ci = 0; ci + 1 < chunks; ++ci) {
+        const int64_t pb = ci == 0 ? 0 : chunk_end(k_total, chunks, ci - 1);
+        const int64_t p1 = chunk_end(k_total, chunks, ci);
+        if (p1 > pb)
+          FS_CUDA(cudaMemcpyAsync(bound + ci, sorted_val + (p1 - 1), 4, cudaMemcpyDeviceToDevice,
+                                  stream),
+                  "bounds");
+      }
+    }
 
     // front-to-back depth chunks: a chunk lists only tiles not yet saturated
-    const int chunks = std::max(1, c->depth_chunks);
     int64_t p0 = 0;
     for (int ci = 0; ci < chunks; ++ci) {
-      const int64_t p1 = (ci == chunks - 1) ? k_total : (k_total >> (chunks - 1 - ci));
+      const int64_t p1 = chunk_end(k_total, chunks, ci);
       const int64_t n_pos = p1 - p0;
-      if (n_pos <= 0) continue;
-      uint32_t* total_d = c->total.as<uint32_t>();
-      c->stats.kernel_launches += 1 + scan_launches(n_pos);
-      FS_CUDA(fs::launch_chunk_count(p0, n_pos, n, vd, sorted_val, c->cnt.as<uint32_t>(),
-                                     c->foot.as<fs::Footprint>(), sat, c->ccnt.as<uint32_t>(),
-                                     stream),
-              "chunk count");
-      FS_CUDA(fs::exclusive_scan(c->ccnt.as<uint32_t>(), nullptr, c->offs.as<uint32_t>(), n_pos,
-                                 total_d, c->scan_tmp.p, stream),
-              "count scan");
-      FS_CUDA(cudaMemcpyAsync(total_h, total_d, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream),
-              "count readback");
-      FS_CUDA(cudaStreamSynchronize(stream), "count readback");
-      const int64_t I = *total_h;
-      if (I >= (static_cast<int64_t>(1) << 31))
-        return fail(FS_UNSUPPORTED, "fs_accumulate: %lld list entries in one chunk; use fewer "
-                    "views per batch", (long long)I);
-      c->stats.list_entries += I;
-      if (I == 0) {
-        p0 = p1;
+      DevBuf* val_dst = keep ? &c->kl_val[static_cast<size_t>(b) * chunks + ci] : &c->lv_a;
+      uint2* ranges_dst =
+          keep ? c->kl_ranges.as<uint2>() + (c->kl_tile_off[b] * chunks +
+                                             static_cast<int64_t>(ci) * total_tiles)
+               : c->ranges.as<uint2>();
+      if (n_pos <= 0) {
+        if (keep)
+          FS_CUDA(cudaMemsetAsync(ranges_dst, 0, static_cast<size_t>(total_tiles) * 8, stream),
+                  "ranges clear");
         continue;
       }
-      FS_TRY(c->lk_a.ensure(static_cast<size_t>(I) * 4, "list keys"));
-      FS_TRY(c->lv_a.ensure(static_cast<size_t>(I) * 4, "list values"));
-      FS_TRY(c->lk_b.ensure(static_cast<size_t>(I) * 4, "list keys"));
-      FS_TRY(c->lv_b.ensure(static_cast<size_t>(I) * 4, "list values"));
-      FS_TRY(c->sort_tmp.ensure(fs::radix_temp_bytes(std::max<int64_t>(I, kcap)), "sort temp"));
-      c->stats.kernel_launches += 3 + radix_launches(I, tile_bits);
-      FS_CUDA(fs::launch_emit(p0, n_pos, n, vd, sorted_val, c->offs.as<uint32_t>(),
-                              c->ccnt.as<uint32_t>(), c->cnt.as<uint32_t>(),
-                              c->foot.as<fs::Footprint>(), sat,
-                              c->lk_a.as<uint32_t>(), c->lv_a.as<uint32_t>(), ctr, stream),
-              "emit");
-      bool alt2 = false;
-      FS_CUDA(fs::radix_sort_pairs(c->lk_a.as<uint32_t>(), c->lv_a.as<uint32_t>(),
-                                   c->lk_b.as<uint32_t>(), c->lv_b.as<uint32_t>(), I, tile_bits,
-                                   c->sort_tmp.p, &alt2, stream),
-              "tile sort");
-      const uint32_t* lkey = alt2 ? c->lk_b.as<uint32_t>() : c->lk_a.as<uint32_t>();
-      const uint32_t* lval = alt2 ? c->lv_b.as<uint32_t>() : c->lv_a.as<uint32_t>();
-      FS_CUDA(cudaMemsetAsync(c->ranges.p, 0, static_cast<size_t>(total_tiles) * 8, stream),
-              "ranges clear");
-      FS_CUDA(fs::launch_ranges(I, lkey, c->ranges.as<uint2>(), stream), "ranges");
+      int64_t I = 0;
+      FS_TRY(bin_positions(c, p0, n_pos, n, vd, sorted_val, P, sat, total_tiles, tile_bits, kcap,
+                           true, val_dst, ranges_dst, stream, &I));
+      p0 = p1;
+      if (I == 0) continue;
       cudaEvent_t ev0 = nullptr, ev1 = nullptr;
       if (c->time_stages) {
         while (c->events.size() < c->events_used + 2) {
@@ -535,14 +694,183 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
         c->events_used += 2;
         FS_CUDA(cudaEventRecord(ev0, stream), "cudaEventRecord");
       }
-      FS_CUDA(fs::launch_blend(vd, nb, max_tiles, c->ranges.as<uint2>(), lval,
-                               c->rec.as<fs::ProjRecord>(), n, E, mask_dtype, table, table_dtype,
-                               state, sat, subsat, ctr, stream),
+      FS_CUDA(fs::launch_blend(vd, nb, max_tiles, ranges_dst, val_dst->as<uint32_t>(), P.rec, n,
+                               E, mask_dtype, table, table_dtype, state, sat, subsat, satc, ci,
+                               ctr, stream),
               "blend");
       if (ev1) FS_CUDA(cudaEventRecord(ev1, stream), "cudaEventRecord");
-      p0 = p1;
     }
   }
+  c->kl_valid = keep;
+  return FS_OK;
+}
+
+// Dedicated binning of the tiles whose `skip` bit is clear (all depths, one
+// list per tile) and the re-check compositing of them into R.
+fs_status recheck_batch_rebin(fs_ctx* c, const fs_scene* s, int64_t n, int nb, int64_t kcap,
+                              const BatchLayout& L, const fs::ViewParams* vd, const ProjPtrs& P,
+                              const uint32_t* key_src, uint64_t* skip, int32_t mask_dtype,
+                              int32_t E, const int32_t* map, double* R, cudaStream_t stream) {
+  const int total_tiles = L.total_tiles;
+  const int tile_bits = std::max(1, ceil_log2(total_tiles));
+  const int64_t k_total = static_cast<int64_t>(nb) * n;
+  unsigned long long* ctr = c->counters.as<unsigned long long>();
+  c->stats.kernel_launches += 1 + scan_launches(k_total);
+  FS_CUDA(fs::launch_candidates(k_total, n, vd, P.cnt, P.foot, skip, c->ccnt.as<uint32_t>(),
+                                stream),
+          "candidates");
+  FS_CUDA(fs::exclusive_scan(c->ccnt.as<uint32_t>(), nullptr, c->offs.as<uint32_t>(), k_total,
+                             c->total.as<uint32_t>(), c->scan_tmp.p, stream),
+          "candidate scan");
+  int64_t C = 0;
+  FS_TRY(read_total(c, stream, &C));
+  if (C == 0) return FS_OK;
+  c->stats.kernel_launches += 2 + radix_launches(C, 32);
+  FS_CUDA(fs::launch_compact(k_total, c->ccnt.as<uint32_t>(), c->offs.as<uint32_t>(), key_src,
+                             c->key_b.as<uint32_t>(), c->val_b.as<uint32_t>(), stream),
+          "compact");
+  bool alt = false;
+  FS_CUDA(fs::radix_sort_pairs(c->key_b.as<uint32_t>(), c->val_b.as<uint32_t>(),
+                               c->key_a.as<uint32_t>(), c->val_a.as<uint32_t>(), C, 32,
+                               c->sort_tmp.p, &alt, stream),
+          "candidate sort");
+  uint32_t* sorted_key = alt ? c->key_a.as<uint32_t>() : c->key_b.as<uint32_t>();
+  uint32_t* sorted_val = alt ? c->val_a.as<uint32_t>() : c->val_b.as<uint32_t>();
+  FS_CUDA(fs::launch_depth_tie_fix(C, n, sorted_key, sorted_val, P.dlo, stream), "depth ties");
+  int64_t I = 0;
+  FS_TRY(bin_positions(c, 0, C, n, vd, sorted_val, P, skip, total_tiles, tile_bits, kcap, false,
+                       &c->lv_a, c->ranges.as<uint2>(), stream, &I));
+  if (I == 0) return FS_OK;
+  fs::RecheckLists Ls{};
+  Ls.val[0] = c->lv_a.as<uint32_t>();
+  Ls.ranges[0] = c->ranges.as<uint2>();
+  Ls.chunks = 1;
+  c->stats.kernel_launches += 1;
+  FS_CUDA(fs::launch_recheck_blend(vd, nb, L.max_tiles, Ls, skip, P.rec, n, E, mask_dtype, map,
+                                   R, ctr, stream),
+          "re-check blend");
+  return FS_OK;
+}
+
+// Re-check of the Gaussians whose margin is below c->recheck_margin (see
+// fs_recheck.cu): their rows of `table` and their bits / label / margin are
+// replaced.  `margin` holds the FP32 decision's margins on entry.
+fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t V,
+                       int32_t mask_dtype, int32_t E, float gamma, void* table,
+                       int32_t table_dtype, uint64_t* bits, int32_t* label, float* margin,
+                       bool keep, cudaStream_t stream) {
+  const int64_t n = s->n;
+  if (n == 0 || V == 0) return FS_OK;
+  const size_t nn = static_cast<size_t>(n);
+  FS_TRY(c->rk_flag.ensure(nn * 4, "re-check flags"));
+  FS_TRY(c->rk_offs.ensure(nn * 4, "re-check offsets"));
+  FS_TRY(c->rk_F.ensure(nn * 4, "re-check set"));
+  FS_TRY(c->rk_map.ensure(nn * 4, "re-check map"));
+  FS_TRY(c->scan_tmp.ensure(fs::scan_temp_bytes(n), "scan temp"));
+  uint32_t* F = c->rk_F.as<uint32_t>();
+  int32_t* map = c->rk_map.as<int32_t>();
+  c->stats.kernel_launches += 2 + scan_launches(n);
+  FS_CUDA(fs::launch_flag_margin(n, margin, c->recheck_margin, c->rk_flag.as<uint32_t>(), stream),
+          "re-check flags");
+  FS_CUDA(fs::exclusive_scan(c->rk_flag.as<uint32_t>(), nullptr, c->rk_offs.as<uint32_t>(), n,
+                             c->total.as<uint32_t>(), c->scan_tmp.p, stream),
+          "re-check scan");
+  FS_CUDA(fs::launch_scatter_flagged(n, c->rk_flag.as<uint32_t>(), c->rk_offs.as<uint32_t>(), F,
+                                     map, stream),
+          "re-check set");
+  int64_t nF = 0;
+  FS_TRY(read_total(c, stream, &nF));
+  c->stats.rechecked = nF;
+  if (nF == 0) return FS_OK;
+  const size_t rbytes = static_cast<size_t>(nF) * E * 8;
+  FS_TRY(c->rk_R.ensure(rbytes, "re-check rows"));
+  double* R = c->rk_R.as<double>();
+  FS_CUDA(cudaMemsetAsync(R, 0, rbytes, stream), "re-check rows clear");
+  const bool kept = keep && c->kl_valid;
+  double* Rb = nullptr;
+  if (kept) {
+    FS_TRY(c->rk_Rb.ensure(rbytes, "re-check batch rows"));
+    Rb = c->rk_Rb.as<double>();
+  }
+
+  const int vb = batch_views(c, n);
+  const int64_t kcap = static_cast<int64_t>(vb) * n;
+  const int chunks = c->kl_chunks;
+  fs::ViewParams* vh = c->views_host.as<fs::ViewParams>();
+  unsigned long long* ctr = c->counters.as<unsigned long long>();
+  unsigned long long* ctr_h = c->counters_host.as<unsigned long long>();
+  for (int32_t v0 = 0, b = 0; v0 < V; v0 += vb, ++b) {
+    const int nb = std::min(vb, V - v0);
+    const BatchLayout L = layout_batch(c, cams, v0, nb);
+    const int total_tiles = L.total_tiles;
+    const size_t sat_bytes = static_cast<size_t>((total_tiles + 63) / 64) * 8;
+    FS_TRY(c->sat.ensure(sat_bytes, "tile flags"));
+    FS_TRY(c->subsat.ensure(sat_bytes, "deep tile flags"));
+    FS_TRY(c->ranges.ensure(static_cast<size_t>(total_tiles) * 8, "tile ranges"));
+    fs::ViewParams* vd = c->views.as<fs::ViewParams>();
+    uint64_t* skip = c->sat.as<uint64_t>();
+    uint64_t* deep = c->subsat.as<uint64_t>();
+    FS_CUDA(cudaMemcpyAsync(vd, vh, sizeof(fs::ViewParams) * nb, cudaMemcpyHostToDevice, stream),
+            "view upload");
+    const ProjPtrs P = proj_ptrs(c, keep, v0, n);
+    const uint32_t* key_src = P.dkey;
+    if (!keep) {
+      c->stats.kernel_launches += 1;
+      FS_CUDA(fs::launch_project(n, nb, vd, s->pos_op.as<float4>(), s->cov.as<float4>(), P.rec,
+                                 P.foot, P.cnt, c->key_a.as<uint32_t>(), c->val_a.as<uint32_t>(),
+                                 P.dlo, stream),
+              "project");
+      key_src = c->key_a.as<uint32_t>();
+    }
+    // tiles to re-render: those the flagged Gaussians reach
+    FS_CUDA(cudaMemsetAsync(skip, 0xFF, sat_bytes, stream), "skip bits");
+    FS_CUDA(cudaMemsetAsync(deep, 0, sat_bytes, stream), "deep bits");
+    FS_CUDA(cudaMemsetAsync(c->total.p, 0, sizeof(uint32_t), stream), "visible clear");
+    const uint8_t* satc = kept ? c->kl_satc.as<uint8_t>() + c->kl_tile_off[b] : nullptr;
+    const uint32_t* bound = kept ? c->kl_bound.as<uint32_t>() + static_cast<int64_t>(b) * chunks
+                                 : nullptr;
+    c->stats.kernel_launches += 1;
+    FS_CUDA(fs::launch_mark_tiles(nF, nb, n, F, vd, P.cnt, P.foot, skip, c->total.as<uint32_t>(),
+                                  bound, chunks, P.dkey, P.dlo, satc, deep, stream),
+            "mark tiles");
+    int64_t visible = 0;
+    FS_TRY(read_total(c, stream, &visible));
+    if (visible == 0) continue;  // no re-checked Gaussian in these views
+    if (kept) {
+      // walk the main pass's kept chunk lists
+      fs::RecheckLists Ls{};
+      for (int ci = 0; ci < chunks; ++ci) {
+        Ls.val[ci] = c->kl_val[static_cast<size_t>(b) * chunks + ci].as<uint32_t>();
+        Ls.ranges[ci] = c->kl_ranges.as<uint2>() +
+                        (c->kl_tile_off[b] * chunks + static_cast<int64_t>(ci) * total_tiles);
+      }
+      Ls.chunks = chunks;
+      Ls.sat_chunk = satc;
+      Ls.deep = deep;
+      FS_CUDA(cudaMemsetAsync(Rb, 0, rbytes, stream), "batch rows clear");
+      FS_CUDA(cudaMemsetAsync(ctr + fs::kRecheckIncomplete, 0, 8, stream), "incomplete clear");
+      c->stats.kernel_launches += 1;
+      FS_CUDA(fs::launch_recheck_blend(vd, nb, L.max_tiles, Ls, skip, P.rec, n, E, mask_dtype,
+                                       map, Rb, ctr, stream),
+              "re-check blend");
+      FS_CUDA(cudaMemcpyAsync(ctr_h + fs::kRecheckIncomplete, ctr + fs::kRecheckIncomplete, 8,
+                              cudaMemcpyDeviceToHost, stream),
+              "incomplete readback");
+      FS_CUDA(cudaStreamSynchronize(stream), "incomplete readback");
+      if (ctr_h[fs::kRecheckIncomplete] == 0) {
+        c->stats.kernel_launches += 1;
+        FS_CUDA(fs::launch_add_rows(static_cast<int64_t>(nF) * E, Rb, R, stream), "rows add");
+        continue;
+      }
+      c->stats.recheck_rebinned += 1;  // kept lists end too early: bin these tiles anew
+    }
+    FS_TRY(recheck_batch_rebin(c, s, n, nb, kcap, L, vd, P, key_src, skip, mask_dtype, E, map, R,
+                               stream));
+  }
+  c->stats.kernel_launches += 1;
+  FS_CUDA(fs::launch_assign_rows(R, F, nF, E, gamma, table, table_dtype, bits, label, margin,
+                                 stream),
+          "re-check assign");
   return FS_OK;
 }
 
@@ -581,7 +909,8 @@ fs_status fs_accumulate(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int
   c->stats = fs_stats{};
   c->events_used = 0;
   FS_CUDA(cudaMemsetAsync(c->counters.p, 0, c->counters.bytes, st), "counters clear");
-  return accumulate_impl(c, s, cams, V, masks, mask_dtype, mask_memory, E, table, table_dtype, st);
+  return accumulate_impl(c, s, cams, V, masks, mask_dtype, mask_memory, E, table, table_dtype,
+                         false, st);
 }
 
 fs_status fs_assign(fs_ctx* c, const void* table, int32_t table_dtype, int64_t n, int32_t E,
@@ -631,28 +960,48 @@ fs_status fs_solve(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t 
   c->events_used = 0;
   FS_CUDA(cudaMemsetAsync(c->counters.p, 0, c->counters.bytes, st), "counters clear");
   if (tbytes) FS_CUDA(cudaMemsetAsync(table, 0, tbytes, st), "table clear");
-  FS_TRY(accumulate_impl(c, s, cams, V, masks, mask_dtype, mask_memory, E, table, tdt, st));
+  const bool recheck = c->recheck_margin > 0.f && n > 0 && V > 0;
+  // keep every view's projection resident for the re-check when it fits in
+  // half of the free device memory (108 B per Gaussian and view)
+  bool keep = false;
+  if (recheck && !c->recheck_reproject) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      const double need = 108.0 * static_cast<double>(n) * V;
+      const double have = static_cast<double>(c->rec.bytes + c->foot.bytes + c->cnt.bytes +
+                                              c->dlo.bytes + c->dkey.bytes);
+      keep = need <= have + 0.5 * static_cast<double>(free_b);
+    }
+  }
+  FS_TRY(accumulate_impl(c, s, cams, V, masks, mask_dtype, mask_memory, E, table, tdt, keep, st));
   uint64_t* bits = out->member_bits;
   int32_t* label = out->label;
   float* margin = out->margin;
+  const size_t nn = static_cast<size_t>(n > 0 ? n : 1);
   if (!dev_out) {
-    const size_t nn = static_cast<size_t>(n > 0 ? n : 1);
     if (bits) { FS_TRY(c->bits_tmp.ensure(nn * 8, "bits")); bits = c->bits_tmp.as<uint64_t>(); }
     if (label) { FS_TRY(c->label_tmp.ensure(nn * 4, "labels")); label = c->label_tmp.as<int32_t>(); }
     if (margin) { FS_TRY(c->margin_tmp.ensure(nn * 4, "margins")); margin = c->margin_tmp.as<float>(); }
+  }
+  if (recheck && !margin) {  // the re-check needs the margins
+    FS_TRY(c->margin_tmp.ensure(nn * 4, "margins"));
+    margin = c->margin_tmp.as<float>();
   }
   if (bits || label || margin) {
     FS_CUDA(fs::launch_assign(table, tdt, n, E, gamma, bits, label, margin, st), "assign");
     if (n > 0) c->stats.kernel_launches += 1;
   }
+  if (recheck)
+    FS_TRY(recheck_impl(c, s, cams, V, mask_dtype, E, gamma, table, tdt, bits, label, margin,
+                        keep, st));
   if (!dev_out && n > 0) {
     if (out->table)
       FS_CUDA(cudaMemcpyAsync(out->table, table, tbytes, cudaMemcpyDeviceToHost, st), "table D2H");
-    if (bits)
+    if (out->member_bits)
       FS_CUDA(cudaMemcpyAsync(out->member_bits, bits, n * 8, cudaMemcpyDeviceToHost, st), "D2H");
-    if (label)
+    if (out->label)
       FS_CUDA(cudaMemcpyAsync(out->label, label, n * 4, cudaMemcpyDeviceToHost, st), "D2H");
-    if (margin)
+    if (out->margin)
       FS_CUDA(cudaMemcpyAsync(out->margin, margin, n * 4, cudaMemcpyDeviceToHost, st), "D2H");
   }
   return FS_OK;
@@ -671,6 +1020,7 @@ fs_status fs_synchronize(fs_ctx* c, void* stream, fs_stats* stats) {
   c->stats.bad_labels = static_cast<int64_t>(ch[fs::kBadLabels]);
   c->stats.pairs = static_cast<int64_t>(ch[fs::kPairs]);
   c->stats.staged_entries = static_cast<int64_t>(ch[fs::kStaged]);
+  c->stats.recheck_pairs = static_cast<int64_t>(ch[fs::kRecheckPairs]);
   if (ch[fs::kBinningMismatch])
     return fail(FS_CUDA_ERROR, "internal error: tile binning count and emission disagreed for "
                 "%llu Gaussian(s)", ch[fs::kBinningMismatch]);

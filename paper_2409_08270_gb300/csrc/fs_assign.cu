@@ -14,14 +14,14 @@ namespace fs {
 
 namespace {
 
+struct Decision {
+  uint64_t bits;
+  int32_t label;
+  float margin;
+};
+
 template <typename T>
-__global__ void __launch_bounds__(256) assign_kernel(const T* __restrict__ table, int64_t n, int E,
-                                                     T gamma, uint64_t* __restrict__ bits,
-                                                     int32_t* __restrict__ label,
-                                                     float* __restrict__ margin) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const T* row = table + i * E;
+__device__ __forceinline__ Decision decide(const T* row, int E, T gamma) {
   T S = 0;
   for (int e = 0; e < E; ++e) S += row[e];
   uint64_t b = 0;
@@ -43,9 +43,39 @@ __global__ void __launch_bounds__(256) assign_kernel(const T* __restrict__ table
       mmin = fminf(mmin, static_cast<float>(mg));
     }
   }
-  if (bits) bits[i] = b;
-  if (label) label[i] = members == 1 ? lab : -1;
-  if (margin) margin[i] = mmin;
+  return {b, members == 1 ? lab : -1, mmin};
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) assign_kernel(const T* __restrict__ table, int64_t n, int E,
+                                                     T gamma, uint64_t* __restrict__ bits,
+                                                     int32_t* __restrict__ label,
+                                                     float* __restrict__ margin) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Decision d = decide<T>(table + i * E, E, gamma);
+  if (bits) bits[i] = d.bits;
+  if (label) label[i] = d.label;
+  if (margin) margin[i] = d.margin;
+}
+
+// Rows re-evaluated in FP64: row j of R belongs to Gaussian F[j].  The row
+// replaces the table's (rounded to its type) and the decision is taken again
+// in FP64.
+template <typename TableT>
+__global__ void __launch_bounds__(256) assign_rows_kernel(
+    const double* __restrict__ R, const uint32_t* __restrict__ F, int64_t n_rows, int E,
+    double gamma, TableT* __restrict__ table, uint64_t* __restrict__ bits,
+    int32_t* __restrict__ label, float* __restrict__ margin) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= n_rows) return;
+  const double* row = R + j * E;
+  const int64_t i = F[j];
+  for (int e = 0; e < E; ++e) table[i * E + e] = static_cast<TableT>(row[e]);
+  const Decision d = decide<double>(row, E, gamma);
+  if (bits) bits[i] = d.bits;
+  if (label) label[i] = d.label;
+  if (margin) margin[i] = d.margin;
 }
 
 }  // namespace
@@ -63,6 +93,23 @@ cudaError_t launch_assign(const void* table, int table_dtype, int64_t n, int E, 
     assign_kernel<double><<<blocks, threads, 0, stream>>>(static_cast<const double*>(table), n, E,
                                                           static_cast<double>(gamma), member_bits,
                                                           label, margin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assign_rows(const double* R, const uint32_t* F, int64_t n_rows, int E,
+                               float gamma, void* table, int table_dtype, uint64_t* member_bits,
+                               int32_t* label, float* margin, cudaStream_t stream) {
+  if (n_rows == 0) return cudaSuccess;
+  const int threads = 256;
+  const unsigned blocks = static_cast<unsigned>((n_rows + threads - 1) / threads);
+  if (table_dtype == 0)
+    assign_rows_kernel<float><<<blocks, threads, 0, stream>>>(
+        R, F, n_rows, E, static_cast<double>(gamma), static_cast<float*>(table), member_bits,
+        label, margin);
+  else
+    assign_rows_kernel<double><<<blocks, threads, 0, stream>>>(
+        R, F, n_rows, E, static_cast<double>(gamma), static_cast<double*>(table), member_bits,
+        label, margin);
   return cudaGetLastError();
 }
 

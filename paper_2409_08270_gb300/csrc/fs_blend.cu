@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(32) blend_kernel(
     const ViewParams* __restrict__ views, const uint2* __restrict__ ranges,
     const uint32_t* __restrict__ list_val, const ProjRecord* __restrict__ rec, int64_t n, int E,
     TableT* __restrict__ table, float* __restrict__ state, uint64_t* __restrict__ sat,
-    uint64_t* __restrict__ subsat, unsigned long long* __restrict__ counters) {
+    uint64_t* __restrict__ subsat, uint8_t* __restrict__ sat_chunk, int chunk,
+    unsigned long long* __restrict__ counters) {
   __shared__ SubSmem S;
   const int v = blockIdx.y;
   const int tiles_x = views[v].tiles_x;
@@ -278,7 +279,11 @@ __global__ void __launch_bounds__(32) blend_kernel(
     const unsigned long long nib = 0xFull << (gsub & 63 & ~3);
     const unsigned long long old =
         atomicOr(reinterpret_cast<unsigned long long*>(subsat + (gsub >> 6)), bit);
-    if (((old | bit) & nib) == nib) set_bit(sat, gtile);
+    if (((old | bit) & nib) == nib) {
+      set_bit(sat, gtile);
+      // the tile's lists are complete up to this chunk only
+      if (sat_chunk) sat_chunk[gtile] = static_cast<uint8_t>(chunk);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) n_eval += __shfl_xor_sync(0xffffffffu, n_eval, o);
@@ -292,11 +297,12 @@ template <typename LabelT, typename TableT>
 cudaError_t launch_typed(const ViewParams* views, int n_views, int max_tiles, const uint2* ranges,
                          const uint32_t* list_val, const ProjRecord* rec, int64_t n, int E,
                          void* table, float* state, uint64_t* sat, uint64_t* subsat,
-                         unsigned long long* counters, cudaStream_t stream) {
+                         uint8_t* sat_chunk, int chunk, unsigned long long* counters,
+                         cudaStream_t stream) {
   dim3 grid(static_cast<unsigned>(4 * max_tiles), static_cast<unsigned>(n_views));
   blend_kernel<LabelT, TableT><<<grid, 32, 0, stream>>>(views, ranges, list_val, rec, n, E,
                                                         static_cast<TableT*>(table), state, sat,
-                                                        subsat, counters);
+                                                        subsat, sat_chunk, chunk, counters);
   return cudaGetLastError();
 }
 
@@ -317,22 +323,22 @@ cudaError_t launch_state_init(const ViewParams* views, int n_views, int max_tile
 cudaError_t launch_blend(const ViewParams* views, int n_views, int max_tiles_per_view,
                          const uint2* ranges, const uint32_t* list_val, const ProjRecord* rec,
                          int64_t n, int E, int mask_dtype, void* table, int table_dtype,
-                         float* state, uint64_t* sat, uint64_t* subsat,
-                         unsigned long long* counters, cudaStream_t stream) {
+                         float* state, uint64_t* sat, uint64_t* subsat, uint8_t* sat_chunk,
+                         int chunk, unsigned long long* counters, cudaStream_t stream) {
   if (n_views == 0 || max_tiles_per_view == 0) return cudaSuccess;
   const int mt = max_tiles_per_view;
   if (mask_dtype == 4) {
     if (table_dtype == 0)
       return launch_typed<uint8_t, float>(views, n_views, mt, ranges, list_val, rec, n, E, table,
-                                          state, sat, subsat, counters, stream);
+                                          state, sat, subsat, sat_chunk, chunk, counters, stream);
     return launch_typed<uint8_t, double>(views, n_views, mt, ranges, list_val, rec, n, E, table,
-                                         state, sat, subsat, counters, stream);
+                                         state, sat, subsat, sat_chunk, chunk, counters, stream);
   }
   if (table_dtype == 0)
     return launch_typed<int32_t, float>(views, n_views, mt, ranges, list_val, rec, n, E, table,
-                                        state, sat, subsat, counters, stream);
+                                        state, sat, subsat, sat_chunk, chunk, counters, stream);
   return launch_typed<int32_t, double>(views, n_views, mt, ranges, list_val, rec, n, E, table,
-                                       state, sat, subsat, counters, stream);
+                                       state, sat, subsat, sat_chunk, chunk, counters, stream);
 }
 
 }  // namespace fs

@@ -19,6 +19,8 @@ constexpr float kTMin = 1e-4f;
 constexpr float kLowPass = 0.3f;          // px^2 added to the 2D covariance diagonal
 // 0.5 * log2(e): alpha = o * 2^(-|W d|^2) with W = sqrt(kHalfLog2e) Lambda^-1/2 V^T
 constexpr double kHalfLog2e = 0.72134752044448170368;
+constexpr float kHalfLog2eHi = static_cast<float>(kHalfLog2e);
+constexpr float kHalfLog2eLo = static_cast<float>(kHalfLog2e - static_cast<double>(kHalfLog2eHi));
 
 // Per-view parameters, prepared on the host.  Double precision quantities are
 // carried as float pairs (hi + lo) so the projection needs no FP64 pipe.

@@ -62,21 +62,84 @@ cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
 cudaError_t launch_state_init(const ViewParams* views, int n_views, int max_tiles_per_view, int E,
                               int mask_dtype, float* state, uint64_t* sat, uint64_t* subsat,
                               unsigned long long* counters, cudaStream_t stream);
+// sat_chunk (may be NULL): per batch tile, set to `chunk` when the tile
+// saturates during this launch (its later chunks get no list entries).
 cudaError_t launch_blend(const ViewParams* views, int n_views, int max_tiles_per_view,
                          const uint2* ranges, const uint32_t* list_val, const ProjRecord* rec,
                          int64_t n, int E, int mask_dtype, void* table, int table_dtype,
-                         float* state, uint64_t* sat, uint64_t* subsat,
-                         unsigned long long* counters, cudaStream_t stream);
+                         float* state, uint64_t* sat, uint64_t* subsat, uint8_t* sat_chunk,
+                         int chunk, unsigned long long* counters, cudaStream_t stream);
 
 // assignment (fs_assign.cu) -------------------------------------------------
 cudaError_t launch_assign(const void* table, int table_dtype, int64_t n, int E, float gamma,
                           uint64_t* member_bits, int32_t* label, float* margin,
                           cudaStream_t stream);
 
+// Table rows re-decided from FP64 rows R[n_rows][E] (row j is Gaussian F[j]):
+// the table row is overwritten with R's (rounded to table_dtype).
+cudaError_t launch_assign_rows(const double* R, const uint32_t* F, int64_t n_rows, int E,
+                               float gamma, void* table, int table_dtype, uint64_t* member_bits,
+                               int32_t* label, float* margin, cudaStream_t stream);
+
+// FP64 near-tie re-check (fs_recheck.cu) -------------------------------------
+// flag[i] = margin[i] < tau
+cudaError_t launch_flag_margin(int64_t n, const float* margin, float tau, uint32_t* flag,
+                               cudaStream_t stream);
+// F[offs[i]] = i and map[i] = offs[i] for flagged i; map[i] = -1 otherwise
+cudaError_t launch_scatter_flagged(int64_t n, const uint32_t* flag, const uint32_t* offs,
+                                   uint32_t* F, int32_t* map, cudaStream_t stream);
+// clears the skip bits of every tile a flagged Gaussian reaches in the batch;
+// *visible += the number of visible (view, flagged Gaussian) pairs.  With
+// kept chunk lists (bound: the last slot of each depth chunk; dkey / dlo: the
+// batch's depth keys and low words; sat_chunk: the chunk in which each tile
+// saturated, 0xFF = never), sets the `deep` bit of every tile that saturated
+// before the flagged Gaussian's own chunk.  bound == NULL: no kept lists.
+cudaError_t launch_mark_tiles(int64_t n_flagged, int n_views, int64_t n, const uint32_t* F,
+                              const ViewParams* views, const uint32_t* cnt, const Footprint* foot,
+                              uint64_t* skip, uint32_t* visible, const uint32_t* bound,
+                              int chunks, const uint32_t* dkey, const uint32_t* dlo,
+                              const uint8_t* sat_chunk, uint64_t* deep, cudaStream_t stream);
+// dst[i] += src[i], i < count
+cudaError_t launch_add_rows(int64_t count, const double* src, double* dst, cudaStream_t stream);
+// flag[slot] = the slot's footprint reaches an unskipped tile
+cudaError_t launch_candidates(int64_t k_total, int64_t n, const ViewParams* views,
+                              const uint32_t* cnt, const Footprint* foot, const uint64_t* skip,
+                              uint32_t* flag, cudaStream_t stream);
+// (out_key, out_val)[offs[slot]] = (key_src[slot], slot) for flagged slots
+cudaError_t launch_compact(int64_t k_total, const uint32_t* flag, const uint32_t* offs,
+                           const uint32_t* key_src, uint32_t* out_key, uint32_t* out_val,
+                           cudaStream_t stream);
+// Depth-ordered tile lists for the re-check: `chunks` consecutive depth
+// chunks, each with its list values and per-batch-tile ranges; sat_chunk and
+// deep as in launch_mark_tiles (NULL when the lists are complete).
+constexpr int kMaxChunks = 16;
+struct RecheckLists {
+  const uint32_t* val[kMaxChunks];
+  const uint2* ranges[kMaxChunks];
+  int chunks;
+  const uint8_t* sat_chunk;
+  const uint64_t* deep;
+};
+// Float-pair compositing of the tiles whose skip bit is clear; adds alpha*T of
+// Gaussian i (map[i] >= 0) at a pixel of label e into R[map[i] * E + e].
+cudaError_t launch_recheck_blend(const ViewParams* views, int n_views, int max_tiles_per_view,
+                                 const RecheckLists& lists, const uint64_t* skip,
+                                 const ProjRecord* rec, int64_t n, int E, int mask_dtype,
+                                 const int32_t* map, double* R, unsigned long long* counters,
+                                 cudaStream_t stream);
+
 // Sets the calling thread's fs_last_error() message (fs_api.cu).
 void set_last_error(const char* msg);
 
 // device counters (unsigned long long) written by the kernels
-enum Counter { kBadLabels = 0, kPairs = 1, kStaged = 2, kBinningMismatch = 3, kNumCounters = 4 };
+enum Counter {
+  kBadLabels = 0,
+  kPairs = 1,
+  kStaged = 2,
+  kBinningMismatch = 3,
+  kRecheckPairs = 4,
+  kRecheckIncomplete = 5,
+  kNumCounters = 6
+};
 
 }  // namespace fs

@@ -286,7 +286,7 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
         NA_CUDA(cudaMemsetAsync(ranges, 0, static_cast<size_t>(tiles) * 8, strm), "clear");
         NA_CUDA(launch_ranges(I, lkey, ranges, strm), "ranges");
         NA_CUDA(launch_blend(vd, 1, tiles, ranges, lval, rec, n, E, mask_dtype, table, FS_F32,
-                             state, sat, subsat, ctr, strm),
+                             state, sat, subsat, nullptr, 0, ctr, strm),
                 "blend");
       }
       p0 = p1;

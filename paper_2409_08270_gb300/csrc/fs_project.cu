@@ -22,6 +22,7 @@
 // so far fewer tiles are listed than with the bounding box.
 #include <cuda_fp16.h>
 
+#include "fs_binning.cuh"
 #include "fs_common.cuh"
 #include "fs_internal.h"
 
@@ -94,63 +95,6 @@ __global__ void scene_prep_kernel(int64_t n, const float* __restrict__ mean, con
   cov[3 * i] = make_float4(h[0], lo[0], h[1], lo[1]);
   cov[3 * i + 1] = make_float4(h[2], lo[2], h[3], lo[3]);
   cov[3 * i + 2] = make_float4(h[4], lo[4], h[5], lo[5]);
-}
-
-// ---------------------------------------------------------------------------
-// binning geometry
-// ---------------------------------------------------------------------------
-
-// Inflated r2 used for binning (conservative against FP32 rounding).  The
-// binning arithmetic uses explicit round-to-nearest intrinsics so that the
-// count (projection kernel) and the emission (emit kernel) evaluate it
-// bit-identically whatever the compiler contracts elsewhere.
-__device__ __forceinline__ float binning_r2(float r2) {
-  return __fadd_rn(__fmul_rn(r2, 1.001f), 1e-3f);
-}
-
-__device__ __forceinline__ void footprint_rows(const Footprint& f, int* ty0, int* ty1) {
-  *ty0 = static_cast<int>(f.rows & 0xFFFFu);
-  *ty1 = static_cast<int>(f.rows >> 16);
-}
-
-// Saturated tiles are bits of a bit array over the batch's tile ids.
-// Number of unsaturated tiles among ids [a, b].
-__device__ __forceinline__ uint32_t count_free(const uint64_t* __restrict__ sat, int a, int b) {
-  uint32_t c = 0;
-  const int wa = a >> 6, wb = b >> 6;
-  for (int w = wa; w <= wb; ++w) {
-    uint64_t m = ~0ull;
-    if (w == wa) m &= ~0ull << (a & 63);
-    if (w == wb) m &= ~0ull >> (63 - (b & 63));
-    c += static_cast<uint32_t>(__popcll(~sat[w] & m));
-  }
-  return c;
-}
-
-// Tiles [tx0, tx1] of tile row ty touched by the footprint (false if none).
-// The band of pixel-centre rows of the tile, widened by one pixel, is
-// intersected with the ellipse; over the band the right boundary x(dy) is
-// concave, so its maximum is at the rightmost point dy* clamped to the band
-// (and the left boundary's minimum at -dy*, clamped).
-__device__ __forceinline__ bool row_span(const Footprint& f, int ty, int width, int* tx0,
-                                         int* tx1) {
-  const float yt = static_cast<float>(ty * kTile);
-  const float y0 = __fsub_rn(__fadd_rn(yt, -0.5f), f.my);   // band widened by one pixel
-  const float y1 = __fsub_rn(__fadd_rn(yt, 16.5f), f.my);
-  const float u0 = fmaxf(y0, -f.hy), u1 = fminf(y1, f.hy);
-  if (!(u0 <= u1)) return false;
-  const float dr = fminf(fmaxf(f.dys, u0), u1), dl = fminf(fmaxf(-f.dys, u0), u1);
-  const float sr = __fsqrt_rn(__fmul_rn(f.b2, fmaxf(0.f, __fsub_rn(f.syr, __fmul_rn(dr, dr)))));
-  const float sl = __fsqrt_rn(__fmul_rn(f.b2, fmaxf(0.f, __fsub_rn(f.syr, __fmul_rn(dl, dl)))));
-  const float xr = __fadd_rn(__fadd_rn(f.mx, __fmul_rn(f.a, dr)), sr);
-  const float xl = __fsub_rn(__fadd_rn(f.mx, __fmul_rn(f.a, dl)), sl);
-  float px0 = ceilf(__fsub_rn(xl, 1.5f)), px1 = floorf(__fadd_rn(xr, 0.5f));
-  px0 = fmaxf(px0, 0.f);
-  px1 = fminf(px1, static_cast<float>(width - 1));
-  if (!(px0 <= px1)) return false;
-  *tx0 = static_cast<int>(px0) / kTile;
-  *tx1 = static_cast<int>(px1) / kTile;
-  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -266,11 +210,13 @@ __global__ void __launch_bounds__(256) project_kernel(
         ex = f2_from(1.f);
         ey = f2_from(0.f);
       }
-      // axis scales only need FP32 accuracy
-      const float k1 = sqrtf(static_cast<float>(kHalfLog2e) / lam1.hi);
-      const float k2 = sqrtf(static_cast<float>(kHalfLog2e) / lam2.hi);
-      const f2 W00 = f2_mul_f(ex, k1), W01 = f2_mul_f(ey, k1);
-      const f2 W10 = f2_mul_f(f2_neg(ey), k2), W11 = f2_mul_f(ex, k2);
+      // axis scales sqrt(0.5 log2 e / lambda) as float pairs too: the FP64
+      // near-tie re-check evaluates alpha from this record
+      const f2 hl = {kHalfLog2eHi, kHalfLog2eLo};
+      const f2 k1 = f2_sqrt(f2_div(hl, lam1));
+      const f2 k2 = f2_sqrt(f2_div(hl, lam2));
+      const f2 W00 = f2_mul(ex, k1), W01 = f2_mul(ey, k1);
+      const f2 W10 = f2_mul(f2_neg(ey), k2), W11 = f2_mul(ex, k2);
       const f2 c0 = f2_neg(f2_add(f2_mul(W00, mx), f2_mul(W01, my)));
       const f2 c1 = f2_neg(f2_add(f2_mul(W10, mx), f2_mul(W11, my)));
       R.w_hi = make_float4(W00.hi, W01.hi, W10.hi, W11.hi);

@@ -34,7 +34,8 @@ EXPORTS = ["fs_version", "fs_last_error", "fs_create", "fs_destroy", "fs_scene_c
 
 class fs_options(ctypes.Structure):
     _fields_ = [("views_per_batch", ctypes.c_int32), ("time_stages", ctypes.c_int32),
-                ("depth_chunks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 13)]
+                ("depth_chunks", ctypes.c_int32), ("recheck_margin", ctypes.c_float),
+                ("recheck_reproject", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
 
 
 class fs_gaussians(ctypes.Structure):
@@ -55,7 +56,8 @@ class fs_stats(ctypes.Structure):
                 ("list_entries", ctypes.c_int64), ("bad_labels", ctypes.c_int64),
                 ("pairs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("blend_ms", ctypes.c_double), ("blend_launches", ctypes.c_int64),
-                ("staged_entries", ctypes.c_int64), ("reserved", ctypes.c_int64 * 3)]
+                ("staged_entries", ctypes.c_int64), ("rechecked", ctypes.c_int64),
+                ("recheck_pairs", ctypes.c_int64), ("recheck_rebinned", ctypes.c_int64)]
 
 
 class fs_result(ctypes.Structure):
@@ -130,12 +132,15 @@ def fs_last_error() -> str:
 
 
 def fs_create(device: int = 0, views_per_batch: int = 0, time_stages: bool = False,
-              depth_chunks: int = 0) -> int:
+              depth_chunks: int = 0, recheck_margin: float = 0.0,
+              recheck_reproject: bool = False) -> int:
     ctx = ctypes.c_void_p()
     opt = fs_options()
     opt.views_per_batch = views_per_batch
     opt.time_stages = 1 if time_stages else 0
     opt.depth_chunks = depth_chunks
+    opt.recheck_margin = recheck_margin
+    opt.recheck_reproject = 1 if recheck_reproject else 0
     check(load().fs_create(ctypes.byref(ctx), device, ctypes.byref(opt)))
     return ctx.value
 
@@ -219,10 +224,12 @@ class Solver:
     _DT = {"float32": FS_F32, "bfloat16": FS_BF16, "float16": FS_F16}
 
     def __init__(self, gaussians, device: int = 0, views_per_batch: int = 0,
-                 time_stages: bool = False, depth_chunks: int = 0):
+                 time_stages: bool = False, depth_chunks: int = 0, recheck_margin: float = 0.0,
+                 recheck_reproject: bool = False):
         torch = _torch()
         self.device = torch.device("cuda", device)
-        self.ctx = fs_create(device, views_per_batch, time_stages, depth_chunks)
+        self.ctx = fs_create(device, views_per_batch, time_stages, depth_chunks, recheck_margin,
+                             recheck_reproject)
         self.scene = None
         dev = {}
         for k in ("mean", "quat", "scale", "opacity"):

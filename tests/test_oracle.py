@@ -407,3 +407,13 @@ def test_risk_bounds_are_local(tiny):
     rel = r[s > 0] / s[s > 0]
     assert np.median(rel) < 1e-5
     assert (rel > 1e-3).mean() < 0.01
+
+
+def test_event_window_changes_risk_only(tiny):
+    """The near-threshold window shapes the risk bookkeeping, never the table:
+    a narrower window gives the same FP64 table and no more risk."""
+    a = oracle.accumulate(tiny.gaussians, tiny.cams[:3], tiny.masks[:3], tiny.E)
+    b = oracle.accumulate(tiny.gaussians, tiny.cams[:3], tiny.masks[:3], tiny.E, event_rel=1e-9)
+    assert np.array_equal(a.table, b.table)
+    assert b.risk.sum() <= a.risk.sum()
+    assert (b.risk > 0).sum() < (a.risk > 0).sum()
