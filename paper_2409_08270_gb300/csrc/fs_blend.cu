@@ -10,17 +10,20 @@
 //    sub-tile centre o (float pairs) and keeps the entry only when the
 //    alpha >= 1/255 region can reach the sub-tile; kept entries are compacted
 //    into shared memory in list order.
-//  * Per pixel, per kept Gaussian, without branches: w = W p + b,
+//  * Per pixel, per kept Gaussian, without branches and with packed FP32
+//    pairs for the lane's two pixels: w = W p + b,
 //    alpha = min(0.99, o 2^-|w|^2); alpha < 1/255 is skipped; the pixel stops
 //    before a Gaussian that would take T below 1e-4; else it adds alpha*T.
-//    T is kept per pixel across depth chunks (0 = stopped); a sub-tile whose
-//    pixels have all stopped is done, and a tile with four done sub-tiles is
-//    saturated (no later chunk lists it).
+//    The decisions are 1.0/0.0 factors, so a stopped pixel simply carries
+//    T = 0.  T is kept per pixel across depth chunks (0 = stopped); a
+//    sub-tile whose pixels have all stopped is done, and a tile with four
+//    done sub-tiles is saturated (no later chunk lists it).
 //  * No per-pixel atomics: the lane adds its two contributions when they
 //    share a label and writes one value per Gaussian into a shared row whose
 //    positions are ordered by label; lane j then sums Gaussian j's row per
-//    label (second pixels of another label are added one by one) and issues
-//    one global atomic add per non-zero (Gaussian, label).
+//    label and issues one global atomic add per non-zero (Gaussian, label).
+//    A lane whose two pixels straddle a label boundary adds its second
+//    pixel's contribution with its own atomic.
 #include "fs_common.cuh"
 #include "fs_internal.h"
 
@@ -45,21 +48,35 @@ __device__ __forceinline__ void table_add(TableT* p, float v) {
   atomicAdd(p, static_cast<TableT>(v));
 }
 
-// One compositing step of one pixel (Eq. 1), branch-free.
-__device__ __forceinline__ float composite(const float4& W, const float4& bo, float x, float y,
-                                          float& T, bool& done) {
-  const float w0 = fmaf(W.x, x, fmaf(W.y, y, bo.x));
-  const float w1 = fmaf(W.z, x, fmaf(W.w, y, bo.y));
-  const float q = fmaf(w0, w0, w1 * w1);
-  float a = fminf(kAlphaMax, bo.z * ex2_approx(-q));
-  a = done ? 0.f : a;
-  const float test_T = T * (1.f - a);
-  const bool ok = a >= kAlphaMin;
-  const bool stop = ok && (test_T < kTMin);
-  const bool add = ok && !stop;
-  const float c = add ? a * T : 0.f;
-  T = add ? test_T : T;
-  done = done || stop;
+// 1.0f if a >= b else 0.0f
+__device__ __forceinline__ float step_ge(float a, float b) {
+  float r;
+  asm("set.ge.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
+// One compositing step (Eq. 1) of the lane's two pixels, (x0, y) and
+// (x0 + 1, y), branch-free and with packed FP32 pairs.  T == 0 marks a pixel
+// that has stopped: its later steps give alpha' T = 0 and keep T = 0.
+//   alpha = min(0.99, o 2^-|w|^2),  alpha' = alpha if alpha >= 1/255 else 0
+//   T' = T (1 - alpha');  the pixel stops (T' < 1e-4) without adding,
+//   else it adds alpha' T and continues with T'.
+// `live` counts, per pixel, the steps taken while running on (not stopping).
+__device__ __forceinline__ float2 composite2(const float4& W, const float4& bo, float2 X, float y,
+                                             float2& T, float2& live) {
+  const float t0 = fmaf(W.y, y, bo.x), t1 = fmaf(W.w, y, bo.y);
+  const float2 w0 = __ffma2_rn(make_float2(W.x, W.x), X, make_float2(t0, t0));
+  const float2 w1 = __ffma2_rn(make_float2(W.z, W.z), X, make_float2(t1, t1));
+  const float2 q = __ffma2_rn(w0, w0, __fmul2_rn(w1, w1));
+  float2 a = __fmul2_rn(make_float2(bo.z, bo.z), make_float2(ex2_approx(-q.x), ex2_approx(-q.y)));
+  a.x = fminf(kAlphaMax, a.x);
+  a.y = fminf(kAlphaMax, a.y);
+  a = __fmul2_rn(a, make_float2(step_ge(a.x, kAlphaMin), step_ge(a.y, kAlphaMin)));
+  const float2 tt = __ffma2_rn(make_float2(-T.x, -T.y), a, T);
+  const float2 go = make_float2(step_ge(tt.x, kTMin), step_ge(tt.y, kTMin));
+  const float2 c = __fmul2_rn(__fmul2_rn(a, T), go);
+  T = __fmul2_rn(tt, go);
+  live = __fadd2_rn(live, go);
   return c;
 }
 
@@ -117,9 +134,7 @@ struct SubSmem {
   float4 bo[kStage];      // (b0, b1, opacity, -)
   int32_t gid[kStage];    // scene index of each staged Gaussian
   float buf[kStage][33];  // [Gaussian][lane position in label order]: main-label sums
-  float mbuf[kStage][33]; // [Gaussian][lane]: the lane's second pixel when its label differs
   int32_t poslab[32];     // label of each lane position (INT_MAX: none)
-  int32_t minlab[32];     // label of each lane's second pixel
 };
 
 template <typename LabelT, typename TableT>
@@ -154,8 +169,9 @@ __global__ void __launch_bounds__(32) blend_kernel(
   if (py < H && px0 + 1 < W) lab1 = static_cast<int>(mask[p0 + 1]);
   const bool valid0 = lab0 >= 0 && lab0 < E, valid1 = lab1 >= 0 && lab1 < E;
   float* const st = state + views[v].state_off;
-  float T0 = valid0 ? st[p0] : 0.f, T1 = valid1 ? st[p0 + 1] : 0.f;
-  bool done0 = !(T0 > 0.f), done1 = !(T1 > 0.f);
+  float2 T = make_float2(valid0 ? st[p0] : 0.f, valid1 ? st[p0 + 1] : 0.f);
+  const float2 T_start = T;
+  float2 live = make_float2(0.f, 0.f);
   // the lane's main label, and whether its second pixel has another one
   const int main_lab = valid0 ? lab0 : (valid1 ? lab1 : -1);
   const bool minor = valid0 && valid1 && lab1 != lab0;
@@ -170,7 +186,6 @@ __global__ void __launch_bounds__(32) blend_kernel(
     pos += (k < mkey || (k == mkey && l < lane)) ? 1 : 0;
   }
   S.poslab[pos] = mkey;
-  S.minlab[lane] = lab1;
   const uint32_t minor_lanes = __ballot_sync(0xffffffffu, minor);
   __syncwarp();
   const int plab = S.poslab[lane];
@@ -178,16 +193,16 @@ __global__ void __launch_bounds__(32) blend_kernel(
   const uint32_t segmask = __ballot_sync(0xffffffffu, lane == 0 || plab != plab_prev);
 
   // pixel centres relative to the sub-tile centre, in [-3.5, 3.5]
-  const float x0 = static_cast<float>(lx) - 3.5f, x1 = x0 + 1.f;
+  const float2 X = make_float2(static_cast<float>(lx) - 3.5f, static_cast<float>(lx) - 2.5f);
   const float yy = static_cast<float>(ly) - 3.5f;
   const float ox = static_cast<float>(tx * kTile + sx * 8 + 4);
   const float oy = static_cast<float>(ty * kTile + sy * 8 + 4);
   const uint32_t gbase = static_cast<uint32_t>(static_cast<int64_t>(v) * n);
   const uint32_t lt = lanemask_lt();
-  uint32_t n_eval = 0, n_staged = 0;
+  uint32_t n_staged = 0;
 
   for (uint32_t base = rg.x; base < rg.y; base += kStage) {
-    if (!__any_sync(0xffffffffu, !(done0 && done1))) break;
+    if (!__any_sync(0xffffffffu, T.x > 0.f || T.y > 0.f)) break;
     const int nin = static_cast<int>(min(static_cast<uint32_t>(kStage), rg.y - base));
     // stage the Gaussians whose alpha >= 1/255 region can reach this sub-tile
     bool keep = false;
@@ -226,23 +241,17 @@ __global__ void __launch_bounds__(32) blend_kernel(
     n_staged += static_cast<uint32_t>(ns);
     __syncwarp();
     if (minor_lanes) {
+      // a lane whose second pixel has another label adds that pixel's
+      // contribution itself (label boundaries only)
       for (int jj = 0; jj < ns; ++jj) {
-        const float4 wm = S.w[jj];
-        const float4 bo = S.bo[jj];
-        n_eval += (done0 ? 0u : 1u) + (done1 ? 0u : 1u);
-        const float c0 = composite(wm, bo, x0, yy, T0, done0);
-        const float c1 = composite(wm, bo, x1, yy, T1, done1);
-        S.buf[jj][pos] = fmaf(c0, w0, c1 * w1);
-        S.mbuf[jj][lane] = c1;
+        const float2 c = composite2(S.w[jj], S.bo[jj], X, yy, T, live);
+        S.buf[jj][pos] = fmaf(c.x, w0, c.y * w1);
+        if (minor && c.y != 0.f) table_add(&table[static_cast<int64_t>(S.gid[jj]) * E + lab1], c.y);
       }
     } else {
       for (int jj = 0; jj < ns; ++jj) {
-        const float4 wm = S.w[jj];
-        const float4 bo = S.bo[jj];
-        n_eval += (done0 ? 0u : 1u) + (done1 ? 0u : 1u);
-        const float c0 = composite(wm, bo, x0, yy, T0, done0);
-        const float c1 = composite(wm, bo, x1, yy, T1, done1);
-        S.buf[jj][pos] = fmaf(c0, w0, c1 * w1);
+        const float2 c = composite2(S.w[jj], S.bo[jj], X, yy, T, live);
+        S.buf[jj][pos] = fmaf(c.x, w0, c.y * w1);
       }
     }
     __syncwarp();
@@ -261,20 +270,17 @@ __global__ void __launch_bounds__(32) blend_kernel(
         for (int l = s0; l < s1; ++l) sum += S.buf[j][l];
         if (sum != 0.f) table_add(&table[rowbase + lab], sum);
       }
-      uint32_t mm = minor_lanes;
-      while (mm) {
-        const int l = __ffs(mm) - 1;
-        mm &= mm - 1;
-        const float c = S.mbuf[j][l];
-        if (c != 0.f) table_add(&table[rowbase + S.minlab[l]], c);
-      }
     }
     __syncwarp();
   }
 
-  if (valid0) st[p0] = done0 ? 0.f : T0;
-  if (valid1) st[p0 + 1] = done1 ? 0.f : T1;
-  if (__all_sync(0xffffffffu, done0 && done1) && lane == 0) {
+  if (valid0) st[p0] = T.x;
+  if (valid1) st[p0 + 1] = T.y;
+  // steps evaluated up to termination: those that ran on, plus the stop
+  uint32_t n_eval = static_cast<uint32_t>(live.x) + static_cast<uint32_t>(live.y) +
+                    ((T_start.x > 0.f && T.x == 0.f) ? 1u : 0u) +
+                    ((T_start.y > 0.f && T.y == 0.f) ? 1u : 0u);
+  if (__all_sync(0xffffffffu, T.x == 0.f && T.y == 0.f) && lane == 0) {
     const unsigned long long bit = 1ull << (gsub & 63);
     const unsigned long long nib = 0xFull << (gsub & 63 & ~3);
     const unsigned long long old =
