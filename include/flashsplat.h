@@ -230,6 +230,9 @@ fs_status fs_assign(fs_ctx* ctx, const void* table, int32_t table_dtype, int64_t
  * for this when device memory allows (about 4 B per list entry); a view
  * batch whose kept lists end before an exact walk does is binned anew
  * (counted in fs_stats.recheck_rebinned).
+ * The table itself is accumulated in FP64 (the cross-view sum of Eq. 6/7: a
+ * Gaussian seen in many views collects up to ~1e5 additions, too many for
+ * FP32 at 1e-5) and rounded once to out->table_dtype.
  * Outputs go where `out` says (out->memory: device buffers, or host buffers
  * filled by asynchronous copies on `stream` -- pinned host memory keeps them
  * asynchronous).  When out->table is NULL the table lives in the context's

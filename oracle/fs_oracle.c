@@ -209,8 +209,8 @@ typedef struct {
  * the oracle does not add but another walk could are listed with c = 0.
  * `use_bbox` skips candidates whose pixel bounding box excludes the pixel. */
 static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use_bbox,
-                      int px_i, int py_i, double ev_rel, fso_hit* hits, double* t_final,
-                      int64_t* n_eval) {
+                      int px_i, int py_i, double ev_rel, double depth_limit, fso_hit* hits,
+                      double* t_final, int64_t* n_eval) {
   const double px = px_i + 0.5, py = py_i + 0.5;
   double T = 1.0;
   int nh = 0;
@@ -222,6 +222,7 @@ static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use
   for (int64_t k = 0; k < n; ++k) {
     const int32_t g = cand[k];
     const fso_proj* p = &P[g];
+    if (p->depth > depth_limit) break; /* nothing tracked lies further back */
     if (use_bbox && (px_i < p->x0 || px_i > p->x1 || py_i < p->y0 || py_i > p->y1)) continue;
     ++*n_eval;
     const double dx = px - p->mx, dy = py - p->my;
@@ -334,10 +335,9 @@ typedef struct {
   int32_t* bin_list;  /* Gaussians per bin, each bin in depth order */
 } view_index;
 
-static int build_view(int64_t N, const float* mean, const float* quat, const float* scale,
-                      const float* opacity, const fso_camera* cam, int nthreads, fso_proj* P,
-                      int build_bins, view_index* vi) {
-  memset(vi, 0, sizeof(*vi));
+/* Projects all N Gaussians into the view (threads over index ranges). */
+static int project_all(int64_t N, const float* mean, const float* quat, const float* scale,
+                       const float* opacity, const fso_camera* cam, int nthreads, fso_proj* P) {
   if (nthreads < 1) nthreads = 1;
   proj_job* jobs = (proj_job*)calloc((size_t)nthreads, sizeof(proj_job));
   pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
@@ -353,14 +353,25 @@ static int build_view(int64_t N, const float* mean, const float* quat, const flo
   }
   free(jobs);
   free(th);
-  if (status) return status;
+  return status;
+}
 
+/* Depth order and spatial bins of the projected Gaussians P.  rect
+ * (x0, x1, y0, y1) or NULL: only Gaussians whose pixel bounding box meets the
+ * rect are indexed (the others cannot reach a pixel inside it). */
+static int index_view(int64_t N, const fso_camera* cam, const fso_proj* P, int build_bins,
+                      const int* rect, view_index* vi) {
+  memset(vi, 0, sizeof(*vi));
   int64_t nv = 0;
   for (int64_t i = 0; i < N; ++i) nv += P[i].valid;
   vi->order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
   nv = 0;
-  for (int64_t i = 0; i < N; ++i)
-    if (P[i].valid) vi->order[nv++] = (int32_t)i;
+  for (int64_t i = 0; i < N; ++i) {
+    if (!P[i].valid) continue;
+    if (rect && (P[i].x1 < rect[0] || P[i].x0 > rect[1] || P[i].y1 < rect[2] || P[i].y0 > rect[3]))
+      continue;
+    vi->order[nv++] = (int32_t)i;
+  }
   vi->n_valid = nv;
   g_sort_P = P;
   qsort(vi->order, (size_t)nv, sizeof(int32_t), cmp_depth);
@@ -412,6 +423,7 @@ typedef struct {
   int32_t E;
   int cull_mode;
   double ev_rel;            /* near-threshold window (relative) */
+  double depth_limit;       /* walks end beyond this depth (tracked rows only) */
   int nthreads, tid;
   double* t_final;          /* this view's slice or NULL */
   /* per thread */
@@ -440,8 +452,8 @@ static void* acc_worker(void* arg) {
         n = j->vi->bin_start[b + 1] - j->vi->bin_start[b];
       }
       double tf;
-      const int nh = walk_pixel(j->P, cand, n, j->cull_mode != 1, x, y, j->ev_rel, j->hits, &tf,
-                                &j->n_eval);
+      const int nh = walk_pixel(j->P, cand, n, j->cull_mode != 1, x, y, j->ev_rel,
+                                j->depth_limit, j->hits, &tf, &j->n_eval);
       if (j->t_final) j->t_final[pix] = tf;
       const int32_t lab = j->mask[pix];
       const int lab_ok = (lab >= 0 && lab < j->E);
@@ -461,6 +473,101 @@ static void* acc_worker(void* arg) {
   return NULL;
 }
 
+/* Tracked rows (sel): each tracked Gaussian g is handled on its own, per
+ * view.  Its candidates are the Gaussians whose bounding box meets g's, in
+ * (depth, index) order -- every Gaussian that covers a pixel of g's box is
+ * among them -- and only the pixels of g's box are walked, adding only g's
+ * terms.  Row r belongs to thread r % nthreads, so each row's sum has a fixed
+ * order. */
+typedef struct {
+  const fso_proj* P;
+  int64_t N;
+  const fso_camera* cam;
+  const int32_t* mask;
+  const int64_t* sel;
+  int64_t n_sel;
+  int32_t E;
+  double ev_rel;
+  int nthreads, tid;
+  double* table;            /* [rows][E], this thread's rows only */
+  double* risk;
+  uint8_t* flags;
+  int32_t* cand;            /* capacity N */
+  fso_hit* hits;            /* capacity N */
+  int64_t n_eval, n_hit, n_bad;
+} sel_job;
+
+static void* sel_worker(void* arg) {
+  sel_job* j = (sel_job*)arg;
+  const fso_proj* P = j->P;
+  const int W = j->cam->width;
+  for (int64_t r = j->tid; r < j->n_sel; r += j->nthreads) {
+    const int32_t g = (int32_t)j->sel[r];
+    const fso_proj* pg = &P[g];
+    if (!pg->valid) continue;
+    int64_t nc = 0;
+    for (int64_t i = 0; i < j->N; ++i) {
+      const fso_proj* q = &P[i];
+      if (q->valid && !(q->x1 < pg->x0 || q->x0 > pg->x1 || q->y1 < pg->y0 || q->y0 > pg->y1))
+        j->cand[nc++] = (int32_t)i;
+    }
+    qsort(j->cand, (size_t)nc, sizeof(int32_t), cmp_depth);
+    /* 8x8-pixel bins over g's box, each holding its candidates in order */
+    const int nbx = (pg->x1 - pg->x0) / FSO_BIN + 1, nby = (pg->y1 - pg->y0) / FSO_BIN + 1;
+    const int64_t nb = (int64_t)nbx * nby;
+    int64_t* start = (int64_t*)calloc((size_t)nb + 1, sizeof(int64_t));
+    for (int64_t k = 0; k < nc; ++k) {
+      const fso_proj* q = &P[j->cand[k]];
+      const int bx0 = ((q->x0 > pg->x0 ? q->x0 : pg->x0) - pg->x0) / FSO_BIN;
+      const int bx1 = ((q->x1 < pg->x1 ? q->x1 : pg->x1) - pg->x0) / FSO_BIN;
+      const int by0 = ((q->y0 > pg->y0 ? q->y0 : pg->y0) - pg->y0) / FSO_BIN;
+      const int by1 = ((q->y1 < pg->y1 ? q->y1 : pg->y1) - pg->y0) / FSO_BIN;
+      for (int by = by0; by <= by1; ++by)
+        for (int bx = bx0; bx <= bx1; ++bx) start[(int64_t)by * nbx + bx + 1]++;
+    }
+    for (int64_t b = 0; b < nb; ++b) start[b + 1] += start[b];
+    int32_t* list = (int32_t*)malloc(sizeof(int32_t) * (size_t)(start[nb] > 0 ? start[nb] : 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)nb);
+    memcpy(fill, start, sizeof(int64_t) * (size_t)nb);
+    for (int64_t k = 0; k < nc; ++k) {
+      const fso_proj* q = &P[j->cand[k]];
+      const int bx0 = ((q->x0 > pg->x0 ? q->x0 : pg->x0) - pg->x0) / FSO_BIN;
+      const int bx1 = ((q->x1 < pg->x1 ? q->x1 : pg->x1) - pg->x0) / FSO_BIN;
+      const int by0 = ((q->y0 > pg->y0 ? q->y0 : pg->y0) - pg->y0) / FSO_BIN;
+      const int by1 = ((q->y1 < pg->y1 ? q->y1 : pg->y1) - pg->y0) / FSO_BIN;
+      for (int by = by0; by <= by1; ++by)
+        for (int bx = bx0; bx <= bx1; ++bx) list[fill[(int64_t)by * nbx + bx]++] = j->cand[k];
+    }
+    free(fill);
+    /* a walk can end past g: later Gaussians do not change earlier terms
+     * (the margin keeps exact depth ties with g inside the walk) */
+    const double depth_limit = pg->depth * (1.0 + 1e-9);
+    for (int y = pg->y0; y <= pg->y1; ++y) {
+      for (int x = pg->x0; x <= pg->x1; ++x) {
+        double tf;
+        const int64_t b = (int64_t)((y - pg->y0) / FSO_BIN) * nbx + (x - pg->x0) / FSO_BIN;
+        const int nh = walk_pixel(P, list + start[b], start[b + 1] - start[b], 1, x, y, j->ev_rel,
+                                  depth_limit, j->hits, &tf, &j->n_eval);
+        const int32_t lab = j->mask[(int64_t)y * W + x];
+        const int lab_ok = (lab >= 0 && lab < j->E);
+        if (!lab_ok) j->n_bad++;
+        for (int h = 0; h < nh; ++h) {
+          if (j->hits[h].g != g) continue;
+          if (j->hits[h].c > 0.0) j->n_hit++;
+          j->flags[r] |= j->hits[h].flag;
+          if (lab_ok) {
+            j->table[r * j->E + lab] += j->hits[h].c;
+            j->risk[r * j->E + lab] += j->hits[h].risk;
+          }
+        }
+      }
+    }
+    free(start);
+    free(list);
+  }
+  return NULL;
+}
+
 /*
  * fso_accumulate: fill table[rows][E] (FP64) with the per-label contribution
  * sums of Eq. 6/7 over all V views, and risk[rows][E] with the summed bounds
@@ -469,11 +576,11 @@ static void* acc_worker(void* arg) {
  *   mean[N*3], quat[N*4] (w,x,y,z), scale[N*3] (linear), opacity[N] (activated)
  *   cams[V]; masks: view v's int32 labels at masks + mask_offsets[v] (H*W)
  *   sel: NULL -> rows = N, row i = Gaussian i; otherwise n_sel sorted Gaussian
- *        indices and only those rows are tracked (pixels outside the union of
- *        their bounding boxes are not walked, which does not change the rows)
+ *        indices and only those rows are tracked (each is walked on its own
+ *        over its bounding box; see sel_worker -- the rows do not change)
  *   cull_mode: 0 = spatial bins, 1 = every pixel walks every Gaussian
  *   t_final: NULL or [sum_v H*W] transmittance left at each pixel (-1 where
- *        the pixel was not walked)
+ *        the pixel was not walked); only without sel
  *   stats[4]: evaluated pairs, contributing pairs, pixels with bad labels,
  *        tracked Gaussians that were never valid in any view
  *   event_rel: relative window around the 1/255 and 1e-4 thresholds inside
@@ -487,6 +594,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
                    double* table, double* risk, uint8_t* flags, double* t_final,
                    int64_t* stats, double event_rel) {
   if (N < 0 || V < 0 || E < 1 || (sel && n_sel < 0)) return -2;
+  if (sel && t_final) return -2;
   if (!(event_rel > 0.0)) event_rel = FSO_EVENT_REL;
   if (nthreads < 1) nthreads = 1;
   const int64_t rows = sel ? n_sel : N;
@@ -519,22 +627,40 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
     const fso_camera* cam = &cams[v];
     const int64_t npix = (int64_t)cam->width * cam->height;
     view_index vi;
-    status = build_view(N, mean, quat, scale, opacity, cam, nthreads, P, cull_mode != 1, &vi);
+    status = project_all(N, mean, quat, scale, opacity, cam, nthreads, P);
+    if (status) break;
+    if (sel) {
+      int any = 0;
+      for (int64_t r = 0; r < n_sel; ++r)
+        if (P[sel[r]].valid) seen[r] = any = 1;
+      if (any) {
+        g_sort_P = P;
+        sel_job* sj = (sel_job*)calloc((size_t)nthreads, sizeof(sel_job));
+        for (int t = 0; t < nthreads; ++t) {
+          sj[t] = (sel_job){P, N, cam, masks + mask_offsets[v], sel, n_sel, E, event_rel,
+                            nthreads, t, jobs[t].table, jobs[t].risk, jobs[t].flags,
+                            (int32_t*)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1)),
+                            (fso_hit*)malloc(sizeof(fso_hit) * (size_t)(N > 0 ? N : 1)), 0, 0, 0};
+          pthread_create(&th[t], NULL, sel_worker, &sj[t]);
+        }
+        for (int t = 0; t < nthreads; ++t) {
+          pthread_join(th[t], NULL);
+          jobs[t].n_eval += sj[t].n_eval;
+          jobs[t].n_hit += sj[t].n_hit;
+          jobs[t].n_bad += sj[t].n_bad;
+          free(sj[t].cand);
+          free(sj[t].hits);
+        }
+        free(sj);
+      }
+      pix_base += npix;
+      continue;
+    }
+    status = index_view(N, cam, P, cull_mode != 1, NULL, &vi);
     if (status) { free_view(&vi); break; }
     for (int64_t i = 0; i < N; ++i)
-      if (P[i].valid) {
-        const int64_t r = slot ? slot[i] : i;
-        if (r >= 0) seen[r] = 1;
-      }
+      if (P[i].valid) seen[i] = 1;
     uint8_t* pix_sel = NULL;
-    if (sel) { /* union of the tracked Gaussians' bounding boxes */
-      pix_sel = (uint8_t*)calloc((size_t)(npix > 0 ? npix : 1), 1);
-      for (int64_t r = 0; r < n_sel; ++r) {
-        const fso_proj* p = &P[sel[r]];
-        if (!p->valid) continue;
-        for (int y = p->y0; y <= p->y1; ++y) memset(pix_sel + (int64_t)y * cam->width + p->x0, 1, (size_t)(p->x1 - p->x0 + 1));
-      }
-    }
     if (t_final) {
       for (int64_t k = 0; k < npix; ++k) t_final[pix_base + k] = -1.0;
     }
@@ -553,6 +679,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
       j->P = P; j->vi = &vi; j->cam = cam; j->mask = masks + mask_offsets[v];
       j->slot = slot; j->pix_sel = pix_sel; j->E = E; j->cull_mode = cull_mode;
       j->ev_rel = event_rel;
+      j->depth_limit = INFINITY;
       j->nthreads = nthreads; j->tid = t;
       j->t_final = t_final ? t_final + pix_base : NULL;
       j->hits = (fso_hit*)malloc(sizeof(fso_hit) * (size_t)(max_cand > 0 ? max_cand : 1));
@@ -608,7 +735,8 @@ int64_t fso_pixel_lists(int64_t N, const float* mean, const float* quat, const f
   for (int32_t v = 0; v < V; ++v) {
     const fso_camera* cam = &cams[v];
     view_index vi;
-    const int st = build_view(N, mean, quat, scale, opacity, cam, 1, P, cull_mode != 1, &vi);
+    int st = project_all(N, mean, quat, scale, opacity, cam, 1, P);
+    if (st == 0) st = index_view(N, cam, P, cull_mode != 1, NULL, &vi);
     if (st) { free_view(&vi); free(P); free(hits); return -1; }
     for (int y = 0; y < cam->height; ++y)
       for (int x = 0; x < cam->width; ++x) {
@@ -622,8 +750,8 @@ int64_t fso_pixel_lists(int64_t N, const float* mean, const float* quat, const f
           n = vi.bin_start[b + 1] - vi.bin_start[b];
         }
         double tf;
-        const int nh = walk_pixel(P, cand, n, cull_mode != 1, x, y, FSO_EVENT_REL, hits, &tf,
-                                &n_eval);
+        const int nh = walk_pixel(P, cand, n, cull_mode != 1, x, y, FSO_EVENT_REL, INFINITY,
+                                hits, &tf, &n_eval);
         pix_offsets[pix] = total;
         if (t_final) t_final[pix] = tf;
         for (int h = 0; h < nh; ++h) {

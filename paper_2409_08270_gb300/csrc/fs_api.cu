@@ -169,7 +169,7 @@ struct fs_ctx {
   // workspace
   DevBuf views, rec, foot, cnt, key_a, val_a, key_b, val_b, offs, ccnt, dlo, state, sat, subsat;
   DevBuf lk_a, lv_a, lk_b, lv_b, ranges, sort_tmp, scan_tmp, total, counters;
-  DevBuf mask_stage, table_tmp, bits_tmp, label_tmp, margin_tmp;
+  DevBuf mask_stage, table_tmp, table32_tmp, bits_tmp, label_tmp, margin_tmp;
   // near-tie re-check: resident per-view depth keys, flagged set, FP64 rows
   float recheck_margin = 1e-4f;  // <= 0: off
   bool recheck_reproject = false;
@@ -249,7 +249,7 @@ fs_status fs_destroy(fs_ctx* c) {
   DevBuf* bufs[] = {&c->subsat, &c->ccnt, &c->dlo, &c->state, &c->sat, &c->views, &c->rec, &c->foot, &c->cnt, &c->key_a, &c->val_a, &c->key_b,
                     &c->val_b, &c->offs, &c->lk_a, &c->lv_a, &c->lk_b, &c->lv_b, &c->ranges,
                     &c->sort_tmp, &c->scan_tmp, &c->total, &c->counters, &c->mask_stage,
-                    &c->table_tmp, &c->bits_tmp, &c->label_tmp, &c->margin_tmp,
+                    &c->table_tmp, &c->table32_tmp, &c->bits_tmp, &c->label_tmp, &c->margin_tmp,
                     &c->dkey, &c->rk_flag, &c->rk_offs, &c->rk_F, &c->rk_map, &c->rk_R,
                     &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_bound};
   for (DevBuf& b : c->kl_val) b.release();
@@ -949,9 +949,12 @@ fs_status fs_solve(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t 
   DeviceGuard g(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = s->n;
-  const size_t tbytes = static_cast<size_t>(n) * E * dtype_size(tdt);
+  // The cross-view reduction always runs in FP64: a Gaussian seen in many
+  // views collects up to ~1e5 atomic adds, whose FP32 rounding alone would
+  // exceed 1e-5 relative.  An FP32 result is rounded once at the end.
+  const size_t tbytes = static_cast<size_t>(n) * E * 8;
   const bool dev_out = out->memory == FS_MEM_DEVICE;
-  void* table = (dev_out && out->table) ? out->table : nullptr;
+  void* table = (dev_out && out->table && tdt == FS_F64) ? out->table : nullptr;
   if (!table) {
     FS_TRY(c->table_tmp.ensure(tbytes > 0 ? tbytes : 8, "table"));
     table = c->table_tmp.p;
@@ -973,7 +976,8 @@ fs_status fs_solve(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t 
       keep = need <= have + 0.5 * static_cast<double>(free_b);
     }
   }
-  FS_TRY(accumulate_impl(c, s, cams, V, masks, mask_dtype, mask_memory, E, table, tdt, keep, st));
+  FS_TRY(accumulate_impl(c, s, cams, V, masks, mask_dtype, mask_memory, E, table, FS_F64, keep,
+                         st));
   uint64_t* bits = out->member_bits;
   int32_t* label = out->label;
   float* margin = out->margin;
@@ -988,15 +992,34 @@ fs_status fs_solve(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t 
     margin = c->margin_tmp.as<float>();
   }
   if (bits || label || margin) {
-    FS_CUDA(fs::launch_assign(table, tdt, n, E, gamma, bits, label, margin, st), "assign");
+    FS_CUDA(fs::launch_assign(table, FS_F64, n, E, gamma, bits, label, margin, st), "assign");
     if (n > 0) c->stats.kernel_launches += 1;
   }
   if (recheck)
-    FS_TRY(recheck_impl(c, s, cams, V, mask_dtype, E, gamma, table, tdt, bits, label, margin,
+    FS_TRY(recheck_impl(c, s, cams, V, mask_dtype, E, gamma, table, FS_F64, bits, label, margin,
                         keep, st));
+  // the caller's table: rounded once to FP32, or the FP64 sums themselves
+  const int64_t count = n * static_cast<int64_t>(E);
+  const void* result = table;
+  if (out->table && tdt == FS_F32) {
+    float* dst = static_cast<float*>(out->table);
+    if (!dev_out) {
+      FS_TRY(c->table32_tmp.ensure(static_cast<size_t>(count > 0 ? count : 1) * 4, "table"));
+      dst = c->table32_tmp.as<float>();
+    }
+    c->stats.kernel_launches += count > 0 ? 1 : 0;
+    FS_CUDA(fs::launch_round_table(count, static_cast<const double*>(table), dst, st),
+            "table rounding");
+    result = dst;
+  } else if (out->table && dev_out && table != out->table) {
+    FS_CUDA(cudaMemcpyAsync(out->table, table, tbytes, cudaMemcpyDeviceToDevice, st),
+            "table copy");
+  }
   if (!dev_out && n > 0) {
     if (out->table)
-      FS_CUDA(cudaMemcpyAsync(out->table, table, tbytes, cudaMemcpyDeviceToHost, st), "table D2H");
+      FS_CUDA(cudaMemcpyAsync(out->table, result, static_cast<size_t>(count) * dtype_size(tdt),
+                              cudaMemcpyDeviceToHost, st),
+              "table D2H");
     if (out->member_bits)
       FS_CUDA(cudaMemcpyAsync(out->member_bits, bits, n * 8, cudaMemcpyDeviceToHost, st), "D2H");
     if (out->label)

@@ -59,6 +59,13 @@ __global__ void __launch_bounds__(256) assign_kernel(const T* __restrict__ table
   if (margin) margin[i] = d.margin;
 }
 
+__global__ void __launch_bounds__(256) round_table_kernel(int64_t count,
+                                                          const double* __restrict__ src,
+                                                          float* __restrict__ dst) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = static_cast<float>(src[i]);
+}
+
 // Rows re-evaluated in FP64: row j of R belongs to Gaussian F[j].  The row
 // replaces the table's (rounded to its type) and the decision is taken again
 // in FP64.
@@ -93,6 +100,15 @@ cudaError_t launch_assign(const void* table, int table_dtype, int64_t n, int E, 
     assign_kernel<double><<<blocks, threads, 0, stream>>>(static_cast<const double*>(table), n, E,
                                                           static_cast<double>(gamma), member_bits,
                                                           label, margin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_round_table(int64_t count, const double* src, float* dst,
+                               cudaStream_t stream) {
+  if (count == 0) return cudaSuccess;
+  const int threads = 256;
+  round_table_kernel<<<static_cast<unsigned>((count + threads - 1) / threads), threads, 0,
+                       stream>>>(count, src, dst);
   return cudaGetLastError();
 }
 

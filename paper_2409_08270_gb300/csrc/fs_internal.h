@@ -75,6 +75,8 @@ cudaError_t launch_assign(const void* table, int table_dtype, int64_t n, int E, 
                           uint64_t* member_bits, int32_t* label, float* margin,
                           cudaStream_t stream);
 
+// dst[i] = (float) src[i], i < count
+cudaError_t launch_round_table(int64_t count, const double* src, float* dst, cudaStream_t stream);
 // Table rows re-decided from FP64 rows R[n_rows][E] (row j is Gaussian F[j]):
 // the table row is overwritten with R's (rounded to table_dtype).
 cudaError_t launch_assign_rows(const double* R, const uint32_t* F, int64_t n_rows, int E,
