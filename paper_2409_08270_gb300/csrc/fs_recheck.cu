@@ -21,8 +21,9 @@
 // batch with the dedicated binning.
 //
 // alpha = o 2^-|W p + c|^2 from the float-pair whitening record of the
-// projection; 2^-q uses a 64-entry table of 2^(-j/64) (computed in FP64) and
-// a degree-4 Taylor polynomial of e^-x on the remaining [0, ln2/64).
+// projection; 2^-q follows Tang's table-driven method (ACM TOMS 15(2), 1989):
+// a 64-entry table of 2^(-j/64) (computed in FP64) times a degree-4 Taylor
+// polynomial of e^-x on the remaining [0, ln2/64).
 #include <math.h>
 
 #include "fs_binning.cuh"
