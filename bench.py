@@ -52,15 +52,22 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-views", type=int, default=12)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"],
+                    help="fp16: the reduced-precision form (BF16 quat/scale, FP16 opacity, "
+                         "per-view records with an FP16 whitening matrix and FP32 mean)")
     ap.add_argument("--recheck-margin", type=float, default=0.0,
                     help="FP64 re-check of decisions with a margin below this (0: library "
                          "default 1e-4; negative: off)")
     return ap.parse_args()
 
 
-def workload(args):
+def synth_mod():
     from paper_2409_08270_gb300 import synth
-    return synth.binary_scene(n=args.n, views=args.views)
+    return synth
+
+
+def workload(args):
+    return synth_mod().binary_scene(n=args.n, views=args.views)
 
 
 def config_of(w, args, extra=None):
@@ -68,7 +75,9 @@ def config_of(w, args, extra=None):
                      f"{w.cams[0]['width']}x{w.cams[0]['height']}, uint8 masks, gamma {w.gamma}",
          "gaussians": w.n, "views": len(w.cams), "width": w.cams[0]["width"],
          "height": w.cams[0]["height"], "labels": w.E, "gamma": w.gamma,
-         "pixels_per_scene": w.pixels, "table": "fp32 [N x E]",
+         "pixels_per_scene": w.pixels, "table": "fp32 [N x E] (FP64 cross-view sum)",
+         "form": ("reduced precision: BF16 quat/scale, FP16 opacity, FP16 whitening + FP32 "
+                  "mean per view" if args.precision == "fp16" else "plain FP32"),
          "mask_noise_fraction": round(w.info.get("noise_fraction", 0.0), 4)}
     if extra:
         c.update(extra)
@@ -147,8 +156,16 @@ def run_flashsplat(args, rank, world, local_rank):
     w = workload(args)
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
-    solver = fsb.Solver(w.gaussians, device=local_rank, views_per_batch=args.views_per_batch,
-                        time_stages=True, recheck_margin=args.recheck_margin)
+    gaussians = w.gaussians
+    if args.precision == "fp16":
+        r = synth_mod().rounded_gaussians(w.gaussians)
+        gaussians = {"mean": torch.from_numpy(r["mean"]),
+                     "quat": torch.from_numpy(r["quat"]).to(torch.bfloat16),
+                     "scale": torch.from_numpy(r["scale"]).to(torch.bfloat16),
+                     "opacity": torch.from_numpy(r["opacity"]).to(torch.float16)}
+    solver = fsb.Solver(gaussians, device=local_rank, views_per_batch=args.views_per_batch,
+                        time_stages=True, recheck_margin=args.recheck_margin,
+                        record_precision=fsb.FS_F16 if args.precision == "fp16" else 0)
     dmasks = solver.upload_masks(w.masks)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)

@@ -88,7 +88,13 @@ typedef struct fs_options {
    * memory allows (about 108 B per Gaussian and view), else project again;
    * 1: always project again. */
   int32_t recheck_reproject;
-  int32_t reserved[11];
+  /* 0: per-view projected records in float pairs (64 B); FS_F16: the
+   * reduced-precision form -- each (view, Gaussian) keeps its projected mean
+   * in FP32 and its whitening matrix W (|W d|^2 = 0.5 log2(e) d^T
+   * Sigma2D^-1 d) in FP16, 16 B, and alpha = o 2^-|W (p - m)|^2 is evaluated
+   * from those rounded values (blending in FP32, table in FP64). */
+  int32_t record_precision;
+  int32_t reserved[10];
 } fs_options;
 
 /* A Gaussian scene (Sec. 3.1: G_i = {m_i, q_i, s_i, o_i}; colour unused). */

@@ -70,7 +70,7 @@ def _load():
     i64, i32, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
     lib.fso_accumulate.restype = ctypes.c_int
     lib.fso_accumulate.argtypes = [i64, vp, vp, vp, vp, i32, vp, vp, vp, i32, vp, i64, i32, i32,
-                                   vp, vp, vp, vp, vp, ctypes.c_double]
+                                   vp, vp, vp, vp, vp, ctypes.c_double, i32]
     lib.fso_pixel_lists.restype = ctypes.c_int64
     lib.fso_pixel_lists.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, i64, vp, vp, vp, vp]
     lib.fso_project_view.restype = ctypes.c_int
@@ -119,7 +119,7 @@ class Accumulation:
 
 def accumulate(gaussians, cams, masks, E: int, sel=None, cull_mode: int = 0,
                nthreads: int | None = None, want_t_final: bool = False,
-               event_rel: float = 1e-4) -> Accumulation:
+               event_rel: float = 1e-4, record_f16: bool = False) -> Accumulation:
     """Contribution table of Eq. 6 / Eq. 7 in FP64.
 
     gaussians: dict with mean [N,3], quat [N,4] (w,x,y,z), scale [N,3] (linear),
@@ -128,6 +128,9 @@ def accumulate(gaussians, cams, masks, E: int, sel=None, cull_mode: int = 0,
     event_rel: relative window around the 1/255 and 1e-4 thresholds inside
     which a decision counts as marginal in `risk` (1e-4 suits an FP32
     implementation; an FP64 one is compared with a far narrower window).
+    record_f16: alpha from the reduced-precision record of each (view,
+    Gaussian) -- the whitening matrix rounded to FP16 and the mean to FP32 --
+    evaluated in FP64 (the oracle of the reduced-precision form).
     """
     lib = _load()
     mean = _f32(gaussians["mean"], 3)
@@ -167,7 +170,7 @@ def accumulate(gaussians, cams, masks, E: int, sel=None, cull_mode: int = 0,
                             _ptr(allm), _ptr(offs), E, _ptr(sel),
                             0 if sel is None else sel.size, cull_mode, nthreads,
                             _ptr(table), _ptr(risk), _ptr(flags), _ptr(tf), _ptr(stats),
-                            float(event_rel))
+                            float(event_rel), 1 if record_f16 else 0)
     if rc != 0:
         raise ValueError(f"fso_accumulate failed with code {rc}")
     return Accumulation(table, risk, flags[:rows], None if tf is None else tf[:acc],

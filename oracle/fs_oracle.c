@@ -46,6 +46,7 @@
 #define FSO_NEAR_PLANE 0.2
 #define FSO_LOWPASS 0.3
 #define FSO_BIN 8
+#define FSO_HALF_LOG2E 0.72134752044448170368 /* 0.5 log2(e) */
 
 /* Default near-threshold window (relative) used to flag discrete decisions
  * that a lower-precision implementation may legitimately take the other way.
@@ -82,6 +83,11 @@ typedef struct {
   double ca, cb, cc;   /* conic = inverse 2D covariance [[ca cb][cb cc]] */
   double opacity;
   int x0, x1, y0, y1;  /* inclusive pixel bounding box of the alpha>=1/255 ellipse */
+  /* reduced-precision record (record_f16): alpha = o 2^-|W (p - m)|^2 with
+   * the whitening matrix W rounded to FP16 and the mean m rounded to FP32 */
+  int f16;
+  double w[4];         /* W row-major, each entry an FP16 value */
+  double mxr, myr;     /* mean, each an FP32 value */
 } fso_proj;
 
 /* ------------------------------------------------------------------------ */
@@ -90,8 +96,9 @@ typedef struct {
 /* ------------------------------------------------------------------------ */
 
 static int project_one(const fso_camera* cam, const float* m, const float* q4,
-                       const float* s3, float opac, fso_proj* p) {
+                       const float* s3, float opac, int record_f16, fso_proj* p) {
   p->valid = 0;
+  p->f16 = 0;
   const double mx = m[0], my = m[1], mz = m[2];
   const double* R = cam->R;
   const double tx = R[0] * mx + R[1] * my + R[2] * mz + cam->t[0];
@@ -165,6 +172,28 @@ static int project_one(const fso_camera* cam, const float* m, const float* q4,
   p->cb = -sb / det;
   p->cc = sa / det;
   p->opacity = o;
+  if (record_f16) {
+    /* Whitening matrix W with |W d|^2 = 0.5 log2(e) d^T Sigma^-1 d:
+     * W = sqrt(0.5 log2 e) diag(lambda1, lambda2)^-1/2 [e1 e2]^T, e1 the unit
+     * eigenvector of the larger eigenvalue taken as (h + r, b) for h >= 0 and
+     * (b, r - h) otherwise (h = (a - c)/2, r = sqrt(h^2 + b^2)), e2 = e1
+     * turned by +90 degrees; then each entry rounded to FP16 and the mean to
+     * FP32 (the reduced-precision record). */
+    const double h = 0.5 * (sa - sc), rr = sqrt(h * h + sb * sb);
+    const double l1 = 0.5 * (sa + sc) + rr, l2 = det / l1;
+    double ex, ey;
+    if (h >= 0.0) { ex = h + rr; ey = sb; } else { ex = sb; ey = rr - h; }
+    const double en = sqrt(ex * ex + ey * ey);
+    if (en > 0.0) { ex /= en; ey /= en; } else { ex = 1.0; ey = 0.0; }
+    const double k1 = sqrt(FSO_HALF_LOG2E / l1), k2 = sqrt(FSO_HALF_LOG2E / l2);
+    p->w[0] = (double)(_Float16)(ex * k1);
+    p->w[1] = (double)(_Float16)(ey * k1);
+    p->w[2] = (double)(_Float16)(-ey * k2);
+    p->w[3] = (double)(_Float16)(ex * k2);
+    p->mxr = (double)(float)p->mx;
+    p->myr = (double)(float)p->my;
+    p->f16 = 1;
+  }
 
   /* alpha >= 1/255 requires d^T C d <= 2 ln(255 o); the ellipse
    * {d : d^T Sigma^-1 d <= r2} has half extents sqrt(Sigma_xx r2),
@@ -225,9 +254,16 @@ static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use
     if (p->depth > depth_limit) break; /* nothing tracked lies further back */
     if (use_bbox && (px_i < p->x0 || px_i > p->x1 || py_i < p->y0 || py_i > p->y1)) continue;
     ++*n_eval;
-    const double dx = px - p->mx, dy = py - p->my;
-    const double power = -0.5 * (p->ca * dx * dx + p->cc * dy * dy) - p->cb * dx * dy;
-    double alpha = p->opacity * exp(power);
+    double alpha;
+    if (p->f16) {
+      const double dx = px - p->mxr, dy = py - p->myr;
+      const double w0 = p->w[0] * dx + p->w[1] * dy, w1 = p->w[2] * dx + p->w[3] * dy;
+      alpha = p->opacity * exp2(-(w0 * w0 + w1 * w1));
+    } else {
+      const double dx = px - p->mx, dy = py - p->my;
+      const double power = -0.5 * (p->ca * dx * dx + p->cc * dy * dy) - p->cb * dx * dy;
+      alpha = p->opacity * exp(power);
+    }
     if (alpha > FSO_ALPHA_MAX) alpha = FSO_ALPHA_MAX;
     const int a_edge = fabs(alpha - FSO_ALPHA_MIN) <= ev_rel * FSO_ALPHA_MIN;
     if (stopped) {
@@ -314,6 +350,7 @@ typedef struct {
   const fso_camera* cam;
   fso_proj* P;
   int64_t begin, end;
+  int record_f16;
   int status;
 } proj_job;
 
@@ -321,7 +358,7 @@ static void* proj_worker(void* arg) {
   proj_job* j = (proj_job*)arg;
   for (int64_t i = j->begin; i < j->end; ++i) {
     if (project_one(j->cam, j->mean + 3 * i, j->quat + 4 * i, j->scale + 3 * i, j->opacity[i],
-                    &j->P[i]) < 0)
+                    j->record_f16, &j->P[i]) < 0)
       j->status = -1;
   }
   return NULL;
@@ -337,13 +374,14 @@ typedef struct {
 
 /* Projects all N Gaussians into the view (threads over index ranges). */
 static int project_all(int64_t N, const float* mean, const float* quat, const float* scale,
-                       const float* opacity, const fso_camera* cam, int nthreads, fso_proj* P) {
+                       const float* opacity, const fso_camera* cam, int nthreads, int record_f16,
+                       fso_proj* P) {
   if (nthreads < 1) nthreads = 1;
   proj_job* jobs = (proj_job*)calloc((size_t)nthreads, sizeof(proj_job));
   pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
   for (int t = 0; t < nthreads; ++t) {
     jobs[t] = (proj_job){N, mean, quat, scale, opacity, cam, P, N * t / nthreads,
-                         N * (t + 1) / nthreads, 0};
+                         N * (t + 1) / nthreads, record_f16, 0};
     pthread_create(&th[t], NULL, proj_worker, &jobs[t]);
   }
   int status = 0;
@@ -585,6 +623,8 @@ static void* sel_worker(void* arg) {
  *        tracked Gaussians that were never valid in any view
  *   event_rel: relative window around the 1/255 and 1e-4 thresholds inside
  *        which a decision is counted as marginal in `risk` (<= 0: 1e-4)
+ *   record_f16: non-zero -> alpha from the reduced-precision record (FP16
+ *        whitening matrix, FP32 mean; see fso_proj), all else unchanged
  * Returns 0, or -1 on a zero quaternion, -2 on bad arguments.
  */
 int fso_accumulate(int64_t N, const float* mean, const float* quat, const float* scale,
@@ -592,7 +632,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
                    const int32_t* masks, const int64_t* mask_offsets, int32_t E,
                    const int64_t* sel, int64_t n_sel, int32_t cull_mode, int32_t nthreads,
                    double* table, double* risk, uint8_t* flags, double* t_final,
-                   int64_t* stats, double event_rel) {
+                   int64_t* stats, double event_rel, int32_t record_f16) {
   if (N < 0 || V < 0 || E < 1 || (sel && n_sel < 0)) return -2;
   if (sel && t_final) return -2;
   if (!(event_rel > 0.0)) event_rel = FSO_EVENT_REL;
@@ -627,7 +667,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
     const fso_camera* cam = &cams[v];
     const int64_t npix = (int64_t)cam->width * cam->height;
     view_index vi;
-    status = project_all(N, mean, quat, scale, opacity, cam, nthreads, P);
+    status = project_all(N, mean, quat, scale, opacity, cam, nthreads, record_f16, P);
     if (status) break;
     if (sel) {
       int any = 0;
@@ -735,7 +775,7 @@ int64_t fso_pixel_lists(int64_t N, const float* mean, const float* quat, const f
   for (int32_t v = 0; v < V; ++v) {
     const fso_camera* cam = &cams[v];
     view_index vi;
-    int st = project_all(N, mean, quat, scale, opacity, cam, 1, P);
+    int st = project_all(N, mean, quat, scale, opacity, cam, 1, 0, P);
     if (st == 0) st = index_view(N, cam, P, cull_mode != 1, NULL, &vi);
     if (st) { free_view(&vi); free(P); free(hits); return -1; }
     for (int y = 0; y < cam->height; ++y)
@@ -782,7 +822,8 @@ int fso_project_view(int64_t N, const float* mean, const float* quat, const floa
   for (int64_t i = 0; i < N; ++i) {
     fso_proj p;
     memset(&p, 0, sizeof(p));
-    if (project_one(cam, mean + 3 * i, quat + 4 * i, scale + 3 * i, opacity[i], &p) < 0) return -1;
+    if (project_one(cam, mean + 3 * i, quat + 4 * i, scale + 3 * i, opacity[i], 0, &p) < 0)
+      return -1;
     double* o = out + 10 * i;
     o[0] = p.valid;
     o[1] = p.depth; o[2] = p.mx; o[3] = p.my;

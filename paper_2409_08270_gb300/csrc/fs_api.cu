@@ -173,6 +173,7 @@ struct fs_ctx {
   // near-tie re-check: resident per-view depth keys, flagged set, FP64 rows
   float recheck_margin = 1e-4f;  // <= 0: off
   bool recheck_reproject = false;
+  bool compact = false;  // reduced-precision records (FP16 whitening matrix, FP32 mean)
   DevBuf dkey, rk_flag, rk_offs, rk_F, rk_map, rk_R, rk_Rb;
   // the main pass's tile lists, kept for the re-check (see kept_layout)
   bool kl_valid = false;
@@ -224,6 +225,11 @@ fs_status fs_create(fs_ctx** out, int32_t device, const fs_options* opt) {
   if (opt && !(opt->recheck_margin == opt->recheck_margin))
     c->recheck_margin = 0.f;  // NaN: off
   c->recheck_reproject = opt && opt->recheck_reproject;
+  if (opt && opt->record_precision != 0 && opt->record_precision != FS_F16) {
+    delete c;
+    return fail(FS_INVALID_ARGUMENT, "fs_create: record_precision must be 0 or FS_F16");
+  }
+  c->compact = opt && opt->record_precision == FS_F16;
   DeviceGuard g(device);
   fs_status st;
   if ((st = c->views.ensure(sizeof(fs::ViewParams) * fs::kMaxViewsPerBatch, "views")) != FS_OK ||
@@ -449,7 +455,8 @@ int batch_views(const fs_ctx* c, int64_t n) {
 // batch * n + i) or, when `keep` is set, the slice of a buffer that holds
 // every view of the solve, so the near-tie re-check can read it again.
 struct ProjPtrs {
-  fs::ProjRecord* rec;
+  fs::ProjRecord* rec;       // float-pair records, or NULL
+  fs::CompactRecord* rec16;  // reduced-precision records, or NULL
   fs::Footprint* foot;
   uint32_t* cnt;
   uint32_t* dlo;
@@ -458,7 +465,9 @@ struct ProjPtrs {
 
 ProjPtrs proj_ptrs(fs_ctx* c, bool keep, int32_t v0, int64_t n) {
   const int64_t off = keep ? static_cast<int64_t>(v0) * n : 0;
-  return {c->rec.as<fs::ProjRecord>() + off, c->foot.as<fs::Footprint>() + off,
+  return {c->compact ? nullptr : c->rec.as<fs::ProjRecord>() + off,
+          c->compact ? c->rec.as<fs::CompactRecord>() + off : nullptr,
+          c->foot.as<fs::Footprint>() + off,
           c->cnt.as<uint32_t>() + off, c->dlo.as<uint32_t>() + off,
           keep ? c->dkey.as<uint32_t>() + off : nullptr};
 }
@@ -466,7 +475,8 @@ ProjPtrs proj_ptrs(fs_ctx* c, bool keep, int32_t v0, int64_t n) {
 fs_status ensure_window(fs_ctx* c, int64_t n, int vb, int32_t V, bool keep) {
   const int64_t kcap = static_cast<int64_t>(vb) * n;
   const int64_t pcap = keep ? static_cast<int64_t>(V) * n : kcap;
-  FS_TRY(c->rec.ensure(static_cast<size_t>(pcap) * sizeof(fs::ProjRecord), "records"));
+  const size_t rec_bytes = c->compact ? sizeof(fs::CompactRecord) : sizeof(fs::ProjRecord);
+  FS_TRY(c->rec.ensure(static_cast<size_t>(pcap) * rec_bytes, "records"));
   FS_TRY(c->foot.ensure(static_cast<size_t>(pcap) * sizeof(fs::Footprint), "footprints"));
   FS_TRY(c->cnt.ensure(static_cast<size_t>(pcap) * 4, "counts"));
   FS_TRY(c->dlo.ensure(static_cast<size_t>(pcap) * 4, "depth low words"));
@@ -624,8 +634,8 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     // project every Gaussian into the batch's views, sort by depth
     c->stats.kernel_launches += 3 + radix_launches(k_total, 32);
     FS_CUDA(fs::launch_project(n, nb, vd, s->pos_op.as<float4>(), s->cov.as<float4>(), P.rec,
-                               P.foot, P.cnt, c->key_a.as<uint32_t>(), c->val_a.as<uint32_t>(),
-                               P.dlo, stream),
+                               P.rec16, P.foot, P.cnt, c->key_a.as<uint32_t>(),
+                               c->val_a.as<uint32_t>(), P.dlo, stream),
             "project");
     if (P.dkey)
       FS_CUDA(cudaMemcpyAsync(P.dkey, c->key_a.p, static_cast<size_t>(k_total) * 4,
@@ -694,9 +704,9 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
         c->events_used += 2;
         FS_CUDA(cudaEventRecord(ev0, stream), "cudaEventRecord");
       }
-      FS_CUDA(fs::launch_blend(vd, nb, max_tiles, ranges_dst, val_dst->as<uint32_t>(), P.rec, n,
-                               E, mask_dtype, table, table_dtype, state, sat, subsat, satc, ci,
-                               ctr, stream),
+      FS_CUDA(fs::launch_blend(vd, nb, max_tiles, ranges_dst, val_dst->as<uint32_t>(), P.rec,
+                               P.rec16, s->pos_op.as<float4>(), n, E, mask_dtype, table,
+                               table_dtype, state, sat, subsat, satc, ci, ctr, stream),
               "blend");
       if (ev1) FS_CUDA(cudaEventRecord(ev1, stream), "cudaEventRecord");
     }
@@ -746,8 +756,8 @@ fs_status recheck_batch_rebin(fs_ctx* c, const fs_scene* s, int64_t n, int nb, i
   Ls.ranges[0] = c->ranges.as<uint2>();
   Ls.chunks = 1;
   c->stats.kernel_launches += 1;
-  FS_CUDA(fs::launch_recheck_blend(vd, nb, L.max_tiles, Ls, skip, P.rec, n, E, mask_dtype, map,
-                                   R, ctr, stream),
+  FS_CUDA(fs::launch_recheck_blend(vd, nb, L.max_tiles, Ls, skip, P.rec, P.rec16,
+                                   s->pos_op.as<float4>(), n, E, mask_dtype, map, R, ctr, stream),
           "re-check blend");
   return FS_OK;
 }
@@ -817,8 +827,8 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
     if (!keep) {
       c->stats.kernel_launches += 1;
       FS_CUDA(fs::launch_project(n, nb, vd, s->pos_op.as<float4>(), s->cov.as<float4>(), P.rec,
-                                 P.foot, P.cnt, c->key_a.as<uint32_t>(), c->val_a.as<uint32_t>(),
-                                 P.dlo, stream),
+                                 P.rec16, P.foot, P.cnt, c->key_a.as<uint32_t>(),
+                                 c->val_a.as<uint32_t>(), P.dlo, stream),
               "project");
       key_src = c->key_a.as<uint32_t>();
     }
@@ -850,8 +860,9 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
       FS_CUDA(cudaMemsetAsync(Rb, 0, rbytes, stream), "batch rows clear");
       FS_CUDA(cudaMemsetAsync(ctr + fs::kRecheckIncomplete, 0, 8, stream), "incomplete clear");
       c->stats.kernel_launches += 1;
-      FS_CUDA(fs::launch_recheck_blend(vd, nb, L.max_tiles, Ls, skip, P.rec, n, E, mask_dtype,
-                                       map, Rb, ctr, stream),
+      FS_CUDA(fs::launch_recheck_blend(vd, nb, L.max_tiles, Ls, skip, P.rec, P.rec16,
+                                       s->pos_op.as<float4>(), n, E, mask_dtype, map, Rb, ctr,
+                                       stream),
               "re-check blend");
       FS_CUDA(cudaMemcpyAsync(ctr_h + fs::kRecheckIncomplete, ctr + fs::kRecheckIncomplete, 8,
                               cudaMemcpyDeviceToHost, stream),
@@ -970,7 +981,7 @@ fs_status fs_solve(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t 
   if (recheck && !c->recheck_reproject) {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-      const double need = 108.0 * static_cast<double>(n) * V;
+      const double need = (c->compact ? 60.0 : 108.0) * static_cast<double>(n) * V;
       const double have = static_cast<double>(c->rec.bytes + c->foot.bytes + c->cnt.bytes +
                                               c->dlo.bytes + c->dkey.bytes);
       keep = need <= have + 0.5 * static_cast<double>(free_b);

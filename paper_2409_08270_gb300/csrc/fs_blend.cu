@@ -24,6 +24,8 @@
 //    label and issues one global atomic add per non-zero (Gaussian, label).
 //    A lane whose two pixels straddle a label boundary adds its second
 //    pixel's contribution with its own atomic.
+#include <cuda_fp16.h>
+
 #include "fs_common.cuh"
 #include "fs_internal.h"
 
@@ -140,7 +142,8 @@ struct SubSmem {
 template <typename LabelT, typename TableT>
 __global__ void __launch_bounds__(32) blend_kernel(
     const ViewParams* __restrict__ views, const uint2* __restrict__ ranges,
-    const uint32_t* __restrict__ list_val, const ProjRecord* __restrict__ rec, int64_t n, int E,
+    const uint32_t* __restrict__ list_val, const ProjRecord* __restrict__ rec,
+    const CompactRecord* __restrict__ rec16, const float4* __restrict__ pos_op, int64_t n, int E,
     TableT* __restrict__ table, float* __restrict__ state, uint64_t* __restrict__ sat,
     uint64_t* __restrict__ subsat, uint8_t* __restrict__ sat_chunk, int chunk,
     unsigned long long* __restrict__ counters) {
@@ -209,7 +212,20 @@ __global__ void __launch_bounds__(32) blend_kernel(
     float4 wk;
     float b0f = 0.f, b1f = 0.f, ok_ = 0.f;
     uint32_t g = 0;
-    if (lane < nin) {
+    float qc = 0.f;
+    if (lane < nin && rec16) {
+      // reduced-precision record: b = W16 (o - m) in FP32
+      g = list_val[base + lane];
+      const CompactRecord r = rec16[g];
+      const float2 wa = __half22float2(*reinterpret_cast<const __half2*>(&r.w01));
+      const float2 wb = __half22float2(*reinterpret_cast<const __half2*>(&r.w23));
+      wk = make_float4(wa.x, wa.y, wb.x, wb.y);
+      const float dx = ox - r.mx, dy = oy - r.my;
+      b0f = fmaf(wk.x, dx, wk.y * dy);
+      b1f = fmaf(wk.z, dx, wk.w * dy);
+      ok_ = pos_op[g - gbase].w;
+      qc = fmaxf(log2f(255.f * ok_), 0.f) * 1.001f + 1e-3f;
+    } else if (lane < nin) {
       // b = W o + c for the sub-tile centre o (W = W_hi + W_lo, c: float pairs)
       g = list_val[base + lane];
       const ProjRecord r = rec[g];
@@ -223,12 +239,15 @@ __global__ void __launch_bounds__(32) blend_kernel(
       b0f = b0.hi + b0.lo;
       b1f = b1.hi + b1.lo;
       ok_ = r.misc.x;
+      qc = r.misc.y;
+    }
+    if (lane < nin) {
       // over the sub-tile's pixel centres w ranges inside the box
       // b +- 3.5 (|W_k0| + |W_k1|); keep if that box meets |w|^2 <= q_cut
       const float h0 = 3.5f * (fabsf(wk.x) + fabsf(wk.y));
       const float h1 = 3.5f * (fabsf(wk.z) + fabsf(wk.w));
       const float d0 = fmaxf(0.f, fabsf(b0f) - h0), d1 = fmaxf(0.f, fabsf(b1f) - h1);
-      keep = fmaf(d0, d0, d1 * d1) <= r.misc.y;
+      keep = fmaf(d0, d0, d1 * d1) <= qc;
     }
     const uint32_t bal = __ballot_sync(0xffffffffu, keep);
     if (keep) {
@@ -301,12 +320,14 @@ __global__ void __launch_bounds__(32) blend_kernel(
 
 template <typename LabelT, typename TableT>
 cudaError_t launch_typed(const ViewParams* views, int n_views, int max_tiles, const uint2* ranges,
-                         const uint32_t* list_val, const ProjRecord* rec, int64_t n, int E,
+                         const uint32_t* list_val, const ProjRecord* rec,
+                         const CompactRecord* rec16, const float4* pos_op, int64_t n, int E,
                          void* table, float* state, uint64_t* sat, uint64_t* subsat,
                          uint8_t* sat_chunk, int chunk, unsigned long long* counters,
                          cudaStream_t stream) {
   dim3 grid(static_cast<unsigned>(4 * max_tiles), static_cast<unsigned>(n_views));
-  blend_kernel<LabelT, TableT><<<grid, 32, 0, stream>>>(views, ranges, list_val, rec, n, E,
+  blend_kernel<LabelT, TableT><<<grid, 32, 0, stream>>>(views, ranges, list_val, rec, rec16,
+                                                        pos_op, n, E,
                                                         static_cast<TableT*>(table), state, sat,
                                                         subsat, sat_chunk, chunk, counters);
   return cudaGetLastError();
@@ -328,23 +349,28 @@ cudaError_t launch_state_init(const ViewParams* views, int n_views, int max_tile
 
 cudaError_t launch_blend(const ViewParams* views, int n_views, int max_tiles_per_view,
                          const uint2* ranges, const uint32_t* list_val, const ProjRecord* rec,
-                         int64_t n, int E, int mask_dtype, void* table, int table_dtype,
-                         float* state, uint64_t* sat, uint64_t* subsat, uint8_t* sat_chunk,
-                         int chunk, unsigned long long* counters, cudaStream_t stream) {
+                         const CompactRecord* rec16, const float4* pos_op, int64_t n, int E,
+                         int mask_dtype, void* table, int table_dtype, float* state,
+                         uint64_t* sat, uint64_t* subsat, uint8_t* sat_chunk, int chunk,
+                         unsigned long long* counters, cudaStream_t stream) {
   if (n_views == 0 || max_tiles_per_view == 0) return cudaSuccess;
   const int mt = max_tiles_per_view;
   if (mask_dtype == 4) {
     if (table_dtype == 0)
-      return launch_typed<uint8_t, float>(views, n_views, mt, ranges, list_val, rec, n, E, table,
-                                          state, sat, subsat, sat_chunk, chunk, counters, stream);
-    return launch_typed<uint8_t, double>(views, n_views, mt, ranges, list_val, rec, n, E, table,
-                                         state, sat, subsat, sat_chunk, chunk, counters, stream);
+      return launch_typed<uint8_t, float>(views, n_views, mt, ranges, list_val, rec, rec16, pos_op,
+                                          n, E, table, state, sat, subsat, sat_chunk, chunk,
+                                          counters, stream);
+    return launch_typed<uint8_t, double>(views, n_views, mt, ranges, list_val, rec, rec16, pos_op,
+                                         n, E, table, state, sat, subsat, sat_chunk, chunk,
+                                         counters, stream);
   }
   if (table_dtype == 0)
-    return launch_typed<int32_t, float>(views, n_views, mt, ranges, list_val, rec, n, E, table,
-                                        state, sat, subsat, sat_chunk, chunk, counters, stream);
-  return launch_typed<int32_t, double>(views, n_views, mt, ranges, list_val, rec, n, E, table,
-                                       state, sat, subsat, sat_chunk, chunk, counters, stream);
+    return launch_typed<int32_t, float>(views, n_views, mt, ranges, list_val, rec, rec16, pos_op,
+                                        n, E, table, state, sat, subsat, sat_chunk, chunk,
+                                        counters, stream);
+  return launch_typed<int32_t, double>(views, n_views, mt, ranges, list_val, rec, rec16, pos_op,
+                                       n, E, table, state, sat, subsat, sat_chunk, chunk,
+                                       counters, stream);
 }
 
 }  // namespace fs

@@ -54,6 +54,17 @@ struct alignas(16) ProjRecord {
   float4 misc;
 };
 
+// Reduced-precision record of one (view, Gaussian): 16 B.  The mean stays
+// FP32; the whitening matrix W is stored as four FP16 values (correctly
+// rounded from the float pairs), so alpha = o 2^-|W16 (p - m)|^2 with the
+// opacity o read from the scene.  |W d|^2 stays a sum of squares whatever
+// the rounding, unlike an FP16 conic, which can lose positive definiteness
+// for elongated footprints.
+struct alignas(16) CompactRecord {
+  float mx, my;
+  uint32_t w01, w23;  // (W00, W01), (W10, W11) as FP16 pairs, low half first
+};
+
 // Footprint of one (view, Gaussian) for the tile binning: the alpha >= 1/255
 // ellipse {d : d^T Sigma2D^-1 d <= r2} around the projected mean, r2 slightly
 // inflated, in FP32 (the binning is conservative: it also adds a pixel of

@@ -11,6 +11,7 @@ constexpr int kMaxLabels = 4096;
 
 struct ViewParams;
 struct ProjRecord;
+struct CompactRecord;
 struct Footprint;
 
 // scan / sort (fs_sort.cu) --------------------------------------------------
@@ -34,9 +35,12 @@ cudaError_t launch_scene_prep(int64_t n, const float* mean, const void* quat, in
                               const void* scale, int scale_dtype, const void* opacity,
                               int opacity_dtype, float4* pos_op, float4* cov, unsigned int* err,
                               cudaStream_t stream);
+// rec16 != NULL: reduced-precision records (FP16 whitening matrix, FP32 mean)
+// are written to rec16 instead of the float-pair records to rec
 cudaError_t launch_project(int64_t n, int n_views, const ViewParams* views, const float4* pos_op,
-                           const float4* cov, ProjRecord* rec, Footprint* foot, uint32_t* cnt,
-                           uint32_t* key, uint32_t* val, uint32_t* depth_lo, cudaStream_t stream);
+                           const float4* cov, ProjRecord* rec, CompactRecord* rec16,
+                           Footprint* foot, uint32_t* cnt, uint32_t* key, uint32_t* val,
+                           uint32_t* depth_lo, cudaStream_t stream);
 // re-orders runs of equal 32-bit depth keys by the depth's low word, then slot
 // (n_total elements; slot / n is the view of a slot)
 cudaError_t launch_depth_tie_fix(int64_t n_total, int64_t n, const uint32_t* key, uint32_t* val,
@@ -64,11 +68,14 @@ cudaError_t launch_state_init(const ViewParams* views, int n_views, int max_tile
                               unsigned long long* counters, cudaStream_t stream);
 // sat_chunk (may be NULL): per batch tile, set to `chunk` when the tile
 // saturates during this launch (its later chunks get no list entries).
+// Records: float pairs in rec, or reduced precision in rec16 (then the
+// opacity comes from pos_op[i].w of the scene).
 cudaError_t launch_blend(const ViewParams* views, int n_views, int max_tiles_per_view,
                          const uint2* ranges, const uint32_t* list_val, const ProjRecord* rec,
-                         int64_t n, int E, int mask_dtype, void* table, int table_dtype,
-                         float* state, uint64_t* sat, uint64_t* subsat, uint8_t* sat_chunk,
-                         int chunk, unsigned long long* counters, cudaStream_t stream);
+                         const CompactRecord* rec16, const float4* pos_op, int64_t n, int E,
+                         int mask_dtype, void* table, int table_dtype, float* state,
+                         uint64_t* sat, uint64_t* subsat, uint8_t* sat_chunk, int chunk,
+                         unsigned long long* counters, cudaStream_t stream);
 
 // assignment (fs_assign.cu) -------------------------------------------------
 cudaError_t launch_assign(const void* table, int table_dtype, int64_t n, int E, float gamma,
@@ -126,7 +133,8 @@ struct RecheckLists {
 // Gaussian i (map[i] >= 0) at a pixel of label e into R[map[i] * E + e].
 cudaError_t launch_recheck_blend(const ViewParams* views, int n_views, int max_tiles_per_view,
                                  const RecheckLists& lists, const uint64_t* skip,
-                                 const ProjRecord* rec, int64_t n, int E, int mask_dtype,
+                                 const ProjRecord* rec, const CompactRecord* rec16,
+                                 const float4* pos_op, int64_t n, int E, int mask_dtype,
                                  const int32_t* map, double* R, unsigned long long* counters,
                                  cudaStream_t stream);
 

@@ -249,7 +249,8 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
     const int tiles = vp.tiles_x * vp.tiles_y;
     // pageable source: the copy has taken the bytes when the call returns
     NA_CUDA(cudaMemcpyAsync(vd, &vp, sizeof(vp), cudaMemcpyHostToDevice, strm), "view upload");
-    NA_CUDA(launch_project(n, 1, vd, pos, cov, rec, foot, cnt, key_a, val_a, dlo, strm), "project");
+    NA_CUDA(launch_project(n, 1, vd, pos, cov, rec, nullptr, foot, cnt, key_a, val_a, dlo, strm),
+            "project");
     bool alt = false;
     NA_CUDA(radix_sort_pairs(key_a, val_a, key_b, val_b, n, 32, sort_tmp, &alt, strm), "sort");
     uint32_t* skey = alt ? key_b : key_a;
@@ -285,7 +286,8 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
         const uint32_t* lval = alt2 ? lv_b : lv_a;
         NA_CUDA(cudaMemsetAsync(ranges, 0, static_cast<size_t>(tiles) * 8, strm), "clear");
         NA_CUDA(launch_ranges(I, lkey, ranges, strm), "ranges");
-        NA_CUDA(launch_blend(vd, 1, tiles, ranges, lval, rec, n, E, mask_dtype, table, FS_F32,
+        NA_CUDA(launch_blend(vd, 1, tiles, ranges, lval, rec, nullptr, nullptr, n, E, mask_dtype,
+                             table, FS_F32,
                              state, sat, subsat, nullptr, 0, ctr, strm),
                 "blend");
       }

@@ -112,13 +112,33 @@ __device__ __forceinline__ f2 f2_clamp(f2 x, float lim_hi, float lim_lo) {
   return x;
 }
 
+// x rounded to FP16 (round to nearest, ties to even), x a float pair: the
+// float rounding of hi is corrected when hi sits exactly halfway between two
+// FP16 values and lo says on which side x lies.
+__device__ __forceinline__ uint16_t f2_to_half_rn(f2 x) {
+  const __half h = __float2half_rn(x.hi);
+  const float hf = __half2float(h);
+  if (x.lo == 0.f || hf == x.hi) return __half_as_ushort(h);
+  // the FP16 neighbour on the other side of hi
+  const uint16_t hb = __half_as_ushort(h);
+  const bool up_in_magnitude = (fabsf(x.hi) > fabsf(hf));
+  const uint16_t ob = static_cast<uint16_t>(up_in_magnitude ? hb + 1 : hb - 1);
+  const float of = __half2float(__ushort_as_half(ob));
+  if (0.5f * (hf + of) != x.hi) return hb;  // not a tie: hi's rounding is x's
+  // tie on hi alone: x lies towards lo's side
+  const bool towards_other = (x.lo > 0.f) == (of > hf);
+  return towards_other ? ob : hb;
+}
+
 // One thread per Gaussian; it projects the Gaussian into every view of the
-// batch so the scene is read once per batch.
+// batch so the scene is read once per batch.  rec16 != NULL: the record is
+// written in the reduced-precision form instead (rec is not written).
 __global__ void __launch_bounds__(256) project_kernel(
     int64_t n, int n_views, const ViewParams* __restrict__ views_g,
     const float4* __restrict__ pos_op, const float4* __restrict__ cov3,
-    ProjRecord* __restrict__ rec, Footprint* __restrict__ foot, uint32_t* __restrict__ cnt,
-    uint32_t* __restrict__ key, uint32_t* __restrict__ val, uint32_t* __restrict__ depth_lo) {
+    ProjRecord* __restrict__ rec, CompactRecord* __restrict__ rec16, Footprint* __restrict__ foot,
+    uint32_t* __restrict__ cnt, uint32_t* __restrict__ key, uint32_t* __restrict__ val,
+    uint32_t* __restrict__ depth_lo) {
   __shared__ ViewParams views[kMaxViewsPerBatch];
   for (int k = threadIdx.x; k < n_views * (int)(sizeof(ViewParams) / 4); k += blockDim.x)
     reinterpret_cast<uint32_t*>(views)[k] = reinterpret_cast<const uint32_t*>(views_g)[k];
@@ -146,6 +166,7 @@ __global__ void __launch_bounds__(256) project_kernel(
     float depth = 0.f, depth_l = 0.f;
     ProjRecord R;
     R.w_hi = R.w_lo = R.c = make_float4(0.f, 0.f, 0.f, 0.f);
+    CompactRecord R16 = {0.f, 0.f, 0u, 0u};
     // misc.y: |w|^2 at which alpha falls to 1/255, log2(255 o), widened by
     // 0.1% + 1e-3 so the blend's sub-tile test stays conservative in FP32
     const float qcut = opaque_enough ? fmaxf(log2f(255.f * o), 0.f) * 1.001f + 1e-3f : 0.f;
@@ -222,6 +243,14 @@ __global__ void __launch_bounds__(256) project_kernel(
       R.w_hi = make_float4(W00.hi, W01.hi, W10.hi, W11.hi);
       R.w_lo = make_float4(W00.lo, W01.lo, W10.lo, W11.lo);
       R.c = make_float4(c0.hi, c1.hi, c0.lo, c1.lo);
+      if (rec16) {
+        R16.mx = mx.hi;  // the float pair is normalised: hi is the FP32 rounding
+        R16.my = my.hi;
+        R16.w01 = static_cast<uint32_t>(f2_to_half_rn(W00)) |
+                  (static_cast<uint32_t>(f2_to_half_rn(W01)) << 16);
+        R16.w23 = static_cast<uint32_t>(f2_to_half_rn(W10)) |
+                  (static_cast<uint32_t>(f2_to_half_rn(W11)) << 16);
+      }
       // binning footprint (FP32 is plenty: the binning keeps a pixel of margin)
       const float r2b = binning_r2(r2);
       const float sxx = a.hi, sxy = b.hi, syy = c.hi;
@@ -249,7 +278,10 @@ __global__ void __launch_bounds__(256) project_kernel(
         count = 1;
       }
     }
-    rec[slot] = R;
+    if (rec16)
+      rec16[slot] = R16;
+    else
+      rec[slot] = R;
     foot[slot] = F;
     cnt[slot] = visible ? count : 0u;
     key[slot] = visible ? depth_key(depth) : 0xFFFFFFFFu;
@@ -499,13 +531,14 @@ cudaError_t launch_scene_prep(int64_t n, const float* mean, const void* quat, in
 }
 
 cudaError_t launch_project(int64_t n, int n_views, const ViewParams* views, const float4* pos_op,
-                           const float4* cov, ProjRecord* rec, Footprint* foot, uint32_t* cnt,
-                           uint32_t* key, uint32_t* val, uint32_t* depth_lo, cudaStream_t stream) {
+                           const float4* cov, ProjRecord* rec, CompactRecord* rec16,
+                           Footprint* foot, uint32_t* cnt, uint32_t* key, uint32_t* val,
+                           uint32_t* depth_lo, cudaStream_t stream) {
   if (n == 0 || n_views == 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = (n + threads - 1) / threads;
   project_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-      n, n_views, views, pos_op, cov, rec, foot, cnt, key, val, depth_lo);
+      n, n_views, views, pos_op, cov, rec, rec16, foot, cnt, key, val, depth_lo);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@
 // projection; 2^-q follows Tang's table-driven method (ACM TOMS 15(2), 1989):
 // a 64-entry table of 2^(-j/64) (computed in FP64) times a degree-4 Taylor
 // polynomial of e^-x on the remaining [0, ln2/64).
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "fs_binning.cuh"
@@ -208,6 +209,26 @@ __device__ __forceinline__ Staged stage_entry(const ProjRecord& r, float cx, flo
   return st;
 }
 
+// Reduced-precision record: W16 and the FP32 mean are exact float values, so
+// b = W (ctr - m) is formed from the exact difference in float pairs.
+__device__ __forceinline__ Staged stage_compact(const CompactRecord& r, float o, float cx,
+                                                float cy, int j) {
+  Staged st;
+  const float2 wa = __half22float2(*reinterpret_cast<const __half2*>(&r.w01));
+  const float2 wb = __half22float2(*reinterpret_cast<const __half2*>(&r.w23));
+  st.w[0] = f2_from(wa.x);
+  st.w[1] = f2_from(wa.y);
+  st.w[2] = f2_from(wb.x);
+  st.w[3] = f2_from(wb.y);
+  const f2 dx = two_sum(cx, -r.mx), dy = two_sum(cy, -r.my);
+  st.b[0] = f2_add(f2_mul(st.w[0], dx), f2_mul(st.w[1], dy));
+  st.b[1] = f2_add(f2_mul(st.w[2], dx), f2_mul(st.w[3], dy));
+  st.o = o;
+  st.qc = fmaxf(log2f(255.f * o), 0.f) * 1.001f + 1e-3f + 0.05f;
+  st.j = j;
+  return st;
+}
+
 // FP32 screen: can the entry's alpha >= 1/255 region reach this pixel?
 __device__ __forceinline__ bool reaches(const Staged& e, float lx, float ly) {
   const float q0 = fmaf(e.w[0].hi, lx, fmaf(e.w[1].hi, ly, e.b[0].hi));
@@ -222,7 +243,8 @@ __device__ __forceinline__ bool reaches(const Staged& e, float lx, float ly) {
 template <typename LabelT>
 __global__ void __launch_bounds__(kTilePixels) recheck_blend_kernel(
     const ViewParams* __restrict__ views, RecheckLists L, const uint64_t* __restrict__ skip,
-    const ProjRecord* __restrict__ rec, int64_t n, int E, const int32_t* __restrict__ map,
+    const ProjRecord* __restrict__ rec, const CompactRecord* __restrict__ rec16,
+    const float4* __restrict__ pos_op, int64_t n, int E, const int32_t* __restrict__ map,
     double* __restrict__ R, unsigned long long* __restrict__ counters) {
   __shared__ Staged s_e[kRB];
   __shared__ float2 s_tab[64];
@@ -264,9 +286,12 @@ __global__ void __launch_bounds__(kTilePixels) recheck_blend_kernel(
       __syncthreads();
       if (threadIdx.x < cnt) {
         const uint32_t slot = L.val[c][b0 + threadIdx.x];
-        const int j = map[slot % static_cast<uint64_t>(n)];
+        const uint32_t gi = static_cast<uint32_t>(slot % static_cast<uint64_t>(n));
+        const int j = map[gi];
         s_e[threadIdx.x].j = j;
-        if (j >= 0) s_e[threadIdx.x] = stage_entry(rec[slot], cx, cy, j);
+        if (j >= 0)
+          s_e[threadIdx.x] = rec16 ? stage_compact(rec16[slot], pos_op[gi].w, cx, cy, j)
+                                   : stage_entry(rec[slot], cx, cy, j);
       }
       __syncthreads();
       if (label >= 0)
@@ -294,8 +319,9 @@ __global__ void __launch_bounds__(kTilePixels) recheck_blend_kernel(
       const int cnt = static_cast<int>(min(static_cast<uint32_t>(kRB), rg.y - b0));
       if (threadIdx.x < cnt) {
         const uint32_t slot = L.val[c][b0 + threadIdx.x];
-        s_e[threadIdx.x] =
-            stage_entry(rec[slot], cx, cy, map[slot % static_cast<uint64_t>(n)]);
+        const uint32_t gi = static_cast<uint32_t>(slot % static_cast<uint64_t>(n));
+        s_e[threadIdx.x] = rec16 ? stage_compact(rec16[slot], pos_op[gi].w, cx, cy, map[gi])
+                                 : stage_entry(rec[slot], cx, cy, map[gi]);
       }
       __syncthreads();
       if (live) {
@@ -403,18 +429,19 @@ cudaError_t launch_compact(int64_t k_total, const uint32_t* flag, const uint32_t
 
 cudaError_t launch_recheck_blend(const ViewParams* views, int n_views, int max_tiles_per_view,
                                  const RecheckLists& lists, const uint64_t* skip,
-                                 const ProjRecord* rec, int64_t n, int E, int mask_dtype,
+                                 const ProjRecord* rec, const CompactRecord* rec16,
+                                 const float4* pos_op, int64_t n, int E, int mask_dtype,
                                  const int32_t* map, double* R, unsigned long long* counters,
                                  cudaStream_t stream) {
   if (n_views == 0 || max_tiles_per_view == 0) return cudaSuccess;
   if (lists.chunks < 1 || lists.chunks > kMaxChunks) return cudaErrorInvalidValue;
   const dim3 grid(static_cast<unsigned>(max_tiles_per_view), static_cast<unsigned>(n_views));
   if (mask_dtype == 4)
-    recheck_blend_kernel<uint8_t><<<grid, kTilePixels, 0, stream>>>(views, lists, skip, rec, n,
-                                                                    E, map, R, counters);
+    recheck_blend_kernel<uint8_t><<<grid, kTilePixels, 0, stream>>>(
+        views, lists, skip, rec, rec16, pos_op, n, E, map, R, counters);
   else
-    recheck_blend_kernel<int32_t><<<grid, kTilePixels, 0, stream>>>(views, lists, skip, rec, n,
-                                                                    E, map, R, counters);
+    recheck_blend_kernel<int32_t><<<grid, kTilePixels, 0, stream>>>(
+        views, lists, skip, rec, rec16, pos_op, n, E, map, R, counters);
   return cudaGetLastError();
 }
 

@@ -35,7 +35,8 @@ EXPORTS = ["fs_version", "fs_last_error", "fs_create", "fs_destroy", "fs_scene_c
 class fs_options(ctypes.Structure):
     _fields_ = [("views_per_batch", ctypes.c_int32), ("time_stages", ctypes.c_int32),
                 ("depth_chunks", ctypes.c_int32), ("recheck_margin", ctypes.c_float),
-                ("recheck_reproject", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
+                ("recheck_reproject", ctypes.c_int32), ("record_precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 10)]
 
 
 class fs_gaussians(ctypes.Structure):
@@ -133,7 +134,7 @@ def fs_last_error() -> str:
 
 def fs_create(device: int = 0, views_per_batch: int = 0, time_stages: bool = False,
               depth_chunks: int = 0, recheck_margin: float = 0.0,
-              recheck_reproject: bool = False) -> int:
+              recheck_reproject: bool = False, record_precision: int = 0) -> int:
     ctx = ctypes.c_void_p()
     opt = fs_options()
     opt.views_per_batch = views_per_batch
@@ -141,6 +142,7 @@ def fs_create(device: int = 0, views_per_batch: int = 0, time_stages: bool = Fal
     opt.depth_chunks = depth_chunks
     opt.recheck_margin = recheck_margin
     opt.recheck_reproject = 1 if recheck_reproject else 0
+    opt.record_precision = record_precision
     check(load().fs_create(ctypes.byref(ctx), device, ctypes.byref(opt)))
     return ctx.value
 
@@ -225,11 +227,11 @@ class Solver:
 
     def __init__(self, gaussians, device: int = 0, views_per_batch: int = 0,
                  time_stages: bool = False, depth_chunks: int = 0, recheck_margin: float = 0.0,
-                 recheck_reproject: bool = False):
+                 recheck_reproject: bool = False, record_precision: int = 0):
         torch = _torch()
         self.device = torch.device("cuda", device)
         self.ctx = fs_create(device, views_per_batch, time_stages, depth_chunks, recheck_margin,
-                             recheck_reproject)
+                             recheck_reproject, record_precision)
         self.scene = None
         dev = {}
         for k in ("mean", "quat", "scale", "opacity"):

@@ -345,3 +345,12 @@ def round_bf16(x):
 def round_fp16(x):
     """Round float32 values to IEEE half (round-to-nearest-even), kept as float32."""
     return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float32)
+
+
+def rounded_gaussians(g):
+    """The reduced-precision storage of a scene's attributes: positions stay
+    FP32, quaternions and scales are rounded to bfloat16 and opacities to
+    FP16 (values kept as float32, so any consumer sees the rounded values)."""
+    return {"mean": np.asarray(g["mean"], np.float32),
+            "quat": round_bf16(g["quat"]), "scale": round_bf16(g["scale"]),
+            "opacity": round_fp16(g["opacity"])}

@@ -417,3 +417,59 @@ def test_event_window_changes_risk_only(tiny):
     assert np.array_equal(a.table, b.table)
     assert b.risk.sum() <= a.risk.sum()
     assert (b.risk > 0).sum() < (a.risk > 0).sum()
+
+
+# --------------------------------------------------------------------------
+# reduced-precision record (FP16 whitening matrix, FP32 mean)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("theta,sx,sy,o", [(0.0, 0.05, 0.05, 0.7), (0.6, 0.08, 0.02, 0.9),
+                                           (-1.1, 0.03, 0.11, 0.995)])
+def test_record_f16_closed_form(theta, sx, sy, o):
+    """One Gaussian on the optical axis, rotated by theta about z: Sigma2D =
+    (f/z)^2 R(theta) diag(sx^2, sy^2) R(theta)^T + 0.3 I exactly.  Its
+    whitening matrix is formed here from that closed form (major unit
+    eigenvector (h + r, b) / |.| for h >= 0, else (b, r - h) / |.|), rounded
+    with numpy's float16, and sum_p min(0.99, o 2^-|W (p - m)|^2) over the
+    pixels where alpha >= 1/255 must equal the table (T = 1 throughout)."""
+    z, f, W_, H_ = 2.0, 60.0, 48, 40
+    q = [math.cos(theta / 2), 0.0, 0.0, math.sin(theta / 2)]
+    g = _gauss([[0.0, 0.0, z]], quats=[q], scales=[[sx, sy, 0.05]], opac=[o])
+    cam = _cam(W_, H_, fx=f, cx=W_ / 2 + 0.3, cy=H_ / 2 - 0.2)
+    acc = oracle.accumulate(g, [cam], [np.ones((H_, W_), np.int32)], 2, record_f16=True)
+    s32 = np.float32([sx, sy])
+    R2 = np.array([[math.cos(theta), -math.sin(theta)], [math.sin(theta), math.cos(theta)]])
+    S = (f / z) ** 2 * R2 @ np.diag(np.float64(s32) ** 2) @ R2.T + 0.3 * np.eye(2)
+    a, b, c = S[0, 0], S[0, 1], S[1, 1]
+    h = 0.5 * (a - c)
+    r = math.hypot(h, b)
+    l1 = 0.5 * (a + c) + r
+    l2 = (a * c - b * b) / l1
+    e = np.array([h + r, b]) if h >= 0 else np.array([b, r - h])
+    e = e / np.linalg.norm(e) if np.linalg.norm(e) > 0 else np.array([1.0, 0.0])
+    k = np.sqrt(0.5 * math.log2(math.e) / np.array([l1, l2]))
+    W = np.array([[e[0] * k[0], e[1] * k[0]], [-e[1] * k[1], e[0] * k[1]]])
+    W16 = W.astype(np.float16).astype(np.float64)
+    m = np.array([np.float32(cam["cx"]), np.float32(cam["cy"])], np.float64)
+    ys, xs = np.mgrid[0:H_, 0:W_]
+    d = np.stack([xs + 0.5 - m[0], ys + 0.5 - m[1]], -1)
+    w = d @ W16.T
+    alpha = np.minimum(0.99, np.float64(np.float32(o)) * np.exp2(-(w ** 2).sum(-1)))
+    expect = alpha[alpha >= 1 / 255].sum()
+    assert acc.table[0, 1] == pytest.approx(expect, rel=1e-12)
+    # rounding W to FP16 moves the sum, but by far less than the 1/255 cut
+    plain = oracle.accumulate(g, [cam], [np.ones((H_, W_), np.int32)], 2)
+    assert acc.table[0, 1] == pytest.approx(plain.table[0, 1], rel=2e-2)
+
+
+def test_record_f16_close_to_plain(tiny):
+    """The FP16 record perturbs alpha by ~1e-3 relative: the tables agree to
+    a few per cent on every substantial entry and the labels on nearly all."""
+    a = oracle.accumulate(tiny.gaussians, tiny.cams[:3], tiny.masks[:3], tiny.E)
+    b = oracle.accumulate(tiny.gaussians, tiny.cams[:3], tiny.masks[:3], tiny.E, record_f16=True)
+    big = a.table > 1e-3 * a.table.max()
+    rel = np.abs(b.table[big] - a.table[big]) / a.table[big]
+    assert np.median(rel) < 5e-3 and rel.max() < 0.2
+    assert not np.array_equal(a.table, b.table)
+    agree = (assign(a.table, tiny.gamma) == assign(b.table, tiny.gamma)).mean()
+    assert agree > 0.99
