@@ -55,6 +55,13 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"],
                     help="fp16: the reduced-precision form (BF16 quat/scale, FP16 opacity, "
                          "per-view records with an FP16 whitening matrix and FP32 mean)")
+    ap.add_argument("--serve", action="store_true",
+                    help="request-server benchmark: 16 resident scenes of uneven size, a "
+                         "Poisson request trace, p50/p99 latency vs sequential solves")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=4.0)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--serve-scale", type=float, default=1.0)
     ap.add_argument("--recheck-margin", type=float, default=0.0,
                     help="FP64 re-check of decisions with a margin below this (0: library "
                          "default 1e-4; negative: off)")
@@ -347,8 +354,112 @@ def run_reference(args, rank, world):
     }
 
 
+# ---------------------------------------------------------------------------
+# request server: latency under a Poisson trace, throughput vs sequential
+# ---------------------------------------------------------------------------
+
+def run_serve(args):
+    import threading
+    import numpy as np
+    from paper_2409_08270_gb300 import build as lib_build, flashsplat as fsb
+    synth = synth_mod()
+    lib_build.build()
+    fsb.load()
+    t_gen = time.perf_counter()
+    scenes = synth.serving_scenes(scale=args.serve_scale)
+    # two seeded noise draws per scene, prepared before the timed region
+    variants = [[synth.request_masks(w, 7919 * k + j) for j in range(2)]
+                for k, w in enumerate(scenes)]
+    t_gen = time.perf_counter() - t_gen
+    rng = np.random.default_rng(synth.SEED_BASE + 55)
+    R = args.requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, R))
+    picks = rng.integers(0, len(scenes), R)
+
+    def run_trace(srv, ids, paced, window=2 * args.slots):
+        tickets = [None] * R
+        fetched = [0]
+
+        def submitter():
+            t0 = time.perf_counter()
+            for i in range(R):
+                if paced:
+                    dt = t0 + arrivals[i] - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                else:   # back to back, with at most `window` requests outstanding
+                    while i - fetched[0] >= window:
+                        time.sleep(0.0005)
+                k = int(picks[i])
+                tickets[i] = srv.submit(ids[k], scenes[k].cams, variants[k][i % 2], scenes[k].E,
+                                        scenes[k].gamma)
+
+        th = threading.Thread(target=submitter)
+        t_start = time.perf_counter()
+        th.start()
+        infos = []
+        for i in range(R):
+            while tickets[i] is None:
+                time.sleep(0.0005)
+            infos.append(srv.fetch(tickets[i])["info"])
+            fetched[0] = i + 1
+        th.join()
+        wall = time.perf_counter() - t_start
+        lat = np.array([x.done_s - x.submit_s for x in infos])
+        svc = np.array([x.done_s - x.start_s for x in infos])
+        return wall, lat, svc, infos
+
+    def make(slots):
+        srv = fsb.Server(slots=slots, autotune=True)
+        ids = [srv.add_scene(w.gaussians) for w in scenes]
+        for k, w in enumerate(scenes):      # warm-up: tuning, untimed
+            srv.fetch(srv.submit(ids[k], w.cams, variants[k][0], w.E, w.gamma))
+        # every slot sizes its workspace once for the largest scenes (a slot
+        # that grows later frees memory, which waits for the whole device)
+        big = {int(np.argmax([w.n for w in scenes])), int(np.argmax([w.pixels for w in scenes]))}
+        for k in big:
+            ts = [srv.submit(ids[k], scenes[k].cams, variants[k][0], scenes[k].E, scenes[k].gamma)
+                  for _ in range(slots)]
+            for t in ts:
+                srv.fetch(t)
+        return srv, ids
+
+    srv, ids = make(args.slots)
+    wall, lat, svc, infos = run_trace(srv, ids, paced=True)
+    wall_b, lat_b, _, _ = run_trace(srv, ids, paced=False)
+    srv.close()
+    seq, seq_ids = make(1)
+    wall_s, lat_s, svc_s, _ = run_trace(seq, seq_ids, paced=False, window=1)
+    seq.close()
+    pix = sum(scenes[int(k)].pixels for k in picks)
+    q = lambda a, p: float(np.quantile(a, p))
+    return {
+        "metric": "request server: p50/p99 latency under a Poisson trace; requests/s",
+        "value": q(lat, 0.5), "unit": "s (p50 latency)", "n_gpus": 1, "higher_is_better": False,
+        "p99_latency_s": q(lat, 0.99), "p50_latency_s": q(lat, 0.5),
+        "requests_per_s": R / wall, "offered_rate": args.rate, "requests": R,
+        "burst": {"requests_per_s": R / wall_b, "gpix_per_s": pix / wall_b / 1e9,
+                  "p50_latency_s": q(lat_b, 0.5), "p99_latency_s": q(lat_b, 0.99)},
+        "sequential": {"requests_per_s": R / wall_s, "gpix_per_s": pix / wall_s / 1e9,
+                       "p50_service_s": q(svc_s, 0.5), "p99_service_s": q(svc_s, 0.99)},
+        "service_s": {"p50": q(svc, 0.5), "p99": q(svc, 0.99)},
+        "dtype": "f32", "data": "synthetic (16 seeded clustered scenes, orbit cameras, "
+                                "noisy label masks; two noise draws per scene)",
+        "config": {"workload": "16 resident scenes: N log-uniform 2e5..2e6, 20..150 views, "
+                               "512^2..1600x1200, 1..16 labels, gamma 0.5",
+                   "scale": args.serve_scale, "slots": args.slots, "autotune": True,
+                   "scene_gaussians": [w.n for w in scenes],
+                   "scene_views": [len(w.cams) for w in scenes],
+                   "generation_s": round(t_gen, 1)},
+        "tuned": sorted({(x.views_per_batch, x.depth_chunks) for x in infos}),
+    }
+
+
 def main():
     args = parse()
+    if args.serve:
+        print(json.dumps(run_serve(args)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

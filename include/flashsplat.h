@@ -162,7 +162,8 @@ fs_status fs_create(fs_ctx** out, int32_t device, const fs_options* opt);
 fs_status fs_destroy(fs_ctx* ctx);
 
 /* Make a scene resident on the context's device (Sec. 3.1, Sec. 4.2: only
- * {m, q, s, o} are used).  The library copies the arrays into its own device
+ * {m, q, s, o} are used).  Any context on the same device may use the scene
+ * (read-only) while it lives.  The library copies the arrays into its own device
  * storage (quaternions normalised, the 3D covariance precomputed in FP64);
  * the caller may free its buffers when the call returns (the call is
  * synchronous).  Errors: FS_INVALID_ARGUMENT (NULL pointers, n out of
@@ -253,6 +254,77 @@ fs_status fs_solve(fs_ctx* ctx, const fs_scene* scene, const fs_camera* cams, in
 /* Wait for the context's work on `stream` and report errors recorded by its
  * kernels (FS_CUDA_ERROR with a message).  Fills *stats if non-NULL. */
 fs_status fs_synchronize(fs_ctx* ctx, void* stream, fs_stats* stats);
+
+/* ---- request server (continuous batching) -----------------------------------
+ * Segmentation requests against resident scenes, served by `slots` workers
+ * that each own a context and a CUDA stream.  A request (scene, cameras,
+ * host masks, E, gamma) is queued on submission; a free slot admits the
+ * oldest queued request whose estimated device footprint fits beside the
+ * requests already running (budget_bytes), so requests that arrive while
+ * others run start as soon as a slot and memory free up, and their work
+ * overlaps on the device.  Each request is an fs_solve (Sec. 3.2-3.3,
+ * near-tie re-check included) on the slot's stream.  The paper has no
+ * serving layer; this is the batching pattern the solve is deployed with.
+ */
+typedef struct fs_server fs_server;
+
+typedef struct fs_server_options {
+  int32_t device;         /* CUDA device */
+  int32_t slots;          /* concurrent requests (default 4) */
+  int64_t budget_bytes;   /* device bytes the running requests may use
+                             (default: half the free memory at creation) */
+  int32_t autotune;       /* non-zero: the first request of each scene also
+                             times a few (views per batch, depth chunks)
+                             settings on a sample of its views and keeps the
+                             fastest for the scene's later requests */
+  int32_t reserved[9];
+} fs_server_options;
+
+/* Outcome and timing of one request (steady-clock seconds). */
+typedef struct fs_server_info {
+  int32_t status;         /* fs_status of the request's solve */
+  int32_t done;           /* 1 once finished (or cancelled) */
+  double submit_s;        /* when fs_server_submit accepted it */
+  double start_s;         /* when a slot admitted it */
+  double done_s;          /* when its results were on the host */
+  int32_t slot;           /* the slot that ran it */
+  int32_t views_per_batch, depth_chunks;  /* the settings it ran with */
+  int32_t pad;
+  int64_t bytes_estimate; /* the footprint admission used */
+  fs_stats stats;         /* the solve's counters */
+} fs_server_info;
+
+/* Create a server (threads start immediately).  Errors: FS_INVALID_ARGUMENT,
+ * FS_UNSUPPORTED (device), FS_OUT_OF_MEMORY, FS_CUDA_ERROR. */
+fs_status fs_server_create(const fs_server_options* opt, fs_server** out);
+
+/* Make a scene resident for the server's requests (as fs_scene_create);
+ * *scene_id identifies it in fs_server_submit.  Thread-safe. */
+fs_status fs_server_add_scene(fs_server* srv, const fs_gaussians* g, int32_t* scene_id);
+
+/* Queue a request.  cams[n_views] and the host masks (row-major H x W,
+ * FS_U8 or FS_I32) are copied before the call returns.  *ticket identifies
+ * the request.  Thread-safe.  Errors: FS_INVALID_ARGUMENT (bad scene id,
+ * cameras, dtype, E or gamma). */
+fs_status fs_server_submit(fs_server* srv, int32_t scene_id, const fs_camera* cams,
+                           int32_t n_views, const void* const* masks, int32_t mask_dtype,
+                           int32_t E, float gamma, int64_t* ticket);
+
+/* Results of a request: wait != 0 blocks until it is done; otherwise
+ * FS_TIMEOUT is returned while it is still queued or running.  Copies the
+ * scene's n member bits / labels / margins into the caller's host buffers
+ * (each may be NULL; member_bits needs E <= 64), fills *info (may be NULL)
+ * and forgets the request.  Returns the request's own status once done. */
+fs_status fs_server_fetch(fs_server* srv, int64_t ticket, int32_t wait, uint64_t* member_bits,
+                          int32_t* label, float* margin, fs_server_info* info);
+
+/* Drop a request that has not started (FS_CANCELLED when fetched);
+ * FS_UNSUPPORTED if it is already running or done. */
+fs_status fs_server_cancel(fs_server* srv, int64_t ticket);
+
+/* Stop accepting requests, finish the running ones, drop the queued ones,
+ * join the threads and free everything. */
+fs_status fs_server_destroy(fs_server* srv);
 
 /* ---- solve without allocating ----------------------------------------------
  * The paper has no counterpart of this call; it exists for callers that may

@@ -193,6 +193,49 @@ struct fs_scene {
   DevBuf pos_op, cov;  // (m, o) and Sigma3D as float pairs
 };
 
+namespace {
+DevBuf* const* workspace_bufs(fs_ctx* c, size_t* count) {
+  static thread_local DevBuf* bufs[64];
+  size_t k = 0;
+  DevBuf* list[] = {&c->rec, &c->foot, &c->cnt, &c->key_a, &c->val_a, &c->key_b, &c->val_b,
+                    &c->offs, &c->ccnt, &c->dlo, &c->state, &c->sat, &c->subsat, &c->lk_a,
+                    &c->lv_a, &c->lk_b, &c->lv_b, &c->ranges, &c->sort_tmp, &c->scan_tmp,
+                    &c->mask_stage, &c->table_tmp, &c->table32_tmp, &c->bits_tmp,
+                    &c->label_tmp, &c->margin_tmp, &c->dkey, &c->rk_flag, &c->rk_offs,
+                    &c->rk_F, &c->rk_map, &c->rk_R, &c->rk_Rb, &c->kl_ranges, &c->kl_satc,
+                    &c->kl_bound};
+  for (DevBuf* b : list) bufs[k++] = b;
+  *count = k;
+  return bufs;
+}
+}  // namespace
+
+// Device bytes the context's growable workspace holds now.
+size_t fs::ctx_workspace_bytes(const fs_ctx* c) {
+  size_t count = 0, total = 0;
+  DevBuf* const* b = workspace_bufs(const_cast<fs_ctx*>(c), &count);
+  for (size_t k = 0; k < count; ++k) total += b[k]->bytes;
+  for (const DevBuf& v : c->kl_val) total += v.bytes;
+  return total;
+}
+
+// Frees the growable workspace (after the context's work has finished).
+void fs::ctx_release_workspace(fs_ctx* c) {
+  DeviceGuard g(c->device);
+  cudaDeviceSynchronize();
+  size_t count = 0;
+  DevBuf* const* b = workspace_bufs(c, &count);
+  for (size_t k = 0; k < count; ++k) b[k]->release();
+  for (DevBuf& v : c->kl_val) v.release();
+  c->kl_valid = false;
+}
+
+// Per-solve batching (views per batch, depth chunks), as fs_options sets them.
+void fs::ctx_set_batching(fs_ctx* c, int views_per_batch, int depth_chunks) {
+  if (views_per_batch > 0) c->views_per_batch = std::min(views_per_batch, fs::kMaxViewsPerBatch);
+  if (depth_chunks > 0) c->depth_chunks = std::min(depth_chunks, 16);
+}
+
 extern "C" {
 
 int32_t fs_version(void) { return FS_VERSION_MAJOR * 1000 + FS_VERSION_MINOR; }
@@ -889,7 +932,9 @@ fs_status check_accumulate_args(fs_ctx* c, const fs_scene* s, const fs_camera* c
                                 const void* const* masks, int32_t mask_dtype, int32_t mask_memory,
                                 int32_t E) {
   if (!c || !s) return fail(FS_INVALID_ARGUMENT, "NULL context or scene");
-  if (s->ctx != c) return fail(FS_INVALID_ARGUMENT, "scene belongs to another context");
+  if (s->ctx->device != c->device)
+    return fail(FS_INVALID_ARGUMENT, "scene lives on device %d, context on device %d",
+                s->ctx->device, c->device);
   if (V < 0) return fail(FS_INVALID_ARGUMENT, "n_views = %d", V);
   if (V > 0 && (!cams || !masks)) return fail(FS_INVALID_ARGUMENT, "NULL cams or masks");
   if (mask_dtype != FS_U8 && mask_dtype != FS_I32)

@@ -2,7 +2,10 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
+
+struct fs_ctx;
 
 namespace fs {
 
@@ -137,6 +140,11 @@ cudaError_t launch_recheck_blend(const ViewParams* views, int n_views, int max_t
                                  const float4* pos_op, int64_t n, int E, int mask_dtype,
                                  const int32_t* map, double* R, unsigned long long* counters,
                                  cudaStream_t stream);
+
+// Context workspace management for the request server (fs_api.cu).
+size_t ctx_workspace_bytes(const fs_ctx* c);
+void ctx_release_workspace(fs_ctx* c);
+void ctx_set_batching(fs_ctx* c, int views_per_batch, int depth_chunks);
 
 // Sets the calling thread's fs_last_error() message (fs_api.cu).
 void set_last_error(const char* msg);

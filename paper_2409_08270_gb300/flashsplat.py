@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "FS_OK", 1: "FS_INVALID_ARGUMENT", 2: "FS_OUT_OF_MEMORY", 3: 
 # every entry point declared in include/flashsplat.h
 EXPORTS = ["fs_version", "fs_last_error", "fs_create", "fs_destroy", "fs_scene_create",
            "fs_scene_destroy", "fs_scene_size", "fs_accumulate", "fs_assign", "fs_solve",
-           "fs_synchronize", "fs_solve_noalloc"]
+           "fs_synchronize", "fs_solve_noalloc", "fs_server_create", "fs_server_add_scene",
+           "fs_server_submit", "fs_server_fetch", "fs_server_cancel", "fs_server_destroy"]
 
 
 class fs_options(ctypes.Structure):
@@ -65,6 +66,21 @@ class fs_result(ctypes.Structure):
     _fields_ = [("memory", ctypes.c_int32), ("table_dtype", ctypes.c_int32),
                 ("table", ctypes.c_void_p), ("member_bits", ctypes.c_void_p),
                 ("label", ctypes.c_void_p), ("margin", ctypes.c_void_p)]
+
+
+class fs_server_options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("slots", ctypes.c_int32),
+                ("budget_bytes", ctypes.c_int64), ("autotune", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 9)]
+
+
+class fs_server_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("done", ctypes.c_int32),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("slot", ctypes.c_int32),
+                ("views_per_batch", ctypes.c_int32), ("depth_chunks", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("bytes_estimate", ctypes.c_int64),
+                ("stats", fs_stats)]
 
 
 class FlashSplatError(RuntimeError):
@@ -107,6 +123,13 @@ def load(path: str | None = None):
         "fs_synchronize": (i32, [vp, vp, ctypes.POINTER(fs_stats)]),
         "fs_solve_noalloc": (i32, [i32, ctypes.POINTER(fs_gaussians), ctypes.POINTER(fs_camera),
                                    i32, ctypes.POINTER(vp), i32, i32, f32, vp, vp, vp, vp, vp]),
+        "fs_server_create": (i32, [ctypes.POINTER(fs_server_options), ctypes.POINTER(vp)]),
+        "fs_server_add_scene": (i32, [vp, ctypes.POINTER(fs_gaussians), ctypes.POINTER(i32)]),
+        "fs_server_submit": (i32, [vp, i32, ctypes.POINTER(fs_camera), i32, ctypes.POINTER(vp),
+                                   i32, i32, f32, ctypes.POINTER(i64)]),
+        "fs_server_fetch": (i32, [vp, i64, i32, vp, vp, vp, ctypes.POINTER(fs_server_info)]),
+        "fs_server_cancel": (i32, [vp, i64]),
+        "fs_server_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -334,3 +357,109 @@ class Solver:
         if sync:
             out["stats"] = fs_synchronize(self.ctx, st)
         return out
+
+
+# ---- request server ---------------------------------------------------------
+
+def fs_server_create(device: int = 0, slots: int = 4, budget_bytes: int = 0,
+                     autotune: bool = False) -> int:
+    opt = fs_server_options()
+    opt.device, opt.slots, opt.budget_bytes = device, slots, budget_bytes
+    opt.autotune = 1 if autotune else 0
+    out = ctypes.c_void_p()
+    check(load().fs_server_create(ctypes.byref(opt), ctypes.byref(out)))
+    return out.value
+
+
+def fs_server_add_scene(srv: int, g: fs_gaussians) -> int:
+    sid = ctypes.c_int32()
+    check(load().fs_server_add_scene(srv, ctypes.byref(g), ctypes.byref(sid)))
+    return sid.value
+
+
+def fs_server_submit(srv: int, scene_id: int, cams, mask_ptrs, mask_dtype: int, E: int,
+                     gamma: float) -> int:
+    arr = (ctypes.c_void_p * max(len(mask_ptrs), 1))(*mask_ptrs)
+    ticket = ctypes.c_int64()
+    check(load().fs_server_submit(srv, scene_id, cams, len(mask_ptrs), arr, mask_dtype, E,
+                                  ctypes.c_float(gamma), ctypes.byref(ticket)))
+    return ticket.value
+
+
+def fs_server_fetch(srv: int, ticket: int, wait: bool, bits_ptr, label_ptr, margin_ptr):
+    info = fs_server_info()
+    st = load().fs_server_fetch(srv, ticket, 1 if wait else 0, bits_ptr, label_ptr, margin_ptr,
+                                ctypes.byref(info))
+    return st, info
+
+
+def fs_server_cancel(srv: int, ticket: int):
+    check(load().fs_server_cancel(srv, ticket))
+
+
+def fs_server_destroy(srv: int):
+    check(load().fs_server_destroy(srv))
+
+
+class Server:
+    """Request server over resident scenes (continuous batching; see
+    fs_server_create in flashsplat.h).  Scenes and masks are numpy arrays in
+    host memory; results come back as numpy arrays."""
+
+    def __init__(self, device: int = 0, slots: int = 4, budget_bytes: int = 0,
+                 autotune: bool = False):
+        self.srv = fs_server_create(device, slots, budget_bytes, autotune)
+        self.sizes = []
+        self._keep = {}
+
+    def add_scene(self, gaussians) -> int:
+        arrs = {k: np.ascontiguousarray(np.asarray(gaussians[k], dtype=np.float32))
+                for k in ("mean", "quat", "scale", "opacity")}
+        g = fs_gaussians()
+        g.n = int(arrs["mean"].shape[0])
+        g.mean, g.quat = arrs["mean"].ctypes.data, arrs["quat"].ctypes.data
+        g.scale, g.opacity = arrs["scale"].ctypes.data, arrs["opacity"].ctypes.data
+        g.quat_dtype = g.scale_dtype = g.opacity_dtype = FS_F32
+        g.memory = FS_MEM_HOST
+        sid = fs_server_add_scene(self.srv, g)
+        self.sizes.append(g.n)
+        return sid
+
+    def submit(self, scene_id: int, cams, masks, E: int, gamma: float) -> int:
+        ms = [np.ascontiguousarray(m) for m in masks]
+        dt = FS_I32 if ms[0].dtype == np.int32 else FS_U8
+        ms = [m.astype(np.int32 if dt == FS_I32 else np.uint8, copy=False) for m in ms]
+        t = fs_server_submit(self.srv, scene_id, make_cameras(cams), [m.ctypes.data for m in ms],
+                             dt, E, gamma)
+        self._keep[t] = (scene_id, E)
+        return t
+
+    def fetch(self, ticket: int, wait: bool = True):
+        sid, E = self._keep[ticket]
+        n = self.sizes[sid]
+        bits = np.empty(n, np.uint64) if E <= 64 else None
+        label = np.empty(n, np.int32)
+        margin = np.empty(n, np.float32)
+        st, info = fs_server_fetch(self.srv, ticket, wait,
+                                   bits.ctypes.data if bits is not None else None,
+                                   label.ctypes.data, margin.ctypes.data)
+        if st == FS_TIMEOUT and not wait:
+            return None
+        del self._keep[ticket]
+        if st != FS_OK:
+            raise FlashSplatError(st, load().fs_last_error().decode(errors="replace"))
+        return {"bits": bits, "label": label, "margin": margin, "info": info}
+
+    def cancel(self, ticket: int):
+        fs_server_cancel(self.srv, ticket)
+
+    def close(self):
+        if self.srv:
+            fs_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -21,6 +21,7 @@ call gives bit-identical inputs on every machine.
 from __future__ import annotations
 
 import math
+import zlib
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -354,3 +355,72 @@ def rounded_gaussians(g):
     return {"mean": np.asarray(g["mean"], np.float32),
             "quat": round_bf16(g["quat"]), "scale": round_bf16(g["scale"]),
             "opacity": round_fp16(g["opacity"])}
+
+
+SERVE_RESOLUTIONS = ((512, 512), (800, 600), (1008, 756), (1256, 828), (1600, 1200))
+
+
+def serving_scenes(seed=SEED_BASE + 5, count=16, n_lo=200_000, n_hi=2_000_000, v_lo=20,
+                   v_hi=150, labels_hi=16, scale=1.0):
+    """Scenes of uneven size for the request server: N log-uniform in
+    [n_lo, n_hi], V uniform in {v_lo..v_hi}, a resolution from
+    SERVE_RESOLUTIONS, 1..labels_hi object labels (clusters grouped into
+    labels), a 360-degree orbit at two elevations like multi_scene, uint8
+    clean label masks (E = labels + 1).  `scale` shrinks N, V and the
+    resolution together (for quick tests).  Returns a list of Workloads."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))) * scale)
+        v = max(2, int(rng.integers(v_lo, v_hi + 1) * scale))
+        wd, ht = SERVE_RESOLUTIONS[int(rng.integers(0, len(SERVE_RESOLUTIONS)))]
+        wd, ht = max(16, int(wd * scale)), max(16, int(ht * scale))
+        labels = int(rng.integers(1, labels_hi + 1))
+        n_clusters = max(labels, int(rng.integers(labels, 33)))
+        sub = np.random.default_rng(int(rng.integers(1 << 62)))
+        g, cl, objects = _clustered_scene(sub, n, n_clusters, [-1.5] * 3, [1.5] * 3,
+                                          0.05, 0.3, -4.0, 1.0, 1.5)
+        group = sub.integers(0, labels, size=n_clusters) + 1   # cluster -> label
+        fx = fx_from_hfov(wd, 60.0)
+        cams, masks = [], []
+        per_ring = max(1, v // 2)
+        for i in range(v):
+            el = math.radians(15.0 if i < per_ring else 40.0)
+            az = math.radians((i % per_ring) * 360.0 / per_ring)
+            pos = (5.0 * math.cos(el) * math.sin(az), 5.0 * math.sin(el),
+                   -5.0 * math.cos(el) * math.cos(az))
+            cam = camera(pos, wd, ht, fx)
+            lab = label_map(cam, [(int(group[c]), objects[c][1], objects[c][2], objects[c][3])
+                                  for c in range(n_clusters)])
+            masks.append(lab.astype(np.uint8))
+            cams.append(cam)
+        out.append(Workload(f"serve{k}", g, cams, masks, labels + 1, 0.5,
+                            group[cl].astype(np.int32), {"P": sum(m.size for m in masks)}))
+    return out
+
+
+def request_masks(w, seed, flip=0.02):
+    """A request's masks: the scene's clean masks with fresh seeded noise --
+    every pixel flipped to a random other label with probability `flip`,
+    drawn as one noise field per view shifted by a seeded offset (cheap
+    enough to make per request)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for v, m in enumerate(w.masks):
+        field = _noise_field(w.name, v, m.shape, flip, w.E)
+        dy, dx = int(rng.integers(0, m.shape[0])), int(rng.integers(0, m.shape[1]))
+        f = np.roll(field, (dy, dx), axis=(0, 1))
+        out.append(np.where(f > 0, (m.astype(np.int64) + f) % w.E, m).astype(m.dtype))
+    return out
+
+
+_NOISE = {}
+
+
+def _noise_field(name, v, shape, flip, E):
+    key = (name, v, shape, flip, E)
+    if key not in _NOISE:
+        rng = np.random.default_rng(zlib.crc32(repr(key).encode()))
+        f = np.where(rng.random(shape) < flip, rng.integers(1, max(E, 2), size=shape), 0)
+        _NOISE[key] = f.astype(np.int16)
+    return _NOISE[key]
