@@ -175,6 +175,7 @@ struct fs_ctx {
   bool recheck_reproject = false;
   bool compact = false;  // reduced-precision records (FP16 whitening matrix, FP32 mean)
   DevBuf dkey, rk_flag, rk_offs, rk_F, rk_map, rk_R, rk_Rb;
+  DevBuf key_range;  // min / max visible depth key of the current batch
   // the main pass's tile lists, kept for the re-check (see kept_layout)
   bool kl_valid = false;
   int kl_chunks = 1;
@@ -300,7 +301,7 @@ fs_status fs_destroy(fs_ctx* c) {
                     &c->sort_tmp, &c->scan_tmp, &c->total, &c->counters, &c->mask_stage,
                     &c->table_tmp, &c->table32_tmp, &c->bits_tmp, &c->label_tmp, &c->margin_tmp,
                     &c->dkey, &c->rk_flag, &c->rk_offs, &c->rk_F, &c->rk_map, &c->rk_R,
-                    &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_bound};
+                    &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_bound, &c->key_range};
   for (DevBuf& b : c->kl_val) b.release();
   for (DevBuf* b : bufs) b->release();
   c->views_host.release();
@@ -674,20 +675,36 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
               "saturation chunks");
     }
 
-    // project every Gaussian into the batch's views, sort by depth
-    c->stats.kernel_launches += 3 + radix_launches(k_total, 32);
+    // project every Gaussian into the batch's views, sort by depth (only the
+    // bits in which the batch's visible depth keys differ)
+    FS_TRY(c->key_range.ensure(16, "depth key range"));
+    uint32_t* kr = c->key_range.as<uint32_t>();
+    FS_CUDA(cudaMemsetAsync(kr, 0xFF, 4, stream), "key range");
+    FS_CUDA(cudaMemsetAsync(kr + 1, 0, 4, stream), "key range");
+    c->stats.kernel_launches += 2;
     FS_CUDA(fs::launch_project(n, nb, vd, s->pos_op.as<float4>(), s->cov.as<float4>(), P.rec,
                                P.rec16, P.foot, P.cnt, c->key_a.as<uint32_t>(),
-                               c->val_a.as<uint32_t>(), P.dlo, stream),
+                               c->val_a.as<uint32_t>(), P.dlo, kr, stream),
             "project");
     if (P.dkey)
       FS_CUDA(cudaMemcpyAsync(P.dkey, c->key_a.p, static_cast<size_t>(k_total) * 4,
                               cudaMemcpyDeviceToDevice, stream),
               "depth key copy");
+    uint32_t* krh = c->total_host.as<uint32_t>() + 4;
+    FS_CUDA(cudaMemcpyAsync(krh, kr, 8, cudaMemcpyDeviceToHost, stream), "key range readback");
+    FS_CUDA(cudaStreamSynchronize(stream), "key range readback");
+    uint32_t kmin = 0, span = 0;
+    int key_bits = 0;
+    if (krh[0] <= krh[1]) {
+      kmin = krh[0];
+      span = krh[1] - krh[0] + 1;  // invisible slots map to span, after every visible one
+      key_bits = std::max(1, ceil_log2(static_cast<int64_t>(span) + 1));
+    }
+    c->stats.kernel_launches += radix_launches(k_total, key_bits);
     bool alt = false;
     FS_CUDA(fs::radix_sort_pairs(c->key_a.as<uint32_t>(), c->val_a.as<uint32_t>(),
-                                 c->key_b.as<uint32_t>(), c->val_b.as<uint32_t>(), k_total, 32,
-                                 c->sort_tmp.p, &alt, stream),
+                                 c->key_b.as<uint32_t>(), c->val_b.as<uint32_t>(), k_total,
+                                 key_bits, c->sort_tmp.p, &alt, stream, kmin, span),
             "depth sort");
     uint32_t* sorted_key = alt ? c->key_b.as<uint32_t>() : c->key_a.as<uint32_t>();
     uint32_t* sorted_val = alt ? c->val_b.as<uint32_t>() : c->val_a.as<uint32_t>();
@@ -871,7 +888,7 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
       c->stats.kernel_launches += 1;
       FS_CUDA(fs::launch_project(n, nb, vd, s->pos_op.as<float4>(), s->cov.as<float4>(), P.rec,
                                  P.rec16, P.foot, P.cnt, c->key_a.as<uint32_t>(),
-                                 c->val_a.as<uint32_t>(), P.dlo, stream),
+                                 c->val_a.as<uint32_t>(), P.dlo, nullptr, stream),
               "project");
       key_src = c->key_a.as<uint32_t>();
     }

@@ -25,12 +25,14 @@ cudaError_t exclusive_scan(const uint32_t* in, const uint32_t* gather, uint32_t*
                            uint32_t* total, void* temp, cudaStream_t stream);
 // Temporary storage of radix_sort_pairs for n elements (bytes).
 size_t radix_temp_bytes(int64_t n);
-// Stable LSD radix sort of (key, val) pairs on the low `bits` bits of key.
+// Stable LSD radix sort of (key, val) pairs on the low `bits` bits of
+// min(key - kmin, span) (the keys themselves are moved unchanged).
 // Ping-pongs between (keys, vals) and (keys_alt, vals_alt); *in_alt tells the
 // caller which pair holds the result.
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                              uint32_t* vals_alt, int64_t n, int bits, void* temp, bool* in_alt,
-                             cudaStream_t stream);
+                             cudaStream_t stream, uint32_t kmin = 0u,
+                             uint32_t span = 0xFFFFFFFFu);
 
 // projection / binning (fs_project.cu) --------------------------------------
 // pos_op[n] = (m, o); cov[3n] = Sigma3D as float pairs (FP64 once per scene)
@@ -39,11 +41,13 @@ cudaError_t launch_scene_prep(int64_t n, const float* mean, const void* quat, in
                               int opacity_dtype, float4* pos_op, float4* cov, unsigned int* err,
                               cudaStream_t stream);
 // rec16 != NULL: reduced-precision records (FP16 whitening matrix, FP32 mean)
-// are written to rec16 instead of the float-pair records to rec
+// are written to rec16 instead of the float-pair records to rec.
+// key_range (2 uint32, may be NULL): atomic min / max of the visible slots'
+// depth keys (the caller initialises it to {0xFFFFFFFF, 0}).
 cudaError_t launch_project(int64_t n, int n_views, const ViewParams* views, const float4* pos_op,
                            const float4* cov, ProjRecord* rec, CompactRecord* rec16,
                            Footprint* foot, uint32_t* cnt, uint32_t* key, uint32_t* val,
-                           uint32_t* depth_lo, cudaStream_t stream);
+                           uint32_t* depth_lo, uint32_t* key_range, cudaStream_t stream);
 // re-orders runs of equal 32-bit depth keys by the depth's low word, then slot
 // (n_total elements; slot / n is the view of a slot)
 cudaError_t launch_depth_tie_fix(int64_t n_total, int64_t n, const uint32_t* key, uint32_t* val,

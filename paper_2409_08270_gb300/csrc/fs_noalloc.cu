@@ -249,7 +249,8 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
     const int tiles = vp.tiles_x * vp.tiles_y;
     // pageable source: the copy has taken the bytes when the call returns
     NA_CUDA(cudaMemcpyAsync(vd, &vp, sizeof(vp), cudaMemcpyHostToDevice, strm), "view upload");
-    NA_CUDA(launch_project(n, 1, vd, pos, cov, rec, nullptr, foot, cnt, key_a, val_a, dlo, strm),
+    NA_CUDA(launch_project(n, 1, vd, pos, cov, rec, nullptr, foot, cnt, key_a, val_a, dlo, nullptr,
+                           strm),
             "project");
     bool alt = false;
     NA_CUDA(radix_sort_pairs(key_a, val_a, key_b, val_b, n, 32, sort_tmp, &alt, strm), "sort");

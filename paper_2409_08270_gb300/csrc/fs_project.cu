@@ -133,19 +133,19 @@ __device__ __forceinline__ uint16_t f2_to_half_rn(f2 x) {
 // One thread per Gaussian; it projects the Gaussian into every view of the
 // batch so the scene is read once per batch.  rec16 != NULL: the record is
 // written in the reduced-precision form instead (rec is not written).
-__global__ void __launch_bounds__(256) project_kernel(
+__global__ void __launch_bounds__(256, 4) project_kernel(
     int64_t n, int n_views, const ViewParams* __restrict__ views_g,
     const float4* __restrict__ pos_op, const float4* __restrict__ cov3,
     ProjRecord* __restrict__ rec, CompactRecord* __restrict__ rec16, Footprint* __restrict__ foot,
     uint32_t* __restrict__ cnt, uint32_t* __restrict__ key, uint32_t* __restrict__ val,
-    uint32_t* __restrict__ depth_lo) {
+    uint32_t* __restrict__ depth_lo, uint32_t* __restrict__ key_range) {
   __shared__ ViewParams views[kMaxViewsPerBatch];
   for (int k = threadIdx.x; k < n_views * (int)(sizeof(ViewParams) / 4); k += blockDim.x)
     reinterpret_cast<uint32_t*>(views)[k] = reinterpret_cast<const uint32_t*>(views_g)[k];
   __syncthreads();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-
+  uint32_t kmin = 0xFFFFFFFFu, kmax = 0u;  // visible depth keys of this thread
+  if (i < n) {
   const float4 po = pos_op[i];
   const float4 ca = cov3[3 * i], cb = cov3[3 * i + 1], cc = cov3[3 * i + 2];
   const f2 S00 = {ca.x, ca.y}, S01 = {ca.z, ca.w}, S02 = {cb.x, cb.y};
@@ -284,9 +284,23 @@ __global__ void __launch_bounds__(256) project_kernel(
       rec[slot] = R;
     foot[slot] = F;
     cnt[slot] = visible ? count : 0u;
-    key[slot] = visible ? depth_key(depth) : 0xFFFFFFFFu;
+    const uint32_t k = visible ? depth_key(depth) : 0xFFFFFFFFu;
+    if (visible) {
+      kmin = min(kmin, k);
+      kmax = max(kmax, k);
+    }
+    key[slot] = k;
     val[slot] = static_cast<uint32_t>(slot);
     depth_lo[slot] = float_order_key(depth_l);
+  }
+  }
+  if (key_range) {
+    kmin = __reduce_min_sync(0xffffffffu, kmin);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    if ((threadIdx.x & 31) == 0 && kmin <= kmax) {
+      atomicMin(&key_range[0], kmin);
+      atomicMax(&key_range[1], kmax);
+    }
   }
 }
 
@@ -533,12 +547,12 @@ cudaError_t launch_scene_prep(int64_t n, const float* mean, const void* quat, in
 cudaError_t launch_project(int64_t n, int n_views, const ViewParams* views, const float4* pos_op,
                            const float4* cov, ProjRecord* rec, CompactRecord* rec16,
                            Footprint* foot, uint32_t* cnt, uint32_t* key, uint32_t* val,
-                           uint32_t* depth_lo, cudaStream_t stream) {
+                           uint32_t* depth_lo, uint32_t* key_range, cudaStream_t stream) {
   if (n == 0 || n_views == 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = (n + threads - 1) / threads;
   project_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-      n, n_views, views, pos_op, cov, rec, rec16, foot, cnt, key, val, depth_lo);
+      n, n_views, views, pos_op, cov, rec, rec16, foot, cnt, key, val, depth_lo, key_range);
   return cudaGetLastError();
 }
 

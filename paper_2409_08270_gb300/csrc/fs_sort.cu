@@ -110,8 +110,16 @@ __global__ void __launch_bounds__(kThreads) scan_down_kernel(const uint32_t* __r
   }
 }
 
+// Digits are taken from min(key - kmin, span): a key range [kmin, kmin + span)
+// (and everything above it mapped to span) needs only the bits of span.
+__device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t kmin, uint32_t span,
+                                             int shift) {
+  return (min(key - kmin, span) >> shift) & 0xFFu;
+}
+
 __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint32_t* __restrict__ keys,
                                                               int64_t n, int shift, int64_t nb,
+                                                              uint32_t kmin, uint32_t span,
                                                               uint32_t* __restrict__ hist) {
   __shared__ uint32_t s_h[kRadix];
   s_h[threadIdx.x] = 0;
@@ -120,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint32_t* __
 #pragma unroll 4
   for (int r = 0; r < kRounds; ++r) {
     const int64_t j = base + r * kThreads + threadIdx.x;
-    if (j < n) atomicAdd(&s_h[(keys[j] >> shift) & 0xFFu], 1u);
+    if (j < n) atomicAdd(&s_h[digit_of(keys[j], kmin, span, shift)], 1u);
   }
   __syncthreads();
   hist[static_cast<int64_t>(threadIdx.x) * nb + blockIdx.x] = s_h[threadIdx.x];
@@ -134,8 +142,8 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint32_t* __
 // offset with consecutive threads on consecutive addresses.
 __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
     const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n, int shift,
-    int64_t nb, const uint32_t* __restrict__ hist_pre, uint32_t* __restrict__ keys_out,
-    uint32_t* __restrict__ vals_out) {
+    int64_t nb, uint32_t kmin, uint32_t span, const uint32_t* __restrict__ hist_pre,
+    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
   __shared__ uint32_t s_key[kTileElems];
   __shared__ uint32_t s_val[kTileElems];
   __shared__ uint32_t s_wcnt[kWarps][kRadix];  // per-warp digit counts, then warp prefixes
@@ -157,7 +165,7 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
     const int j = wbase + i * 32 + lane;
     const bool ok = j < n_here;
     key[i] = ok ? keys[base + j] : 0u;
-    const uint32_t d = ok ? ((key[i] >> shift) & 0xFFu) : 0x100u;
+    const uint32_t d = ok ? digit_of(key[i], kmin, span, shift) : 0x100u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t before = ok ? s_wcnt[warp][d] : 0u;
     rank[i] = before + __popc(peers & lt);
@@ -182,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
   for (int i = 0; i < kRounds; ++i) {
     const int j = wbase + i * 32 + lane;
     if (j < n_here) {
-      const uint32_t d = (key[i] >> shift) & 0xFFu;
+      const uint32_t d = digit_of(key[i], kmin, span, shift);
       const uint32_t pos = s_loc[d] + s_wcnt[warp][d] + rank[i];
       s_key[pos] = key[i];
       s_val[pos] = vals[base + j];
@@ -192,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
   // coalesced write-out of the digit runs
   for (int j = threadIdx.x; j < n_here; j += kThreads) {
     const uint32_t k = s_key[j];
-    const uint32_t d = (k >> shift) & 0xFFu;
+    const uint32_t d = digit_of(k, kmin, span, shift);
     const uint32_t dst = s_glob[d] + (static_cast<uint32_t>(j) - s_loc[d]);
     keys_out[dst] = k;
     vals_out[dst] = s_val[j];
@@ -229,7 +237,7 @@ size_t radix_temp_bytes(int64_t n) {
 
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                              uint32_t* vals_alt, int64_t n, int bits, void* temp, bool* in_alt,
-                             cudaStream_t stream) {
+                             cudaStream_t stream, uint32_t kmin, uint32_t span) {
   *in_alt = false;
   if (n <= 1 || bits <= 0) return cudaSuccess;
   const int64_t nb = tiles_of(n);
@@ -239,11 +247,11 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
   uint32_t *src_k = keys, *src_v = vals, *dst_k = keys_alt, *dst_v = vals_alt;
   for (int shift = 0; shift < bits; shift += 8) {
     radix_hist_kernel<<<static_cast<unsigned>(nb), kThreads, 0, stream>>>(src_k, n, shift, nb,
-                                                                          hist);
+                                                                          kmin, span, hist);
     cudaError_t e = exclusive_scan(hist, nullptr, hist, nb * kRadix, nullptr, scan_tmp, stream);
     if (e != cudaSuccess) return e;
     radix_scatter_kernel<<<static_cast<unsigned>(nb), kThreads, 0, stream>>>(
-        src_k, src_v, n, shift, nb, hist, dst_k, dst_v);
+        src_k, src_v, n, shift, nb, kmin, span, hist, dst_k, dst_v);
     uint32_t* tk = src_k;
     uint32_t* tv = src_v;
     src_k = dst_k;
