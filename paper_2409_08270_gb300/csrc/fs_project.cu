@@ -304,11 +304,12 @@ __global__ void __launch_bounds__(256, 4) project_kernel(
   }
 }
 
-// The radix sort orders by the float depth key hi, stably by slot.  Runs of
-// equal hi are re-ordered here by the low word of the float-pair depth (and
-// then by slot), so the order is that of the full-precision depth with ties
-// by index -- the order the compositing of Eq. 1 walks.  Runs are short; one
-// thread sorts each run by insertion.
+// The radix sort orders by the float depth key hi, stably by slot, so equal
+// keys already come in (view, index) order.  Only elements of one view that
+// share a key need another order: by the low word of the float-pair depth,
+// then by slot -- the order of the full-precision depth with ties by index
+// that the compositing of Eq. 1 walks.  A thread acts only where such a
+// same-view run starts; the runs are short and sorted by insertion.
 __global__ void depth_tie_fix_kernel(int64_t n_total, int64_t n, const uint32_t* __restrict__ key,
                                      uint32_t* __restrict__ val,
                                      const uint32_t* __restrict__ depth_lo) {
@@ -316,28 +317,21 @@ __global__ void depth_tie_fix_kernel(int64_t n_total, int64_t n, const uint32_t*
   if (k + 1 >= n_total) return;
   const uint32_t kk = key[k];
   if (kk == 0xFFFFFFFFu || key[k + 1] != kk) return;
-  if (k > 0 && key[k - 1] == kk) return;  // not the start of the run
-  int64_t e = k + 2;
-  while (e < n_total && key[e] == kk) ++e;
-  // Only the order of the same view's elements matters (views are separated
-  // later by a stable sort); order by (view, low word, slot).
   const uint32_t nn = static_cast<uint32_t>(n);
+  const uint32_t v0 = val[k];
+  const uint32_t view = v0 / nn;
+  if (val[k + 1] / nn != view) return;                       // no same-view tie here
+  if (k > 0 && key[k - 1] == kk && val[k - 1] / nn == view) return;  // not the run's start
+  int64_t e = k + 2;
+  while (e < n_total && key[e] == kk && val[e] / nn == view) ++e;
   for (int64_t a = k + 1; a < e; ++a) {
     const uint32_t va = val[a];
-    const uint32_t view_a = va / nn;
+    const uint64_t ka = (static_cast<uint64_t>(depth_lo[va]) << 32) | va;
     int64_t b = a - 1;
     while (b >= k) {
       const uint32_t vb = val[b];
-      const uint32_t view_b = vb / nn;
-      bool greater;  // element b goes after element a
-      if (view_b != view_a) {
-        greater = view_b > view_a;
-      } else {
-        const uint64_t ka = (static_cast<uint64_t>(depth_lo[va]) << 32) | va;
-        const uint64_t kb = (static_cast<uint64_t>(depth_lo[vb]) << 32) | vb;
-        greater = kb > ka;
-      }
-      if (!greater) break;
+      const uint64_t kb = (static_cast<uint64_t>(depth_lo[vb]) << 32) | vb;
+      if (kb <= ka) break;
       val[b + 1] = vb;
       --b;
     }
