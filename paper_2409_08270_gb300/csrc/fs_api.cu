@@ -64,12 +64,12 @@ struct DevBuf {
   size_t bytes = 0;
   fs_status ensure(size_t need, const char* what) {
     if (need <= bytes) return FS_OK;
+    size_t want = std::max(need, static_cast<size_t>(bytes + bytes / 4));  // grow geometrically
     if (p) {
       cudaFree(p);
       p = nullptr;
       bytes = 0;
     }
-    size_t want = std::max(need, static_cast<size_t>(bytes + bytes / 4));
     want = (want + 255) & ~static_cast<size_t>(255);
     cudaError_t e = cudaMalloc(&p, want);
     if (e != cudaSuccess) {
@@ -176,6 +176,7 @@ struct fs_ctx {
   bool compact = false;  // reduced-precision records (FP16 whitening matrix, FP32 mean)
   DevBuf dkey, rk_flag, rk_offs, rk_F, rk_map, rk_R, rk_Rb;
   DevBuf key_range;  // min / max visible depth key of the current batch
+  DevBuf lb_tmp;     // look-back words of the fused binning
   // the main pass's tile lists, kept for the re-check (see kept_layout)
   bool kl_valid = false;
   int kl_chunks = 1;
@@ -204,7 +205,7 @@ DevBuf* const* workspace_bufs(fs_ctx* c, size_t* count) {
                     &c->mask_stage, &c->table_tmp, &c->table32_tmp, &c->bits_tmp,
                     &c->label_tmp, &c->margin_tmp, &c->dkey, &c->rk_flag, &c->rk_offs,
                     &c->rk_F, &c->rk_map, &c->rk_R, &c->rk_Rb, &c->kl_ranges, &c->kl_satc,
-                    &c->kl_bound};
+                    &c->kl_bound, &c->key_range, &c->lb_tmp};
   for (DevBuf* b : list) bufs[k++] = b;
   *count = k;
   return bufs;
@@ -301,7 +302,7 @@ fs_status fs_destroy(fs_ctx* c) {
                     &c->sort_tmp, &c->scan_tmp, &c->total, &c->counters, &c->mask_stage,
                     &c->table_tmp, &c->table32_tmp, &c->bits_tmp, &c->label_tmp, &c->margin_tmp,
                     &c->dkey, &c->rk_flag, &c->rk_offs, &c->rk_F, &c->rk_map, &c->rk_R,
-                    &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_bound, &c->key_range};
+                    &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_bound, &c->key_range, &c->lb_tmp};
   for (DevBuf& b : c->kl_val) b.release();
   for (DevBuf* b : bufs) b->release();
   c->views_host.release();
@@ -562,31 +563,33 @@ fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
   *I_out = 0;
   FS_CUDA(cudaMemsetAsync(ranges_dst, 0, static_cast<size_t>(total_tiles) * 8, stream),
           "ranges clear");
-  c->stats.kernel_launches += 1 + scan_launches(n_pos);
-  FS_CUDA(fs::launch_chunk_count(p0, n_pos, n, vd, sorted_val, P.cnt, P.foot, sat,
-                                 c->ccnt.as<uint32_t>(), stream),
-          "chunk count");
-  FS_CUDA(fs::exclusive_scan(c->ccnt.as<uint32_t>(), nullptr, c->offs.as<uint32_t>(), n_pos,
-                             c->total.as<uint32_t>(), c->scan_tmp.p, stream),
-          "count scan");
+  FS_TRY(c->lb_tmp.ensure(fs::bin_fused_temp_bytes(n_pos), "binning look-back"));
+  // count, offsets and emission in one launch into the buffers' current
+  // capacity; a chunk with more entries than fit runs again after growing
   int64_t I = 0;
-  FS_TRY(read_total(c, stream, &I));
-  if (I >= (static_cast<int64_t>(1) << 31))
-    return fail(FS_UNSUPPORTED, "%lld list entries in one chunk; use fewer views per batch",
-                (long long)I);
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const size_t cap_bytes = std::min(c->lk_a.bytes, val_dst->bytes);
+    const uint32_t capacity = static_cast<uint32_t>(std::min<size_t>(cap_bytes / 4, 0x7FFFFFFFu));
+    c->stats.kernel_launches += 1;
+    FS_CUDA(fs::launch_bin_fused(p0, n_pos, n, vd, sorted_val, P.cnt, P.foot, sat,
+                                 c->lk_a.as<uint32_t>(), val_dst->as<uint32_t>(), capacity,
+                                 c->lb_tmp.p, c->total.as<uint32_t>(), ctr, stream),
+            "binning");
+    FS_TRY(read_total(c, stream, &I));
+    if (I >= (static_cast<int64_t>(1) << 31))
+      return fail(FS_UNSUPPORTED, "%lld list entries in one chunk; use fewer views per batch",
+                  (long long)I);
+    if (I <= static_cast<int64_t>(capacity)) break;
+    FS_TRY(c->lk_a.ensure(static_cast<size_t>(I) * 4, "list keys"));
+    FS_TRY(val_dst->ensure(static_cast<size_t>(I) * 4, "list values"));
+  }
   if (count_entries) c->stats.list_entries += I;
   *I_out = I;
   if (I == 0) return FS_OK;
-  FS_TRY(c->lk_a.ensure(static_cast<size_t>(I) * 4, "list keys"));
-  FS_TRY(val_dst->ensure(static_cast<size_t>(I) * 4, "list values"));
   FS_TRY(c->lk_b.ensure(static_cast<size_t>(I) * 4, "list keys"));
   FS_TRY(c->lv_b.ensure(static_cast<size_t>(I) * 4, "list values"));
   FS_TRY(c->sort_tmp.ensure(fs::radix_temp_bytes(std::max<int64_t>(I, kcap)), "sort temp"));
-  c->stats.kernel_launches += 2 + radix_launches(I, tile_bits);
-  FS_CUDA(fs::launch_emit(p0, n_pos, n, vd, sorted_val, c->offs.as<uint32_t>(),
-                          c->ccnt.as<uint32_t>(), P.cnt, P.foot, sat, c->lk_a.as<uint32_t>(),
-                          val_dst->as<uint32_t>(), ctr, stream),
-          "emit");
+  c->stats.kernel_launches += 1 + radix_launches(I, tile_bits);
   bool alt2 = false;
   FS_CUDA(fs::radix_sort_pairs(c->lk_a.as<uint32_t>(), val_dst->as<uint32_t>(),
                                c->lk_b.as<uint32_t>(), c->lv_b.as<uint32_t>(), I, tile_bits,

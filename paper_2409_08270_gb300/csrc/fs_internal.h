@@ -61,6 +61,16 @@ cudaError_t launch_emit(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* 
                         const uint32_t* chunk_cnt, const uint32_t* cnt, const Footprint* foot,
                         const uint64_t* sat, uint32_t* out_key, uint32_t* out_val,
                         unsigned long long* counters, cudaStream_t stream);
+// Count, scan and emit of sorted positions [p0, p0 + n_pos) in one launch
+// (decoupled look-back).  Entries at positions >= capacity are not written;
+// *total (device) receives the entry count.  lookback: bin_fused_temp_bytes
+// of scratch (cleared by the launcher).
+cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
+                             const uint32_t* sorted_val, const uint32_t* cnt,
+                             const Footprint* foot, const uint64_t* sat, uint32_t* out_key,
+                             uint32_t* out_val, uint32_t capacity, void* lookback,
+                             uint32_t* total, unsigned long long* counters, cudaStream_t stream);
+size_t bin_fused_temp_bytes(int64_t n_pos);
 cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
                           cudaStream_t stream);
 

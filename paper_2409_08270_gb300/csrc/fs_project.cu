@@ -512,6 +512,108 @@ __global__ void __launch_bounds__(256) emit_kernel(
   if (lane == 0 && jw < n_pos && wbeg + carry != wend) atomicAdd(&counters[kBinningMismatch], 1ull);
 }
 
+// Count, offset and emit in one pass.  Blocks take virtual ids in launch
+// order (a ticket), so every block's predecessors are running or done.  A
+// block counts its 256 positions' entries, publishes the count, then adds
+// up its predecessors' published words (decoupled look-back: a word is
+// either a block's own count or the inclusive prefix up to it; the walk
+// stops at the first prefix), publishes its own prefix and emits from its
+// offset.  No block waits on a later one.  Entries at or past `capacity`
+// are not written; *total receives the entry count either way, so the
+// caller can grow the buffer and run the chunk again.  A look-back that
+// waits longer than its bound counts an error and uses 0.
+constexpr unsigned long long kLbCount = 1ull << 32;   // word holds the block's own count
+constexpr unsigned long long kLbPrefix = 2ull << 32;  // word holds the inclusive prefix
+constexpr int kLbSpinLimit = 1 << 26;
+
+__global__ void __launch_bounds__(256) bin_fused_kernel(
+    int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
+    const uint32_t* __restrict__ sorted_val, const uint32_t* __restrict__ cnt,
+    const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
+    uint32_t* __restrict__ out_key, uint32_t* __restrict__ out_val, uint32_t capacity,
+    unsigned long long* __restrict__ status, uint32_t* __restrict__ ticket,
+    uint32_t* __restrict__ total, unsigned long long* __restrict__ counters) {
+  __shared__ uint32_t s_vb, s_boff;
+  __shared__ uint32_t s_wtot[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_vb = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const uint32_t vb = s_vb;
+  const int64_t j = static_cast<int64_t>(vb) * blockDim.x + threadIdx.x;
+  uint32_t g, nrows;
+  int ty0;
+  lane_rows(j, n_pos, p0, sorted_val, cnt, foot, &g, &ty0, &nrows);
+  const uint32_t incl = warp_incl_scan(nrows, lane);
+  const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
+  // count
+  uint32_t wtot = 0;
+  for (int r0 = 0; r0 < R; r0 += 32) {
+    const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
+    int a, b;
+    uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fr += __shfl_xor_sync(0xffffffffu, fr, o);
+    wtot += fr;
+  }
+  if (lane == 0) s_wtot[warp] = wtot;
+  __syncthreads();
+  // offset of the block: decoupled look-back over the predecessors, 32 at a
+  // time (lane l reads predecessor vb - 1 - l)
+  if (warp == 0) {
+    uint32_t btot = 0;
+    for (int w = 0; w < 8; ++w) btot += s_wtot[w];
+    if (lane == 0) atomicExch(&status[vb], (vb == 0 ? kLbPrefix : kLbCount) | btot);
+    volatile unsigned long long* vs = status;
+    uint32_t excl = 0;
+    for (int64_t base = static_cast<int64_t>(vb) - 1; base >= 0; base -= 32) {
+      const int64_t q = base - lane;
+      unsigned long long word = kLbPrefix;  // before block 0: an empty prefix
+      if (q >= 0) {
+        word = vs[q];
+        int spins = 0;
+        while ((word >> 32) == 0ull && spins < kLbSpinLimit) {
+          __nanosleep(32);
+          word = vs[q];
+          ++spins;
+        }
+        if ((word >> 32) == 0ull) {  // gave up: report, count it as an empty prefix
+          atomicAdd(&counters[kBinningMismatch], 1ull);
+          word = kLbPrefix;
+        }
+      }
+      const uint32_t pre = __ballot_sync(0xffffffffu, (word & ~0xFFFFFFFFull) == kLbPrefix);
+      const int first = pre ? __ffs(pre) - 1 : 31;  // nearest predecessor holding a prefix
+      uint32_t v = lane <= first ? static_cast<uint32_t>(word & 0xFFFFFFFFull) : 0u;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      excl += v;
+      if (pre) break;
+    }
+    if (lane == 0) {
+      if (vb > 0) atomicExch(&status[vb], kLbPrefix | (excl + btot));
+      s_boff = excl;
+      if (vb == gridDim.x - 1) *total = excl + btot;
+    }
+  }
+  __syncthreads();
+  uint32_t wbeg = s_boff;
+  for (int w = 0; w < warp; ++w) wbeg += s_wtot[w];
+  const uint32_t wend = wbeg + wtot;
+  // emit, in the same (Gaussian, row) order as the count
+  uint32_t carry = 0;
+  for (int r0 = 0; r0 < R; r0 += 32) {
+    const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
+    int a, b;
+    const uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
+    const uint32_t sc = warp_incl_scan(fr, lane);
+    const uint32_t o = wbeg + carry + sc - fr;
+    if (fr && o < capacity)
+      emit_free(sat, a, b, jb.g, out_key, out_val, o, min(min(o + fr, wend), capacity));
+    carry += __shfl_sync(0xffffffffu, sc, 31);
+  }
+  if (lane == 0 && wbeg + carry != wend) atomicAdd(&counters[kBinningMismatch], 1ull);
+}
+
 // [start, end) of every tile's run in the tile-sorted list.
 __global__ void ranges_kernel(int64_t n_entries, const uint32_t* __restrict__ key,
                               uint2* __restrict__ ranges) {
@@ -584,6 +686,29 @@ cudaError_t launch_emit(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* 
       p0, n_pos, n, views, sorted_val, offsets, chunk_cnt, cnt, foot, sat, out_key, out_val,
       counters);
   return cudaGetLastError();
+}
+
+cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
+                             const uint32_t* sorted_val, const uint32_t* cnt,
+                             const Footprint* foot, const uint64_t* sat, uint32_t* out_key,
+                             uint32_t* out_val, uint32_t capacity, void* lookback,
+                             uint32_t* total, unsigned long long* counters, cudaStream_t stream) {
+  if (n_pos <= 0) return cudaMemsetAsync(total, 0, sizeof(uint32_t), stream);
+  const int threads = 256;
+  const int64_t blocks = (n_pos + threads - 1) / threads;
+  uint32_t* ticket = static_cast<uint32_t*>(lookback);
+  unsigned long long* status = reinterpret_cast<unsigned long long*>(
+      static_cast<char*>(lookback) + 256);
+  cudaError_t e = cudaMemsetAsync(lookback, 0, 256 + static_cast<size_t>(blocks) * 8, stream);
+  if (e != cudaSuccess) return e;
+  bin_fused_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
+      p0, n_pos, n, views, sorted_val, cnt, foot, sat, out_key, out_val, capacity, status, ticket,
+      total, counters);
+  return cudaGetLastError();
+}
+
+size_t bin_fused_temp_bytes(int64_t n_pos) {
+  return 256 + static_cast<size_t>((n_pos + 255) / 256) * 8;
 }
 
 cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
