@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="flashsplat", choices=["flashsplat", "reference"])
     ap.add_argument("--views-per-batch", type=int, default=0)
+    ap.add_argument("--depth-chunks", type=int, default=0)
     ap.add_argument("--views", type=int, default=100)
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -171,7 +172,8 @@ def run_flashsplat(args, rank, world, local_rank):
                      "scale": torch.from_numpy(r["scale"]).to(torch.bfloat16),
                      "opacity": torch.from_numpy(r["opacity"]).to(torch.float16)}
     solver = fsb.Solver(gaussians, device=local_rank, views_per_batch=args.views_per_batch,
-                        time_stages=True, recheck_margin=args.recheck_margin,
+                        depth_chunks=args.depth_chunks, time_stages=True,
+                        recheck_margin=args.recheck_margin,
                         record_precision=fsb.FS_F16 if args.precision == "fp16" else 0)
     dmasks = solver.upload_masks(w.masks)
     stream = torch.cuda.current_stream(dev)

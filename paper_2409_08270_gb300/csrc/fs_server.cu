@@ -50,7 +50,7 @@ struct SceneEntry {
   fs_scene* scene = nullptr;
   int64_t n = 0;
   bool tuned = false;
-  int views_per_batch = 16, depth_chunks = 4;
+  int views_per_batch = 32, depth_chunks = 5;
   std::mutex tune_mu;
 };
 
@@ -125,7 +125,7 @@ fs_status solve_request(fs_server* s, int slot, const SceneEntry& se, Request* r
 // The first request of a scene (autotune on): time a few batching settings
 // on a sample of its views and keep the fastest for the scene.
 void tune_scene(fs_server* s, int slot, SceneEntry& se, Request* r) {
-  static const int cand[][2] = {{16, 4}, {8, 4}, {32, 4}, {16, 2}, {16, 6}};
+  static const int cand[][2] = {{32, 5}, {16, 4}, {32, 4}, {16, 6}, {32, 3}};
   const int32_t V = static_cast<int32_t>(std::min<size_t>(r->cams.size(), 32));
   double best = 1e300;
   fs_stats st{};

@@ -127,4 +127,4 @@ def test_autotune_keeps_results(fsb):
     for r in b:
         _same(a, r)
         assert (r["info"].views_per_batch, r["info"].depth_chunks) in \
-            {(16, 4), (8, 4), (32, 4), (16, 2), (16, 6)}
+            {(32, 5), (16, 4), (32, 4), (16, 6), (32, 3)}
