@@ -226,18 +226,15 @@ __global__ void __launch_bounds__(32) blend_kernel(
       ok_ = pos_op[g - gbase].w;
       qc = fmaxf(log2f(255.f * ok_), 0.f) * 1.001f + 1e-3f;
     } else if (lane < nin) {
-      // b = W o + c for the sub-tile centre o (W = W_hi + W_lo, c: float pairs)
+      // b = W (o - m) for the sub-tile centre o: o - m_hi is exact whenever
+      // the mean lies within a factor of two of o (and off by far less than
+      // a pixel's 1e-7 otherwise); W = W_hi + W_lo
       g = list_val[base + lane];
       const ProjRecord r = rec[g];
-      f2 b0 = f2_add(two_prod(r.w_hi.x, ox), two_prod(r.w_hi.y, oy));
-      f2 b1 = f2_add(two_prod(r.w_hi.z, ox), two_prod(r.w_hi.w, oy));
-      b0 = f2_add(b0, f2{r.c.x, r.c.z});
-      b1 = f2_add(b1, f2{r.c.y, r.c.w});
-      b0 = f2_add(b0, f2_from(fmaf(r.w_lo.x, ox, r.w_lo.y * oy)));
-      b1 = f2_add(b1, f2_from(fmaf(r.w_lo.z, ox, r.w_lo.w * oy)));
+      const float dx = (ox - r.m.x) - r.m.z, dy = (oy - r.m.y) - r.m.w;
       wk = r.w_hi;
-      b0f = b0.hi + b0.lo;
-      b1f = b1.hi + b1.lo;
+      b0f = fmaf(wk.x, dx, fmaf(wk.y, dy, fmaf(r.w_lo.x, dx, r.w_lo.y * dy)));
+      b1f = fmaf(wk.z, dx, fmaf(wk.w, dy, fmaf(r.w_lo.z, dx, r.w_lo.w * dy)));
       ok_ = r.misc.x;
       qc = r.misc.y;
     }

@@ -42,15 +42,16 @@ struct ViewParams {
 // Projected record of one (view, Gaussian): 4 x float4 = 64 B.
 //   w_hi, w_lo = whitening matrix W (row-major 2x2) as float pairs, with
 //                |W d|^2 = 0.5 log2(e) d^T Sigma2D^-1 d
-//   c          = (c0_hi, c1_hi, c0_lo, c1_lo), c = -W m2D as float pairs
+//   m          = (mx_hi, my_hi, mx_lo, my_lo): the projected mean as float pairs
 //   misc       = (opacity, q_cut, -, -), q_cut ~ log2(255 o): alpha = o 2^-|w|^2
 //                reaches 1/255 at |w|^2 = log2(255 o) (stored slightly widened)
-// For a sub-tile whose centre is o the blend forms b = W o + c (float pairs)
-// and evaluates w = W_hi (p - o) + b for the pixel centre p, |p - o| <= 5 px.
+// For a sub-tile whose centre is o the blend forms b = W (o - m) in FP32 (o - m
+// is exact or nearly so) and evaluates w = W_hi (p - o) + b for the pixel
+// centre p, |p - o| <= 5 px.
 struct alignas(16) ProjRecord {
   float4 w_hi;
   float4 w_lo;
-  float4 c;
+  float4 m;
   float4 misc;
 };
 

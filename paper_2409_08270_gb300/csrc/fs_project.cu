@@ -8,8 +8,8 @@
 //   Sigma2D = (J W) Sigma3D (J W)^T + 0.3 I,   W = camera rotation
 //   Sigma2D = lambda1 e e^T + lambda2 e' e'^T  (lambda2 = det / lambda1)
 // The record stores the whitening matrix W_ws = sqrt(0.5 log2 e)
-// diag(lambda1, lambda2)^-1/2 [e e']^T as a float pair (hi, lo) and
-// c = -W_ws m2D, so alpha = o 2^-|W_ws (p - m2D)|^2.  Carrying the eigenvectors
+// diag(lambda1, lambda2)^-1/2 [e e']^T and the mean m2D as float pairs (hi,
+// lo), so alpha = o 2^-|W_ws (p - m2D)|^2.  Carrying the eigenvectors
 // to ~1e-14 keeps thin ("needle") Gaussians correctly oriented: an FP32
 // orientation error of 1e-7 rad moves alpha at the tip of a 4500:1 Gaussian
 // by ~1e-4.  Sigma3D = R(q) diag(s^2) R(q)^T is formed once per scene in FP64
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256, 4) project_kernel(
     uint32_t count = 0;
     float depth = 0.f, depth_l = 0.f;
     ProjRecord R;
-    R.w_hi = R.w_lo = R.c = make_float4(0.f, 0.f, 0.f, 0.f);
+    R.w_hi = R.w_lo = R.m = make_float4(0.f, 0.f, 0.f, 0.f);
     CompactRecord R16 = {0.f, 0.f, 0u, 0u};
     // misc.y: |w|^2 at which alpha falls to 1/255, log2(255 o), widened by
     // 0.1% + 1e-3 so the blend's sub-tile test stays conservative in FP32
@@ -238,11 +238,9 @@ __global__ void __launch_bounds__(256, 4) project_kernel(
       const f2 k2 = f2_sqrt(f2_div(hl, lam2));
       const f2 W00 = f2_mul(ex, k1), W01 = f2_mul(ey, k1);
       const f2 W10 = f2_mul(f2_neg(ey), k2), W11 = f2_mul(ex, k2);
-      const f2 c0 = f2_neg(f2_add(f2_mul(W00, mx), f2_mul(W01, my)));
-      const f2 c1 = f2_neg(f2_add(f2_mul(W10, mx), f2_mul(W11, my)));
       R.w_hi = make_float4(W00.hi, W01.hi, W10.hi, W11.hi);
       R.w_lo = make_float4(W00.lo, W01.lo, W10.lo, W11.lo);
-      R.c = make_float4(c0.hi, c1.hi, c0.lo, c1.lo);
+      R.m = make_float4(mx.hi, my.hi, mx.lo, my.lo);
       if (rec16) {
         R16.mx = mx.hi;  // the float pair is normalised: hi is the FP32 rounding
         R16.my = my.hi;

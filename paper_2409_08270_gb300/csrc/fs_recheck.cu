@@ -20,7 +20,7 @@
 // exact stop decisions differ there) is reported so the caller redoes the
 // batch with the dedicated binning.
 //
-// alpha = o 2^-|W p + c|^2 from the float-pair whitening record of the
+// alpha = o 2^-|W (p - m)|^2 from the float-pair whitening record of the
 // projection; 2^-q follows Tang's table-driven method (ACM TOMS 15(2), 1989):
 // a 64-entry table of 2^(-j/64) (computed in FP64) times a degree-4 Taylor
 // polynomial of e^-x on the remaining [0, ln2/64).
@@ -185,7 +185,7 @@ __device__ __forceinline__ f2 f2_exp2_neg(f2 q, const float2* __restrict__ tab) 
   return {e.hi * sc, e.lo * sc};
 }
 
-// Staged list entry: W (float pairs), b = W ctr + c relative to the tile
+// Staged list entry: W (float pairs), b = W (ctr - m) relative to the tile
 // centre (float pairs), opacity, q_cut + slack, re-check row (-1: none).
 struct Staged {
   f2 w[4];
@@ -200,8 +200,11 @@ __device__ __forceinline__ Staged stage_entry(const ProjRecord& r, float cx, flo
   st.w[1] = {r.w_hi.y, r.w_lo.y};
   st.w[2] = {r.w_hi.z, r.w_lo.z};
   st.w[3] = {r.w_hi.w, r.w_lo.w};
-  st.b[0] = f2_add(f2_add(f2_mul_f(st.w[0], cx), f2_mul_f(st.w[1], cy)), f2{r.c.x, r.c.z});
-  st.b[1] = f2_add(f2_add(f2_mul_f(st.w[2], cx), f2_mul_f(st.w[3], cy)), f2{r.c.y, r.c.w});
+  // b = W (ctr - m) with the difference of the centre and the float-pair mean
+  const f2 dx = f2_sub(f2_from(cx), f2{r.m.x, r.m.z});
+  const f2 dy = f2_sub(f2_from(cy), f2{r.m.y, r.m.w});
+  st.b[0] = f2_add(f2_mul(st.w[0], dx), f2_mul(st.w[1], dy));
+  st.b[1] = f2_add(f2_mul(st.w[2], dx), f2_mul(st.w[3], dy));
   st.o = r.misc.x;
   // near the cut the FP32 screen |W_hi l + b_hi|^2 is off by far less than 0.05
   st.qc = r.misc.y + 0.05f;
