@@ -149,7 +149,7 @@ int64_t scan_launches(int64_t n) { return n > 0 ? 3 : 0; }
 int64_t radix_launches(int64_t n, int bits) {
   if (n <= 1 || bits <= 0) return 0;
   const int64_t nb = (n + 4095) / 4096;
-  return static_cast<int64_t>((bits + 7) / 8) * (2 + scan_launches(nb * 256));
+  return static_cast<int64_t>(fs::radix_passes(bits)) * (2 + scan_launches(nb * 512));
 }
 
 }  // namespace

@@ -23,6 +23,8 @@ size_t scan_temp_bytes(int64_t n);
 // out[k] = sum_{j<k} in[gather ? gather[j] : j]; *total = the full sum (device).
 cudaError_t exclusive_scan(const uint32_t* in, const uint32_t* gather, uint32_t* out, int64_t n,
                            uint32_t* total, void* temp, cudaStream_t stream);
+// Passes radix_sort_pairs makes for a `bits`-bit key (8- or 9-bit digits).
+int radix_passes(int bits);
 // Temporary storage of radix_sort_pairs for n elements (bytes).
 size_t radix_temp_bytes(int64_t n);
 // Stable LSD radix sort of (key, val) pairs on the low `bits` bits of

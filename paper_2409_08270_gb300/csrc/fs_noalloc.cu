@@ -35,7 +35,7 @@ constexpr int64_t kNA_N = FS_NOALLOC_MAX_GAUSSIANS;
 constexpr int kNA_Side = FS_NOALLOC_MAX_SIDE;
 constexpr int64_t kNA_Entries = FS_NOALLOC_MAX_LIST_ENTRIES;
 constexpr int kNA_Tiles = (kNA_Side / kTile) * (kNA_Side / kTile);
-constexpr size_t kNA_SortTmp = 256 * 1024;  // >= radix_temp_bytes(kNA_Entries), checked at run time
+constexpr size_t kNA_SortTmp = 512 * 1024;  // >= radix_temp_bytes(kNA_Entries), checked at run time
 constexpr size_t kNA_ScanTmp = 4 * 1024;    // >= scan_temp_bytes(kNA_N), checked at run time
 
 constexpr size_t al(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }

@@ -15,7 +15,6 @@ constexpr int kThreads = 256;
 constexpr int kRounds = 16;
 constexpr int kTileElems = kThreads * kRounds;
 constexpr int kWarps = kThreads / 32;
-constexpr int kRadix = 256;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -112,27 +111,43 @@ __global__ void __launch_bounds__(kThreads) scan_down_kernel(const uint32_t* __r
 
 // Digits are taken from min(key - kmin, span): a key range [kmin, kmin + span)
 // (and everything above it mapped to span) needs only the bits of span.
+// A pass takes DB bits (8 or 9: a 17-bit tile key sorts in two passes).
+template <int DB>
 __device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t kmin, uint32_t span,
                                              int shift) {
-  return (min(key - kmin, span) >> shift) & 0xFFu;
+  return (min(key - kmin, span) >> shift) & ((1u << DB) - 1u);
 }
 
+template <int DB>
 __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint32_t* __restrict__ keys,
                                                               int64_t n, int shift, int64_t nb,
                                                               uint32_t kmin, uint32_t span,
                                                               uint32_t* __restrict__ hist) {
-  __shared__ uint32_t s_h[kRadix];
-  s_h[threadIdx.x] = 0;
+  constexpr int kRad = 1 << DB;
+  __shared__ uint32_t s_h[kRad];
+  for (int d = threadIdx.x; d < kRad; d += kThreads) s_h[d] = 0;
   __syncthreads();
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTileElems;
 #pragma unroll 4
   for (int r = 0; r < kRounds; ++r) {
     const int64_t j = base + r * kThreads + threadIdx.x;
-    if (j < n) atomicAdd(&s_h[digit_of(keys[j], kmin, span, shift)], 1u);
+    if (j < n) atomicAdd(&s_h[digit_of<DB>(keys[j], kmin, span, shift)], 1u);
   }
   __syncthreads();
-  hist[static_cast<int64_t>(threadIdx.x) * nb + blockIdx.x] = s_h[threadIdx.x];
+  for (int d = threadIdx.x; d < kRad; d += kThreads)
+    hist[static_cast<int64_t>(d) * nb + blockIdx.x] = s_h[d];
 }
+
+// Shared memory of one scatter block (dynamic: the 9-bit form needs 52 KB).
+template <int DB>
+struct ScatterSmem {
+  uint32_t key[kTileElems];
+  uint32_t val[kTileElems];
+  uint32_t wcnt[kWarps][1 << DB];  // per-warp digit counts, then warp prefixes
+  uint32_t loc[1 << DB];           // local start of each digit's run
+  uint32_t glob[1 << DB];          // global start of this block's run per digit
+  uint32_t warp_sums[kWarps];
+};
 
 // Stable scatter of one radix pass.  Each warp ranks its 512 elements (16
 // coalesced columns of 32) by digit with a warp match per column and per-warp
@@ -140,22 +155,21 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint32_t* __
 // turns (digit, warp) counts into local offsets, places its 4096 elements
 // digit-sorted in shared memory and writes each digit's run to its global
 // offset with consecutive threads on consecutive addresses.
+template <int DB>
 __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
     const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n, int shift,
     int64_t nb, uint32_t kmin, uint32_t span, const uint32_t* __restrict__ hist_pre,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
-  __shared__ uint32_t s_key[kTileElems];
-  __shared__ uint32_t s_val[kTileElems];
-  __shared__ uint32_t s_wcnt[kWarps][kRadix];  // per-warp digit counts, then warp prefixes
-  __shared__ uint32_t s_loc[kRadix];           // local start of each digit's run
-  __shared__ uint32_t s_glob[kRadix];          // global start of this block's run per digit
-  __shared__ uint32_t s_warp[kWarps];
+  constexpr int kRad = 1 << DB;
+  constexpr int kPer = kRad / kThreads;  // digits per thread in the block-wide steps
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ScatterSmem<DB>& S = *reinterpret_cast<ScatterSmem<DB>*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTileElems;
   const int n_here = static_cast<int>(min(static_cast<int64_t>(kTileElems), n - base));
   const int wbase = warp * (kTileElems / kWarps);  // 512 elements per warp
 #pragma unroll
-  for (int k = 0; k < kRadix / 32; ++k) s_wcnt[warp][lane + 32 * k] = 0;
+  for (int k = 0; k < kRad / 32; ++k) S.wcnt[warp][lane + 32 * k] = 0;
   __syncwarp();
 
   const uint32_t lt = lanemask_lt();
@@ -165,47 +179,65 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
     const int j = wbase + i * 32 + lane;
     const bool ok = j < n_here;
     key[i] = ok ? keys[base + j] : 0u;
-    const uint32_t d = ok ? digit_of(key[i], kmin, span, shift) : 0x100u;
+    const uint32_t d = ok ? digit_of<DB>(key[i], kmin, span, shift) : static_cast<uint32_t>(kRad);
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t before = ok ? s_wcnt[warp][d] : 0u;
+    const uint32_t before = ok ? S.wcnt[warp][d] : 0u;
     rank[i] = before + __popc(peers & lt);
     __syncwarp();
-    if (ok && (peers & lt) == 0) s_wcnt[warp][d] = before + __popc(peers);
+    if (ok && (peers & lt) == 0) S.wcnt[warp][d] = before + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  // per digit (thread t): warp prefixes, then the block-wide digit offsets
-  uint32_t running = 0;
+  // per digit (thread t holds digits t * kPer .. t * kPer + kPer - 1): warp
+  // prefixes, then the block-wide digit offsets
+  uint32_t running[kPer], own = 0;
 #pragma unroll
-  for (int w = 0; w < kWarps; ++w) {
-    const uint32_t c = s_wcnt[w][threadIdx.x];
-    s_wcnt[w][threadIdx.x] = running;
-    running += c;
+  for (int q = 0; q < kPer; ++q) {
+    const int d = threadIdx.x * kPer + q;
+    running[q] = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = S.wcnt[w][d];
+      S.wcnt[w][d] = running[q];
+      running[q] += c;
+    }
+    own += running[q];
   }
   uint32_t tot;
-  s_loc[threadIdx.x] = block_exclusive_scan(running, s_warp, &tot);
-  s_glob[threadIdx.x] = hist_pre[static_cast<int64_t>(threadIdx.x) * nb + blockIdx.x];
+  uint32_t ex = block_exclusive_scan(own, S.warp_sums, &tot);
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int d = threadIdx.x * kPer + q;
+    S.loc[d] = ex;
+    ex += running[q];
+    S.glob[d] = hist_pre[static_cast<int64_t>(d) * nb + blockIdx.x];
+  }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < kRounds; ++i) {
     const int j = wbase + i * 32 + lane;
     if (j < n_here) {
-      const uint32_t d = digit_of(key[i], kmin, span, shift);
-      const uint32_t pos = s_loc[d] + s_wcnt[warp][d] + rank[i];
-      s_key[pos] = key[i];
-      s_val[pos] = vals[base + j];
+      const uint32_t d = digit_of<DB>(key[i], kmin, span, shift);
+      const uint32_t pos = S.loc[d] + S.wcnt[warp][d] + rank[i];
+      S.key[pos] = key[i];
+      S.val[pos] = vals[base + j];
     }
   }
   __syncthreads();
   // coalesced write-out of the digit runs
   for (int j = threadIdx.x; j < n_here; j += kThreads) {
-    const uint32_t k = s_key[j];
-    const uint32_t d = digit_of(k, kmin, span, shift);
-    const uint32_t dst = s_glob[d] + (static_cast<uint32_t>(j) - s_loc[d]);
+    const uint32_t k = S.key[j];
+    const uint32_t d = digit_of<DB>(k, kmin, span, shift);
+    const uint32_t dst = S.glob[d] + (static_cast<uint32_t>(j) - S.loc[d]);
     keys_out[dst] = k;
-    vals_out[dst] = s_val[j];
+    vals_out[dst] = S.val[j];
   }
 }
+
+template <int DB>
+cudaError_t radix_pass(const uint32_t* src_k, const uint32_t* src_v, uint32_t* dst_k,
+                       uint32_t* dst_v, int64_t n, int shift, int64_t nb, uint32_t kmin,
+                       uint32_t span, uint32_t* hist, void* scan_tmp, cudaStream_t stream);
 
 inline int64_t tiles_of(int64_t n) { return (n + kTileElems - 1) / kTileElems; }
 
@@ -231,8 +263,40 @@ cudaError_t exclusive_scan(const uint32_t* in, const uint32_t* gather, uint32_t*
 
 size_t radix_temp_bytes(int64_t n) {
   const int64_t nb = tiles_of(n);
-  const int64_t hist = nb * kRadix;
+  const int64_t hist = nb * 512;  // the widest digit
   return static_cast<size_t>(hist) * sizeof(uint32_t) + scan_temp_bytes(hist) + 256;
+}
+
+namespace {
+
+template <int DB>
+cudaError_t radix_pass(const uint32_t* src_k, const uint32_t* src_v, uint32_t* dst_k,
+                       uint32_t* dst_v, int64_t n, int shift, int64_t nb, uint32_t kmin,
+                       uint32_t span, uint32_t* hist, void* scan_tmp, cudaStream_t stream) {
+  constexpr int kRad = 1 << DB;
+  const size_t smem = sizeof(ScatterSmem<DB>);
+  static bool attr_set = false;  // dynamic shared memory above 48 KB needs the opt-in
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(radix_scatter_kernel<DB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  radix_hist_kernel<DB><<<static_cast<unsigned>(nb), kThreads, 0, stream>>>(src_k, n, shift, nb,
+                                                                              kmin, span, hist);
+  cudaError_t e = exclusive_scan(hist, nullptr, hist, nb * kRad, nullptr, scan_tmp, stream);
+  if (e != cudaSuccess) return e;
+  radix_scatter_kernel<DB><<<static_cast<unsigned>(nb), kThreads, smem, stream>>>(
+      src_k, src_v, n, shift, nb, kmin, span, hist, dst_k, dst_v);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int radix_passes(int bits) {
+  if (bits <= 0) return 0;
+  return (bits + 8) / 9 < (bits + 7) / 8 ? (bits + 8) / 9 : (bits + 7) / 8;
 }
 
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
@@ -243,15 +307,21 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
   const int64_t nb = tiles_of(n);
   uint32_t* hist = static_cast<uint32_t*>(temp);
   void* scan_tmp = reinterpret_cast<char*>(temp) +
-                   ((static_cast<size_t>(nb) * kRadix * sizeof(uint32_t) + 255) / 256) * 256;
+                   ((static_cast<size_t>(nb) * 512 * sizeof(uint32_t) + 255) / 256) * 256;
+  // digit widths: 8 bits, or 9 where that saves a whole pass (17 -> 9 + 8)
+  const int passes = radix_passes(bits);
+  int wide = bits - 8 * passes;  // passes that take 9 bits
+  if (wide < 0) wide = 0;
   uint32_t *src_k = keys, *src_v = vals, *dst_k = keys_alt, *dst_v = vals_alt;
-  for (int shift = 0; shift < bits; shift += 8) {
-    radix_hist_kernel<<<static_cast<unsigned>(nb), kThreads, 0, stream>>>(src_k, n, shift, nb,
-                                                                          kmin, span, hist);
-    cudaError_t e = exclusive_scan(hist, nullptr, hist, nb * kRadix, nullptr, scan_tmp, stream);
+  int shift = 0;
+  for (int p = 0; p < passes; ++p) {
+    const bool nine = p < wide;
+    cudaError_t e = nine ? radix_pass<9>(src_k, src_v, dst_k, dst_v, n, shift, nb, kmin, span,
+                                         hist, scan_tmp, stream)
+                         : radix_pass<8>(src_k, src_v, dst_k, dst_v, n, shift, nb, kmin, span,
+                                         hist, scan_tmp, stream);
     if (e != cudaSuccess) return e;
-    radix_scatter_kernel<<<static_cast<unsigned>(nb), kThreads, 0, stream>>>(
-        src_k, src_v, n, shift, nb, kmin, span, hist, dst_k, dst_v);
+    shift += nine ? 9 : 8;
     uint32_t* tk = src_k;
     uint32_t* tv = src_v;
     src_k = dst_k;
