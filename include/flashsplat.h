@@ -74,9 +74,9 @@ typedef struct fs_scene fs_scene;
 
 /* Context options.  Zero-initialise and set what you need; 0 = default. */
 typedef struct fs_options {
-  int32_t views_per_batch;  /* views binned and blended per launch group (default 32) */
+  int32_t views_per_batch;  /* views binned and blended per launch group (default 50, at most 64) */
   int32_t time_stages;      /* non-zero: time every blend launch with CUDA events */
-  int32_t depth_chunks;     /* front-to-back binning chunks per batch (default 5, 1 = off) */
+  int32_t depth_chunks;     /* front-to-back binning chunks per batch (default 6, 1 = off) */
   /* fs_solve re-evaluates in FP64 every Gaussian whose FP32 decision margin
    * (see fs_assign) is below this value (default 1e-4 when 0; negative = off).
    * The FP32 table's entries are within ~1e-5 relative of exact, which moves

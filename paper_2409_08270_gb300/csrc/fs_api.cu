@@ -160,8 +160,8 @@ void fs::set_last_error(const char* msg) {
 
 struct fs_ctx {
   int device = 0;
-  int views_per_batch = 32;
-  int depth_chunks = 5;  // front-to-back chunks per batch (sizes 1/16, 1/16, 1/8, 1/4, 1/2)
+  int views_per_batch = 50;
+  int depth_chunks = 6;  // front-to-back chunks per batch (sizes 1/32, 1/32, 1/16, ..., 1/2)
   int n_sm = 0;
   bool time_stages = false;
   std::vector<cudaEvent_t> events;  // (start, stop) pairs around blend launches

@@ -9,7 +9,7 @@ struct fs_ctx;
 
 namespace fs {
 
-constexpr int kMaxViewsPerBatch = 32;
+constexpr int kMaxViewsPerBatch = 64;
 constexpr int kMaxLabels = 4096;
 
 struct ViewParams;

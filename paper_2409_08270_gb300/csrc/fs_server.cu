@@ -50,7 +50,7 @@ struct SceneEntry {
   fs_scene* scene = nullptr;
   int64_t n = 0;
   bool tuned = false;
-  int views_per_batch = 32, depth_chunks = 5;
+  int views_per_batch = 50, depth_chunks = 6;
   std::mutex tune_mu;
 };
 
@@ -125,7 +125,7 @@ fs_status solve_request(fs_server* s, int slot, const SceneEntry& se, Request* r
 // The first request of a scene (autotune on): time a few batching settings
 // on a sample of its views and keep the fastest for the scene.
 void tune_scene(fs_server* s, int slot, SceneEntry& se, Request* r) {
-  static const int cand[][2] = {{32, 5}, {16, 4}, {32, 4}, {16, 6}, {32, 3}};
+  static const int cand[][2] = {{50, 6}, {32, 5}, {64, 6}, {16, 4}, {50, 4}};
   const int32_t V = static_cast<int32_t>(std::min<size_t>(r->cams.size(), 32));
   double best = 1e300;
   fs_stats st{};
@@ -278,7 +278,7 @@ fs_status fs_server_submit(fs_server* s, int32_t scene_id, const fs_camera* cams
     const SceneEntry& e = *s->scenes[static_cast<size_t>(scene_id)];
     n = e.n;
     // before its scene is tuned a request may run with the largest batch
-    vb = (s->autotune && !e.tuned) ? 32 : e.views_per_batch;
+    vb = (s->autotune && !e.tuned) ? 64 : e.views_per_batch;
   }
   std::unique_ptr<Request> r(new Request());
   r->scene = scene_id;

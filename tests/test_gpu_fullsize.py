@@ -1,5 +1,5 @@
 """Full-size workloads through the C ABI, in the benchmark's launch
-configuration (32 views per batch, 5 depth chunks, near-tie re-check on),
+configuration (50 views per batch, 6 depth chunks, near-tie re-check on),
 checked on sampled Gaussians against the oracle and on properties that hold
 at any size.
 

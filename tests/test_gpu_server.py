@@ -127,4 +127,4 @@ def test_autotune_keeps_results(fsb):
     for r in b:
         _same(a, r)
         assert (r["info"].views_per_batch, r["info"].depth_chunks) in \
-            {(32, 5), (16, 4), (32, 4), (16, 6), (32, 3)}
+            {(50, 6), (32, 5), (64, 6), (16, 4), (50, 4)}
