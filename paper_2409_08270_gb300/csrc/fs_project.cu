@@ -543,9 +543,29 @@ __global__ void __launch_bounds__(256) bin_fused_kernel(
   lane_rows(j, n_pos, p0, sorted_val, cnt, foot, &g, &ty0, &nrows);
   const uint32_t incl = warp_incl_scan(nrows, lane);
   const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
-  // count
+  // count; the first kStash rounds' jobs are kept in registers for the emission
+  constexpr int kStash = 4;
+  int st_a[kStash], st_b[kStash];
+  uint32_t st_fr[kStash], st_g[kStash];
   uint32_t wtot = 0;
-  for (int r0 = 0; r0 < R; r0 += 32) {
+#pragma unroll
+  for (int k = 0; k < kStash; ++k) {
+    st_a[k] = 0;
+    st_b[k] = -1;
+    st_fr[k] = 0;
+    st_g[k] = 0;
+    if (32 * k < R) {  // R is the same for the whole warp
+      const RowJob jb = row_job(32 * k + lane, R, incl, g, ty0);
+      const uint32_t fr = job_free(jb, n, views, foot, sat, &st_a[k], &st_b[k]);
+      st_fr[k] = fr;
+      st_g[k] = jb.g;
+      uint32_t sum = fr;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      wtot += sum;
+    }
+  }
+  for (int r0 = 32 * kStash; r0 < R; r0 += 32) {
     const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
     int a, b;
     uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
@@ -599,7 +619,19 @@ __global__ void __launch_bounds__(256) bin_fused_kernel(
   const uint32_t wend = wbeg + wtot;
   // emit, in the same (Gaussian, row) order as the count
   uint32_t carry = 0;
-  for (int r0 = 0; r0 < R; r0 += 32) {
+#pragma unroll
+  for (int k = 0; k < kStash; ++k) {
+    if (32 * k < R) {
+      const uint32_t fr = st_fr[k];
+      const uint32_t sc = warp_incl_scan(fr, lane);
+      const uint32_t o = wbeg + carry + sc - fr;
+      if (fr && o < capacity)
+        emit_free(sat, st_a[k], st_b[k], st_g[k], out_key, out_val, o,
+                  min(min(o + fr, wend), capacity));
+      carry += __shfl_sync(0xffffffffu, sc, 31);
+    }
+  }
+  for (int r0 = 32 * kStash; r0 < R; r0 += 32) {
     const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
     int a, b;
     const uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
