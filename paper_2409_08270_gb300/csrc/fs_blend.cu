@@ -180,13 +180,19 @@ __global__ void __launch_bounds__(32) blend_kernel(
   const bool minor = valid0 && valid1 && lab1 != lab0;
   const float w0 = valid0 ? 1.f : 0.f;
   const float w1 = (valid1 && !minor) ? 1.f : 0.f;
-  // lane positions ordered by main label (labelless lanes last)
+  // lane positions ordered by main label (labelless lanes last): lanes with a
+  // smaller label, then lanes of the same label before this one -- one ballot
+  // per distinct label of the warp (usually one or two)
   const int mkey = main_lab >= 0 ? main_lab : 0x7FFFFFFF;
+  const uint32_t lt_lanes = lanemask_lt();
   int pos = 0;
-#pragma unroll
-  for (int l = 0; l < 32; ++l) {
-    const int k = __shfl_sync(0xffffffffu, mkey, l);
-    pos += (k < mkey || (k == mkey && l < lane)) ? 1 : 0;
+  for (uint32_t rem = 0xffffffffu; rem;) {
+    const int lead = __ffs(rem) - 1;
+    const int k = __shfl_sync(0xffffffffu, mkey, lead);
+    const uint32_t grp = __ballot_sync(0xffffffffu, mkey == k);
+    rem &= ~grp;
+    if (k < mkey) pos += __popc(grp);
+    if (k == mkey) pos += __popc(grp & lt_lanes);
   }
   S.poslab[pos] = mkey;
   const uint32_t minor_lanes = __ballot_sync(0xffffffffu, minor);
