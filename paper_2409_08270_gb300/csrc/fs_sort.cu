@@ -174,13 +174,27 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
 
   const uint32_t lt = lanemask_lt();
   uint32_t key[kRounds], rank[kRounds];
+  // all of the warp's key loads in flight at once (the ranking below has
+  // warp barriers, which no load is moved across)
+#pragma unroll
+  for (int i = 0; i < kRounds; ++i) {
+    const int j = wbase + i * 32 + lane;
+    key[i] = j < n_here ? keys[base + j] : 0u;
+  }
 #pragma unroll
   for (int i = 0; i < kRounds; ++i) {
     const int j = wbase + i * 32 + lane;
     const bool ok = j < n_here;
-    key[i] = ok ? keys[base + j] : 0u;
     const uint32_t d = ok ? digit_of<DB>(key[i], kmin, span, shift) : static_cast<uint32_t>(kRad);
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    // lanes holding the same digit: one ballot per digit bit
+    uint32_t peers = __ballot_sync(0xffffffffu, ok);
+    if (!ok) peers = ~peers;
+#pragma unroll
+    for (int b = 0; b < DB; ++b) {
+      const bool bit = (d >> b) & 1u;
+      const uint32_t bb = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bb : ~bb;
+    }
     const uint32_t before = ok ? S.wcnt[warp][d] : 0u;
     rank[i] = before + __popc(peers & lt);
     __syncwarp();
