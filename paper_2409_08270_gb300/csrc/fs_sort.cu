@@ -239,12 +239,16 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
   }
   __syncthreads();
   // coalesced write-out of the digit runs
-  for (int j = threadIdx.x; j < n_here; j += kThreads) {
-    const uint32_t k = S.key[j];
-    const uint32_t d = digit_of<DB>(k, kmin, span, shift);
-    const uint32_t dst = S.glob[d] + (static_cast<uint32_t>(j) - S.loc[d]);
-    keys_out[dst] = k;
-    vals_out[dst] = S.val[j];
+#pragma unroll
+  for (int i = 0; i < kRounds; ++i) {
+    const int j = i * kThreads + threadIdx.x;
+    if (j < n_here) {
+      const uint32_t k = S.key[j];
+      const uint32_t d = digit_of<DB>(k, kmin, span, shift);
+      const uint32_t dst = S.glob[d] + (static_cast<uint32_t>(j) - S.loc[d]);
+      keys_out[dst] = k;
+      vals_out[dst] = S.val[j];
+    }
   }
 }
 
