@@ -128,10 +128,17 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint32_t* __
   for (int d = threadIdx.x; d < kRad; d += kThreads) s_h[d] = 0;
   __syncthreads();
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTileElems;
-#pragma unroll 4
+  // all of the thread's loads in flight before the first count
+  uint32_t key[kRounds];
+#pragma unroll
   for (int r = 0; r < kRounds; ++r) {
     const int64_t j = base + r * kThreads + threadIdx.x;
-    if (j < n) atomicAdd(&s_h[digit_of<DB>(keys[j], kmin, span, shift)], 1u);
+    key[r] = j < n ? keys[j] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const int64_t j = base + r * kThreads + threadIdx.x;
+    if (j < n) atomicAdd(&s_h[digit_of<DB>(key[r], kmin, span, shift)], 1u);
   }
   __syncthreads();
   for (int d = threadIdx.x; d < kRad; d += kThreads)
