@@ -22,6 +22,19 @@ constexpr double kHalfLog2e = 0.72134752044448170368;
 constexpr float kHalfLog2eHi = static_cast<float>(kHalfLog2e);
 constexpr float kHalfLog2eLo = static_cast<float>(kHalfLog2e - static_cast<double>(kHalfLog2eHi));
 
+// Slot ids are view * n + Gaussian index.  The view of a slot by a multiply:
+// with m = floor((2^32 - 1) / n), umulhi(g, m) is floor(g / n) or one less.
+struct SlotView {
+  uint32_t n, m;
+  __device__ __forceinline__ explicit SlotView(int64_t n_)
+      : n(static_cast<uint32_t>(n_)), m(0xFFFFFFFFu / static_cast<uint32_t>(n_)) {}
+  __device__ __forceinline__ uint32_t operator()(uint32_t g) const {
+    uint32_t q = __umulhi(g, m);
+    if (g - q * n >= n) ++q;
+    return q;
+  }
+};
+
 // Per-view parameters, prepared on the host.  Double precision quantities are
 // carried as float pairs (hi + lo) so the projection needs no FP64 pipe.
 struct ViewParams {

@@ -315,13 +315,13 @@ __global__ void depth_tie_fix_kernel(int64_t n_total, int64_t n, const uint32_t*
   if (k + 1 >= n_total) return;
   const uint32_t kk = key[k];
   if (kk == 0xFFFFFFFFu || key[k + 1] != kk) return;
-  const uint32_t nn = static_cast<uint32_t>(n);
+  const SlotView view_of(n);
   const uint32_t v0 = val[k];
-  const uint32_t view = v0 / nn;
-  if (val[k + 1] / nn != view) return;                       // no same-view tie here
-  if (k > 0 && key[k - 1] == kk && val[k - 1] / nn == view) return;  // not the run's start
+  const uint32_t view = view_of(v0);
+  if (view_of(val[k + 1]) != view) return;                       // no same-view tie here
+  if (k > 0 && key[k - 1] == kk && view_of(val[k - 1]) == view) return;  // not the run's start
   int64_t e = k + 2;
-  while (e < n_total && key[e] == kk && val[e] / nn == view) ++e;
+  while (e < n_total && key[e] == kk && view_of(val[e]) == view) ++e;
   for (int64_t a = k + 1; a < e; ++a) {
     const uint32_t va = val[a];
     const uint64_t ka = (static_cast<uint64_t>(depth_lo[va]) << 32) | va;

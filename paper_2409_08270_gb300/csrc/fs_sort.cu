@@ -57,12 +57,15 @@ __global__ void __launch_bounds__(kThreads) scan_reduce_kernel(const uint32_t* _
                                                                uint32_t* __restrict__ block_sums) {
   __shared__ uint32_t s_warp[kWarps];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTileElems;
-  uint32_t acc = 0;
-#pragma unroll 4
+  uint32_t x[kRounds];
+#pragma unroll
   for (int r = 0; r < kRounds; ++r) {
     const int64_t j = base + r * kThreads + threadIdx.x;
-    if (j < n) acc += load_in(in, gather, j);
+    x[r] = j < n ? load_in(in, gather, j) : 0u;
   }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) acc += x[r];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = acc;
@@ -98,12 +101,19 @@ __global__ void __launch_bounds__(kThreads) scan_down_kernel(const uint32_t* __r
                                                              uint32_t* __restrict__ out) {
   __shared__ uint32_t s_warp[kWarps];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTileElems;
-  uint32_t carry = block_pre[blockIdx.x];
+  // all loads in flight before the first block barrier
+  uint32_t x[kRounds];
+#pragma unroll
   for (int r = 0; r < kRounds; ++r) {
     const int64_t j = base + r * kThreads + threadIdx.x;
-    const uint32_t x = j < n ? load_in(in, gather, j) : 0u;
+    x[r] = j < n ? load_in(in, gather, j) : 0u;
+  }
+  uint32_t carry = block_pre[blockIdx.x];
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const int64_t j = base + r * kThreads + threadIdx.x;
     uint32_t t;
-    const uint32_t ex = block_exclusive_scan(x, s_warp, &t);
+    const uint32_t ex = block_exclusive_scan(x[r], s_warp, &t);
     if (j < n) out[j] = carry + ex;
     carry += t;
   }
