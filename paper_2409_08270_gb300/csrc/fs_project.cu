@@ -524,7 +524,7 @@ constexpr unsigned long long kLbCount = 1ull << 32;   // word holds the block's 
 constexpr unsigned long long kLbPrefix = 2ull << 32;  // word holds the inclusive prefix
 constexpr int kLbSpinLimit = 1 << 26;
 
-__global__ void __launch_bounds__(256) bin_fused_kernel(
+__global__ void __launch_bounds__(256, 6) bin_fused_kernel(
     int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
     const uint32_t* __restrict__ sorted_val, const uint32_t* __restrict__ cnt,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(256) bin_fused_kernel(
   const uint32_t incl = warp_incl_scan(nrows, lane);
   const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
   // count; the first kStash rounds' jobs are kept in registers for the emission
-  constexpr int kStash = 4;
+  constexpr int kStash = 3;
   int st_a[kStash], st_b[kStash];
   uint32_t st_fr[kStash], st_g[kStash];
   uint32_t wtot = 0;
