@@ -33,6 +33,15 @@ __device__ __forceinline__ uint32_t count_free(const uint64_t* __restrict__ sat,
   return c;
 }
 
+// Hardware square root (relative error ~2^-23): far inside the one-pixel
+// margin of the spans below, and the same instruction wherever a span is
+// evaluated, so every kernel that bins gets identical spans.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Tiles [tx0, tx1] of tile row ty touched by the footprint (false if none).
 // The band of pixel-centre rows of the tile, widened by one pixel, is
 // intersected with the ellipse; over the band the right boundary x(dy) is
@@ -46,8 +55,8 @@ __device__ __forceinline__ bool row_span(const Footprint& f, int ty, int width, 
   const float u0 = fmaxf(y0, -f.hy), u1 = fminf(y1, f.hy);
   if (!(u0 <= u1)) return false;
   const float dr = fminf(fmaxf(f.dys, u0), u1), dl = fminf(fmaxf(-f.dys, u0), u1);
-  const float sr = __fsqrt_rn(__fmul_rn(f.b2, fmaxf(0.f, __fsub_rn(f.syr, __fmul_rn(dr, dr)))));
-  const float sl = __fsqrt_rn(__fmul_rn(f.b2, fmaxf(0.f, __fsub_rn(f.syr, __fmul_rn(dl, dl)))));
+  const float sr = sqrt_approx(__fmul_rn(f.b2, fmaxf(0.f, __fsub_rn(f.syr, __fmul_rn(dr, dr)))));
+  const float sl = sqrt_approx(__fmul_rn(f.b2, fmaxf(0.f, __fsub_rn(f.syr, __fmul_rn(dl, dl)))));
   const float xr = __fadd_rn(__fadd_rn(f.mx, __fmul_rn(f.a, dr)), sr);
   const float xl = __fsub_rn(__fadd_rn(f.mx, __fmul_rn(f.a, dl)), sl);
   float px0 = ceilf(__fsub_rn(xl, 1.5f)), px1 = floorf(__fadd_rn(xr, 0.5f));
