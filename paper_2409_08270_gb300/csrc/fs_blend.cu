@@ -210,9 +210,13 @@ __global__ void __launch_bounds__(32) blend_kernel(
   const uint32_t lt = lanemask_lt();
   uint32_t n_staged = 0;
 
+  // list entries one round ahead
+  uint32_t g_next = rg.x + lane < rg.y ? list_val[rg.x + lane] : 0u;
   for (uint32_t base = rg.x; base < rg.y; base += kStage) {
     if (!__any_sync(0xffffffffu, T.x > 0.f || T.y > 0.f)) break;
     const int nin = static_cast<int>(min(static_cast<uint32_t>(kStage), rg.y - base));
+    const uint32_t g_here = g_next;
+    if (base + kStage + lane < rg.y) g_next = list_val[base + kStage + lane];
     // stage the Gaussians whose alpha >= 1/255 region can reach this sub-tile
     bool keep = false;
     float4 wk;
@@ -221,7 +225,7 @@ __global__ void __launch_bounds__(32) blend_kernel(
     float qc = 0.f;
     if (lane < nin && rec16) {
       // reduced-precision record: b = W16 (o - m) in FP32
-      g = list_val[base + lane];
+      g = g_here;
       const CompactRecord r = rec16[g];
       const float2 wa = __half22float2(*reinterpret_cast<const __half2*>(&r.w01));
       const float2 wb = __half22float2(*reinterpret_cast<const __half2*>(&r.w23));
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(32) blend_kernel(
       // b = W (o - m) for the sub-tile centre o: o - m_hi is exact whenever
       // the mean lies within a factor of two of o (and off by far less than
       // a pixel's 1e-7 otherwise); W = W_hi + W_lo
-      g = list_val[base + lane];
+      g = g_here;
       const ProjRecord r = rec[g];
       const float dx = (ox - r.m.x) - r.m.z, dy = (oy - r.m.y) - r.m.w;
       wk = r.w_hi;
