@@ -43,7 +43,7 @@ FP32_LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="flashsplat", choices=["flashsplat", "reference"])
     ap.add_argument("--views-per-batch", type=int, default=0)
@@ -97,14 +97,63 @@ def config_of(w, args, extra=None):
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
+    """SM clock, power and clock-event reasons sampled during the timed region.
+
+    Reads NVML (the driver's libnvidia-ml) from a thread every 20 ms; falls
+    back to `nvidia-smi -lms 100` when NVML cannot be loaded.  Read-only: no
+    setting of the GPU is touched.
+    """
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
     def __init__(self, uuid=None):
+        self.rows, self.p, self.nvml = [], None, None
+        try:
+            self._start_nvml(uuid)
+        except Exception:
+            self.nvml = None
+            self._start_smi(uuid)
+
+    def _start_nvml(self, uuid):
+        import ctypes
+        import threading
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        if uuid:
+            rc = lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h))
+        else:
+            rc = lib.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h))
+        if rc != 0:
+            raise RuntimeError("no NVML handle")
+        mx = ctypes.c_uint()
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))      # 1 = SM clock
+        self.max_mhz = float(mx.value)
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.nvml, self.stop_ev = lib, threading.Event()
+
+        def loop():
+            clk, pw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+            while not self.stop_ev.is_set():
+                if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0:
+                    lib.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw))
+                    get_reasons(h, ctypes.byref(rs))
+                    self.rows.append((float(clk.value), pw.value / 1000.0, int(rs.value)))
+                self.stop_ev.wait(0.02)
+
+        self.th = threading.Thread(target=loop, daemon=True)
+        self.th.start()
+
+    def _start_smi(self, uuid):
         self.path = tempfile.mktemp(prefix="fs_clocks_", suffix=".csv")
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-               "-lms", "200"]
+               "-lms", "100"]
         if uuid:
             cmd += ["-i", uuid]
         try:
@@ -114,6 +163,18 @@ class ClockSampler:
             self.p = None
 
     def stop(self):
+        if self.nvml is not None:
+            self.stop_ev.set()
+            self.th.join()
+            self.nvml.nvmlShutdown()
+            if not self.rows:
+                return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples"]}
+            reasons = sorted({name for _, _, r in self.rows for bit, name in self.REASONS.items()
+                              if r & bit})
+            return {"sm_mhz": statistics.median(r[0] for r in self.rows),
+                    "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                    "samples": len(self.rows), "source": "NVML every 20 ms",
+                    "power_w_max": max(r[1] for r in self.rows)}
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
@@ -142,7 +203,7 @@ class ClockSampler:
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows),
+                "samples": len(rows), "source": "nvidia-smi every 100 ms",
                 "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
 
 

@@ -571,7 +571,7 @@ fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
     const size_t cap_bytes = std::min(c->lk_a.bytes, val_dst->bytes);
     const uint32_t capacity = static_cast<uint32_t>(std::min<size_t>(cap_bytes / 4, 0x7FFFFFFFu));
     c->stats.kernel_launches += 1;
-    FS_CUDA(fs::launch_bin_fused(p0, n_pos, n, vd, sorted_val, P.cnt, P.foot, sat,
+    FS_CUDA(fs::launch_bin_fused(p0, n_pos, n, vd, sorted_val, P.foot, sat,
                                  c->lk_a.as<uint32_t>(), val_dst->as<uint32_t>(), capacity,
                                  c->lb_tmp.p, c->total.as<uint32_t>(), ctr, stream),
             "binning");

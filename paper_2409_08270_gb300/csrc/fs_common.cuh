@@ -68,15 +68,18 @@ struct alignas(16) ProjRecord {
   float4 misc;
 };
 
-// Reduced-precision record of one (view, Gaussian): 16 B.  The mean stays
-// FP32; the whitening matrix W is stored as four FP16 values (correctly
-// rounded from the float pairs), so alpha = o 2^-|W16 (p - m)|^2 with the
-// opacity o read from the scene.  |W d|^2 stays a sum of squares whatever
-// the rounding, unlike an FP16 conic, which can lose positive definiteness
-// for elongated footprints.
+// Reduced-precision record of one (view, Gaussian): 32 B, one DRAM sector.
+// The mean stays FP32; the whitening matrix W is stored as four FP16 values
+// (correctly rounded from the float pairs), so alpha = o 2^-|W16 (p - m)|^2.
+// The opacity o (the scene's own value) and the cut q_cut ~ log2(255 o) ride
+// along so the blend needs no second gather.  |W d|^2 stays a sum of squares
+// whatever the rounding, unlike an FP16 conic, which can lose positive
+// definiteness for elongated footprints.
 struct alignas(16) CompactRecord {
   float mx, my;
   uint32_t w01, w23;  // (W00, W01), (W10, W11) as FP16 pairs, low half first
+  float o, q_cut;
+  float pad0, pad1;
 };
 
 // Footprint of one (view, Gaussian) for the tile binning: the alpha >= 1/255

@@ -55,12 +55,12 @@ cudaError_t launch_project(int64_t n, int n_views, const ViewParams* views, cons
 cudaError_t launch_depth_tie_fix(int64_t n_total, int64_t n, const uint32_t* key, uint32_t* val,
                                  const uint32_t* depth_lo, cudaStream_t stream);
 cudaError_t launch_chunk_count(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
-                               const uint32_t* sorted_val, const uint32_t* cnt,
-                               const Footprint* foot, const uint64_t* sat, uint32_t* out_cnt,
+                               const uint32_t* sorted_val, const Footprint* foot,
+                               const uint64_t* sat, uint32_t* out_cnt,
                                cudaStream_t stream);
 cudaError_t launch_emit(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
                         const uint32_t* sorted_val, const uint32_t* offsets,
-                        const uint32_t* chunk_cnt, const uint32_t* cnt, const Footprint* foot,
+                        const uint32_t* chunk_cnt, const Footprint* foot,
                         const uint64_t* sat, uint32_t* out_key, uint32_t* out_val,
                         unsigned long long* counters, cudaStream_t stream);
 // Count, scan and emit of sorted positions [p0, p0 + n_pos) in one launch
@@ -68,7 +68,7 @@ cudaError_t launch_emit(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* 
 // *total (device) receives the entry count.  lookback: bin_fused_temp_bytes
 // of scratch (cleared by the launcher).
 cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
-                             const uint32_t* sorted_val, const uint32_t* cnt,
+                             const uint32_t* sorted_val,
                              const Footprint* foot, const uint64_t* sat, uint32_t* out_key,
                              uint32_t* out_val, uint32_t capacity, void* lookback,
                              uint32_t* total, unsigned long long* counters, cudaStream_t stream);
@@ -87,8 +87,8 @@ cudaError_t launch_state_init(const ViewParams* views, int n_views, int max_tile
                               unsigned long long* counters, cudaStream_t stream);
 // sat_chunk (may be NULL): per batch tile, set to `chunk` when the tile
 // saturates during this launch (its later chunks get no list entries).
-// Records: float pairs in rec, or reduced precision in rec16 (then the
-// opacity comes from pos_op[i].w of the scene).
+// Records: float pairs in rec, or reduced precision in rec16 (pos_op is
+// not read by the blend).
 cudaError_t launch_blend(const ViewParams* views, int n_views, int max_tiles_per_view,
                          const uint2* ranges, const uint32_t* list_val, const ProjRecord* rec,
                          const CompactRecord* rec16, const float4* pos_op, int64_t n, int E,

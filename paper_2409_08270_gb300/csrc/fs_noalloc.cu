@@ -267,7 +267,7 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
       const int64_t p1 = (ci == chunks - 1) ? n : (n >> (chunks - 1 - ci));
       const int64_t n_pos = p1 - p0;
       if (n_pos <= 0) continue;
-      NA_CUDA(launch_chunk_count(p0, n_pos, n, vd, sval, cnt, foot, sat, ccnt, strm), "count");
+      NA_CUDA(launch_chunk_count(p0, n_pos, n, vd, sval, foot, sat, ccnt, strm), "count");
       NA_CUDA(exclusive_scan(ccnt, nullptr, offs, n_pos, total_d, scan_tmp, strm), "scan");
       uint32_t I = 0;
       NA_CUDA(cudaMemcpyAsync(&I, total_d, 4, cudaMemcpyDeviceToHost, strm), "readback");
@@ -277,7 +277,7 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
                        "fs_solve_noalloc: a view needs more than FS_NOALLOC_MAX_LIST_ENTRIES "
                        "(tile, Gaussian) pairs in one depth chunk; the table is incomplete");
       if (I > 0) {
-        NA_CUDA(launch_emit(p0, n_pos, n, vd, sval, offs, ccnt, cnt, foot, sat, lk_a, lv_a, ctr,
+        NA_CUDA(launch_emit(p0, n_pos, n, vd, sval, offs, ccnt, foot, sat, lk_a, lv_a, ctr,
                             strm),
                 "emit");
         bool alt2 = false;

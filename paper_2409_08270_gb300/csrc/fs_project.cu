@@ -166,14 +166,16 @@ __global__ void __launch_bounds__(256, 4) project_kernel(
     float depth = 0.f, depth_l = 0.f;
     ProjRecord R;
     R.w_hi = R.w_lo = R.m = make_float4(0.f, 0.f, 0.f, 0.f);
-    CompactRecord R16 = {0.f, 0.f, 0u, 0u};
+    CompactRecord R16 = {0.f, 0.f, 0u, 0u, 0.f, 0.f, 0.f, 0.f};
     // misc.y: |w|^2 at which alpha falls to 1/255, log2(255 o), widened by
     // 0.1% + 1e-3 so the blend's sub-tile test stays conservative in FP32
     const float qcut = opaque_enough ? fmaxf(log2f(255.f * o), 0.f) * 1.001f + 1e-3f : 0.f;
     R.misc = make_float4(o, qcut, 0.f, 0.f);
+    R16.o = o;
+    R16.q_cut = qcut;
     Footprint F;
     F.mx = F.my = F.hy = F.syr = F.dys = F.a = F.b2 = 0.f;
-    F.rows = 0;
+    F.rows = 0x0000FFFFu;  // no tile row (first row 65535 > last row 0)
     if (visible) {
       const f2 ux = f2_div(tx, tz), uy = f2_div(ty, tz);
       const f2 fx = {vp.fx_hi, vp.fx_lo}, fy = {vp.fy_hi, vp.fy_lo};
@@ -395,7 +397,6 @@ __device__ __forceinline__ uint32_t job_free(const RowJob& jb, int64_t n,
 
 __device__ __forceinline__ void lane_rows(int64_t j, int64_t n_pos, int64_t p0,
                                           const uint32_t* __restrict__ sorted_val,
-                                          const uint32_t* __restrict__ cnt,
                                           const Footprint* __restrict__ foot, uint32_t* g,
                                           int* ty0, uint32_t* nrows) {
   *g = 0;
@@ -403,12 +404,10 @@ __device__ __forceinline__ void lane_rows(int64_t j, int64_t n_pos, int64_t p0,
   *nrows = 0;
   if (j < n_pos) {
     *g = sorted_val[p0 + j];
-    if (cnt[*g] > 0) {
-      int t0, t1;
-      footprint_rows(foot[*g], &t0, &t1);
-      *ty0 = t0;
-      *nrows = static_cast<uint32_t>(max(0, t1 - t0 + 1));
-    }
+    int t0, t1;
+    footprint_rows(foot[*g], &t0, &t1);
+    *ty0 = t0;
+    *nrows = static_cast<uint32_t>(max(0, t1 - t0 + 1));
   }
 }
 
@@ -423,7 +422,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 
 __global__ void __launch_bounds__(256) chunk_count_kernel(
     int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
-    const uint32_t* __restrict__ sorted_val, const uint32_t* __restrict__ cnt,
+    const uint32_t* __restrict__ sorted_val,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
     uint32_t* __restrict__ out_cnt) {
   __shared__ uint32_t s_cnt[8][32];
@@ -431,7 +430,7 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t g, nrows;
   int ty0;
-  lane_rows(j, n_pos, p0, sorted_val, cnt, foot, &g, &ty0, &nrows);
+  lane_rows(j, n_pos, p0, sorted_val, foot, &g, &ty0, &nrows);
   const uint32_t incl = warp_incl_scan(nrows, lane);
   const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
   s_cnt[warp][lane] = 0;
@@ -476,7 +475,7 @@ __device__ __forceinline__ uint32_t emit_free(const uint64_t* __restrict__ sat, 
 __global__ void __launch_bounds__(256) emit_kernel(
     int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
     const uint32_t* __restrict__ sorted_val, const uint32_t* __restrict__ offsets,
-    const uint32_t* __restrict__ chunk_cnt, const uint32_t* __restrict__ cnt,
+    const uint32_t* __restrict__ chunk_cnt,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
     uint32_t* __restrict__ out_key, uint32_t* __restrict__ out_val,
     unsigned long long* __restrict__ counters) {
@@ -484,7 +483,7 @@ __global__ void __launch_bounds__(256) emit_kernel(
   const int lane = threadIdx.x & 31;
   uint32_t g, nrows;
   int ty0;
-  lane_rows(j, n_pos, p0, sorted_val, cnt, foot, &g, &ty0, &nrows);
+  lane_rows(j, n_pos, p0, sorted_val, foot, &g, &ty0, &nrows);
   const uint32_t incl = warp_incl_scan(nrows, lane);
   const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
   // the warp's output range [wbeg, wend)
@@ -526,7 +525,7 @@ constexpr int kLbSpinLimit = 1 << 26;
 
 __global__ void __launch_bounds__(256, 6) bin_fused_kernel(
     int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
-    const uint32_t* __restrict__ sorted_val, const uint32_t* __restrict__ cnt,
+    const uint32_t* __restrict__ sorted_val,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
     uint32_t* __restrict__ out_key, uint32_t* __restrict__ out_val, uint32_t capacity,
     unsigned long long* __restrict__ status, uint32_t* __restrict__ ticket,
@@ -540,7 +539,7 @@ __global__ void __launch_bounds__(256, 6) bin_fused_kernel(
   const int64_t j = static_cast<int64_t>(vb) * blockDim.x + threadIdx.x;
   uint32_t g, nrows;
   int ty0;
-  lane_rows(j, n_pos, p0, sorted_val, cnt, foot, &g, &ty0, &nrows);
+  lane_rows(j, n_pos, p0, sorted_val, foot, &g, &ty0, &nrows);
   const uint32_t incl = warp_incl_scan(nrows, lane);
   const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
   // count; the first kStash rounds' jobs are kept in registers for the emission
@@ -693,33 +692,33 @@ cudaError_t launch_depth_tie_fix(int64_t n_total, int64_t n, const uint32_t* key
 }
 
 cudaError_t launch_chunk_count(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
-                               const uint32_t* sorted_val, const uint32_t* cnt,
+                               const uint32_t* sorted_val,
                                const Footprint* foot, const uint64_t* sat, uint32_t* out_cnt,
                                cudaStream_t stream) {
   if (n_pos == 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = (n_pos + threads - 1) / threads;
   chunk_count_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-      p0, n_pos, n, views, sorted_val, cnt, foot, sat, out_cnt);
+      p0, n_pos, n, views, sorted_val, foot, sat, out_cnt);
   return cudaGetLastError();
 }
 
 cudaError_t launch_emit(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
                         const uint32_t* sorted_val, const uint32_t* offsets,
-                        const uint32_t* chunk_cnt, const uint32_t* cnt, const Footprint* foot,
+                        const uint32_t* chunk_cnt, const Footprint* foot,
                         const uint64_t* sat, uint32_t* out_key, uint32_t* out_val,
                         unsigned long long* counters, cudaStream_t stream) {
   if (n_pos == 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = (n_pos + threads - 1) / threads;
   emit_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-      p0, n_pos, n, views, sorted_val, offsets, chunk_cnt, cnt, foot, sat, out_key, out_val,
+      p0, n_pos, n, views, sorted_val, offsets, chunk_cnt, foot, sat, out_key, out_val,
       counters);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
-                             const uint32_t* sorted_val, const uint32_t* cnt,
+                             const uint32_t* sorted_val,
                              const Footprint* foot, const uint64_t* sat, uint32_t* out_key,
                              uint32_t* out_val, uint32_t capacity, void* lookback,
                              uint32_t* total, unsigned long long* counters, cudaStream_t stream) {
@@ -732,7 +731,7 @@ cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewPar
   cudaError_t e = cudaMemsetAsync(lookback, 0, 256 + static_cast<size_t>(blocks) * 8, stream);
   if (e != cudaSuccess) return e;
   bin_fused_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-      p0, n_pos, n, views, sorted_val, cnt, foot, sat, out_key, out_val, capacity, status, ticket,
+      p0, n_pos, n, views, sorted_val, foot, sat, out_key, out_val, capacity, status, ticket,
       total, counters);
   return cudaGetLastError();
 }
