@@ -36,8 +36,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "s per scene solve & Gpix/s of α·T accumulation; batched BF16 vs plain FP32"
 UNIT = "Gpix/s"
-FLOPS_PER_PAIR = 19   # FP32 flops of one (pixel, Gaussian) evaluation, FMA = 2 (see DESIGN.md)
+FLOPS_PER_PAIR = 19   # FP32 flops of one (pixel, Gaussian) evaluation, FMA = 2
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of blend_kernel per evaluated pair, from one ncu
+# capture of the current kernel: the six blend launches of an 8-view solve of
+# this scene read and wrote 195.7 MB for 636.1 M pairs.  Scaled by pairs to the
+# launches timed here (the traffic grows with the pairs: records, masks and the
+# table are gathered per staged entry).  Set to None when the kernel changes.
+BLEND_DRAM_BYTES_PER_PAIR = 195.7e6 / 636.1e6
 
 
 def parse():
@@ -342,7 +348,10 @@ def run_flashsplat(args, rank, world, local_rank):
     achieved = (FLOPS_PER_PAIR * pairs) / (blend_ms * 1e-3) / 1e12 if blend_ms > 0 else None
     roofline = {"kernel": "blend_kernel (alpha*T accumulation)", "bound": "alu",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": (achieved / peak_tflops) if achieved else None, "traffic": None,
+                "frac": (achieved / peak_tflops) if achieved else None,
+                "traffic": (BLEND_DRAM_BYTES_PER_PAIR * pairs / max(1, blend_launches)
+                            if BLEND_DRAM_BYTES_PER_PAIR and blend_launches else None),
+                "traffic_unit": "DRAM bytes per launch (ncu, 8-view capture scaled by pairs)",
                 "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_clk:.0f} MHz",
                 "pairs_per_step": pairs // max(1, args.steps),
                 "list_entries_per_step": entries // max(1, args.steps),

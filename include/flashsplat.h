@@ -91,8 +91,9 @@ typedef struct fs_options {
   /* 0: per-view projected records in float pairs (64 B); FS_F16: the
    * reduced-precision form -- each (view, Gaussian) keeps its projected mean
    * in FP32 and its whitening matrix W (|W d|^2 = 0.5 log2(e) d^T
-   * Sigma2D^-1 d) in FP16, 16 B, and alpha = o 2^-|W (p - m)|^2 is evaluated
-   * from those rounded values (blending in FP32, table in FP64). */
+   * Sigma2D^-1 d) in FP16 (a 32 B record with the opacity and its alpha
+   * cut), and alpha = o 2^-|W (p - m)|^2 is evaluated from those rounded
+   * values (blending in FP32, table in FP64). */
   int32_t record_precision;
   int32_t reserved[10];
 } fs_options;

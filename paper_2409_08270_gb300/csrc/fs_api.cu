@@ -1041,12 +1041,13 @@ fs_status fs_solve(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t 
   if (tbytes) FS_CUDA(cudaMemsetAsync(table, 0, tbytes, st), "table clear");
   const bool recheck = c->recheck_margin > 0.f && n > 0 && V > 0;
   // keep every view's projection resident for the re-check when it fits in
-  // half of the free device memory (108 B per Gaussian and view)
+  // half of the free device memory (108 B per Gaussian and view; 76 B with
+  // reduced-precision records)
   bool keep = false;
   if (recheck && !c->recheck_reproject) {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-      const double need = (c->compact ? 60.0 : 108.0) * static_cast<double>(n) * V;
+      const double need = (c->compact ? 76.0 : 108.0) * static_cast<double>(n) * V;
       const double have = static_cast<double>(c->rec.bytes + c->foot.bytes + c->cnt.bytes +
                                               c->dlo.bytes + c->dkey.bytes);
       keep = need <= have + 0.5 * static_cast<double>(free_b);

@@ -4,9 +4,9 @@
 // the table column of that pixel's label, added atomically).
 //
 // One warp per 8x8 sub-tile of a 16x16 tile; each lane walks two adjacent
-// pixels; no block barriers.  Blocks hold two independent warps (two
-// sub-tiles) and the kernel is held to 48 registers, so that up to 38 warps
-// share an SM (shared memory is then the limit) instead of the 32 that
+// pixels; no block barriers.  A block holds the four independent warps of one
+// tile and the kernel is held to 48 registers, so that 40 warps share an SM
+// (registers and shared memory both allow 10 blocks) instead of the 32 that
 // one-warp blocks allow.
 //  * The warp reads its tile's depth-sorted list (one depth chunk of it) 32
 //    entries at a time.  Each lane forms its entry's offset b = W o + c at the
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(64) state_init_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// blend: one warp per 8x8 sub-tile, 2 adjacent pixels per lane, 2 warps a block
+// blend: one warp per 8x8 sub-tile, 2 adjacent pixels per lane, 4 warps a block
 // ---------------------------------------------------------------------------
 constexpr int kStage = 32;  // list entries examined per round (one per lane)
 
@@ -143,18 +143,18 @@ struct SubSmem {
 };
 
 template <typename LabelT, typename TableT>
-__global__ void __launch_bounds__(64, 19) blend_kernel(
+__global__ void __launch_bounds__(128, 10) blend_kernel(
     const ViewParams* __restrict__ views, const uint2* __restrict__ ranges,
     const uint32_t* __restrict__ list_val, const ProjRecord* __restrict__ rec,
     const CompactRecord* __restrict__ rec16, const float4* __restrict__ pos_op, int64_t n, int E,
     TableT* __restrict__ table, float* __restrict__ state, uint64_t* __restrict__ sat,
     uint64_t* __restrict__ subsat, uint8_t* __restrict__ sat_chunk, int chunk,
     unsigned long long* __restrict__ counters) {
-  __shared__ SubSmem S_warp[2];
+  __shared__ SubSmem S_warp[4];
   SubSmem& S = S_warp[threadIdx.x >> 5];
   const int v = blockIdx.y;
   const int tiles_x = views[v].tiles_x;
-  const int bsub = 2 * blockIdx.x + (threadIdx.x >> 5);  // sub-tile of the view
+  const int bsub = 4 * blockIdx.x + (threadIdx.x >> 5);  // sub-tile of the view
   const int tile = bsub >> 2, sub = bsub & 3;
   if (tile >= tiles_x * views[v].tiles_y) return;  // whole warp
   const int gtile = views[v].tile_base + tile;
@@ -337,8 +337,8 @@ cudaError_t launch_typed(const ViewParams* views, int n_views, int max_tiles, co
                          void* table, float* state, uint64_t* sat, uint64_t* subsat,
                          uint8_t* sat_chunk, int chunk, unsigned long long* counters,
                          cudaStream_t stream) {
-  dim3 grid(static_cast<unsigned>(2 * max_tiles), static_cast<unsigned>(n_views));
-  blend_kernel<LabelT, TableT><<<grid, 64, 0, stream>>>(views, ranges, list_val, rec, rec16,
+  dim3 grid(static_cast<unsigned>(max_tiles), static_cast<unsigned>(n_views));
+  blend_kernel<LabelT, TableT><<<grid, 128, 0, stream>>>(views, ranges, list_val, rec, rec16,
                                                         pos_op, n, E,
                                                         static_cast<TableT*>(table), state, sat,
                                                         subsat, sat_chunk, chunk, counters);

@@ -511,7 +511,8 @@ __global__ void __launch_bounds__(256) emit_kernel(
 
 // Count, offset and emit in one pass.  Blocks take virtual ids in launch
 // order (a ticket), so every block's predecessors are running or done.  A
-// block counts its 256 positions' entries, publishes the count, then adds
+// block (4 warps: a short wait at its barriers) counts its 128 positions'
+// entries, publishes the count, then adds
 // up its predecessors' published words (decoupled look-back: a word is
 // either a block's own count or the inclusive prefix up to it; the walk
 // stops at the first prefix), publishes its own prefix and emits from its
@@ -523,7 +524,7 @@ constexpr unsigned long long kLbCount = 1ull << 32;   // word holds the block's 
 constexpr unsigned long long kLbPrefix = 2ull << 32;  // word holds the inclusive prefix
 constexpr int kLbSpinLimit = 1 << 26;
 
-__global__ void __launch_bounds__(256, 6) bin_fused_kernel(
+__global__ void __launch_bounds__(128, 12) bin_fused_kernel(
     int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
     const uint32_t* __restrict__ sorted_val,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(256, 6) bin_fused_kernel(
     unsigned long long* __restrict__ status, uint32_t* __restrict__ ticket,
     uint32_t* __restrict__ total, unsigned long long* __restrict__ counters) {
   __shared__ uint32_t s_vb, s_boff;
-  __shared__ uint32_t s_wtot[8];
+  __shared__ uint32_t s_wtot[4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_vb = atomicAdd(ticket, 1u);
   __syncthreads();
@@ -578,7 +579,7 @@ __global__ void __launch_bounds__(256, 6) bin_fused_kernel(
   // time (lane l reads predecessor vb - 1 - l)
   if (warp == 0) {
     uint32_t btot = 0;
-    for (int w = 0; w < 8; ++w) btot += s_wtot[w];
+    for (int w = 0; w < 4; ++w) btot += s_wtot[w];
     if (lane == 0) atomicExch(&status[vb], (vb == 0 ? kLbPrefix : kLbCount) | btot);
     volatile unsigned long long* vs = status;
     uint32_t excl = 0;
@@ -723,7 +724,7 @@ cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewPar
                              uint32_t* out_val, uint32_t capacity, void* lookback,
                              uint32_t* total, unsigned long long* counters, cudaStream_t stream) {
   if (n_pos <= 0) return cudaMemsetAsync(total, 0, sizeof(uint32_t), stream);
-  const int threads = 256;
+  const int threads = 128;
   const int64_t blocks = (n_pos + threads - 1) / threads;
   uint32_t* ticket = static_cast<uint32_t*>(lookback);
   unsigned long long* status = reinterpret_cast<unsigned long long*>(
@@ -737,7 +738,7 @@ cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewPar
 }
 
 size_t bin_fused_temp_bytes(int64_t n_pos) {
-  return 256 + static_cast<size_t>((n_pos + 255) / 256) * 8;
+  return 256 + static_cast<size_t>((n_pos + 127) / 128) * 8;
 }
 
 cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
