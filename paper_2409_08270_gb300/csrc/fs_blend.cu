@@ -92,20 +92,23 @@ __device__ __forceinline__ void set_bit(uint64_t* bits, int i) {
 // Per-pixel state of a batch before its first depth chunk: T = 1 for pixels
 // with a label in [0, E), 0 ("stopped") for the others.  Sub-tiles (and tiles)
 // without a labelled pixel start saturated.  Counts the pixels with bad
-// labels.  One 64-thread block per 8x8 sub-tile.
+// labels.  One 256-thread block per 16x16 tile: 64 threads (two warps) per
+// 8x8 sub-tile.
 template <typename LabelT>
-__global__ void __launch_bounds__(64) state_init_kernel(
+__global__ void __launch_bounds__(256) state_init_kernel(
     const ViewParams* __restrict__ views, int E, float* __restrict__ state,
     uint64_t* __restrict__ sat, uint64_t* __restrict__ subsat,
     unsigned long long* __restrict__ counters) {
+  __shared__ uint32_t s_bad[8], s_any[8];
   const int v = blockIdx.y;
   const int tiles_x = views[v].tiles_x;
-  const int tile = blockIdx.x >> 2, sub = blockIdx.x & 3;
+  const int tile = blockIdx.x;
   if (tile >= tiles_x * views[v].tiles_y) return;  // whole block
   const int W = views[v].width, H = views[v].height;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
-  const int px = tx * kTile + (sub & 1) * 8 + (threadIdx.x & 7);
-  const int py = ty * kTile + (sub >> 1) * 8 + (threadIdx.x >> 3);
+  const int sub = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int px = tx * kTile + (sub & 1) * 8 + (t & 7);
+  const int py = ty * kTile + (sub >> 1) * 8 + (t >> 3);
   const bool inside = px < W && py < H;
   bool valid = false;
   if (inside) {
@@ -114,17 +117,26 @@ __global__ void __launch_bounds__(64) state_init_kernel(
     valid = label >= 0 && label < E;
     state[views[v].state_off + p] = valid ? 1.f : 0.f;
   }
-  const int n_bad = __syncthreads_count(inside && !valid);
-  const int any = __syncthreads_or(valid);
+  const uint32_t bad = __ballot_sync(0xffffffffu, inside && !valid);
+  const uint32_t any = __ballot_sync(0xffffffffu, valid);
+  if ((threadIdx.x & 31) == 0) {
+    s_bad[threadIdx.x >> 5] = __popc(bad);
+    s_any[threadIdx.x >> 5] = any;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    uint32_t n_bad = 0, empty = 0;  // empty: bit s = sub-tile s has no labelled pixel
+    for (int s = 0; s < 4; ++s) {
+      n_bad += s_bad[2 * s] + s_bad[2 * s + 1];
+      if ((s_any[2 * s] | s_any[2 * s + 1]) == 0u) empty |= 1u << s;
+    }
     if (n_bad) atomicAdd(&counters[kBadLabels], static_cast<unsigned long long>(n_bad));
-    if (!any) {
+    if (empty) {
       const int g = views[v].tile_base + tile;
-      const int gs = 4 * g + sub;
-      const unsigned long long nib = 0xFull << (gs & 63 & ~3);
-      const unsigned long long old = atomicOr(
-          reinterpret_cast<unsigned long long*>(subsat + (gs >> 6)), 1ull << (gs & 63));
-      if (((old | (1ull << (gs & 63))) & nib) == nib) set_bit(sat, g);
+      const int gs = 4 * g;  // the tile's four sub-tile bits: one nibble of a word
+      atomicOr(reinterpret_cast<unsigned long long*>(subsat + (gs >> 6)),
+               static_cast<unsigned long long>(empty) << (gs & 63));
+      if (empty == 0xFu) set_bit(sat, g);
     }
   }
 }
@@ -351,11 +363,11 @@ cudaError_t launch_state_init(const ViewParams* views, int n_views, int max_tile
                               int mask_dtype, float* state, uint64_t* sat, uint64_t* subsat,
                               unsigned long long* counters, cudaStream_t stream) {
   if (n_views == 0 || max_tiles_per_view == 0) return cudaSuccess;
-  dim3 grid(static_cast<unsigned>(4 * max_tiles_per_view), static_cast<unsigned>(n_views));
+  dim3 grid(static_cast<unsigned>(max_tiles_per_view), static_cast<unsigned>(n_views));
   if (mask_dtype == 4)
-    state_init_kernel<uint8_t><<<grid, 64, 0, stream>>>(views, E, state, sat, subsat, counters);
+    state_init_kernel<uint8_t><<<grid, 256, 0, stream>>>(views, E, state, sat, subsat, counters);
   else
-    state_init_kernel<int32_t><<<grid, 64, 0, stream>>>(views, E, state, sat, subsat, counters);
+    state_init_kernel<int32_t><<<grid, 256, 0, stream>>>(views, E, state, sat, subsat, counters);
   return cudaGetLastError();
 }
 

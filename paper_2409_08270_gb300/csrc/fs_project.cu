@@ -310,14 +310,10 @@ __global__ void __launch_bounds__(256, 4) project_kernel(
 // then by slot -- the order of the full-precision depth with ties by index
 // that the compositing of Eq. 1 walks.  A thread acts only where such a
 // same-view run starts; the runs are short and sorted by insertion.
-__global__ void depth_tie_fix_kernel(int64_t n_total, int64_t n, const uint32_t* __restrict__ key,
-                                     uint32_t* __restrict__ val,
-                                     const uint32_t* __restrict__ depth_lo) {
-  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k + 1 >= n_total) return;
-  const uint32_t kk = key[k];
-  if (kk == 0xFFFFFFFFu || key[k + 1] != kk) return;
-  const SlotView view_of(n);
+__device__ __forceinline__ void fix_tie_run(int64_t k, int64_t n_total, const SlotView& view_of,
+                                            uint32_t kk, const uint32_t* __restrict__ key,
+                                            uint32_t* __restrict__ val,
+                                            const uint32_t* __restrict__ depth_lo) {
   const uint32_t v0 = val[k];
   const uint32_t view = view_of(v0);
   if (view_of(val[k + 1]) != view) return;                       // no same-view tie here
@@ -336,6 +332,33 @@ __global__ void depth_tie_fix_kernel(int64_t n_total, int64_t n, const uint32_t*
       --b;
     }
     val[b + 1] = va;
+  }
+}
+
+// Each thread screens four consecutive positions (one 16-byte key load when
+// the keys are 16-byte aligned) for the start of an equal-key run.
+__global__ void depth_tie_fix_kernel(int64_t n_total, int64_t n, const uint32_t* __restrict__ key,
+                                     uint32_t* __restrict__ val,
+                                     const uint32_t* __restrict__ depth_lo) {
+  const int64_t k0 = 4 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+  if (k0 + 1 >= n_total) return;
+  uint32_t t[5];  // keys k0 .. k0 + 4 (0xFFFFFFFF past the end: never a run)
+  if (k0 + 4 <= n_total && (reinterpret_cast<uintptr_t>(key) & 15u) == 0) {
+    const uint4 q = *reinterpret_cast<const uint4*>(key + k0);
+    t[0] = q.x;
+    t[1] = q.y;
+    t[2] = q.z;
+    t[3] = q.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[i] = k0 + i < n_total ? key[k0 + i] : 0xFFFFFFFFu;
+  }
+  t[4] = k0 + 4 < n_total ? key[k0 + 4] : 0xFFFFFFFFu;
+  const SlotView view_of(n);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (t[i] != 0xFFFFFFFFu && t[i + 1] == t[i] && k0 + i + 1 < n_total)
+      fix_tie_run(k0 + i, n_total, view_of, t[i], key, val, depth_lo);
   }
 }
 
@@ -644,14 +667,33 @@ __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
   if (lane == 0 && wbeg + carry != wend) atomicAdd(&counters[kBinningMismatch], 1ull);
 }
 
-// [start, end) of every tile's run in the tile-sorted list.
+// [start, end) of every tile's run in the tile-sorted list.  Each thread
+// takes four consecutive entries (one 16-byte load when the list is 16-byte
+// aligned, as the library's buffers are) and the entries on either side.
 __global__ void ranges_kernel(int64_t n_entries, const uint32_t* __restrict__ key,
                               uint2* __restrict__ ranges) {
-  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k >= n_entries) return;
-  const uint32_t t = key[k];
-  if (k == 0 || key[k - 1] != t) ranges[t].x = static_cast<uint32_t>(k);
-  if (k == n_entries - 1 || key[k + 1] != t) ranges[t].y = static_cast<uint32_t>(k + 1);
+  const int64_t k0 = 4 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+  if (k0 >= n_entries) return;
+  uint32_t t[6];  // entries k0 - 1 .. k0 + 4 (0xFFFFFFFF outside the list)
+  t[0] = k0 > 0 ? key[k0 - 1] : 0xFFFFFFFFu;
+  if (k0 + 4 <= n_entries && (reinterpret_cast<uintptr_t>(key) & 15u) == 0) {
+    const uint4 q = *reinterpret_cast<const uint4*>(key + k0);
+    t[1] = q.x;
+    t[2] = q.y;
+    t[3] = q.z;
+    t[4] = q.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[1 + i] = k0 + i < n_entries ? key[k0 + i] : 0xFFFFFFFFu;
+  }
+  t[5] = k0 + 4 < n_entries ? key[k0 + 4] : 0xFFFFFFFFu;
+#pragma unroll
+  for (int i = 1; i <= 4; ++i) {
+    const int64_t k = k0 + i - 1;
+    if (k >= n_entries) break;
+    if (t[i - 1] != t[i]) ranges[t[i]].x = static_cast<uint32_t>(k);
+    if (t[i + 1] != t[i]) ranges[t[i]].y = static_cast<uint32_t>(k + 1);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -686,7 +728,7 @@ cudaError_t launch_depth_tie_fix(int64_t n_total, int64_t n, const uint32_t* key
                                  const uint32_t* depth_lo, cudaStream_t stream) {
   if (n_total < 2) return cudaSuccess;
   const int threads = 256;
-  const int64_t blocks = (n_total + threads - 1) / threads;
+  const int64_t blocks = ((n_total + 3) / 4 + threads - 1) / threads;
   depth_tie_fix_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(n_total, n, key, val,
                                                                               depth_lo);
   return cudaGetLastError();
@@ -745,7 +787,7 @@ cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
                           cudaStream_t stream) {
   if (n_entries == 0) return cudaSuccess;
   const int threads = 256;
-  const int64_t blocks = (n_entries + threads - 1) / threads;
+  const int64_t blocks = ((n_entries + 3) / 4 + threads - 1) / threads;
   ranges_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(n_entries, key, ranges);
   return cudaGetLastError();
 }
