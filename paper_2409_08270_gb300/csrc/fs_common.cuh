@@ -198,6 +198,87 @@ __device__ __forceinline__ f2 f2_sqrt(f2 a) {
   return fast_two_sum(s, c);
 }
 
+// Two float pairs side by side, for the packed FP32 instructions (FADD2,
+// FMUL2, FFMA2): each lane runs exactly the operation sequence of the scalar
+// f2 functions above, so results are bit-identical to them, in about half the
+// issued instructions.  x - y is formed as fma(y, -1, x), which rounds like
+// the subtraction itself.
+struct f2x2 {
+  float2 hi, lo;
+};
+
+__device__ __forceinline__ f2x2 f2x2_pack(f2 x, f2 y) {
+  return {make_float2(x.hi, y.hi), make_float2(x.lo, y.lo)};
+}
+__device__ __forceinline__ f2 f2x2_first(const f2x2& v) { return {v.hi.x, v.lo.x}; }
+__device__ __forceinline__ f2 f2x2_second(const f2x2& v) { return {v.hi.y, v.lo.y}; }
+
+__device__ __forceinline__ float2 add2(float2 x, float2 y) { return __fadd2_rn(x, y); }
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) {
+  return __ffma2_rn(y, make_float2(-1.f, -1.f), x);
+}
+__device__ __forceinline__ float2 neg2(float2 x) { return make_float2(-x.x, -x.y); }
+
+__device__ __forceinline__ f2x2 f2x2_add(const f2x2& a, const f2x2& b) {
+  // two_sum of the hi parts
+  const float2 s = add2(a.hi, b.hi);
+  const float2 bb = sub2(s, a.hi);
+  const float2 e0 = add2(sub2(a.hi, sub2(s, bb)), sub2(b.hi, bb));
+  const float2 e = add2(add2(e0, a.lo), b.lo);
+  // fast_two_sum(s, e)
+  const float2 r = add2(s, e);
+  return {r, sub2(e, sub2(r, s))};
+}
+
+__device__ __forceinline__ f2x2 f2x2_neg(const f2x2& a) { return {neg2(a.hi), neg2(a.lo)}; }
+__device__ __forceinline__ f2x2 f2x2_sub(const f2x2& a, const f2x2& b) {
+  return f2x2_add(a, f2x2_neg(b));
+}
+
+__device__ __forceinline__ f2x2 f2x2_mul(const f2x2& a, const f2x2& b) {
+  // two_prod of the hi parts, then the cross terms
+  const float2 p = __fmul2_rn(a.hi, b.hi);
+  float2 e = __ffma2_rn(a.hi, b.hi, neg2(p));
+  e = __ffma2_rn(a.hi, b.lo, __ffma2_rn(a.lo, b.hi, e));
+  const float2 r = add2(p, e);
+  return {r, sub2(e, sub2(r, p))};
+}
+
+__device__ __forceinline__ f2x2 f2x2_fma(const f2x2& a, const f2x2& b, const f2x2& c) {
+  return f2x2_add(f2x2_mul(a, b), c);
+}
+
+// f2_dot3_add for two rows at once: lane r computes
+// sum_k a_r,k * x_k + c_r with the scalar function's operation sequence.
+__device__ __forceinline__ f2x2 f2x2_dot3_add(const float* a0_hi, const float* a0_lo,
+                                              const float* a1_hi, const float* a1_lo, float x0,
+                                              float x1, float x2, float2 c_hi, float2 c_lo) {
+  const float2 X0 = make_float2(x0, x0), X1 = make_float2(x1, x1), X2 = make_float2(x2, x2);
+  const float2 h0 = make_float2(a0_hi[0], a1_hi[0]), h1 = make_float2(a0_hi[1], a1_hi[1]);
+  const float2 h2 = make_float2(a0_hi[2], a1_hi[2]);
+  const float2 l0 = make_float2(a0_lo[0], a1_lo[0]), l1 = make_float2(a0_lo[1], a1_lo[1]);
+  const float2 l2 = make_float2(a0_lo[2], a1_lo[2]);
+  const float2 p0 = __fmul2_rn(h0, X0), p1 = __fmul2_rn(h1, X1), p2 = __fmul2_rn(h2, X2);
+  const float2 q0 = __ffma2_rn(h0, X0, neg2(p0)), q1 = __ffma2_rn(h1, X1, neg2(p1));
+  const float2 q2 = __ffma2_rn(h2, X2, neg2(p2));
+  float2 err = __ffma2_rn(l0, X0, q0);
+  err = add2(err, __ffma2_rn(l1, X1, q1));
+  err = add2(err, __ffma2_rn(l2, X2, q2));
+  // two_sum(p0, p1), two_sum(s, p2), two_sum(s, c_hi), each error into err
+  float2 s = add2(p0, p1);
+  float2 bb = sub2(s, p0);
+  err = add2(err, add2(sub2(p0, sub2(s, bb)), sub2(p1, bb)));
+  float2 s2 = add2(s, p2);
+  bb = sub2(s2, s);
+  err = add2(err, add2(sub2(s, sub2(s2, bb)), sub2(p2, bb)));
+  float2 s3 = add2(s2, c_hi);
+  bb = sub2(s3, s2);
+  err = add2(err, add2(sub2(s2, sub2(s3, bb)), sub2(c_hi, bb)));
+  err = add2(err, c_lo);
+  const float2 r = add2(s3, err);
+  return {r, sub2(err, sub2(r, s3))};
+}
+
 __device__ __forceinline__ bool f2_lt(f2 a, f2 b) {
   return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
 }

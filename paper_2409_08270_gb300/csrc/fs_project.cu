@@ -132,8 +132,12 @@ __device__ __forceinline__ uint16_t f2_to_half_rn(f2 x) {
 
 // One thread per Gaussian; it projects the Gaussian into every view of the
 // batch so the scene is read once per batch.  rec16 != NULL: the record is
-// written in the reduced-precision form instead (rec is not written).
-__global__ void __launch_bounds__(256, 4) project_kernel(
+// written in the reduced-precision form instead (rec is not written).  The
+// paired float-pair quantities (the two rows of the Jacobian-rotation product,
+// the two rows of T Sigma3D, the x and y halves of the pinhole map, the rows
+// of W) run in packed FP32 (f2x2), bit-identical to the scalar form.  Three
+// blocks per SM (80 registers) spill less than four.
+__global__ void __launch_bounds__(256, 3) project_kernel(
     int64_t n, int n_views, const ViewParams* __restrict__ views_g,
     const float4* __restrict__ pos_op, const float4* __restrict__ cov3,
     ProjRecord* __restrict__ rec, CompactRecord* __restrict__ rec16, Footprint* __restrict__ foot,
@@ -158,8 +162,10 @@ __global__ void __launch_bounds__(256, 4) project_kernel(
   for (int v = 0; v < n_views; ++v) {
     const ViewParams& vp = views[v];
     const int64_t slot = static_cast<int64_t>(v) * n + i;
-    const f2 tx = f2_dot3_add(vp.R_hi + 0, vp.R_lo + 0, po.x, po.y, po.z, vp.t_hi[0], vp.t_lo[0]);
-    const f2 ty = f2_dot3_add(vp.R_hi + 3, vp.R_lo + 3, po.x, po.y, po.z, vp.t_hi[1], vp.t_lo[1]);
+    const f2x2 txy = f2x2_dot3_add(vp.R_hi + 0, vp.R_lo + 0, vp.R_hi + 3, vp.R_lo + 3, po.x, po.y,
+                                   po.z, make_float2(vp.t_hi[0], vp.t_hi[1]),
+                                   make_float2(vp.t_lo[0], vp.t_lo[1]));
+    const f2 tx = f2x2_first(txy), ty = f2x2_second(txy);
     const f2 tz = f2_dot3_add(vp.R_hi + 6, vp.R_lo + 6, po.x, po.y, po.z, vp.t_hi[2], vp.t_lo[2]);
     bool visible = opaque_enough && f2_greater(tz, vp.near_hi, vp.near_lo);
     uint32_t count = 0;
@@ -179,36 +185,41 @@ __global__ void __launch_bounds__(256, 4) project_kernel(
     if (visible) {
       const f2 ux = f2_div(tx, tz), uy = f2_div(ty, tz);
       const f2 fx = {vp.fx_hi, vp.fx_lo}, fy = {vp.fy_hi, vp.fy_lo};
-      const f2 mx = f2_add(f2_mul(fx, ux), f2{vp.cx_hi, vp.cx_lo});
-      const f2 my = f2_add(f2_mul(fy, uy), f2{vp.cy_hi, vp.cy_lo});
+      // the x and y halves of the pinhole map run side by side (f2x2)
+      const f2x2 fxy = f2x2_pack(fx, fy);
+      const f2x2 mxy = f2x2_add(f2x2_mul(fxy, f2x2_pack(ux, uy)),
+                                f2x2_pack(f2{vp.cx_hi, vp.cx_lo}, f2{vp.cy_hi, vp.cy_lo}));
+      const f2 mx = f2x2_first(mxy), my = f2x2_second(mxy);
       depth = tz.hi;
       depth_l = tz.lo;
       const f2 iz = f2_div(f2_from(1.f), tz);
-      const f2 j0 = f2_mul(fx, iz), j1 = f2_mul(fy, iz);
+      const f2x2 J = f2x2_mul(fxy, f2x2_pack(iz, iz));  // (fx / z, fy / z)
       const f2 uxc = f2_clamp(ux, vp.limx_hi, vp.limx_lo);
       const f2 uyc = f2_clamp(uy, vp.limy_hi, vp.limy_lo);
-      // rows of J W: T0 = fx/z (W0 - ux W2), T1 = fy/z (W1 - uy W2)
-      f2 T0[3], T1[3];
+      const f2x2 U = f2x2_pack(uxc, uyc);
+      // rows of J W side by side: T[k] = (T0[k], T1[k]) with
+      // T0 = fx/z (W0 - ux W2), T1 = fy/z (W1 - uy W2)
+      f2x2 T[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const f2 w0 = {vp.R_hi[k], vp.R_lo[k]}, w1 = {vp.R_hi[3 + k], vp.R_lo[3 + k]};
         const f2 w2 = {vp.R_hi[6 + k], vp.R_lo[6 + k]};
-        T0[k] = f2_mul(j0, f2_sub(w0, f2_mul(uxc, w2)));
-        T1[k] = f2_mul(j1, f2_sub(w1, f2_mul(uyc, w2)));
+        T[k] = f2x2_mul(J, f2x2_sub(f2x2_pack(w0, w1), f2x2_mul(U, f2x2_pack(w2, w2))));
       }
-      // Sigma' = T Sigma3D T^T
-      f2 a = f2_from(0.f), b = f2_from(0.f), c = f2_from(0.f);
+      // Sigma' = T Sigma3D T^T: M = (m0, m1) = rows of T Sigma3D, then
+      // (a, c) += (m0 T0[j], m1 T1[j]) side by side and b += m0 T1[j]
+      f2x2 ac = f2x2_pack(f2_from(0.f), f2_from(0.f));
+      f2 a, b = f2_from(0.f), c;
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        f2 m0 = f2_mul(T0[0], S[0][j]), m1 = f2_mul(T1[0], S[0][j]);
-        m0 = f2_fma(T0[1], S[1][j], m0);
-        m1 = f2_fma(T1[1], S[1][j], m1);
-        m0 = f2_fma(T0[2], S[2][j], m0);
-        m1 = f2_fma(T1[2], S[2][j], m1);
-        a = f2_fma(m0, T0[j], a);
-        b = f2_fma(m0, T1[j], b);
-        c = f2_fma(m1, T1[j], c);
+        f2x2 M = f2x2_mul(T[0], f2x2_pack(S[0][j], S[0][j]));
+        M = f2x2_fma(T[1], f2x2_pack(S[1][j], S[1][j]), M);
+        M = f2x2_fma(T[2], f2x2_pack(S[2][j], S[2][j]), M);
+        ac = f2x2_fma(M, T[j], ac);
+        b = f2_fma(f2x2_first(M), f2x2_second(T[j]), b);
       }
+      a = f2x2_first(ac);
+      c = f2x2_second(ac);
       a = f2_add(a, f2_from(kLowPass));
       c = f2_add(c, f2_from(kLowPass));
       const f2 det = f2_sub(f2_mul(a, c), f2_mul(b, b));
@@ -238,8 +249,10 @@ __global__ void __launch_bounds__(256, 4) project_kernel(
       const f2 hl = {kHalfLog2eHi, kHalfLog2eLo};
       const f2 k1 = f2_sqrt(f2_div(hl, lam1));
       const f2 k2 = f2_sqrt(f2_div(hl, lam2));
-      const f2 W00 = f2_mul(ex, k1), W01 = f2_mul(ey, k1);
-      const f2 W10 = f2_mul(f2_neg(ey), k2), W11 = f2_mul(ex, k2);
+      const f2x2 W0 = f2x2_mul(f2x2_pack(ex, ey), f2x2_pack(k1, k1));
+      const f2x2 W1 = f2x2_mul(f2x2_pack(f2_neg(ey), ex), f2x2_pack(k2, k2));
+      const f2 W00 = f2x2_first(W0), W01 = f2x2_second(W0);
+      const f2 W10 = f2x2_first(W1), W11 = f2x2_second(W1);
       R.w_hi = make_float4(W00.hi, W01.hi, W10.hi, W11.hi);
       R.w_lo = make_float4(W00.lo, W01.lo, W10.lo, W11.lo);
       R.m = make_float4(mx.hi, my.hi, mx.lo, my.lo);
