@@ -175,7 +175,13 @@ struct fs_ctx {
   bool recheck_reproject = false;
   bool compact = false;  // reduced-precision records (FP16 whitening matrix, FP32 mean)
   DevBuf dkey, rk_flag, rk_offs, rk_F, rk_map, rk_R, rk_Rb;
-  DevBuf key_range;  // min / max visible depth key of the current batch
+  DevBuf key_range;  // min / max visible depth key of the batch (two slots, by batch parity)
+  // the next batch's projection runs on a side stream while the current
+  // batch bins and blends (resident projections only); its depth keys go to
+  // the second set of sort buffers
+  DevBuf key_a2, val_a2, key_b2, val_b2;
+  cudaStream_t side = nullptr;
+  cudaEvent_t prologue_done[2] = {nullptr, nullptr}, buffers_free = nullptr;
   DevBuf lb_tmp;     // look-back words of the fused binning
   // the main pass's tile lists, kept for the re-check (see kept_layout)
   bool kl_valid = false;
@@ -205,7 +211,8 @@ DevBuf* const* workspace_bufs(fs_ctx* c, size_t* count) {
                     &c->mask_stage, &c->table_tmp, &c->table32_tmp, &c->bits_tmp,
                     &c->label_tmp, &c->margin_tmp, &c->dkey, &c->rk_flag, &c->rk_offs,
                     &c->rk_F, &c->rk_map, &c->rk_R, &c->rk_Rb, &c->kl_ranges, &c->kl_satc,
-                    &c->kl_bound, &c->key_range, &c->lb_tmp};
+                    &c->kl_bound, &c->key_range, &c->lb_tmp, &c->key_a2, &c->val_a2,
+                    &c->key_b2, &c->val_b2};
   for (DevBuf* b : list) bufs[k++] = b;
   *count = k;
   return bufs;
@@ -277,8 +284,8 @@ fs_status fs_create(fs_ctx** out, int32_t device, const fs_options* opt) {
   c->compact = opt && opt->record_precision == FS_F16;
   DeviceGuard g(device);
   fs_status st;
-  if ((st = c->views.ensure(sizeof(fs::ViewParams) * fs::kMaxViewsPerBatch, "views")) != FS_OK ||
-      (st = c->views_host.ensure(sizeof(fs::ViewParams) * fs::kMaxViewsPerBatch)) != FS_OK ||
+  if ((st = c->views.ensure(sizeof(fs::ViewParams) * 2 * fs::kMaxViewsPerBatch, "views")) != FS_OK ||
+      (st = c->views_host.ensure(sizeof(fs::ViewParams) * 2 * fs::kMaxViewsPerBatch)) != FS_OK ||
       (st = c->total.ensure(256, "total")) != FS_OK ||
       (st = c->total_host.ensure(256)) != FS_OK ||
       (st = c->counters.ensure(sizeof(unsigned long long) * fs::kNumCounters, "counters")) != FS_OK ||
@@ -302,13 +309,18 @@ fs_status fs_destroy(fs_ctx* c) {
                     &c->sort_tmp, &c->scan_tmp, &c->total, &c->counters, &c->mask_stage,
                     &c->table_tmp, &c->table32_tmp, &c->bits_tmp, &c->label_tmp, &c->margin_tmp,
                     &c->dkey, &c->rk_flag, &c->rk_offs, &c->rk_F, &c->rk_map, &c->rk_R,
-                    &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_bound, &c->key_range, &c->lb_tmp};
+                    &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_bound, &c->key_range, &c->lb_tmp,
+                    &c->key_a2, &c->val_a2, &c->key_b2, &c->val_b2};
   for (DevBuf& b : c->kl_val) b.release();
   for (DevBuf* b : bufs) b->release();
   c->views_host.release();
   c->total_host.release();
   c->counters_host.release();
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->prologue_done)
+    if (e) cudaEventDestroy(e);
+  if (c->buffers_free) cudaEventDestroy(c->buffers_free);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
   return FS_OK;
 }
@@ -467,15 +479,15 @@ fs_status stage_masks(fs_ctx* c, const fs_camera* cams, int32_t V, const void* c
   return FS_OK;
 }
 
-// The view parameters of views [v0, v0 + nb) (host copy in c->views_host).
+// The view parameters of views [v0, v0 + nb), written to the host array vh.
 struct BatchLayout {
   int total_tiles = 0;
   int max_tiles = 0;
   int64_t pixels = 0;
 };
 
-BatchLayout layout_batch(fs_ctx* c, const fs_camera* cams, int32_t v0, int nb) {
-  fs::ViewParams* vh = c->views_host.as<fs::ViewParams>();
+BatchLayout layout_batch(fs_ctx* c, fs::ViewParams* vh, const fs_camera* cams, int32_t v0,
+                         int nb) {
   BatchLayout L;
   for (int k = 0; k < nb; ++k) {
     fill_view(cams[v0 + k], &vh[k]);
@@ -636,6 +648,22 @@ fs_status kept_layout(fs_ctx* c, const fs_camera* cams, int32_t V, int vb, int c
   return FS_OK;
 }
 
+// The side stream of the batch overlap (created on first use, on the
+// context's device, which is current here).
+fs_status ensure_side_stream(fs_ctx* c) {
+  if (c->side) return FS_OK;
+  FS_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
+  return FS_OK;
+}
+
+fs_status ensure_prologue_events(fs_ctx* c) {
+  for (cudaEvent_t& e : c->prologue_done)
+    if (!e) FS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+  if (!c->buffers_free)
+    FS_CUDA(cudaEventCreateWithFlags(&c->buffers_free, cudaEventDisableTiming), "cudaEventCreate");
+  return FS_OK;
+}
+
 fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t V,
                           const void* const* masks, int32_t mask_dtype, int32_t mask_memory,
                           int32_t E, void* table, int32_t table_dtype, bool keep,
@@ -651,11 +679,77 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
   FS_TRY(stage_masks(c, cams, V, masks, mask_dtype, mask_memory, stream));
   if (keep) FS_TRY(kept_layout(c, cams, V, vb, chunks));
 
-  fs::ViewParams* vh = c->views_host.as<fs::ViewParams>();
   unsigned long long* ctr = c->counters.as<unsigned long long>();
+  const int batches = static_cast<int>((V + vb - 1) / vb);
+  // With every view's projection resident (keep), batch b + 1's projection
+  // writes storage of its own: it is launched on a side stream as soon as
+  // batch b is sorted and runs while batch b bins and blends.  Batches
+  // alternate between two sets of depth-sort buffers, view arrays and
+  // key-range slots (by parity).  Without the memory for the second set the
+  // batches run one after another.
+  bool overlap = keep && batches > 1;
+  if (overlap) {
+    const size_t kb = static_cast<size_t>(kcap) * 4;
+    overlap = ensure_side_stream(c) == FS_OK && c->key_a2.ensure(kb, "keys") == FS_OK &&
+              c->val_a2.ensure(kb, "vals") == FS_OK && c->key_b2.ensure(kb, "keys") == FS_OK &&
+              c->val_b2.ensure(kb, "vals") == FS_OK;
+    cudaGetLastError();
+  }
+  FS_TRY(c->key_range.ensure(32, "depth key range"));
+  struct Prologue {
+    BatchLayout L;
+    fs::ViewParams* vd = nullptr;  // the batch's views on the device
+    uint32_t *key = nullptr, *val = nullptr, *key_alt = nullptr, *val_alt = nullptr;
+    const uint32_t* krh = nullptr;  // depth-key range read back to the host
+  };
+  Prologue pro[2];
+  // Batch b's views go up, every Gaussian is projected into them and the
+  // visible depth-key range is read back, all on `strm`; prologue_done[b & 1]
+  // marks the end.
+  auto launch_prologue = [&](int bb, cudaStream_t strm) -> fs_status {
+    const int q = bb & 1;
+    const int32_t w0 = bb * vb;
+    const int nbb = std::min(vb, V - w0);
+    fs::ViewParams* vhq = c->views_host.as<fs::ViewParams>() + q * fs::kMaxViewsPerBatch;
+    Prologue& pr = pro[q];
+    pr.L = layout_batch(c, vhq, cams, w0, nbb);
+    pr.vd = c->views.as<fs::ViewParams>() + q * fs::kMaxViewsPerBatch;
+    pr.key = (q ? c->key_a2 : c->key_a).as<uint32_t>();
+    pr.val = (q ? c->val_a2 : c->val_a).as<uint32_t>();
+    pr.key_alt = (q ? c->key_b2 : c->key_b).as<uint32_t>();
+    pr.val_alt = (q ? c->val_b2 : c->val_b).as<uint32_t>();
+    uint32_t* krq = c->key_range.as<uint32_t>() + 4 * q;
+    uint32_t* krhq = c->total_host.as<uint32_t>() + 4 + 4 * q;
+    pr.krh = krhq;
+    const ProjPtrs PP = proj_ptrs(c, keep, w0, n);
+    FS_CUDA(cudaMemcpyAsync(pr.vd, vhq, sizeof(fs::ViewParams) * nbb, cudaMemcpyHostToDevice,
+                            strm),
+            "view upload");
+    // project every Gaussian into the batch's views; the depth sort then
+    // takes only the bits in which the batch's visible depth keys differ
+    FS_CUDA(cudaMemsetAsync(krq, 0xFF, 4, strm), "key range");
+    FS_CUDA(cudaMemsetAsync(krq + 1, 0, 4, strm), "key range");
+    c->stats.kernel_launches += 2;
+    FS_CUDA(fs::launch_project(n, nbb, pr.vd, s->pos_op.as<float4>(), s->cov.as<float4>(),
+                               PP.rec, PP.rec16, PP.foot, PP.cnt, pr.key, pr.val, PP.dlo, krq,
+                               strm),
+            "project");
+    if (PP.dkey)
+      FS_CUDA(cudaMemcpyAsync(PP.dkey, pr.key, static_cast<size_t>(nbb) * n * 4,
+                              cudaMemcpyDeviceToDevice, strm),
+              "depth key copy");
+    FS_CUDA(cudaMemcpyAsync(krhq, krq, 8, cudaMemcpyDeviceToHost, strm), "key range readback");
+    FS_CUDA(cudaEventRecord(c->prologue_done[q], strm), "prologue event");
+    return FS_OK;
+  };
+  FS_TRY(ensure_prologue_events(c));
+  if (overlap) FS_TRY(launch_prologue(0, stream));
   for (int32_t v0 = 0, b = 0; v0 < V; v0 += vb, ++b) {
     const int nb = std::min(vb, V - v0);
-    const BatchLayout L = layout_batch(c, cams, v0, nb);
+    const int q = b & 1;
+    if (!overlap) FS_TRY(launch_prologue(b, stream));
+    const Prologue& pr = pro[q];
+    const BatchLayout L = pr.L;
     const int total_tiles = L.total_tiles, max_tiles = L.max_tiles;
     const int tile_bits = std::max(1, ceil_log2(total_tiles));
     const int64_t k_total = static_cast<int64_t>(nb) * n;
@@ -665,11 +759,9 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     const size_t subsat_bytes = static_cast<size_t>((4 * total_tiles + 63) / 64) * 8;
     FS_TRY(c->subsat.ensure(subsat_bytes, "sub-tile flags"));
     FS_TRY(c->ranges.ensure(static_cast<size_t>(total_tiles) * 8, "tile ranges"));
-    fs::ViewParams* vd = c->views.as<fs::ViewParams>();
+    fs::ViewParams* vd = pr.vd;
     float* state = c->state.as<float>();
     uint64_t* sat = c->sat.as<uint64_t>();
-    FS_CUDA(cudaMemcpyAsync(vd, vh, sizeof(fs::ViewParams) * nb, cudaMemcpyHostToDevice, stream),
-            "view upload");
     const ProjPtrs P = proj_ptrs(c, keep, v0, n);
     uint8_t* satc = nullptr;
     if (keep) {
@@ -677,25 +769,10 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
       FS_CUDA(cudaMemsetAsync(satc, 0xFF, static_cast<size_t>(total_tiles), stream),
               "saturation chunks");
     }
-
-    // project every Gaussian into the batch's views, sort by depth (only the
-    // bits in which the batch's visible depth keys differ)
-    FS_TRY(c->key_range.ensure(16, "depth key range"));
-    uint32_t* kr = c->key_range.as<uint32_t>();
-    FS_CUDA(cudaMemsetAsync(kr, 0xFF, 4, stream), "key range");
-    FS_CUDA(cudaMemsetAsync(kr + 1, 0, 4, stream), "key range");
-    c->stats.kernel_launches += 2;
-    FS_CUDA(fs::launch_project(n, nb, vd, s->pos_op.as<float4>(), s->cov.as<float4>(), P.rec,
-                               P.rec16, P.foot, P.cnt, c->key_a.as<uint32_t>(),
-                               c->val_a.as<uint32_t>(), P.dlo, kr, stream),
-            "project");
-    if (P.dkey)
-      FS_CUDA(cudaMemcpyAsync(P.dkey, c->key_a.p, static_cast<size_t>(k_total) * 4,
-                              cudaMemcpyDeviceToDevice, stream),
-              "depth key copy");
-    uint32_t* krh = c->total_host.as<uint32_t>() + 4;
-    FS_CUDA(cudaMemcpyAsync(krh, kr, 8, cudaMemcpyDeviceToHost, stream), "key range readback");
-    FS_CUDA(cudaStreamSynchronize(stream), "key range readback");
+    // the batch's projection (and its key range on the host) is complete
+    FS_CUDA(cudaEventSynchronize(c->prologue_done[q]), "key range readback");
+    if (overlap) FS_CUDA(cudaStreamWaitEvent(stream, c->prologue_done[q], 0), "prologue wait");
+    const uint32_t* krh = pr.krh;
     uint32_t kmin = 0, span = 0;
     int key_bits = 0;
     if (krh[0] <= krh[1]) {
@@ -705,14 +782,20 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     }
     c->stats.kernel_launches += radix_launches(k_total, key_bits);
     bool alt = false;
-    FS_CUDA(fs::radix_sort_pairs(c->key_a.as<uint32_t>(), c->val_a.as<uint32_t>(),
-                                 c->key_b.as<uint32_t>(), c->val_b.as<uint32_t>(), k_total,
-                                 key_bits, c->sort_tmp.p, &alt, stream, kmin, span),
+    FS_CUDA(fs::radix_sort_pairs(pr.key, pr.val, pr.key_alt, pr.val_alt, k_total, key_bits,
+                                 c->sort_tmp.p, &alt, stream, kmin, span),
             "depth sort");
-    uint32_t* sorted_key = alt ? c->key_b.as<uint32_t>() : c->key_a.as<uint32_t>();
-    uint32_t* sorted_val = alt ? c->val_b.as<uint32_t>() : c->val_a.as<uint32_t>();
+    uint32_t* sorted_key = alt ? pr.key_alt : pr.key;
+    uint32_t* sorted_val = alt ? pr.val_alt : pr.val;
     FS_CUDA(fs::launch_depth_tie_fix(k_total, n, sorted_key, sorted_val, P.dlo, stream),
             "depth ties");
+    if (overlap && b + 1 < batches) {
+      // batch b + 1's buffers (the other parity) were last read by batch
+      // b - 1's chunks, which `stream` has passed here
+      FS_CUDA(cudaEventRecord(c->buffers_free, stream), "buffers event");
+      FS_CUDA(cudaStreamWaitEvent(c->side, c->buffers_free, 0), "buffers wait");
+      FS_TRY(launch_prologue(b + 1, c->side));
+    }
     uint64_t* subsat = c->subsat.as<uint64_t>();
     FS_CUDA(cudaMemsetAsync(sat, 0, sat_bytes, stream), "tile flags clear");
     FS_CUDA(cudaMemsetAsync(subsat, 0, subsat_bytes, stream), "sub-tile flags clear");
@@ -874,7 +957,7 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
   unsigned long long* ctr_h = c->counters_host.as<unsigned long long>();
   for (int32_t v0 = 0, b = 0; v0 < V; v0 += vb, ++b) {
     const int nb = std::min(vb, V - v0);
-    const BatchLayout L = layout_batch(c, cams, v0, nb);
+    const BatchLayout L = layout_batch(c, vh, cams, v0, nb);
     const int total_tiles = L.total_tiles;
     const size_t sat_bytes = static_cast<size_t>((total_tiles + 63) / 64) * 8;
     FS_TRY(c->sat.ensure(sat_bytes, "tile flags"));

@@ -5,6 +5,8 @@
 // is the classic three-step pass (per-block digit histogram, scan of the
 // histogram in digit-major order, stable scatter).  No step waits on another
 // block.
+#include <atomic>
+
 #include "fs_internal.h"
 
 namespace fs {
@@ -310,13 +312,18 @@ cudaError_t radix_pass(const uint32_t* src_k, const uint32_t* src_v, uint32_t* d
                        uint32_t span, uint32_t* hist, void* scan_tmp, cudaStream_t stream) {
   constexpr int kRad = 1 << DB;
   const size_t smem = sizeof(ScatterSmem<DB>);
-  static bool attr_set = false;  // dynamic shared memory above 48 KB needs the opt-in
-  if (!attr_set) {
+  // dynamic shared memory above 48 KB needs the opt-in, once per device
+  static std::atomic<uint64_t> attr_set{0};
+  int dev = 0;
+  cudaError_t e0 = cudaGetDevice(&dev);
+  if (e0 != cudaSuccess) return e0;
+  const uint64_t bit = 1ull << (dev & 63);
+  if (!(attr_set.load() & bit)) {
     cudaError_t e = cudaFuncSetAttribute(radix_scatter_kernel<DB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.fetch_or(bit);
   }
   radix_hist_kernel<DB><<<static_cast<unsigned>(nb), kThreads, 0, stream>>>(src_k, n, shift, nb,
                                                                               kmin, span, hist);
