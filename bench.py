@@ -214,6 +214,25 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# multi-rank reduction (one process per GPU; replicas, no data-path collective)
+# ---------------------------------------------------------------------------
+
+def max_over_ranks(x, world, device):
+    """The largest per-rank value over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gpix(world, pixels_per_rank, steps, total_ms):
+    """Whole-job throughput: every rank's pixels over the slowest rank's time."""
+    return world * pixels_per_rank * steps / (total_ms * 1e-3) / 1e9
+
+
+# ---------------------------------------------------------------------------
 # the CUDA arm
 # ---------------------------------------------------------------------------
 
@@ -286,14 +305,11 @@ def run_flashsplat(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    total_ms = sum(ms_steps)
+    total_ms = max_over_ranks(sum(ms_steps), world, dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
-    gpix = world * w.pixels * args.steps / (total_ms * 1e-3) / 1e9
+    gpix = whole_job_gpix(world, w.pixels, args.steps, total_ms)
 
     # ---- end to end through the C ABI: host masks in, host outputs out --------
     e2e = None
@@ -328,17 +344,13 @@ def run_flashsplat(args, rank, world, local_rank):
             e2e_step()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        e2e_ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
         h2d = sum(m.numel() * m.element_size() for m in host_masks)
         d2h = n * (8 + 4 + 4)
         # the result is on the host: check it once (labels in range, some members)
         lab = h_label.numpy()
         assert lab.min() >= -1 and lab.max() < w.E
-        e2e = {"value": world * w.pixels * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+        e2e = {"value": whole_job_gpix(world, w.pixels, args.steps, e2e_ms), "unit": UNIT,
                "ms_per_step": e2e_ms / args.steps, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "api": "fs_solve (host masks, host outputs)"}
 
