@@ -444,7 +444,8 @@ def run_reference(args, rank, world):
     import oracle
     oracle.build()
     w = workload(args)
-    cfg = config_of(w, args, {"sample": "1 view per step (762,048 pixels), all Gaussians"})
+    px1 = int(w.masks[0].size)
+    cfg = config_of(w, args, {"sample": f"1 view per step ({px1:,} pixels), all Gaussians"})
     for _ in range(args.warmup):
         oracle_sample(w, 1)
     pix, tsum = 0, 0.0
@@ -454,7 +455,8 @@ def run_reference(args, rank, world):
         tsum += dt
     val = pix / tsum / 1e9
     ms = tsum / args.steps * 1e3
-    sample = "1 of 100 views per step (762,048 pixels); FP64 oracle over all 1M Gaussians"
+    sample = (f"1 of {len(w.cams)} views per step ({px1:,} pixels); FP64 oracle over all "
+              f"{w.n:,} Gaussians")
     return {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
