@@ -54,8 +54,12 @@ def parse():
     ap.add_argument("--impl", default="flashsplat", choices=["flashsplat", "reference"])
     ap.add_argument("--views-per-batch", type=int, default=0)
     ap.add_argument("--depth-chunks", type=int, default=0)
-    ap.add_argument("--views", type=int, default=100)
-    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--workload", default="binary", choices=["binary", "multi"],
+                    help="binary: 1M Gaussians, 100 forward-facing views 1008x756, uint8 "
+                         "masks (default); multi: 3M Gaussians in 32 instances, 200 orbit "
+                         "views 1256x828, int32 id masks, 33 labels")
+    ap.add_argument("--views", type=int, default=0, help="0: the workload's own count")
+    ap.add_argument("--n", type=int, default=0, help="0: the workload's own count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-views", type=int, default=12)
@@ -81,12 +85,20 @@ def synth_mod():
 
 
 def workload(args):
-    return synth_mod().binary_scene(n=args.n, views=args.views)
+    if args.workload == "multi":
+        return synth_mod().multi_scene(n=args.n or 3_000_000, views=args.views or 200)
+    return synth_mod().binary_scene(n=args.n or 1_000_000, views=args.views or 100)
 
 
 def config_of(w, args, extra=None):
-    c = {"workload": f"binary segmentation, {w.n} Gaussians / 20 clusters, {len(w.cams)} views "
-                     f"{w.cams[0]['width']}x{w.cams[0]['height']}, uint8 masks, gamma {w.gamma}",
+    if w.name == "multi":
+        what = (f"multi-instance segmentation, {w.n} Gaussians / {w.E - 1} instances, "
+                f"{len(w.cams)} orbit views {w.cams[0]['width']}x{w.cams[0]['height']}, int32 "
+                f"id masks, {w.E} labels, gamma {w.gamma}")
+    else:
+        what = (f"binary segmentation, {w.n} Gaussians / 20 clusters, {len(w.cams)} views "
+                f"{w.cams[0]['width']}x{w.cams[0]['height']}, uint8 masks, gamma {w.gamma}")
+    c = {"workload": what,
          "gaussians": w.n, "views": len(w.cams), "width": w.cams[0]["width"],
          "height": w.cams[0]["height"], "labels": w.E, "gamma": w.gamma,
          "pixels_per_scene": w.pixels, "table": "fp32 [N x E] (FP64 cross-view sum)",
@@ -353,9 +365,10 @@ def run_flashsplat(args, rank, world, local_rank):
                                                   h_margin.data_ptr())
         cams = fsb.make_cameras(w.cams)
         mptr = [m.data_ptr() for m in host_masks]
+        mask_dt = fsb.FS_I32 if w.masks[0].dtype == np.int32 else fsb.FS_U8
 
         def e2e_step():
-            fsb.fs_solve(solver.ctx, solver.scene, cams, mptr, fsb.FS_U8, fsb.FS_MEM_HOST, w.E,
+            fsb.fs_solve(solver.ctx, solver.scene, cams, mptr, mask_dt, fsb.FS_MEM_HOST, w.E,
                          float(w.gamma), res, stream.cuda_stream)
             fsb.fs_synchronize(solver.ctx, stream.cuda_stream)
 
