@@ -8,7 +8,6 @@ namespace fs {
 
 constexpr int kTile = 16;                 // 16x16 pixel tiles (Sec. 3.1)
 constexpr int kTilePixels = kTile * kTile;
-constexpr int kBlendThreads = 256;        // one thread per tile pixel
 
 // Thresholds of the compositing rule (Sec. 3.1 Eq. 1 with the rasteriser's
 // conventions): alpha below 1/255 is skipped, alpha is clamped to 0.99, and a
