@@ -36,14 +36,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "s per scene solve & Gpix/s of α·T accumulation; batched BF16 vs plain FP32"
 UNIT = "Gpix/s"
-FLOPS_PER_PAIR = 19   # FP32 flops of one (pixel, Gaussian) evaluation, FMA = 2
+FLOPS_PER_PAIR = 19   # FP32 flops of one (pixel, Gaussian) compositing step, FMA = 2
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of blend_kernel per evaluated pair, from one ncu
-# capture of the current kernel: the six blend launches of an 8-view solve of
-# this scene read and wrote 195.7 MB for 636.1 M pairs.  Scaled by pairs to the
-# launches timed here (the traffic grows with the pairs: records, masks and the
-# table are gathered per staged entry).  Set to None when the kernel changes.
-BLEND_DRAM_BYTES_PER_PAIR = 195.7e6 / 636.1e6
+# DRAM bytes (read + write) of blend_kernel per work unit (census pair), from
+# one ncu capture of the current kernel, scaled by the units of the launches
+# timed here.  None until the current kernel has been captured.
+BLEND_DRAM_BYTES_PER_PAIR = None
 
 
 def parse():
@@ -308,7 +306,6 @@ def run_flashsplat(args, rank, world, local_rank):
         ms_steps.append(e0.elapsed_time(e1))
         blend_ms += st.blend_ms
         blend_launches += st.blend_launches
-        pairs += st.pairs
         entries += st.list_entries
         staged += st.staged_entries
         rechecked += st.rechecked
@@ -322,6 +319,22 @@ def run_flashsplat(args, rank, world, local_rank):
         torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
     gpix = whole_job_gpix(world, w.pixels, args.steps, total_ms)
+
+    # ---- work units of the blend: one census solve (untimed) ----------------
+    # The roofline's unit is a (pixel, Gaussian) pair with alpha >= 1/255 that
+    # the pixel's front-to-back walk reaches, its stop included -- the pairs
+    # the compositing rule of Eq. 1 must evaluate, whatever the culling.  The
+    # workload is fixed, so one census solve (a counting variant of the same
+    # kernels) gives the units of every timed step.
+    csolver = fsb.Solver(gaussians, device=local_rank, views_per_batch=args.views_per_batch,
+                         depth_chunks=args.depth_chunks, recheck_margin=args.recheck_margin,
+                         record_precision=fsb.FS_F16 if args.precision == "fp16" else 0,
+                         census=True)
+    csolver.solve(w.cams, dmasks, w.E, w.gamma, sync=False)
+    cst = fsb.fs_synchronize(csolver.ctx, stream.cuda_stream)
+    census_pairs, census_evaluated = int(cst.census_pairs), int(cst.pairs)
+    csolver.close()
+    pairs = census_pairs * args.steps
 
     # ---- argmax-only re-solve for a new gamma on the resident table ----------
     # (Sec. 4.2: the assignment alone is re-run when only the bias changes)
@@ -403,9 +416,12 @@ def run_flashsplat(args, rank, world, local_rank):
                 "frac": (achieved / peak_tflops) if achieved else None,
                 "traffic": (BLEND_DRAM_BYTES_PER_PAIR * pairs / max(1, blend_launches)
                             if BLEND_DRAM_BYTES_PER_PAIR and blend_launches else None),
-                "traffic_unit": "DRAM bytes per launch (ncu, 8-view capture scaled by pairs)",
+                "traffic_unit": "DRAM bytes per launch (ncu capture scaled by work units)",
                 "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_clk:.0f} MHz",
-                "pairs_per_step": pairs // max(1, args.steps),
+                "unit_of_work": "pair with alpha >= 1/255 reached before the pixel's stop "
+                                "(stop included), counted by a census solve",
+                "pairs_per_step": census_pairs,
+                "evaluated_pairs_per_step": census_evaluated,
                 "list_entries_per_step": entries // max(1, args.steps),
                 "staged_entries_per_step": staged // max(1, args.steps),
                 "flops_per_pair": FLOPS_PER_PAIR,

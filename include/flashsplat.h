@@ -95,7 +95,13 @@ typedef struct fs_options {
    * cut), and alpha = o 2^-|W (p - m)|^2 is evaluated from those rounded
    * values (blending in FP32, table in FP64). */
   int32_t record_precision;
-  int32_t reserved[10];
+  /* non-zero: the blend also counts, in fs_stats.pairs and
+   * fs_stats.census_pairs, the (pixel, Gaussian) pairs it evaluates and the
+   * pairs that take part in the compositing (alpha >= 1/255, reached before
+   * the pixel stops, the stopping one included).  A slower variant, for
+   * measurement; the results are the same. */
+  int32_t census;
+  int32_t reserved[9];
 } fs_options;
 
 /* A Gaussian scene (Sec. 3.1: G_i = {m_i, q_i, s_i, o_i}; colour unused). */
@@ -125,7 +131,7 @@ typedef struct fs_stats {
   int64_t pixels;          /* mask pixels walked */
   int64_t list_entries;    /* (tile, Gaussian) pairs binned, summed over views */
   int64_t bad_labels;      /* pixels whose label was outside [0, E) (skipped) */
-  int64_t pairs;           /* (pixel, Gaussian) pairs evaluated by the blend */
+  int64_t pairs;           /* (pixel, Gaussian) pairs evaluated by the blend (census only) */
   int64_t kernel_launches; /* kernels launched by the library */
   double blend_ms;         /* summed blend time (fs_options.time_stages), else 0 */
   int64_t blend_launches;  /* blend launches timed */
@@ -133,6 +139,8 @@ typedef struct fs_stats {
   int64_t rechecked;       /* Gaussians re-evaluated in FP64 by fs_solve */
   int64_t recheck_pairs;   /* (pixel, list entry) pairs the re-check evaluated */
   int64_t recheck_rebinned;/* view batches the re-check binned anew (see fs_solve) */
+  int64_t census_pairs;    /* pairs with alpha >= 1/255 reached before the pixel's
+                              stop, the stop included (census only) */
 } fs_stats;
 
 /* Outputs of fs_solve.  Any pointer may be NULL to skip that output. */
@@ -253,8 +261,19 @@ fs_status fs_solve(fs_ctx* ctx, const fs_scene* scene, const fs_camera* cams, in
                    float gamma, const fs_result* out, void* stream);
 
 /* Wait for the context's work on `stream` and report errors recorded by its
- * kernels (FS_CUDA_ERROR with a message).  Fills *stats if non-NULL. */
+ * kernels: FS_TIMEOUT when a bounded device-side wait gave up (the tile
+ * binning's wait for a preceding block's offset, about 2 s per poll
+ * sequence; that solve's lists are then incomplete), FS_CUDA_ERROR for an
+ * internal inconsistency.  Fills *stats if non-NULL. */
 fs_status fs_synchronize(fs_ctx* ctx, void* stream, fs_stats* stats);
+
+/* Diagnostic (no counterpart in the paper): runs the tile binning's
+ * decoupled look-back on one block whose predecessor never publishes its
+ * offset, with the wait bounded at `spins` polls (>= 1), on `device`, and
+ * returns FS_TIMEOUT when the bounded wait gives up as it must -- FS_OK would
+ * mean the bound is not enforced.  Synchronous; allocates a few hundred
+ * bytes of device memory for the duration of the call. */
+fs_status fs_check_wait_timeout(int32_t device, int32_t spins);
 
 /* ---- request server (continuous batching) -----------------------------------
  * Segmentation requests against resident scenes, served by `slots` workers
@@ -333,8 +352,14 @@ fs_status fs_server_destroy(fs_server* srv);
  * all device memory through its own pool, or a latency-critical loop that
  * cannot afford cudaMalloc/cudaFree, which may synchronise the whole device.
  *
- * fs_solve_noalloc computes what fs_solve computes (FP32 table), for small
- * scenes, without a context and without allocating anything: its working
+ * fs_solve_noalloc renders and accumulates like fs_solve and assigns with the
+ * same rule, for small scenes, without a context and without allocating
+ * anything.  Two differences from fs_solve: the views are summed with FP32
+ * atomics straight into the caller's FP32 table (no FP64 cross-view
+ * reduction), and there is no near-tie re-check -- so a Gaussian whose
+ * decision margin is within the FP32 table's error (about 1e-5 relative) may
+ * be labelled differently from fs_solve.  Pixels whose label is outside
+ * [0, E) are skipped, as in fs_solve, but not counted anywhere.  Its working
  * memory is a fixed array of about 13 MB in the library's device memory that
  * every GPU loading the library holds until the process exits.  Limits:
  * 1..FS_NOALLOC_MAX_GAUSSIANS Gaussians, views of at most FS_NOALLOC_MAX_SIDE

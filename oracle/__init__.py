@@ -70,7 +70,8 @@ def _load():
     i64, i32, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
     lib.fso_accumulate.restype = ctypes.c_int
     lib.fso_accumulate.argtypes = [i64, vp, vp, vp, vp, i32, vp, vp, vp, i32, vp, i64, i32, i32,
-                                   vp, vp, vp, vp, vp, ctypes.c_double, i32]
+                                   vp, vp, vp, vp, vp, ctypes.c_double, i32, ctypes.c_double,
+                                   ctypes.c_double, i32]
     lib.fso_pixel_lists.restype = ctypes.c_int64
     lib.fso_pixel_lists.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, i64, vp, vp, vp, vp]
     lib.fso_project_view.restype = ctypes.c_int
@@ -115,19 +116,26 @@ class Accumulation:
     n_hit: int          # contributing pairs (alpha*T > 0) on tracked rows
     n_bad_label: int    # pixels whose label is outside [0, E)
     n_unseen: int       # tracked Gaussians valid in no view
+    n_part: int = 0     # pairs taking part: alpha >= 1/255 up to and including the stop (no sel)
 
 
 def accumulate(gaussians, cams, masks, E: int, sel=None, cull_mode: int = 0,
                nthreads: int | None = None, want_t_final: bool = False,
-               event_rel: float = 1e-4, record_f16: bool = False) -> Accumulation:
+               event_rel: float = 1e-5, record_f16: bool = False, alpha_min: float = 0.0,
+               t_min: float = 0.0, tie_reverse: bool = False) -> Accumulation:
     """Contribution table of Eq. 6 / Eq. 7 in FP64.
 
     gaussians: dict with mean [N,3], quat [N,4] (w,x,y,z), scale [N,3] (linear),
     opacity [N] (activated).  cams: list of camera dicts.  masks: list of V
     integer arrays [H, W].  sel: optional sorted Gaussian indices to track.
-    event_rel: relative window around the 1/255 and 1e-4 thresholds inside
-    which a decision counts as marginal in `risk` (1e-4 suits an FP32
-    implementation; an FP64 one is compared with a far narrower window).
+    event_rel: the relative precision assumed for alpha in the implementation
+    compared with; it sets the windows inside which a decision counts as
+    marginal in `risk`: alpha within event_rel of 1/255, and T(1 - alpha)
+    within event_rel * (1 + sum alpha/(1 - alpha)) + 2^-23 per factor of 1e-4
+    (1e-5 suits an FP32 implementation; an FP64-level one is compared with a
+    far narrower window).
+    alpha_min, t_min (0: 1/255 and 1e-4) and tie_reverse (equal depths by
+    higher index first) move the rule's decisions, for tests of the bound.
     record_f16: alpha from the reduced-precision record of each (view,
     Gaussian) -- the whitening matrix rounded to FP16 and the mean to FP32 --
     evaluated in FP64 (the oracle of the reduced-precision form).
@@ -163,18 +171,19 @@ def accumulate(gaussians, cams, masks, E: int, sel=None, cull_mode: int = 0,
     risk = np.zeros((rows, E), dtype=np.float64)
     flags = np.zeros(max(rows, 1), dtype=np.uint8)
     tf = np.zeros(max(acc, 1), dtype=np.float64) if want_t_final else None
-    stats = np.zeros(4, dtype=np.int64)
+    stats = np.zeros(5, dtype=np.int64)
     if nthreads is None:
         nthreads = max(1, len(os.sched_getaffinity(0)))
     rc = lib.fso_accumulate(N, _ptr(mean), _ptr(quat), _ptr(scale), _ptr(opac), V, carr,
                             _ptr(allm), _ptr(offs), E, _ptr(sel),
                             0 if sel is None else sel.size, cull_mode, nthreads,
                             _ptr(table), _ptr(risk), _ptr(flags), _ptr(tf), _ptr(stats),
-                            float(event_rel), 1 if record_f16 else 0)
+                            float(event_rel), 1 if record_f16 else 0, float(alpha_min),
+                            float(t_min), 1 if tie_reverse else 0)
     if rc != 0:
         raise ValueError(f"fso_accumulate failed with code {rc}")
     return Accumulation(table, risk, flags[:rows], None if tf is None else tf[:acc],
-                        int(stats[0]), int(stats[1]), int(stats[2]), int(stats[3]))
+                        int(stats[0]), int(stats[1]), int(stats[2]), int(stats[3]), int(stats[4]))
 
 
 def pixel_lists(gaussians, cams, cull_mode: int = 0):

@@ -1,20 +1,27 @@
 """Assignment step of the oracle (FP64, numpy) -- test infrastructure only.
 
 Paper: FlashSplat (arXiv 2409.08270).
-  Sec. 3.2 Eq. 6        P_i = argmax_n A_n^i (binary majority vote).
+  Sec. 3.2 Eq. 2-6      the binary problem is an integer linear program whose
+                        objective is linear in the labels P_i; its minimiser
+                        takes, per Gaussian, the label with the larger
+                        accumulated contribution (Eq. 6).
   Sec. 3.2 "Regularized ILP for Noise Reduction"
-                        L1-normalise the pair, add the background bias gamma to
-                        the background entry, take the argmax.
-  Sec. 3.3 Eq. 7        object t against "others" = sum of every other label.
-  Supp. Sec. 6, Listing 1 (multi-instance optimisation)
-                        the column sum is taken once; for every object the pair
-                        (others, object) is L1-normalised per Gaussian, gamma is
-                        added to the "others" row and the argmax gives S[e, :].
+                        the background entry gets a bias gamma after both
+                        entries are L1-normalised per Gaussian.
+  Sec. 3.3 Eq. 7        for object e the two entries are A_e and "others",
+                        the sum of every other label's contribution.
 
-Readings where the paper is silent: the L1 normalisation divides by
-max(|others| + |object|, 1e-12) (the listing's normalisation with its default
-epsilon); an exact tie after the bias goes to index 0 ("not a member"), which
-is what an argmax that returns the first maximum does.
+Written here as one inequality per (object e, Gaussian i).  With S = the
+row sum of A (all entries are non-negative, so the L1 norm of the pair
+(others, A_e) is S) and the normalisation guarded by epsilon = 1e-12:
+
+    member(e, i)  <=>  A_e / n > (S - A_e) / n + gamma,   n = max(S, 1e-12)
+                  <=>  2 A_e - S > gamma * max(S, 1e-12).
+
+For S > 0 this is the biased threshold law A_e > (1 + gamma) / 2 * S, i.e.
+(1 - gamma) A_e > (1 + gamma)(S - A_e).  An exact tie is not a member (the
+argmax returns the first maximum, "others").  For S = 0 (an unseen Gaussian)
+it reads 0 > gamma * 1e-12: a member iff gamma < 0.
 """
 from __future__ import annotations
 
@@ -24,24 +31,13 @@ _EPS = 1e-12
 
 
 def assign(A: np.ndarray, gamma: float) -> np.ndarray:
-    """Segmentation matrix S (bool, [E, N]) from the table A ([N, E], FP64).
-
-    For each object e, in order: others = column_sum - A_e; normalise the pair
-    (others, A_e) by its L1 norm; add gamma to the normalised "others"; the
-    Gaussian belongs to e iff the object entry is strictly the larger.
-    """
+    """Segmentation matrix S (bool, [E, N]) from the table A ([N, E], FP64):
+    member(e, i) <=> 2 A[i, e] - S_i > gamma * max(S_i, 1e-12)."""
     A = np.asarray(A, dtype=np.float64)
-    N, E = A.shape
-    col_sum = A.sum(axis=1)                      # taken once
-    S = np.zeros((E, N), dtype=bool)
-    for e in range(E):
-        obj = A[:, e]
-        others = col_sum - obj
-        norm = np.maximum(np.abs(others) + np.abs(obj), _EPS)
-        others_n = others / norm + gamma
-        obj_n = obj / norm
-        S[e] = obj_n > others_n                  # argmax, first index wins ties
-    return S
+    s = A.sum(axis=1)                                       # S_i, taken once
+    lhs = 2.0 * A - s[:, None]
+    rhs = gamma * np.maximum(s, _EPS)[:, None]
+    return (lhs > rhs).T
 
 
 def assign_margin(A: np.ndarray, gamma: float) -> np.ndarray:

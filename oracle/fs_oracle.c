@@ -46,25 +46,40 @@
 #define FSO_NEAR_PLANE 0.2
 #define FSO_LOWPASS 0.3
 #define FSO_BIN 8
+#define FSO_CELL 32 /* coarse grid of the tracked-row mode */
 #define FSO_HALF_LOG2E 0.72134752044448170368 /* 0.5 log2(e) */
 
-/* Default near-threshold window (relative) used to flag discrete decisions
- * that a lower-precision implementation may legitimately take the other way.
- * An FP32 tile rasteriser evaluates the exponent of a thin Gaussian (0.55 px
- * wide) across a 16-px tile with an absolute error of ~2e-5, i.e. alpha to
- * ~1e-5 relative near the 1/255 cut, and T after hundreds of factors to
- * ~1e-5; the window is set an order of magnitude wider than that.  Callers
- * comparing against an FP64 evaluation pass a much narrower window (the
- * window only shapes the risk bookkeeping, never the table itself). */
-#define FSO_EVENT_REL 1e-4
+/* Near-threshold model.  An implementation in another precision computes
+ * alpha with some relative error; event_rel is the bound assumed for it
+ * (default FSO_EVENT_REL: an FP32 rasteriser's alpha is good to a few 1e-6
+ * relative near the 1/255 cut, the exponent being a sum of squares of O(1)
+ * terms).  A decision is marginal -- it may legitimately go the other way --
+ * when it lies within what that error can move:
+ *   alpha vs 1/255:      |alpha - 1/255| <= event_rel * 1/255;
+ *   T(1 - alpha) vs 1e-4: within event_rel * (1 + sum alpha/(1 - alpha)) of
+ *        1e-4 (the relative error alpha's errors carry into the product T
+ *        after the pixel's earlier factors and this one), plus 2^-23 per
+ *        factor (the product's own rounding), plus the uncertainty of T left
+ *        by earlier marginal alpha decisions (`down`).
+ * The window only shapes the risk bookkeeping, never the table itself. */
+#define FSO_EVENT_REL 1e-5
 /* Depths are view-space z in double precision; two Gaussians whose depths
  * agree to 1e-12 relative may be ordered either way by an implementation that
  * computes z with other rounding. */
 #define FSO_DEPTH_TIE_REL 1e-12
 
+/* The compositing rule's thresholds (Sec. 3.1 Eq. 1 with the rasteriser's
+ * conventions) and the near-threshold window.  Tests move the thresholds
+ * within the window to check that the risk bound covers the change. */
+typedef struct {
+  double alpha_min; /* 1/255: smaller alpha is skipped */
+  double t_min;     /* 1e-4: the pixel stops before T would fall below it */
+  double ev_rel;    /* relative precision assumed for alpha (see above) */
+} fso_rule;
+
 /* flag bits per Gaussian */
-#define FSO_FLAG_ALPHA_EDGE 1u   /* alpha within 1e-4 rel. of 1/255 */
-#define FSO_FLAG_T_EDGE 2u       /* T(1-alpha) within 1e-4 rel. of 1e-4 */
+#define FSO_FLAG_ALPHA_EDGE 1u   /* alpha within its window of 1/255 */
+#define FSO_FLAG_T_EDGE 2u       /* T(1-alpha) within its window of 1e-4 */
 #define FSO_FLAG_DEPTH_TIE 4u    /* depth within 1e-12 rel. of a neighbour */
 #define FSO_FLAG_DOWNSTREAM 8u   /* after an event in the same pixel */
 
@@ -238,10 +253,13 @@ typedef struct {
  * the oracle does not add but another walk could are listed with c = 0.
  * `use_bbox` skips candidates whose pixel bounding box excludes the pixel. */
 static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use_bbox,
-                      int px_i, int py_i, double ev_rel, double depth_limit, fso_hit* hits,
-                      double* t_final, int64_t* n_eval) {
+                      int px_i, int py_i, const fso_rule* rule, double depth_limit, fso_hit* hits,
+                      double* t_final, int64_t* n_eval, int64_t* n_part) {
   const double px = px_i + 0.5, py = py_i + 0.5;
+  const double ev_rel = rule->ev_rel, a_min = rule->alpha_min, t_min = rule->t_min;
   double T = 1.0;
+  double sa = 0.0;        /* sum of alpha/(1 - alpha) over the factors of T so far */
+  int64_t n_fac = 0;      /* factors of T so far */
   int nh = 0;
   double down = 0.0;      /* relative uncertainty of T from earlier marginal events */
   int all_risky = 0;      /* a marginal stop was passed: every later term may change */
@@ -265,10 +283,10 @@ static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use
       alpha = p->opacity * exp(power);
     }
     if (alpha > FSO_ALPHA_MAX) alpha = FSO_ALPHA_MAX;
-    const int a_edge = fabs(alpha - FSO_ALPHA_MIN) <= ev_rel * FSO_ALPHA_MIN;
+    const int a_edge = fabs(alpha - a_min) <= ev_rel * a_min;
     if (stopped) {
       /* Beyond a marginal stop: another walk may keep adding terms. */
-      if (alpha >= FSO_ALPHA_MIN * (1.0 - ev_rel)) {
+      if (alpha >= a_min * (1.0 - ev_rel)) {
         hits[nh].g = g; hits[nh].c = 0.0;
         hits[nh].risk = alpha * T_shadow * (1.0 + down) + 1e-300;
         hits[nh].flag = FSO_FLAG_DOWNSTREAM | (a_edge ? FSO_FLAG_ALPHA_EDGE : 0);
@@ -277,7 +295,7 @@ static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use
       }
       continue;
     }
-    if (alpha < FSO_ALPHA_MIN) {
+    if (alpha < a_min) {
       if (a_edge) { /* skipped here, but on the threshold: another walk may add it */
         hits[nh].g = g; hits[nh].c = 0.0;
         hits[nh].risk = alpha * T * (1.0 + down);
@@ -287,12 +305,16 @@ static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use
       }
       continue;
     }
+    ++*n_part; /* alpha >= 1/255 before the stop: this pair takes part (the stop included) */
     const double test_T = T * (1.0 - alpha);
-    /* T itself is uncertain by the relative amount `down` after marginal
-     * alpha decisions earlier in this pixel, so the stop test is marginal
-     * within that much more. */
-    const int t_edge = fabs(test_T - FSO_T_MIN) <= (ev_rel + 1.01 * down) * FSO_T_MIN;
-    if (test_T < FSO_T_MIN) {
+    /* the relative error another implementation's test_T may carry: alpha's
+     * relative error carried through every factor, each factor's rounding,
+     * and the uncertainty `down` of T after marginal alpha decisions earlier
+     * in this pixel */
+    const double t_win = ev_rel * (1.0 + sa + alpha / (1.0 - alpha)) +
+                         (double)(n_fac + 1) * 0x1p-23 + 1.01 * down;
+    const int t_edge = fabs(test_T - t_min) <= t_win * t_min;
+    if (test_T < t_min) {
       if (t_edge || all_risky) {
         /* the stop may not happen in another walk: this term and all
          * later ones are at risk */
@@ -324,6 +346,8 @@ static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use
     last_hit = nh;
     ++nh;
     if (a_edge) down += alpha / (1.0 - alpha);
+    sa += alpha / (1.0 - alpha);
+    ++n_fac;
     T = test_T;
   }
   *t_final = T;
@@ -335,13 +359,14 @@ static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use
 /* ------------------------------------------------------------------------ */
 
 static const fso_proj* g_sort_P; /* qsort has no context argument in C99 */
+static int g_tie_reverse;        /* equal depths by higher index first (tests only) */
 
 static int cmp_depth(const void* a, const void* b) {
   const int32_t ia = *(const int32_t*)a, ib = *(const int32_t*)b;
   const double da = g_sort_P[ia].depth, db = g_sort_P[ib].depth;
   if (da < db) return -1;
   if (da > db) return 1;
-  return (ia > ib) - (ia < ib);
+  return g_tie_reverse ? (ia < ib) - (ia > ib) : (ia > ib) - (ia < ib);
 }
 
 typedef struct {
@@ -460,7 +485,7 @@ typedef struct {
   const uint8_t* pix_sel;   /* NULL or per-pixel "walk this pixel" */
   int32_t E;
   int cull_mode;
-  double ev_rel;            /* near-threshold window (relative) */
+  const fso_rule* rule;     /* thresholds and near-threshold window */
   double depth_limit;       /* walks end beyond this depth (tracked rows only) */
   int nthreads, tid;
   double* t_final;          /* this view's slice or NULL */
@@ -469,7 +494,7 @@ typedef struct {
   double* risk;             /* [rows][E] */
   uint8_t* flags;           /* [rows] */
   fso_hit* hits;            /* scratch, capacity max candidates */
-  int64_t n_eval, n_hit, n_bad;
+  int64_t n_eval, n_hit, n_bad, n_part;
 } acc_job;
 
 static void* acc_worker(void* arg) {
@@ -490,8 +515,8 @@ static void* acc_worker(void* arg) {
         n = j->vi->bin_start[b + 1] - j->vi->bin_start[b];
       }
       double tf;
-      const int nh = walk_pixel(j->P, cand, n, j->cull_mode != 1, x, y, j->ev_rel,
-                                j->depth_limit, j->hits, &tf, &j->n_eval);
+      const int nh = walk_pixel(j->P, cand, n, j->cull_mode != 1, x, y, j->rule,
+                                j->depth_limit, j->hits, &tf, &j->n_eval, &j->n_part);
       if (j->t_final) j->t_final[pix] = tf;
       const int32_t lab = j->mask[pix];
       const int lab_ok = (lab >= 0 && lab < j->E);
@@ -512,10 +537,10 @@ static void* acc_worker(void* arg) {
 }
 
 /* Tracked rows (sel): each tracked Gaussian g is handled on its own, per
- * view.  Its candidates are the Gaussians whose bounding box meets g's, in
- * (depth, index) order -- every Gaussian that covers a pixel of g's box is
- * among them -- and only the pixels of g's box are walked, adding only g's
- * terms.  Row r belongs to thread r % nthreads, so each row's sum has a fixed
+ * view.  Its candidates are the Gaussians whose bounding box meets g's (found
+ * through a coarse grid of the view), in (depth, index) order -- every
+ * Gaussian that covers a pixel of g's box is among them -- and only the
+ * pixels of g's box are walked, adding only g's terms.  Row r belongs to thread r % nthreads, so each row's sum has a fixed
  * order. */
 typedef struct {
   const fso_proj* P;
@@ -525,14 +550,18 @@ typedef struct {
   const int64_t* sel;
   int64_t n_sel;
   int32_t E;
-  double ev_rel;
+  const fso_rule* rule;
+  const int64_t* cell_start; /* coarse grid of the view: Gaussians per cell */
+  const int32_t* cell_list;
+  int cells_x, cells_y;
+  uint32_t* stamp;           /* per Gaussian: last tracked row that listed it */
   int nthreads, tid;
   double* table;            /* [rows][E], this thread's rows only */
   double* risk;
   uint8_t* flags;
   int32_t* cand;            /* capacity N */
   fso_hit* hits;            /* capacity N */
-  int64_t n_eval, n_hit, n_bad;
+  int64_t n_eval, n_hit, n_bad, n_part;
 } sel_job;
 
 static void* sel_worker(void* arg) {
@@ -543,12 +572,24 @@ static void* sel_worker(void* arg) {
     const int32_t g = (int32_t)j->sel[r];
     const fso_proj* pg = &P[g];
     if (!pg->valid) continue;
+    /* candidates: the Gaussians listed in the grid cells g's box meets
+     * whose own box meets g's (each taken once) */
     int64_t nc = 0;
-    for (int64_t i = 0; i < j->N; ++i) {
-      const fso_proj* q = &P[i];
-      if (q->valid && !(q->x1 < pg->x0 || q->x0 > pg->x1 || q->y1 < pg->y0 || q->y0 > pg->y1))
-        j->cand[nc++] = (int32_t)i;
-    }
+    const uint32_t tag = (uint32_t)r + 1u;
+    const int cx0 = pg->x0 / FSO_CELL, cx1 = pg->x1 / FSO_CELL;
+    const int cy0 = pg->y0 / FSO_CELL, cy1 = pg->y1 / FSO_CELL;
+    for (int cy = cy0; cy <= cy1; ++cy)
+      for (int cx = cx0; cx <= cx1; ++cx) {
+        const int64_t c = (int64_t)cy * j->cells_x + cx;
+        for (int64_t k = j->cell_start[c]; k < j->cell_start[c + 1]; ++k) {
+          const int32_t i = j->cell_list[k];
+          if (j->stamp[i] == tag) continue;
+          j->stamp[i] = tag;
+          const fso_proj* q = &P[i];
+          if (!(q->x1 < pg->x0 || q->x0 > pg->x1 || q->y1 < pg->y0 || q->y0 > pg->y1))
+            j->cand[nc++] = i;
+        }
+      }
     qsort(j->cand, (size_t)nc, sizeof(int32_t), cmp_depth);
     /* 8x8-pixel bins over g's box, each holding its candidates in order */
     const int nbx = (pg->x1 - pg->x0) / FSO_BIN + 1, nby = (pg->y1 - pg->y0) / FSO_BIN + 1;
@@ -584,8 +625,8 @@ static void* sel_worker(void* arg) {
       for (int x = pg->x0; x <= pg->x1; ++x) {
         double tf;
         const int64_t b = (int64_t)((y - pg->y0) / FSO_BIN) * nbx + (x - pg->x0) / FSO_BIN;
-        const int nh = walk_pixel(P, list + start[b], start[b + 1] - start[b], 1, x, y, j->ev_rel,
-                                  depth_limit, j->hits, &tf, &j->n_eval);
+        const int nh = walk_pixel(P, list + start[b], start[b + 1] - start[b], 1, x, y, j->rule,
+                                  depth_limit, j->hits, &tf, &j->n_eval, &j->n_part);
         const int32_t lab = j->mask[(int64_t)y * W + x];
         const int lab_ok = (lab >= 0 && lab < j->E);
         if (!lab_ok) j->n_bad++;
@@ -619,12 +660,18 @@ static void* sel_worker(void* arg) {
  *   cull_mode: 0 = spatial bins, 1 = every pixel walks every Gaussian
  *   t_final: NULL or [sum_v H*W] transmittance left at each pixel (-1 where
  *        the pixel was not walked); only without sel
- *   stats[4]: evaluated pairs, contributing pairs, pixels with bad labels,
- *        tracked Gaussians that were never valid in any view
- *   event_rel: relative window around the 1/255 and 1e-4 thresholds inside
- *        which a decision is counted as marginal in `risk` (<= 0: 1e-4)
+ *   stats[5]: evaluated pairs (candidates in the pixel's walk up to its stop),
+ *        contributing pairs (alpha*T added), pixels with bad labels, tracked
+ *        Gaussians that were never valid in any view, and the pairs that take
+ *        part in the compositing (alpha >= 1/255, up to and including the
+ *        stop; without sel only)
+ *   event_rel: the relative precision assumed for alpha, which sets the
+ *        windows of the near-threshold model above (<= 0: FSO_EVENT_REL)
  *   record_f16: non-zero -> alpha from the reduced-precision record (FP16
  *        whitening matrix, FP32 mean; see fso_proj), all else unchanged
+ *   alpha_min, t_min: the rule's thresholds (<= 0: 1/255 and 1e-4); tests
+ *        move them inside their windows
+ *   tie_reverse: non-zero -> equal depths are walked by higher index first
  * Returns 0, or -1 on a zero quaternion, -2 on bad arguments.
  */
 int fso_accumulate(int64_t N, const float* mean, const float* quat, const float* scale,
@@ -632,10 +679,15 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
                    const int32_t* masks, const int64_t* mask_offsets, int32_t E,
                    const int64_t* sel, int64_t n_sel, int32_t cull_mode, int32_t nthreads,
                    double* table, double* risk, uint8_t* flags, double* t_final,
-                   int64_t* stats, double event_rel, int32_t record_f16) {
+                   int64_t* stats, double event_rel, int32_t record_f16, double alpha_min,
+                   double t_min, int32_t tie_reverse) {
   if (N < 0 || V < 0 || E < 1 || (sel && n_sel < 0)) return -2;
   if (sel && t_final) return -2;
-  if (!(event_rel > 0.0)) event_rel = FSO_EVENT_REL;
+  fso_rule rule;
+  rule.ev_rel = event_rel > 0.0 ? event_rel : FSO_EVENT_REL;
+  rule.alpha_min = alpha_min > 0.0 ? alpha_min : FSO_ALPHA_MIN;
+  rule.t_min = t_min > 0.0 ? t_min : FSO_T_MIN;
+  g_tie_reverse = tie_reverse != 0;
   if (nthreads < 1) nthreads = 1;
   const int64_t rows = sel ? n_sel : N;
   int64_t* slot = NULL;
@@ -650,7 +702,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
   memset(table, 0, sizeof(double) * (size_t)(rows * E));
   memset(risk, 0, sizeof(double) * (size_t)(rows * E));
   memset(flags, 0, (size_t)rows);
-  int64_t st[4] = {0, 0, 0, 0};
+  int64_t st[5] = {0, 0, 0, 0, 0};
 
   fso_proj* P = (fso_proj*)malloc(sizeof(fso_proj) * (size_t)(N > 0 ? N : 1));
   acc_job* jobs = (acc_job*)calloc((size_t)nthreads, sizeof(acc_job));
@@ -675,12 +727,38 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
         if (P[sel[r]].valid) seen[r] = any = 1;
       if (any) {
         g_sort_P = P;
+        /* coarse grid of the view: every valid Gaussian listed in the
+         * 32x32-pixel cells its box meets */
+        const int gcx = (cam->width + FSO_CELL - 1) / FSO_CELL;
+        const int gcy = (cam->height + FSO_CELL - 1) / FSO_CELL;
+        const int64_t ncell = (int64_t)gcx * gcy;
+        int64_t* cstart = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+        for (int64_t i = 0; i < N; ++i) {
+          if (!P[i].valid) continue;
+          for (int cy = P[i].y0 / FSO_CELL; cy <= P[i].y1 / FSO_CELL; ++cy)
+            for (int cx = P[i].x0 / FSO_CELL; cx <= P[i].x1 / FSO_CELL; ++cx)
+              cstart[(int64_t)cy * gcx + cx + 1]++;
+        }
+        for (int64_t c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
+        int32_t* clist = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cstart[ncell] > 0 ? cstart[ncell] : 1));
+        int64_t* cfill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ncell > 0 ? ncell : 1));
+        memcpy(cfill, cstart, sizeof(int64_t) * (size_t)ncell);
+        for (int64_t i = 0; i < N; ++i) {
+          if (!P[i].valid) continue;
+          for (int cy = P[i].y0 / FSO_CELL; cy <= P[i].y1 / FSO_CELL; ++cy)
+            for (int cx = P[i].x0 / FSO_CELL; cx <= P[i].x1 / FSO_CELL; ++cx)
+              clist[cfill[(int64_t)cy * gcx + cx]++] = (int32_t)i;
+        }
+        free(cfill);
         sel_job* sj = (sel_job*)calloc((size_t)nthreads, sizeof(sel_job));
         for (int t = 0; t < nthreads; ++t) {
-          sj[t] = (sel_job){P, N, cam, masks + mask_offsets[v], sel, n_sel, E, event_rel,
+          sj[t] = (sel_job){P, N, cam, masks + mask_offsets[v], sel, n_sel, E, &rule,
+                            cstart, clist, gcx, gcy,
+                            (uint32_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(uint32_t)),
                             nthreads, t, jobs[t].table, jobs[t].risk, jobs[t].flags,
                             (int32_t*)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1)),
-                            (fso_hit*)malloc(sizeof(fso_hit) * (size_t)(N > 0 ? N : 1)), 0, 0, 0};
+                            (fso_hit*)malloc(sizeof(fso_hit) * (size_t)(N > 0 ? N : 1)), 0, 0, 0,
+                            0};
           pthread_create(&th[t], NULL, sel_worker, &sj[t]);
         }
         for (int t = 0; t < nthreads; ++t) {
@@ -690,8 +768,11 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
           jobs[t].n_bad += sj[t].n_bad;
           free(sj[t].cand);
           free(sj[t].hits);
+          free(sj[t].stamp);
         }
         free(sj);
+        free(cstart);
+        free(clist);
       }
       pix_base += npix;
       continue;
@@ -718,7 +799,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
       acc_job* j = &jobs[t];
       j->P = P; j->vi = &vi; j->cam = cam; j->mask = masks + mask_offsets[v];
       j->slot = slot; j->pix_sel = pix_sel; j->E = E; j->cull_mode = cull_mode;
-      j->ev_rel = event_rel;
+      j->rule = &rule;
       j->depth_limit = INFINITY;
       j->nthreads = nthreads; j->tid = t;
       j->t_final = t_final ? t_final + pix_base : NULL;
@@ -742,6 +823,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
     st[0] += jobs[t].n_eval;
     st[1] += jobs[t].n_hit;
     st[2] += jobs[t].n_bad;
+    st[4] += jobs[t].n_part;
     free(jobs[t].table);
     free(jobs[t].risk);
     free(jobs[t].flags);
@@ -753,6 +835,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
   free(th);
   free(P);
   free(slot);
+  g_tie_reverse = 0;
   return status;
 }
 
@@ -771,7 +854,8 @@ int64_t fso_pixel_lists(int64_t N, const float* mean, const float* quat, const f
                         int32_t* gidx, double* contrib, double* t_final) {
   fso_proj* P = (fso_proj*)malloc(sizeof(fso_proj) * (size_t)(N > 0 ? N : 1));
   fso_hit* hits = (fso_hit*)malloc(sizeof(fso_hit) * (size_t)(N > 0 ? N : 1));
-  int64_t total = 0, pix = 0, n_eval = 0;
+  int64_t total = 0, pix = 0, n_eval = 0, n_part = 0;
+  const fso_rule rule = {FSO_ALPHA_MIN, FSO_T_MIN, FSO_EVENT_REL};
   for (int32_t v = 0; v < V; ++v) {
     const fso_camera* cam = &cams[v];
     view_index vi;
@@ -790,8 +874,8 @@ int64_t fso_pixel_lists(int64_t N, const float* mean, const float* quat, const f
           n = vi.bin_start[b + 1] - vi.bin_start[b];
         }
         double tf;
-        const int nh = walk_pixel(P, cand, n, cull_mode != 1, x, y, FSO_EVENT_REL, INFINITY,
-                                hits, &tf, &n_eval);
+        const int nh = walk_pixel(P, cand, n, cull_mode != 1, x, y, &rule, INFINITY,
+                                hits, &tf, &n_eval, &n_part);
         pix_offsets[pix] = total;
         if (t_final) t_final[pix] = tf;
         for (int h = 0; h < nh; ++h) {

@@ -154,6 +154,25 @@ int64_t radix_launches(int64_t n, int bits) {
 
 }  // namespace
 
+// Per-view parameters of a camera (float pairs of R, t and the intrinsics,
+// the near plane, the Jacobian clamp at 1.3 tan(half field of view), tiles).
+void fs::fill_view(const fs_camera& cam, fs::ViewParams* vp) {
+  memset(vp, 0, sizeof(*vp));
+  for (int k = 0; k < 9; ++k) split(cam.R[k], &vp->R_hi[k], &vp->R_lo[k]);
+  for (int k = 0; k < 3; ++k) split(cam.t[k], &vp->t_hi[k], &vp->t_lo[k]);
+  split(cam.fx, &vp->fx_hi, &vp->fx_lo);
+  split(cam.fy, &vp->fy_hi, &vp->fy_lo);
+  split(cam.cx, &vp->cx_hi, &vp->cx_lo);
+  split(cam.cy, &vp->cy_hi, &vp->cy_lo);
+  split(0.2, &vp->near_hi, &vp->near_lo);
+  split(1.3 * (0.5 * cam.width / cam.fx), &vp->limx_hi, &vp->limx_lo);
+  split(1.3 * (0.5 * cam.height / cam.fy), &vp->limy_hi, &vp->limy_lo);
+  vp->width = cam.width;
+  vp->height = cam.height;
+  vp->tiles_x = (cam.width + fs::kTile - 1) / fs::kTile;
+  vp->tiles_y = (cam.height + fs::kTile - 1) / fs::kTile;
+}
+
 void fs::set_last_error(const char* msg) {
   snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
 }
@@ -174,6 +193,7 @@ struct fs_ctx {
   float recheck_margin = 1e-4f;  // <= 0: off
   bool recheck_reproject = false;
   bool compact = false;  // reduced-precision records (FP16 whitening matrix, FP32 mean)
+  bool census = false;   // blend counts its pairs (slower variant)
   DevBuf dkey, rk_flag, rk_offs, rk_F, rk_map, rk_R, rk_Rb;
   DevBuf key_range;  // min / max visible depth key of the batch (two slots, by batch parity)
   // the next batch's projection runs on a side stream while the current
@@ -188,7 +208,7 @@ struct fs_ctx {
   int kl_chunks = 1;
   std::vector<DevBuf> kl_val;
   std::vector<int64_t> kl_tile_off;
-  DevBuf kl_ranges, kl_satc, kl_bound;
+  DevBuf kl_ranges, kl_satc, kl_subc, kl_bound;
   std::vector<const void*> mask_dev;  // device pointer of every view's mask (last solve)
   HostBuf views_host, total_host, counters_host;
   fs_stats stats{};
@@ -211,7 +231,7 @@ DevBuf* const* workspace_bufs(fs_ctx* c, size_t* count) {
                     &c->mask_stage, &c->table_tmp, &c->table32_tmp, &c->bits_tmp,
                     &c->label_tmp, &c->margin_tmp, &c->dkey, &c->rk_flag, &c->rk_offs,
                     &c->rk_F, &c->rk_map, &c->rk_R, &c->rk_Rb, &c->kl_ranges, &c->kl_satc,
-                    &c->kl_bound, &c->key_range, &c->lb_tmp, &c->key_a2, &c->val_a2,
+                    &c->kl_subc, &c->kl_bound, &c->key_range, &c->lb_tmp, &c->key_a2, &c->val_a2,
                     &c->key_b2, &c->val_b2};
   for (DevBuf* b : list) bufs[k++] = b;
   *count = k;
@@ -282,6 +302,7 @@ fs_status fs_create(fs_ctx** out, int32_t device, const fs_options* opt) {
     return fail(FS_INVALID_ARGUMENT, "fs_create: record_precision must be 0 or FS_F16");
   }
   c->compact = opt && opt->record_precision == FS_F16;
+  c->census = opt && opt->census;
   DeviceGuard g(device);
   fs_status st;
   if ((st = c->views.ensure(sizeof(fs::ViewParams) * 2 * fs::kMaxViewsPerBatch, "views")) != FS_OK ||
@@ -309,7 +330,7 @@ fs_status fs_destroy(fs_ctx* c) {
                     &c->sort_tmp, &c->scan_tmp, &c->total, &c->counters, &c->mask_stage,
                     &c->table_tmp, &c->table32_tmp, &c->bits_tmp, &c->label_tmp, &c->margin_tmp,
                     &c->dkey, &c->rk_flag, &c->rk_offs, &c->rk_F, &c->rk_map, &c->rk_R,
-                    &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_bound, &c->key_range, &c->lb_tmp,
+                    &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_subc, &c->kl_bound, &c->key_range, &c->lb_tmp,
                     &c->key_a2, &c->val_a2, &c->key_b2, &c->val_b2};
   for (DevBuf& b : c->kl_val) b.release();
   for (DevBuf* b : bufs) b->release();
@@ -437,23 +458,6 @@ fs_status check_camera(const fs_camera& cam, int v) {
   return FS_OK;
 }
 
-void fill_view(const fs_camera& cam, fs::ViewParams* vp) {
-  memset(vp, 0, sizeof(*vp));
-  for (int k = 0; k < 9; ++k) split(cam.R[k], &vp->R_hi[k], &vp->R_lo[k]);
-  for (int k = 0; k < 3; ++k) split(cam.t[k], &vp->t_hi[k], &vp->t_lo[k]);
-  split(cam.fx, &vp->fx_hi, &vp->fx_lo);
-  split(cam.fy, &vp->fy_hi, &vp->fy_lo);
-  split(cam.cx, &vp->cx_hi, &vp->cx_lo);
-  split(cam.cy, &vp->cy_hi, &vp->cy_lo);
-  split(0.2, &vp->near_hi, &vp->near_lo);
-  split(1.3 * (0.5 * cam.width / cam.fx), &vp->limx_hi, &vp->limx_lo);
-  split(1.3 * (0.5 * cam.height / cam.fy), &vp->limy_hi, &vp->limy_lo);
-  vp->width = cam.width;
-  vp->height = cam.height;
-  vp->tiles_x = (cam.width + fs::kTile - 1) / fs::kTile;
-  vp->tiles_y = (cam.height + fs::kTile - 1) / fs::kTile;
-}
-
 // Per-view mask device pointers for views [0, V).  Host masks are staged in
 // one buffer that holds every view, so a later pass can read them again.
 fs_status stage_masks(fs_ctx* c, const fs_camera* cams, int32_t V, const void* const* masks,
@@ -490,7 +494,7 @@ BatchLayout layout_batch(fs_ctx* c, fs::ViewParams* vh, const fs_camera* cams, i
                          int nb) {
   BatchLayout L;
   for (int k = 0; k < nb; ++k) {
-    fill_view(cams[v0 + k], &vh[k]);
+    fs::fill_view(cams[v0 + k], &vh[k]);
     vh[k].tile_base = L.total_tiles;
     vh[k].state_off = L.pixels;
     vh[k].mask = c->mask_dev[v0 + k];
@@ -560,17 +564,17 @@ fs_status read_total(fs_ctx* c, cudaStream_t stream, int64_t* out) {
 }
 
 // Binning of sorted positions [p0, p0 + n_pos) into tile lists (count, scan,
-// emit, stable tile sort, ranges) on tiles whose `sat` bit is clear.  Returns
-// the entry count in *I and the sorted list values in *lval.
-// Binning of sorted positions [p0, p0 + n_pos) into tile lists (count, scan,
-// emit, stable tile sort, ranges) on tiles whose `sat` bit is clear.  The
-// sorted list values go to *val_dst (grown as needed) and the per-tile ranges
-// to ranges_dst.  Returns the entry count in *I_out.
+// emit, stable tile sort, ranges) on tiles whose `sat` bit is clear and, with
+// `done` (4 bits per tile), only where the footprint reaches an unfinished
+// sub-tile.  The sorted list values go to *val_dst (grown as needed), the
+// per-tile ranges to ranges_dst and the sorted keys' location to *key_out.
+// Returns the entry count in *I_out.
 fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
                         const fs::ViewParams* vd, const uint32_t* sorted_val, const ProjPtrs& P,
-                        const uint64_t* sat, int total_tiles, int tile_bits, int64_t kcap,
-                        bool count_entries, DevBuf* val_dst, uint2* ranges_dst,
-                        cudaStream_t stream, int64_t* I_out) {
+                        const uint64_t* sat, const uint64_t* done, int total_tiles,
+                        int tile_bits, int64_t kcap, bool count_entries, DevBuf* val_dst,
+                        uint2* ranges_dst, cudaStream_t stream, int64_t* I_out,
+                        const uint32_t** key_out) {
   unsigned long long* ctr = c->counters.as<unsigned long long>();
   *I_out = 0;
   FS_CUDA(cudaMemsetAsync(ranges_dst, 0, static_cast<size_t>(total_tiles) * 8, stream),
@@ -583,7 +587,7 @@ fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
     const size_t cap_bytes = std::min(c->lk_a.bytes, val_dst->bytes);
     const uint32_t capacity = static_cast<uint32_t>(std::min<size_t>(cap_bytes / 4, 0x7FFFFFFFu));
     c->stats.kernel_launches += 1;
-    FS_CUDA(fs::launch_bin_fused(p0, n_pos, n, vd, sorted_val, P.foot, sat,
+    FS_CUDA(fs::launch_bin_fused(p0, n_pos, n, vd, sorted_val, P.foot, sat, done,
                                  c->lk_a.as<uint32_t>(), val_dst->as<uint32_t>(), capacity,
                                  c->lb_tmp.p, c->total.as<uint32_t>(), ctr, stream),
             "binning");
@@ -597,6 +601,7 @@ fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
   }
   if (count_entries) c->stats.list_entries += I;
   *I_out = I;
+  if (key_out) *key_out = c->lk_a.as<uint32_t>();
   if (I == 0) return FS_OK;
   FS_TRY(c->lk_b.ensure(static_cast<size_t>(I) * 4, "list keys"));
   FS_TRY(c->lv_b.ensure(static_cast<size_t>(I) * 4, "list values"));
@@ -613,6 +618,7 @@ fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
                             cudaMemcpyDeviceToDevice, stream),
             "list copy");
   FS_CUDA(fs::launch_ranges(I, lkey, ranges_dst, stream), "ranges");
+  if (key_out) *key_out = lkey;
   return FS_OK;
 }
 
@@ -644,6 +650,7 @@ fs_status kept_layout(fs_ctx* c, const fs_camera* cams, int32_t V, int vb, int c
   if (c->kl_val.size() < batches * chunks) c->kl_val.resize(batches * chunks);
   FS_TRY(c->kl_ranges.ensure(static_cast<size_t>(tiles) * chunks * 8 + 8, "kept ranges"));
   FS_TRY(c->kl_satc.ensure(static_cast<size_t>(tiles) + 8, "kept saturation chunks"));
+  FS_TRY(c->kl_subc.ensure(static_cast<size_t>(tiles) * 4 + 8, "kept sub-tile chunks"));
   FS_TRY(c->kl_bound.ensure(batches * chunks * 4 + 4, "kept chunk bounds"));
   return FS_OK;
 }
@@ -752,6 +759,9 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     const BatchLayout L = pr.L;
     const int total_tiles = L.total_tiles, max_tiles = L.max_tiles;
     const int tile_bits = std::max(1, ceil_log2(total_tiles));
+    if (tile_bits > 27)  // list keys hold the tile id below a 4-bit sub-tile mask
+      return fail(FS_UNSUPPORTED, "%d tiles in one view batch; use fewer views per batch",
+                  total_tiles);
     const int64_t k_total = static_cast<int64_t>(nb) * n;
     FS_TRY(c->state.ensure(static_cast<size_t>(L.pixels) * 4, "pixel state"));
     const size_t sat_bytes = static_cast<size_t>((total_tiles + 63) / 64) * 8;
@@ -764,10 +774,14 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     uint64_t* sat = c->sat.as<uint64_t>();
     const ProjPtrs P = proj_ptrs(c, keep, v0, n);
     uint8_t* satc = nullptr;
+    uint8_t* subc = nullptr;
     if (keep) {
       satc = c->kl_satc.as<uint8_t>() + c->kl_tile_off[b];
+      subc = c->kl_subc.as<uint8_t>() + 4 * c->kl_tile_off[b];
       FS_CUDA(cudaMemsetAsync(satc, 0xFF, static_cast<size_t>(total_tiles), stream),
               "saturation chunks");
+      FS_CUDA(cudaMemsetAsync(subc, 0xFF, static_cast<size_t>(total_tiles) * 4, stream),
+              "sub-tile chunks");
     }
     // the batch's projection (and its key range on the host) is complete
     FS_CUDA(cudaEventSynchronize(c->prologue_done[q]), "key range readback");
@@ -834,8 +848,10 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
         continue;
       }
       int64_t I = 0;
-      FS_TRY(bin_positions(c, p0, n_pos, n, vd, sorted_val, P, sat, total_tiles, tile_bits, kcap,
-                           true, val_dst, ranges_dst, stream, &I));
+      const uint32_t* lkey = nullptr;
+      FS_TRY(bin_positions(c, p0, n_pos, n, vd, sorted_val, P, sat, c->subsat.as<uint64_t>(),
+                           total_tiles, tile_bits, kcap, true, val_dst, ranges_dst, stream, &I,
+                           &lkey));
       p0 = p1;
       if (I == 0) continue;
       cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -850,9 +866,9 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
         c->events_used += 2;
         FS_CUDA(cudaEventRecord(ev0, stream), "cudaEventRecord");
       }
-      FS_CUDA(fs::launch_blend(vd, nb, max_tiles, ranges_dst, val_dst->as<uint32_t>(), P.rec,
-                               P.rec16, s->pos_op.as<float4>(), n, E, mask_dtype, table,
-                               table_dtype, state, sat, subsat, satc, ci, ctr, stream),
+      FS_CUDA(fs::launch_blend(vd, nb, max_tiles, ranges_dst, lkey, val_dst->as<uint32_t>(), P.rec,
+                               P.rec16, n, E, mask_dtype, table, table_dtype, state, sat, subsat,
+                               satc, subc, ci, ctr, c->census, stream),
               "blend");
       if (ev1) FS_CUDA(cudaEventRecord(ev1, stream), "cudaEventRecord");
     }
@@ -894,8 +910,8 @@ fs_status recheck_batch_rebin(fs_ctx* c, const fs_scene* s, int64_t n, int nb, i
   uint32_t* sorted_val = alt ? c->val_a.as<uint32_t>() : c->val_b.as<uint32_t>();
   FS_CUDA(fs::launch_depth_tie_fix(C, n, sorted_key, sorted_val, P.dlo, stream), "depth ties");
   int64_t I = 0;
-  FS_TRY(bin_positions(c, 0, C, n, vd, sorted_val, P, skip, total_tiles, tile_bits, kcap, false,
-                       &c->lv_a, c->ranges.as<uint2>(), stream, &I));
+  FS_TRY(bin_positions(c, 0, C, n, vd, sorted_val, P, skip, nullptr, total_tiles, tile_bits, kcap,
+                       false, &c->lv_a, c->ranges.as<uint2>(), stream, &I, nullptr));
   if (I == 0) return FS_OK;
   fs::RecheckLists Ls{};
   Ls.val[0] = c->lv_a.as<uint32_t>();
@@ -1002,6 +1018,7 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
       }
       Ls.chunks = chunks;
       Ls.sat_chunk = satc;
+      Ls.sub_chunk = kept ? c->kl_subc.as<uint8_t>() + 4 * c->kl_tile_off[b] : nullptr;
       Ls.deep = deep;
       FS_CUDA(cudaMemsetAsync(Rb, 0, rbytes, stream), "batch rows clear");
       FS_CUDA(cudaMemsetAsync(ctr + fs::kRecheckIncomplete, 0, 8, stream), "incomplete clear");
@@ -1190,6 +1207,40 @@ fs_status fs_solve(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t 
   return FS_OK;
 }
 
+fs_status fs_check_wait_timeout(int32_t device, int32_t spins) {
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= count)
+    return fail(FS_INVALID_ARGUMENT, "fs_check_wait_timeout: bad device %d", device);
+  if (spins < 1) return fail(FS_INVALID_ARGUMENT, "fs_check_wait_timeout: spins < 1");
+  DeviceGuard g(device);
+  // lookback (512) | total (4) | counters | one view | one footprint | tiny arrays
+  const size_t bytes = 512 + 256 + 8 * fs::kNumCounters + 1024 + 256 + 256;
+  DevBuf ws;
+  FS_TRY(ws.ensure(bytes, "wait check"));
+  char* base = ws.as<char>();
+  FS_CUDA(cudaMemset(base, 0, bytes), "wait check");
+  auto* counters = reinterpret_cast<unsigned long long*>(base + 768);
+  const size_t o_view = 768 + 8 * fs::kNumCounters;
+  cudaError_t le = fs::launch_lookback_probe(
+      base, reinterpret_cast<uint32_t*>(base + 512), counters,
+      reinterpret_cast<const fs::ViewParams*>(base + ((o_view + 255) & ~size_t(255))),
+      reinterpret_cast<const uint32_t*>(base + bytes - 256),
+      reinterpret_cast<const fs::Footprint*>(base + bytes - 512),
+      reinterpret_cast<const uint64_t*>(base + bytes - 256),
+      reinterpret_cast<uint32_t*>(base + bytes - 128), reinterpret_cast<uint32_t*>(base + bytes - 64),
+      spins, nullptr);
+  unsigned long long h[fs::kNumCounters] = {};
+  if (le == cudaSuccess) le = cudaMemcpy(h, counters, sizeof(h), cudaMemcpyDeviceToHost);
+  ws.release();
+  if (le != cudaSuccess) return cuda_fail(le, "fs_check_wait_timeout");
+  if (h[fs::kLookbackTimeout])
+    return fail(FS_TIMEOUT, "the binning's bounded wait gave up after %d polls, as it must",
+                spins);
+  return FS_OK;
+}
+
 fs_status fs_synchronize(fs_ctx* c, void* stream, fs_stats* stats) {
   if (!c) return fail(FS_INVALID_ARGUMENT, "NULL context");
   DeviceGuard g(c->device);
@@ -1203,7 +1254,11 @@ fs_status fs_synchronize(fs_ctx* c, void* stream, fs_stats* stats) {
   c->stats.bad_labels = static_cast<int64_t>(ch[fs::kBadLabels]);
   c->stats.pairs = static_cast<int64_t>(ch[fs::kPairs]);
   c->stats.staged_entries = static_cast<int64_t>(ch[fs::kStaged]);
+  c->stats.census_pairs = static_cast<int64_t>(ch[fs::kCensusPairs]);
   c->stats.recheck_pairs = static_cast<int64_t>(ch[fs::kRecheckPairs]);
+  if (ch[fs::kLookbackTimeout])
+    return fail(FS_TIMEOUT, "tile binning: %llu bounded wait(s) for a preceding block's offset "
+                "gave up; the lists of that solve are incomplete", ch[fs::kLookbackTimeout]);
   if (ch[fs::kBinningMismatch])
     return fail(FS_CUDA_ERROR, "internal error: tile binning count and emission disagreed for "
                 "%llu Gaussian(s)", ch[fs::kBinningMismatch]);

@@ -4,31 +4,34 @@
 // the table column of that pixel's label, added atomically).
 //
 // One warp per 8x8 sub-tile of a 16x16 tile; each lane walks two adjacent
-// pixels; no block barriers.  A block holds the four independent warps of one
-// tile and the kernel is held to 48 registers, so that 40 warps share an SM
-// (registers and shared memory both allow 10 blocks) instead of the 32 that
-// one-warp blocks allow.
-//  * The warp reads its tile's depth-sorted list (one depth chunk of it) 32
-//    entries at a time.  Each lane forms its entry's offset b = W o + c at the
-//    sub-tile centre o (float pairs) and keeps the entry only when the
-//    alpha >= 1/255 region can reach the sub-tile; kept entries are compacted
-//    into shared memory in list order.
-//  * Per pixel, per kept Gaussian, without branches and with packed FP32
-//    pairs for the lane's two pixels: w = W p + b,
-//    alpha = min(0.99, o 2^-|w|^2); alpha < 1/255 is skipped; the pixel stops
-//    before a Gaussian that would take T below 1e-4; else it adds alpha*T.
-//    The decisions are 1.0/0.0 factors, so a stopped pixel simply carries
-//    T = 0.  T is kept per pixel across depth chunks (0 = stopped); a
-//    sub-tile whose pixels have all stopped is done, and a tile with four
-//    done sub-tiles is saturated (no later chunk lists it).
-//  * No per-pixel atomics: the lane adds its two contributions when they
-//    share a label and writes one value per Gaussian into a shared row whose
-//    positions are ordered by label; lane j then sums Gaussian j's row per
-//    label and issues one global atomic add per non-zero (Gaussian, label).
-//    A lane whose two pixels straddle a label boundary adds its second
-//    pixel's contribution with its own atomic.
+// pixels; a block holds the four independent warps of one tile (no block
+// barriers).
+//  * The tile's depth-sorted list (one depth chunk of it) carries, per entry,
+//    the mask of the tile's sub-tiles the footprint reaches (top bits of the
+//    key).  A warp reads 32 keys at a time and queues, in list order, only
+//    the entries that reach its sub-tile.
+//  * Rounds of up to 32 queued entries: lane k gathers entry k's record and
+//    writes the Gaussian's whitening matrix W, its offset b = W (o - m) at
+//    the sub-tile centre o and -log2(opacity) into shared memory, two
+//    Gaussians (g, h) side by side so the packed FP32 instructions (FFMA2,
+//    FMUL2, FADD2) evaluate both at once without rearranging registers.
+//  * Per lane, per Gaussian pair, for its pixels P and Q = P + (1, 0):
+//      q = |W p + b|^2 - log2 o,  alpha = 2^-q = o exp(-0.5 d^T Sigma^-1 d)
+//    alpha >= 1/255 is decided by flushing alpha * 255 * 2^-126 to zero when
+//    it falls below the smallest normal float (FTZ multiply), so the skip
+//    costs one packed multiply; the clamp at 0.99 is applied only for pairs
+//    holding a Gaussian of opacity above 0.99.  T is carried as
+//    T * 2^126 / 255, so the flushed product times it is alpha * T.  The
+//    stop before a Gaussian that would take T below 1e-4 is an exact 0/1
+//    factor from a saturated FMA.  A stopped pixel carries T = 0.
+//  * Per Gaussian the lane writes its pixels' sum into a shared row ordered
+//    by label; lane j then sums Gaussian j's row per label and issues one
+//    FP64 atomic add per non-zero (Gaussian, label).  A lane whose two pixels
+//    straddle a label boundary adds its second pixel's contribution with its
+//    own atomic.
 #include <cuda_fp16.h>
 
+#include "fs_binning.cuh"
 #include "fs_common.cuh"
 #include "fs_internal.h"
 
@@ -53,44 +56,21 @@ __device__ __forceinline__ void table_add(TableT* p, float v) {
   atomicAdd(p, static_cast<TableT>(v));
 }
 
-// 1.0f if a >= b else 0.0f
-__device__ __forceinline__ float step_ge(float a, float b) {
-  float r;
-  asm("set.ge.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
-  return r;
-}
-
-// One compositing step (Eq. 1) of the lane's two pixels, (x0, y) and
-// (x0 + 1, y), branch-free and with packed FP32 pairs.  T == 0 marks a pixel
-// that has stopped: its later steps give alpha' T = 0 and keep T = 0.
-//   alpha = min(0.99, o 2^-|w|^2),  alpha' = alpha if alpha >= 1/255 else 0
-//   T' = T (1 - alpha');  the pixel stops (T' < 1e-4) without adding,
-//   else it adds alpha' T and continues with T'.
-// `live` counts, per pixel, the steps taken while running on (not stopping).
-__device__ __forceinline__ float2 composite2(const float4& W, const float4& bo, float2 X, float y,
-                                             float2& T, float2& live) {
-  const float t0 = fmaf(W.y, y, bo.x), t1 = fmaf(W.w, y, bo.y);
-  const float2 w0 = __ffma2_rn(make_float2(W.x, W.x), X, make_float2(t0, t0));
-  const float2 w1 = __ffma2_rn(make_float2(W.z, W.z), X, make_float2(t1, t1));
-  const float2 q = __ffma2_rn(w0, w0, __fmul2_rn(w1, w1));
-  float2 a = __fmul2_rn(make_float2(bo.z, bo.z), make_float2(ex2_approx(-q.x), ex2_approx(-q.y)));
-  a.x = fminf(kAlphaMax, a.x);
-  a.y = fminf(kAlphaMax, a.y);
-  a = __fmul2_rn(a, make_float2(step_ge(a.x, kAlphaMin), step_ge(a.y, kAlphaMin)));
-  const float2 tt = __ffma2_rn(make_float2(-T.x, -T.y), a, T);
-  const float2 go = make_float2(step_ge(tt.x, kTMin), step_ge(tt.y, kTMin));
-  const float2 c = __fmul2_rn(__fmul2_rn(a, T), go);
-  T = __fmul2_rn(tt, go);
-  live = __fadd2_rn(live, go);
-  return c;
-}
+// alpha * 255 * 2^-126 is subnormal exactly when alpha < 1/255 (FTZ flushes it)
+constexpr float kSkipScale = 255.0f * 0x1p-126f;
+// T is carried as T / kSkipScale, so (alpha kSkipScale) (T / kSkipScale) = alpha T
+constexpr float kTScale = 0x1p126f / 255.0f;
+// the scaled stop threshold 1e-4 / kSkipScale lies in [2^104, 2^105): ulp 2^81
+constexpr float kStepScale = 0x1p-81f;
 
 __device__ __forceinline__ void set_bit(uint64_t* bits, int i) {
   atomicOr(reinterpret_cast<unsigned long long*>(bits + (i >> 6)), 1ull << (i & 63));
 }
 
-// Per-pixel state of a batch before its first depth chunk: T = 1 for pixels
-// with a label in [0, E), 0 ("stopped") for the others.  Sub-tiles (and tiles)
+// Per-pixel state of a batch before its first depth chunk: the scaled
+// transmittance T * kTScale (the form the blend carries, so the state passes
+// between depth chunks without rounding), with T = 1 for pixels with a label
+// in [0, E) and 0 ("stopped") for the others.  Sub-tiles (and tiles)
 // without a labelled pixel start saturated.  Counts the pixels with bad
 // labels.  One 256-thread block per 16x16 tile: 64 threads (two warps) per
 // 8x8 sub-tile.
@@ -115,7 +95,7 @@ __global__ void __launch_bounds__(256) state_init_kernel(
     const int64_t p = static_cast<int64_t>(py) * W + px;
     const int label = static_cast<int>(static_cast<const LabelT*>(views[v].mask)[p]);
     valid = label >= 0 && label < E;
-    state[views[v].state_off + p] = valid ? 1.f : 0.f;
+    state[views[v].state_off + p] = valid ? kTScale : 0.f;
   }
   const uint32_t bad = __ballot_sync(0xffffffffu, inside && !valid);
   const uint32_t any = __ballot_sync(0xffffffffu, valid);
@@ -144,24 +124,140 @@ __global__ void __launch_bounds__(256) state_init_kernel(
 // ---------------------------------------------------------------------------
 // blend: one warp per 8x8 sub-tile, 2 adjacent pixels per lane, 4 warps a block
 // ---------------------------------------------------------------------------
-constexpr int kStage = 32;  // list entries examined per round (one per lane)
+constexpr int kRound = 32;     // Gaussians composited per round (one per lane)
+constexpr int kBufStride = 36; // row stride of the partial-sum buffer (16-byte rows)
+constexpr int kMinorCap = 8;   // label-boundary lanes a warp sums in shared memory
 
+// Staged Gaussians of one round, two per float4 (g = first half of each
+// pair of components, h = second): pair k holds Gaussians 2k and 2k + 1.
 struct SubSmem {
-  float4 w[kStage];       // whitening matrix of each staged Gaussian
-  float4 bo[kStage];      // (b0, b1, opacity, -)
-  int32_t gid[kStage];    // scene index of each staged Gaussian
-  float buf[kStage][33];  // [Gaussian][lane position in label order]: main-label sums
-  int32_t poslab[32];     // label of each lane position (INT_MAX: none)
+  float4 wx[kRound / 2];             // (W00 g, W00 h, W10 g, W10 h): x coefficients of w = W p + b
+  float4 wy[kRound / 2];             // (W01 g, W01 h, W11 g, W11 h): y coefficients
+  float4 bb[kRound / 2];             // (b0 g, b0 h, b1 g, b1 h)
+  float4 oo[kRound / 2];             // (-log2 o_g, -log2 o_h, clamp g, clamp h)
+  int32_t gid[kRound];               // scene index of each staged Gaussian
+  uint32_t queue[2 * kRound];        // slots of queued list entries
+  float buf[kRound][kBufStride];     // [Gaussian][lane position, by main label]
+  float buf2[kRound][kMinorCap];     // [Gaussian][boundary lane, by its second label]
+  int32_t poslab[32];                // label of each lane position (INT_MAX: none)
+  int32_t minlab[kMinorCap];         // second label of each boundary-lane position
 };
 
-template <typename LabelT, typename TableT>
-__global__ void __launch_bounds__(128, 10) blend_kernel(
+__device__ __forceinline__ float2 fmul2_ftz(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.ftz.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)),
+        "l"(*reinterpret_cast<unsigned long long*>(&b)));
+  return *reinterpret_cast<float2*>(&d);
+}
+
+// 1.0f if t >= thr (t - thr_below a positive multiple of ulp(thr)), else 0.0f:
+// saturate((t - thr_below) / ulp(thr)), exact for the scaled transmittance.
+__device__ __forceinline__ float step_sat(float t, float neg_thr_scaled) {
+  float d;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(t), "f"(kStepScale), "f"(neg_thr_scaled));
+  return d;
+}
+
+// One round: the lane's two pixels P and Q = P + (1, 0) against the staged
+// Gaussian pairs, in depth order.  kMinor: the warp has label-boundary lanes
+// (P and Q labelled differently); their Q terms go to the second plane
+// (slot mpos < kMinorCap) or, past its capacity, straight to the table.
+template <bool kMinor, bool kCensus, typename TableT>
+__device__ __forceinline__ void composite_round(
+    SubSmem& S, int npairs, float2 X2, float2 Y2, float neg_thr, float wq, int pos, int mpos,
+    bool minor, int lab1, int E, TableT* __restrict__ table, float2& Tu,
+    unsigned long long& n_eval, unsigned long long& n_part) {
+  const float2 nK = make_float2(-kTScale, -kTScale);
+  const float2 skip = make_float2(kSkipScale, kSkipScale);
+  const bool spill = minor && mpos >= kMinorCap;
+  for (int k = 0; k < npairs; ++k) {
+    const float4 rx = S.wx[k], ry = S.wy[k], rb = S.bb[k], ro = S.oo[k];
+    const float2 wx0 = make_float2(rx.x, rx.y), wx1 = make_float2(rx.z, rx.w);
+    const float2 wy0 = make_float2(ry.x, ry.y), wy1 = make_float2(ry.z, ry.w);
+    const float2 b0 = make_float2(rb.x, rb.y), b1 = make_float2(rb.z, rb.w);
+    const float2 nlo = make_float2(ro.x, ro.y);
+    // w at P for (g, h), then q = |w|^2 - log2 o at P and at Q = P + (1, 0)
+    float2 u0 = __ffma2_rn(wx0, X2, __ffma2_rn(wy0, Y2, b0));
+    float2 u1 = __ffma2_rn(wx1, X2, __ffma2_rn(wy1, Y2, b1));
+    const float2 qP = __ffma2_rn(u0, u0, __ffma2_rn(u1, u1, nlo));
+    u0 = __fadd2_rn(u0, wx0);
+    u1 = __fadd2_rn(u1, wx1);
+    const float2 qQ = __ffma2_rn(u0, u0, __ffma2_rn(u1, u1, nlo));
+    float2 ag = make_float2(ex2_approx(-qP.x), ex2_approx(-qQ.x));  // Gaussian g at (P, Q)
+    float2 ah = make_float2(ex2_approx(-qP.y), ex2_approx(-qQ.y));  // Gaussian h at (P, Q)
+    if (ro.z != 0.f || ro.w != 0.f) {
+      ag.x = fminf(ag.x, kAlphaMax);
+      ag.y = fminf(ag.y, kAlphaMax);
+      ah.x = fminf(ah.x, kAlphaMax);
+      ah.y = fminf(ah.y, kAlphaMax);
+    }
+    ag = fmul2_ftz(ag, skip);  // 0 where alpha < 1/255
+    ah = fmul2_ftz(ah, skip);
+    if (kCensus) {
+      n_eval += (Tu.x != 0.f) + (Tu.y != 0.f);
+      n_part += (Tu.x != 0.f && ag.x != 0.f) + (Tu.y != 0.f && ag.y != 0.f);
+    }
+    float2 cg = __fmul2_rn(ag, Tu);              // alpha_g T
+    const float2 T1 = __ffma2_rn(cg, nK, Tu);    // T (1 - alpha_g), scaled
+    if (kCensus) {
+      n_eval += (T1.x != 0.f) + (T1.y != 0.f);
+      n_part += (T1.x != 0.f && ah.x != 0.f) + (T1.y != 0.f && ah.y != 0.f);
+    }
+    float2 ch = __fmul2_rn(ah, T1);
+    const float2 T2 = __ffma2_rn(ch, nK, T1);
+    // the pixel stops before a Gaussian that takes T below 1e-4; once T2
+    // passes the threshold so did T1 (alpha >= 0)
+    const float2 gg = make_float2(step_sat(T1.x, neg_thr), step_sat(T1.y, neg_thr));
+    const float2 gh = make_float2(step_sat(T2.x, neg_thr), step_sat(T2.y, neg_thr));
+    cg = __fmul2_rn(cg, gg);
+    ch = __fmul2_rn(ch, gh);
+    Tu = __fmul2_rn(T2, gh);
+    if (kCensus) {
+      // a pixel that stops at g does not evaluate h: undo its count
+      n_eval -= (T1.x != 0.f && gg.x == 0.f) + (T1.y != 0.f && gg.y == 0.f);
+      n_part -= (T1.x != 0.f && gg.x == 0.f && ah.x != 0.f) +
+                (T1.y != 0.f && gg.y == 0.f && ah.y != 0.f);
+    }
+    S.buf[2 * k][pos] = fmaf(cg.y, wq, cg.x);
+    S.buf[2 * k + 1][pos] = fmaf(ch.y, wq, ch.x);
+    if (kMinor) {
+      if (minor && !spill) {
+        S.buf2[2 * k][mpos] = cg.y;
+        S.buf2[2 * k + 1][mpos] = ch.y;
+      }
+      if (spill && cg.y != 0.f)
+        table_add(&table[static_cast<int64_t>(S.gid[2 * k]) * E + lab1], cg.y);
+      if (spill && ch.y != 0.f)
+        table_add(&table[static_cast<int64_t>(S.gid[2 * k + 1]) * E + lab1], ch.y);
+    }
+  }
+}
+
+// Rank of each lane among the lanes with the same or a smaller key (keys of
+// INT_MAX last): one ballot per distinct key.
+__device__ __forceinline__ int rank_by_key(int key, uint32_t lt) {
+  int r = 0;
+  for (uint32_t rem = 0xffffffffu; rem;) {
+    const int lead = __ffs(rem) - 1;
+    const int k = __shfl_sync(0xffffffffu, key, lead);
+    const uint32_t grp = __ballot_sync(0xffffffffu, key == k);
+    rem &= ~grp;
+    if (k < key) r += __popc(grp);
+    if (k == key) r += __popc(grp & lt);
+  }
+  return r;
+}
+
+template <typename LabelT, typename TableT, bool kCensus>
+__global__ void __launch_bounds__(128, 8) blend_kernel(
     const ViewParams* __restrict__ views, const uint2* __restrict__ ranges,
-    const uint32_t* __restrict__ list_val, const ProjRecord* __restrict__ rec,
-    const CompactRecord* __restrict__ rec16, const float4* __restrict__ pos_op, int64_t n, int E,
+    const uint32_t* __restrict__ list_key, const uint32_t* __restrict__ list_val,
+    const ProjRecord* __restrict__ rec, const CompactRecord* __restrict__ rec16, int64_t n, int E,
     TableT* __restrict__ table, float* __restrict__ state, uint64_t* __restrict__ sat,
-    uint64_t* __restrict__ subsat, uint8_t* __restrict__ sat_chunk, int chunk,
-    unsigned long long* __restrict__ counters) {
+    uint64_t* __restrict__ subsat, uint8_t* __restrict__ sat_chunk,
+    uint8_t* __restrict__ sub_chunk, int chunk, unsigned long long* __restrict__ counters) {
   __shared__ SubSmem S_warp[4];
   SubSmem& S = S_warp[threadIdx.x >> 5];
   const int v = blockIdx.y;
@@ -189,171 +285,253 @@ __global__ void __launch_bounds__(128, 10) blend_kernel(
   if (py < H && px0 + 1 < W) lab1 = static_cast<int>(mask[p0 + 1]);
   const bool valid0 = lab0 >= 0 && lab0 < E, valid1 = lab1 >= 0 && lab1 < E;
   float* const st = state + views[v].state_off;
-  float2 T = make_float2(valid0 ? st[p0] : 0.f, valid1 ? st[p0 + 1] : 0.f);
-  const float2 T_start = T;
-  float2 live = make_float2(0.f, 0.f);
-  // the lane's main label, and whether its second pixel has another one
+  float2 Tu = make_float2(valid0 ? st[p0] : 0.f, valid1 ? st[p0 + 1] : 0.f);
+  // the lane's main label (its first labelled pixel's), and whether its
+  // second pixel has another one (a label-boundary lane)
   const int main_lab = valid0 ? lab0 : (valid1 ? lab1 : -1);
   const bool minor = valid0 && valid1 && lab1 != lab0;
-  const float w0 = valid0 ? 1.f : 0.f;
-  const float w1 = (valid1 && !minor) ? 1.f : 0.f;
-  // lane positions ordered by main label (labelless lanes last): lanes with a
-  // smaller label, then lanes of the same label before this one -- one ballot
-  // per distinct label of the warp (usually one or two)
+  const float wq = minor ? 0.f : 1.f;  // weight of the second pixel in the main-label sum
+  const uint32_t lt = lanemask_lt();
+  // lane positions ordered by main label (labelless lanes last), and the
+  // boundary lanes ordered by their second label
   const int mkey = main_lab >= 0 ? main_lab : 0x7FFFFFFF;
-  const uint32_t lt_lanes = lanemask_lt();
-  int pos = 0;
-  for (uint32_t rem = 0xffffffffu; rem;) {
-    const int lead = __ffs(rem) - 1;
-    const int k = __shfl_sync(0xffffffffu, mkey, lead);
-    const uint32_t grp = __ballot_sync(0xffffffffu, mkey == k);
-    rem &= ~grp;
-    if (k < mkey) pos += __popc(grp);
-    if (k == mkey) pos += __popc(grp & lt_lanes);
-  }
-  S.poslab[pos] = mkey;
+  const int pos = rank_by_key(mkey, lt);
   const uint32_t minor_lanes = __ballot_sync(0xffffffffu, minor);
+  const int mpos = minor_lanes ? rank_by_key(minor ? lab1 : 0x7FFFFFFF, lt) : 0;
+  S.poslab[pos] = mkey;
+  if (minor && mpos < kMinorCap) S.minlab[mpos] = lab1;
   __syncwarp();
   const int plab = S.poslab[lane];
   const int plab_prev = __shfl_up_sync(0xffffffffu, plab, 1);
   const uint32_t segmask = __ballot_sync(0xffffffffu, lane == 0 || plab != plab_prev);
+  const int lab_first = S.poslab[0];
+  // one label over every position (lanes without a label carry zeros)
+  const bool one_label = __popc(segmask & __ballot_sync(0xffffffffu, plab != 0x7FFFFFFF)) <= 1;
+  const int n_minor = min(__popc(minor_lanes), kMinorCap);
 
   // pixel centres relative to the sub-tile centre, in [-3.5, 3.5]
-  const float2 X = make_float2(static_cast<float>(lx) - 3.5f, static_cast<float>(lx) - 2.5f);
-  const float yy = static_cast<float>(ly) - 3.5f;
+  const float2 X2 = make_float2(static_cast<float>(lx) - 3.5f, static_cast<float>(lx) - 3.5f);
+  const float2 Y2 = make_float2(static_cast<float>(ly) - 3.5f, static_cast<float>(ly) - 3.5f);
   const float ox = static_cast<float>(tx * kTile + sx * 8 + 4);
   const float oy = static_cast<float>(ty * kTile + sy * 8 + 4);
   const uint32_t gbase = static_cast<uint32_t>(static_cast<int64_t>(v) * n);
-  const uint32_t lt = lanemask_lt();
+  // -(1e-4 / kSkipScale rounded down to the float below) / ulp
+  const float thr = 1e-4f * kTScale;
+  const float neg_thr = -__uint_as_float(__float_as_uint(thr) - 1u) * kStepScale;
+  const uint32_t my_bit = 1u << (kSubMaskShift + sub);
   uint32_t n_staged = 0;
+  unsigned long long n_eval = 0, n_part = 0;
 
-  // list entries one round ahead
-  uint32_t g_next = rg.x + lane < rg.y ? list_val[rg.x + lane] : 0u;
-  for (uint32_t base = rg.x; base < rg.y; base += kStage) {
-    if (!__any_sync(0xffffffffu, T.x > 0.f || T.y > 0.f)) break;
-    const int nin = static_cast<int>(min(static_cast<uint32_t>(kStage), rg.y - base));
-    const uint32_t g_here = g_next;
-    if (base + kStage + lane < rg.y) g_next = list_val[base + kStage + lane];
-    // stage the Gaussians whose alpha >= 1/255 region can reach this sub-tile
-    bool keep = false;
-    float4 wk;
-    float b0f = 0.f, b1f = 0.f, ok_ = 0.f;
-    uint32_t g = 0;
-    float qc = 0.f;
-    if (lane < nin && rec16) {
-      // reduced-precision record: b = W16 (o - m) in FP32
-      g = g_here;
-      const CompactRecord r = rec16[g];
-      const float2 wa = __half22float2(*reinterpret_cast<const __half2*>(&r.w01));
-      const float2 wb = __half22float2(*reinterpret_cast<const __half2*>(&r.w23));
-      wk = make_float4(wa.x, wa.y, wb.x, wb.y);
-      const float dx = ox - r.mx, dy = oy - r.my;
-      b0f = fmaf(wk.x, dx, wk.y * dy);
-      b1f = fmaf(wk.z, dx, wk.w * dy);
-      ok_ = r.o;
-      qc = r.q_cut;
-    } else if (lane < nin) {
-      // b = W (o - m) for the sub-tile centre o: o - m_hi is exact whenever
-      // the mean lies within a factor of two of o (and off by far less than
-      // a pixel's 1e-7 otherwise); W = W_hi + W_lo
-      g = g_here;
-      const ProjRecord r = rec[g];
-      const float dx = (ox - r.m.x) - r.m.z, dy = (oy - r.m.y) - r.m.w;
-      wk = r.w_hi;
-      b0f = fmaf(wk.x, dx, fmaf(wk.y, dy, fmaf(r.w_lo.x, dx, r.w_lo.y * dy)));
-      b1f = fmaf(wk.z, dx, fmaf(wk.w, dy, fmaf(r.w_lo.z, dx, r.w_lo.w * dy)));
-      ok_ = r.misc.x;
-      qc = r.misc.y;
+  uint32_t next = rg.x;  // next list entry to read
+  uint32_t qn = 0;       // queued entries (warp-uniform)
+  for (;;) {
+    // queue, in list order, the entries whose footprint reaches this sub-tile
+    while (qn < kRound && next < rg.y) {
+      const uint32_t e = next + lane;
+      bool keep = false;
+      uint32_t val = 0;
+      if (e < rg.y) {
+        keep = (list_key[e] & my_bit) != 0u;
+        if (keep) val = list_val[e];
+      }
+      const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+      if (keep) S.queue[qn + __popc(bal & lt)] = val;
+      qn += __popc(bal);
+      next += 32;
     }
-    if (lane < nin) {
-      // over the sub-tile's pixel centres w ranges inside the box
-      // b +- 3.5 (|W_k0| + |W_k1|); keep if that box meets |w|^2 <= q_cut
-      const float h0 = 3.5f * (fabsf(wk.x) + fabsf(wk.y));
-      const float h1 = 3.5f * (fabsf(wk.z) + fabsf(wk.w));
-      const float d0 = fmaxf(0.f, fabsf(b0f) - h0), d1 = fmaxf(0.f, fabsf(b1f) - h1);
-      keep = fmaf(d0, d0, d1 * d1) <= qc;
-    }
-    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-    if (keep) {
-      const int k = __popc(bal & lt);
-      S.w[k] = wk;
-      S.bo[k] = make_float4(b0f, b1f, ok_, 0.f);
-      S.gid[k] = static_cast<int32_t>(g - gbase);
-    }
-    const int ns = __popc(bal);
-    n_staged += static_cast<uint32_t>(ns);
+    if (qn == 0) break;
     __syncwarp();
-    if (minor_lanes) {
-      // a lane whose second pixel has another label adds that pixel's
-      // contribution itself (label boundaries only)
-      for (int jj = 0; jj < ns; ++jj) {
-        const float2 c = composite2(S.w[jj], S.bo[jj], X, yy, T, live);
-        S.buf[jj][pos] = fmaf(c.x, w0, c.y * w1);
-        if (minor && c.y != 0.f) table_add(&table[static_cast<int64_t>(S.gid[jj]) * E + lab1], c.y);
+    const int nq = static_cast<int>(min(qn, static_cast<uint32_t>(kRound)));
+    // stage: lane k < nq takes queued entry k; an odd count gets an empty
+    // partner (q = +inf: alpha 0)
+    if (lane < nq || (lane == nq && (nq & 1))) {
+      float4 wk = make_float4(0.f, 0.f, 0.f, 0.f);
+      float b0f = 0.f, b1f = 0.f, nlo = __int_as_float(0x7f800000), clampf = 0.f;
+      if (lane < nq) {
+        const uint32_t g = S.queue[lane];
+        float o;
+        if (rec16) {
+          // reduced-precision record: b = W16 (o - m) in FP32
+          const CompactRecord r = rec16[g];
+          const float2 wa = __half22float2(*reinterpret_cast<const __half2*>(&r.w01));
+          const float2 wb = __half22float2(*reinterpret_cast<const __half2*>(&r.w23));
+          wk = make_float4(wa.x, wa.y, wb.x, wb.y);
+          const float dx = ox - r.mx, dy = oy - r.my;
+          b0f = fmaf(wk.x, dx, wk.y * dy);
+          b1f = fmaf(wk.z, dx, wk.w * dy);
+          o = r.o;
+          nlo = r.nlo;
+        } else {
+          // b = W (o - m) for the sub-tile centre o: o - m_hi is exact
+          // whenever the mean lies within a factor of two of o (and off by
+          // far less than a pixel's 1e-7 otherwise); W = W_hi + W_lo
+          const ProjRecord r = rec[g];
+          const float dx = (ox - r.m.x) - r.m.z, dy = (oy - r.m.y) - r.m.w;
+          wk = r.w_hi;
+          b0f = fmaf(wk.x, dx, fmaf(wk.y, dy, fmaf(r.w_lo.x, dx, r.w_lo.y * dy)));
+          b1f = fmaf(wk.z, dx, fmaf(wk.w, dy, fmaf(r.w_lo.z, dx, r.w_lo.w * dy)));
+          o = r.misc.x;
+          nlo = r.misc.z;
+        }
+        clampf = o > kAlphaMax ? 1.f : 0.f;
+        S.gid[lane] = static_cast<int32_t>(g - gbase);
       }
-    } else {
-      for (int jj = 0; jj < ns; ++jj) {
-        const float2 c = composite2(S.w[jj], S.bo[jj], X, yy, T, live);
-        S.buf[jj][pos] = fmaf(c.x, w0, c.y * w1);
-      }
+      const int k = lane >> 1, c = lane & 1;
+      float* wx = reinterpret_cast<float*>(&S.wx[k]);
+      float* wy = reinterpret_cast<float*>(&S.wy[k]);
+      float* bb = reinterpret_cast<float*>(&S.bb[k]);
+      float* oo = reinterpret_cast<float*>(&S.oo[k]);
+      wx[c] = wk.x;
+      wx[2 + c] = wk.z;
+      wy[c] = wk.y;
+      wy[2 + c] = wk.w;
+      bb[c] = b0f;
+      bb[2 + c] = b1f;
+      oo[c] = nlo;
+      oo[2 + c] = clampf;
     }
     __syncwarp();
-    if (lane < ns) {
+    const int npairs = (nq + 1) >> 1;
+    if (minor_lanes)
+      composite_round<true, kCensus>(S, npairs, X2, Y2, neg_thr, wq, pos, mpos, minor, lab1, E,
+                                     table, Tu, n_eval, n_part);
+    else
+      composite_round<false, kCensus>(S, npairs, X2, Y2, neg_thr, wq, pos, mpos, minor, lab1, E,
+                                      table, Tu, n_eval, n_part);
+    __syncwarp();
+    if (lane < nq) {
       // lane j owns staged Gaussian j: one atomic per label it reached here
       const int j = lane;
       const int64_t rowbase = static_cast<int64_t>(S.gid[j]) * E;
-      uint32_t m = segmask;
-      while (m) {
-        const int s0 = __ffs(m) - 1;
-        m &= m - 1;
-        const int s1 = m ? __ffs(m) - 1 : 32;
-        const int lab = S.poslab[s0];
-        if (lab == 0x7FFFFFFF) continue;
-        float sum = 0.f;
-        for (int l = s0; l < s1; ++l) sum += S.buf[j][l];
-        if (sum != 0.f) table_add(&table[rowbase + lab], sum);
+      // the boundary lanes' second pixels: folded into the main sum of the
+      // same label when they all share one label (the usual case)
+      float extra = 0.f;
+      int extra_lab = -1;
+      if (n_minor > 0) {
+        const int l0 = S.minlab[0];
+        bool one = true;
+        for (int r = 0; r < n_minor; ++r) one = one && S.minlab[r] == l0;
+        if (one) {
+          for (int r = 0; r < n_minor; ++r) extra += S.buf2[j][r];
+          extra_lab = l0;
+        } else {
+          float acc = 0.f;
+          int lab = l0;
+          for (int r = 0; r < n_minor; ++r) {
+            if (S.minlab[r] != lab) {
+              if (acc != 0.f) table_add(&table[rowbase + lab], acc);
+              acc = 0.f;
+              lab = S.minlab[r];
+            }
+            acc += S.buf2[j][r];
+          }
+          if (acc != 0.f) table_add(&table[rowbase + lab], acc);
+        }
       }
+      const float4* row = reinterpret_cast<const float4*>(S.buf[j]);
+      if (one_label) {
+        float sum = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 x = row[q];
+          sum += (x.x + x.y) + (x.z + x.w);
+        }
+        if (lab_first == extra_lab) {
+          sum += extra;
+          extra = 0.f;
+        }
+        if (sum != 0.f && lab_first != 0x7FFFFFFF) table_add(&table[rowbase + lab_first], sum);
+      } else {
+        // segments of equal label over the positions (segmask: their starts)
+        float acc = 0.f;
+        int lab = lab_first;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 x = row[q];
+          const uint32_t starts = (segmask >> (4 * q)) & (q == 0 ? 0xEu : 0xFu);
+          if (starts == 0u) {
+            acc += (x.x + x.y) + (x.z + x.w);
+          } else {
+            const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              if ((starts >> i) & 1u) {
+                if (lab == extra_lab) {
+                  acc += extra;
+                  extra = 0.f;
+                }
+                if (acc != 0.f && lab != 0x7FFFFFFF) table_add(&table[rowbase + lab], acc);
+                acc = 0.f;
+                lab = S.poslab[4 * q + i];
+              }
+              acc += xs[i];
+            }
+          }
+        }
+        if (lab == extra_lab) {
+          acc += extra;
+          extra = 0.f;
+        }
+        if (acc != 0.f && lab != 0x7FFFFFFF) table_add(&table[rowbase + lab], acc);
+      }
+      if (extra != 0.f) table_add(&table[rowbase + extra_lab], extra);
     }
+    n_staged += static_cast<uint32_t>(nq);
+    // the rest of the queue moves to its front
+    const uint32_t rest = qn - static_cast<uint32_t>(nq);
+    const uint32_t moved = lane < rest ? S.queue[nq + lane] : 0u;
     __syncwarp();
+    if (lane < rest) S.queue[lane] = moved;
+    qn = rest;
+    __syncwarp();
+    if (!__any_sync(0xffffffffu, Tu.x != 0.f || Tu.y != 0.f)) break;
   }
 
-  if (valid0) st[p0] = T.x;
-  if (valid1) st[p0 + 1] = T.y;
-  // steps evaluated up to termination: those that ran on, plus the stop
-  uint32_t n_eval = static_cast<uint32_t>(live.x) + static_cast<uint32_t>(live.y) +
-                    ((T_start.x > 0.f && T.x == 0.f) ? 1u : 0u) +
-                    ((T_start.y > 0.f && T.y == 0.f) ? 1u : 0u);
-  if (__all_sync(0xffffffffu, T.x == 0.f && T.y == 0.f) && lane == 0) {
+  if (valid0) st[p0] = Tu.x;
+  if (valid1) st[p0 + 1] = Tu.y;
+  if (__all_sync(0xffffffffu, Tu.x == 0.f && Tu.y == 0.f) && lane == 0) {
     const unsigned long long bit = 1ull << (gsub & 63);
     const unsigned long long nib = 0xFull << (gsub & 63 & ~3);
     const unsigned long long old =
         atomicOr(reinterpret_cast<unsigned long long*>(subsat + (gsub >> 6)), bit);
+    // later chunks list nothing for this sub-tile alone: its pixels' lists
+    // are complete up to this chunk only
+    if (sub_chunk) sub_chunk[gsub] = static_cast<uint8_t>(chunk);
     if (((old | bit) & nib) == nib) {
       set_bit(sat, gtile);
-      // the tile's lists are complete up to this chunk only
       if (sat_chunk) sat_chunk[gtile] = static_cast<uint8_t>(chunk);
     }
   }
+  if (kCensus) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) n_eval += __shfl_xor_sync(0xffffffffu, n_eval, o);
-  if (lane == 0) {
-    if (n_eval) atomicAdd(&counters[kPairs], static_cast<unsigned long long>(n_eval));
-    if (n_staged) atomicAdd(&counters[kStaged], static_cast<unsigned long long>(n_staged));
+    for (int o = 16; o > 0; o >>= 1) {
+      n_eval += __shfl_xor_sync(0xffffffffu, n_eval, o);
+      n_part += __shfl_xor_sync(0xffffffffu, n_part, o);
+    }
+    if (lane == 0) {
+      if (n_eval) atomicAdd(&counters[kPairs], n_eval);
+      if (n_part) atomicAdd(&counters[kCensusPairs], n_part);
+    }
   }
+  if (lane == 0 && n_staged) atomicAdd(&counters[kStaged], static_cast<unsigned long long>(n_staged));
 }
 
 template <typename LabelT, typename TableT>
 cudaError_t launch_typed(const ViewParams* views, int n_views, int max_tiles, const uint2* ranges,
-                         const uint32_t* list_val, const ProjRecord* rec,
-                         const CompactRecord* rec16, const float4* pos_op, int64_t n, int E,
-                         void* table, float* state, uint64_t* sat, uint64_t* subsat,
-                         uint8_t* sat_chunk, int chunk, unsigned long long* counters,
+                         const uint32_t* list_key, const uint32_t* list_val, const ProjRecord* rec,
+                         const CompactRecord* rec16, int64_t n, int E, void* table, float* state,
+                         uint64_t* sat, uint64_t* subsat, uint8_t* sat_chunk, uint8_t* sub_chunk,
+                         int chunk, unsigned long long* counters, bool census,
                          cudaStream_t stream) {
   dim3 grid(static_cast<unsigned>(max_tiles), static_cast<unsigned>(n_views));
-  blend_kernel<LabelT, TableT><<<grid, 128, 0, stream>>>(views, ranges, list_val, rec, rec16,
-                                                        pos_op, n, E,
-                                                        static_cast<TableT*>(table), state, sat,
-                                                        subsat, sat_chunk, chunk, counters);
+  if (census)
+    blend_kernel<LabelT, TableT, true><<<grid, 128, 0, stream>>>(
+        views, ranges, list_key, list_val, rec, rec16, n, E, static_cast<TableT*>(table), state,
+        sat, subsat, sat_chunk, sub_chunk, chunk, counters);
+  else
+    blend_kernel<LabelT, TableT, false><<<grid, 128, 0, stream>>>(
+        views, ranges, list_key, list_val, rec, rec16, n, E, static_cast<TableT*>(table), state,
+        sat, subsat, sat_chunk, sub_chunk, chunk, counters);
   return cudaGetLastError();
 }
 
@@ -372,29 +550,30 @@ cudaError_t launch_state_init(const ViewParams* views, int n_views, int max_tile
 }
 
 cudaError_t launch_blend(const ViewParams* views, int n_views, int max_tiles_per_view,
-                         const uint2* ranges, const uint32_t* list_val, const ProjRecord* rec,
-                         const CompactRecord* rec16, const float4* pos_op, int64_t n, int E,
+                         const uint2* ranges, const uint32_t* list_key, const uint32_t* list_val,
+                         const ProjRecord* rec, const CompactRecord* rec16, int64_t n, int E,
                          int mask_dtype, void* table, int table_dtype, float* state,
-                         uint64_t* sat, uint64_t* subsat, uint8_t* sat_chunk, int chunk,
-                         unsigned long long* counters, cudaStream_t stream) {
+                         uint64_t* sat, uint64_t* subsat, uint8_t* sat_chunk,
+                         uint8_t* sub_chunk, int chunk, unsigned long long* counters, bool census,
+                         cudaStream_t stream) {
   if (n_views == 0 || max_tiles_per_view == 0) return cudaSuccess;
   const int mt = max_tiles_per_view;
   if (mask_dtype == 4) {
     if (table_dtype == 0)
-      return launch_typed<uint8_t, float>(views, n_views, mt, ranges, list_val, rec, rec16, pos_op,
-                                          n, E, table, state, sat, subsat, sat_chunk, chunk,
-                                          counters, stream);
-    return launch_typed<uint8_t, double>(views, n_views, mt, ranges, list_val, rec, rec16, pos_op,
-                                         n, E, table, state, sat, subsat, sat_chunk, chunk,
-                                         counters, stream);
+      return launch_typed<uint8_t, float>(views, n_views, mt, ranges, list_key, list_val, rec,
+                                          rec16, n, E, table, state, sat, subsat, sat_chunk,
+                                          sub_chunk, chunk, counters, census, stream);
+    return launch_typed<uint8_t, double>(views, n_views, mt, ranges, list_key, list_val, rec,
+                                         rec16, n, E, table, state, sat, subsat, sat_chunk,
+                                         sub_chunk, chunk, counters, census, stream);
   }
   if (table_dtype == 0)
-    return launch_typed<int32_t, float>(views, n_views, mt, ranges, list_val, rec, rec16, pos_op,
-                                        n, E, table, state, sat, subsat, sat_chunk, chunk,
-                                        counters, stream);
-  return launch_typed<int32_t, double>(views, n_views, mt, ranges, list_val, rec, rec16, pos_op,
-                                       n, E, table, state, sat, subsat, sat_chunk, chunk,
-                                       counters, stream);
+    return launch_typed<int32_t, float>(views, n_views, mt, ranges, list_key, list_val, rec, rec16,
+                                        n, E, table, state, sat, subsat, sat_chunk, sub_chunk,
+                                        chunk, counters, census, stream);
+  return launch_typed<int32_t, double>(views, n_views, mt, ranges, list_key, list_val, rec, rec16,
+                                       n, E, table, state, sat, subsat, sat_chunk, sub_chunk,
+                                       chunk, counters, census, stream);
 }
 
 }  // namespace fs

@@ -55,8 +55,9 @@ struct ViewParams {
 //   w_hi, w_lo = whitening matrix W (row-major 2x2) as float pairs, with
 //                |W d|^2 = 0.5 log2(e) d^T Sigma2D^-1 d
 //   m          = (mx_hi, my_hi, mx_lo, my_lo): the projected mean as float pairs
-//   misc       = (opacity, q_cut, -, -), q_cut ~ log2(255 o): alpha = o 2^-|w|^2
-//                reaches 1/255 at |w|^2 = log2(255 o) (stored slightly widened)
+//   misc       = (opacity, q_cut, -log2 o, -), q_cut ~ log2(255 o): alpha =
+//                o 2^-|w|^2 reaches 1/255 at |w|^2 = log2(255 o) (stored
+//                slightly widened)
 // For a sub-tile whose centre is o the blend forms b = W (o - m) in FP32 (o - m
 // is exact or nearly so) and evaluates w = W_hi (p - o) + b for the pixel
 // centre p, |p - o| <= 5 px.
@@ -78,7 +79,8 @@ struct alignas(16) CompactRecord {
   float mx, my;
   uint32_t w01, w23;  // (W00, W01), (W10, W11) as FP16 pairs, low half first
   float o, q_cut;
-  float pad0, pad1;
+  float nlo;          // -log2 o
+  float pad1;
 };
 
 // Footprint of one (view, Gaussian) for the tile binning: the alpha >= 1/255

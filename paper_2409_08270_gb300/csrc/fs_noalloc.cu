@@ -112,12 +112,6 @@ fs_status scratch_address(int device, unsigned char** out) {
   return FS_OK;
 }
 
-void split_pair(double x, float* hi, float* lo) {
-  const float h = static_cast<float>(x);
-  *hi = h;
-  *lo = static_cast<float>(x - static_cast<double>(h));
-}
-
 int bits_for(int64_t x) {
   int b = 0;
   while ((static_cast<int64_t>(1) << b) < x) ++b;
@@ -227,22 +221,8 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
                    "fs_solve_noalloc: a Gaussian has a zero quaternion or a non-finite attribute");
 
   for (int v = 0; v < n_views; ++v) {
-    const fs_camera& cam = cams[v];
     ViewParams vp;
-    memset(&vp, 0, sizeof(vp));
-    for (int k = 0; k < 9; ++k) split_pair(cam.R[k], &vp.R_hi[k], &vp.R_lo[k]);
-    for (int k = 0; k < 3; ++k) split_pair(cam.t[k], &vp.t_hi[k], &vp.t_lo[k]);
-    split_pair(cam.fx, &vp.fx_hi, &vp.fx_lo);
-    split_pair(cam.fy, &vp.fy_hi, &vp.fy_lo);
-    split_pair(cam.cx, &vp.cx_hi, &vp.cx_lo);
-    split_pair(cam.cy, &vp.cy_hi, &vp.cy_lo);
-    split_pair(0.2, &vp.near_hi, &vp.near_lo);
-    split_pair(1.3 * (0.5 * cam.width / cam.fx), &vp.limx_hi, &vp.limx_lo);
-    split_pair(1.3 * (0.5 * cam.height / cam.fy), &vp.limy_hi, &vp.limy_lo);
-    vp.width = cam.width;
-    vp.height = cam.height;
-    vp.tiles_x = (cam.width + kTile - 1) / kTile;
-    vp.tiles_y = (cam.height + kTile - 1) / kTile;
+    fill_view(cams[v], &vp);  // the same view set-up as fs_solve
     vp.tile_base = 0;
     vp.state_off = 0;
     vp.mask = masks[v];
@@ -267,7 +247,8 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
       const int64_t p1 = (ci == chunks - 1) ? n : (n >> (chunks - 1 - ci));
       const int64_t n_pos = p1 - p0;
       if (n_pos <= 0) continue;
-      NA_CUDA(launch_chunk_count(p0, n_pos, n, vd, sval, foot, sat, ccnt, strm), "count");
+      NA_CUDA(launch_chunk_count(p0, n_pos, n, vd, sval, foot, sat, subsat, ccnt, strm),
+              "count");
       NA_CUDA(exclusive_scan(ccnt, nullptr, offs, n_pos, total_d, scan_tmp, strm), "scan");
       uint32_t I = 0;
       NA_CUDA(cudaMemcpyAsync(&I, total_d, 4, cudaMemcpyDeviceToHost, strm), "readback");
@@ -277,8 +258,8 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
                        "fs_solve_noalloc: a view needs more than FS_NOALLOC_MAX_LIST_ENTRIES "
                        "(tile, Gaussian) pairs in one depth chunk; the table is incomplete");
       if (I > 0) {
-        NA_CUDA(launch_emit(p0, n_pos, n, vd, sval, offs, ccnt, foot, sat, lk_a, lv_a, ctr,
-                            strm),
+        NA_CUDA(launch_emit(p0, n_pos, n, vd, sval, offs, ccnt, foot, sat, subsat, lk_a, lv_a,
+                            ctr, strm),
                 "emit");
         bool alt2 = false;
         NA_CUDA(radix_sort_pairs(lk_a, lv_a, lk_b, lv_b, I, bits_for(tiles), sort_tmp, &alt2, strm),
@@ -287,9 +268,8 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
         const uint32_t* lval = alt2 ? lv_b : lv_a;
         NA_CUDA(cudaMemsetAsync(ranges, 0, static_cast<size_t>(tiles) * 8, strm), "clear");
         NA_CUDA(launch_ranges(I, lkey, ranges, strm), "ranges");
-        NA_CUDA(launch_blend(vd, 1, tiles, ranges, lval, rec, nullptr, nullptr, n, E, mask_dtype,
-                             table, FS_F32,
-                             state, sat, subsat, nullptr, 0, ctr, strm),
+        NA_CUDA(launch_blend(vd, 1, tiles, ranges, lkey, lval, rec, nullptr, n, E, mask_dtype,
+                             table, FS_F32, state, sat, subsat, nullptr, nullptr, 0, ctr, false, strm),
                 "blend");
       }
       p0 = p1;

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "FS_OK", 1: "FS_INVALID_ARGUMENT", 2: "FS_OUT_OF_MEMORY", 3: 
 # every entry point declared in include/flashsplat.h
 EXPORTS = ["fs_version", "fs_last_error", "fs_create", "fs_destroy", "fs_scene_create",
            "fs_scene_destroy", "fs_scene_size", "fs_accumulate", "fs_assign", "fs_solve",
-           "fs_synchronize", "fs_solve_noalloc", "fs_server_create", "fs_server_add_scene",
+           "fs_synchronize", "fs_check_wait_timeout", "fs_solve_noalloc", "fs_server_create", "fs_server_add_scene",
            "fs_server_submit", "fs_server_fetch", "fs_server_cancel", "fs_server_destroy"]
 
 
@@ -37,7 +37,7 @@ class fs_options(ctypes.Structure):
     _fields_ = [("views_per_batch", ctypes.c_int32), ("time_stages", ctypes.c_int32),
                 ("depth_chunks", ctypes.c_int32), ("recheck_margin", ctypes.c_float),
                 ("recheck_reproject", ctypes.c_int32), ("record_precision", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 10)]
+                ("census", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
 
 
 class fs_gaussians(ctypes.Structure):
@@ -59,7 +59,8 @@ class fs_stats(ctypes.Structure):
                 ("pairs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("blend_ms", ctypes.c_double), ("blend_launches", ctypes.c_int64),
                 ("staged_entries", ctypes.c_int64), ("rechecked", ctypes.c_int64),
-                ("recheck_pairs", ctypes.c_int64), ("recheck_rebinned", ctypes.c_int64)]
+                ("recheck_pairs", ctypes.c_int64), ("recheck_rebinned", ctypes.c_int64),
+                ("census_pairs", ctypes.c_int64)]
 
 
 class fs_result(ctypes.Structure):
@@ -121,6 +122,7 @@ def load(path: str | None = None):
         "fs_solve": (i32, [vp, vp, ctypes.POINTER(fs_camera), i32, ctypes.POINTER(vp), i32, i32,
                            i32, f32, ctypes.POINTER(fs_result), vp]),
         "fs_synchronize": (i32, [vp, vp, ctypes.POINTER(fs_stats)]),
+        "fs_check_wait_timeout": (i32, [i32, i32]),
         "fs_solve_noalloc": (i32, [i32, ctypes.POINTER(fs_gaussians), ctypes.POINTER(fs_camera),
                                    i32, ctypes.POINTER(vp), i32, i32, f32, vp, vp, vp, vp, vp]),
         "fs_server_create": (i32, [ctypes.POINTER(fs_server_options), ctypes.POINTER(vp)]),
@@ -157,7 +159,8 @@ def fs_last_error() -> str:
 
 def fs_create(device: int = 0, views_per_batch: int = 0, time_stages: bool = False,
               depth_chunks: int = 0, recheck_margin: float = 0.0,
-              recheck_reproject: bool = False, record_precision: int = 0) -> int:
+              recheck_reproject: bool = False, record_precision: int = 0,
+              census: bool = False) -> int:
     ctx = ctypes.c_void_p()
     opt = fs_options()
     opt.views_per_batch = views_per_batch
@@ -166,6 +169,7 @@ def fs_create(device: int = 0, views_per_batch: int = 0, time_stages: bool = Fal
     opt.recheck_margin = recheck_margin
     opt.recheck_reproject = 1 if recheck_reproject else 0
     opt.record_precision = record_precision
+    opt.census = 1 if census else 0
     check(load().fs_create(ctypes.byref(ctx), device, ctypes.byref(opt)))
     return ctx.value
 
@@ -210,6 +214,11 @@ def fs_synchronize(ctx, stream=0) -> fs_stats:
     return st
 
 
+def fs_check_wait_timeout(device: int, spins: int) -> int:
+    """Status of the bounded-wait diagnostic (FS_TIMEOUT expected)."""
+    return load().fs_check_wait_timeout(device, spins)
+
+
 def fs_solve_noalloc(device, g: fs_gaussians, cams, masks, mask_dtype, E, gamma, table,
                      bits=None, label=None, margin=None, stream=0):
     """Allocation-free small-scene solve (see include/flashsplat.h)."""
@@ -250,11 +259,12 @@ class Solver:
 
     def __init__(self, gaussians, device: int = 0, views_per_batch: int = 0,
                  time_stages: bool = False, depth_chunks: int = 0, recheck_margin: float = 0.0,
-                 recheck_reproject: bool = False, record_precision: int = 0):
+                 recheck_reproject: bool = False, record_precision: int = 0,
+                 census: bool = False):
         torch = _torch()
         self.device = torch.device("cuda", device)
         self.ctx = fs_create(device, views_per_batch, time_stages, depth_chunks, recheck_margin,
-                             recheck_reproject, record_precision)
+                             recheck_reproject, record_precision, census)
         self.scene = None
         dev = {}
         for k in ("mean", "quat", "scale", "opacity"):

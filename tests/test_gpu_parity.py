@@ -219,3 +219,57 @@ def test_golden_stacks_on_one_pixel(fsb, case):
     got = [float(gpu["table"][i, 1]) for i in order]
     exp = list(gd["contributions"]) + [0.0] * (n - len(gd["contributions"]))
     np.testing.assert_allclose(got, exp, rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("kind", ["tiny", "binary"])
+def test_census_counts_the_oracles_work_unit(fsb, tiny, kind):
+    """The work unit of the blend's roofline: (pixel, Gaussian) pairs with
+    alpha >= 1/255 that a pixel's front-to-back walk reaches, its stop
+    included (Sec. 3.1 Eq. 1 with the rasteriser's skip and stop rules).  The
+    census variant counts them on the GPU; the oracle counts them in its own
+    walk.  They may differ only where a decision sits on its threshold.  The
+    census variant must give the same table as the timed one."""
+    w = tiny if kind == "tiny" else synth.binary_scene(n=40000, views=2, width=1008, height=756)
+    s = fsb.Solver(w.gaussians, census=True, recheck_margin=-1.0)
+    try:
+        c = s.solve(w.cams, w.masks, w.E, w.gamma)
+        c = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in c.items()}
+    finally:
+        s.close()
+    p = _solve(fsb, w, recheck_margin=-1.0)
+    np.testing.assert_allclose(c["table"], p["table"], rtol=1e-6, atol=1e-12)
+    acc = oracle.accumulate(w.gaussians, w.cams, w.masks, w.E)
+    st = c["stats"]
+    print(kind, "census", st.census_pairs, "oracle", acc.n_part, "evaluated", st.pairs,
+          "staged", st.staged_entries)
+    assert acc.n_part > 0
+    assert abs(st.census_pairs - acc.n_part) <= max(16, 1e-5 * acc.n_part)
+    assert st.pairs >= st.census_pairs
+    assert p["stats"].census_pairs == 0 and p["stats"].pairs == 0
+
+
+def test_label_boundaries_inside_sub_tiles(fsb, tiny):
+    """Masks whose labels change inside 8x8 sub-tiles and between the two
+    pixels a lane walks (vertical stripes of odd width, checkerboard blocks),
+    with bad labels mixed in: every (Gaussian, label) sum still matches."""
+    H, W = tiny.cams[0]["height"], tiny.cams[0]["width"]
+    yy, xx = np.mgrid[0:H, 0:W]
+    m1 = ((xx // 3) % 4).astype(np.int32)                 # stripes 3 px wide, 4 labels
+    m2 = (((xx // 5) + (yy // 7)) % 3).astype(np.int32)    # blocks
+    m2[::11, ::13] = 9                                     # out of range: skipped
+    masks = [m1, m2] * 4
+    w = synth.Workload("stripes", tiny.gaussians, tiny.cams, masks, 4, 0.3, tiny.gt)
+    gpu = _solve(fsb, w)
+    acc = oracle.accumulate(tiny.gaussians, tiny.cams, masks, 4)
+    _check(gpu, acc, 0.3)
+    assert gpu["stats"].bad_labels == acc.n_bad_label > 0
+
+
+def test_bounded_wait_gives_up_with_timeout(fsb, tiny):
+    """The binning's wait for a preceding block's offset is bounded: on a
+    grid whose predecessor never publishes, it gives up after the given
+    number of polls and reports FS_TIMEOUT; the device stays usable."""
+    assert fsb.fs_check_wait_timeout(0, 2000) == fsb.FS_TIMEOUT
+    assert "gave up" in fsb.fs_last_error()
+    gpu = _solve(fsb, synth.tiny_scene(n=500, views=1))
+    assert gpu["table"].sum() > 0

@@ -225,6 +225,25 @@ def test_thread_count_and_selection(tiny):
     np.testing.assert_allclose(c.table, a.table[sel], rtol=1e-13, atol=1e-16)
 
 
+def test_tracked_rows_equal_full_walk_on_clustered_scene():
+    """Tracked rows (each Gaussian walked over its own box, candidates from a
+    coarse grid of the view) equal the full walk's rows on a clustered scene
+    whose footprints span many grid cells, small and large ones alike."""
+    w = synth.binary_scene(n=20000, views=2, width=320, height=240)
+    full = oracle.accumulate(w.gaussians, w.cams, w.masks, w.E)
+    seen = np.flatnonzero(full.table.sum(1) > 0)
+    area = np.zeros(w.n)
+    for cam in w.cams:
+        pv = oracle.project_view(w.gaussians, cam)
+        area = np.maximum(area, pv[:, 8] * pv[:, 9])
+    big = seen[np.argsort(-area[seen])[:20]]
+    rng = np.random.default_rng(2)
+    sel = np.unique(np.concatenate([big, rng.choice(seen, 80, replace=False)]))
+    assert area[big].min() > 64 * 64
+    t = oracle.accumulate(w.gaussians, w.cams, w.masks, w.E, sel=sel)
+    np.testing.assert_allclose(t.table, full.table[sel], rtol=1e-12, atol=1e-15)
+
+
 def test_column_sums_independent_of_labels(tiny):
     """sum_e A[i, e] depends on the scene and cameras only; relabelling the
     masks permutes the columns."""
@@ -366,6 +385,43 @@ def test_assign_threshold_law(gamma):
         np.testing.assert_array_equal(S, (A > 0).T | (s == 0)[None, :])
 
 
+def _normalise_bias_argmax(A, gamma):
+    """The multi-instance assignment as Supp. Sec. 6 states its steps, with
+    torch's own primitives in float64: the row sum is taken once; for every
+    object the pair (others, object) is L1-normalised over the pair (torch's
+    F.normalize, p = 1, default epsilon), the bias is added to the "others"
+    entry and the argmax (first maximum) decides membership."""
+    import torch
+    import torch.nn.functional as F
+    t = torch.from_numpy(np.asarray(A, dtype=np.float64)).T      # [E, N]
+    total = t.sum(0)
+    rows = []
+    for e in range(t.shape[0]):
+        pair = torch.stack([total - t[e], t[e]])                 # [2, N]
+        pair = F.normalize(pair, p=1, dim=0)
+        pair[0] += gamma
+        rows.append(torch.argmax(pair, dim=0) == 1)
+    return torch.stack(rows).numpy()
+
+
+@pytest.mark.parametrize("gamma", GOLDEN["gamma_grid"]["values"] + GOLDEN["gamma_grid"]["ends"])
+def test_assign_equals_normalise_bias_argmax(gamma, tiny):
+    """The oracle's closed-form rule gives the same segmentation matrix as
+    the normalise / bias / argmax procedure run with torch, on oracle tables
+    (binary and multi-label, unseen rows included) and on a random table with
+    rows far below the normalisation epsilon."""
+    acc2 = oracle.accumulate(tiny.gaussians, tiny.cams[:3], tiny.masks[:3], 2)
+    rng = np.random.default_rng(4)
+    masks4 = [rng.integers(0, 4, m.shape).astype(np.int32) for m in tiny.masks[:3]]
+    acc4 = oracle.accumulate(tiny.gaussians, tiny.cams[:3], masks4, 4)
+    R = rng.exponential(1.0, (3000, 5)) * (rng.random((3000, 5)) < 0.5)
+    R[:300] *= 1e-15                                              # below epsilon = 1e-12
+    R[300:320] = 0.0
+    for A in (acc2.table, acc4.table, R):
+        A = np.vstack([A, np.zeros((3, A.shape[1]))])             # three unseen Gaussians
+        np.testing.assert_array_equal(assign(A, gamma), _normalise_bias_argmax(A, gamma))
+
+
 def test_assign_overlap_only_below_zero():
     A = np.array([[1.0, 1.0, 1.0], [2.0, 1.0, 1.0]])
     assert assign(A, -0.5)[:, 0].sum() == 3       # Sec. 3.3: subsets overlap for gamma < 0
@@ -395,6 +451,80 @@ def test_special_masks(tiny):
     for gamma in (-0.8, 0.0, 0.9):
         assert assign(fg.table, gamma)[1][seen].all()
         assert not assign(bg.table, gamma)[1][seen].any()
+
+
+def _on_axis_scene(means_z, opac, sigma_px, width=24, fx=20.0):
+    """Isotropic Gaussians on the optical axis of a camera at the origin
+    looking down +z, with projected standard deviation sigma_px pixels."""
+    n = len(means_z)
+    z = np.asarray(means_z, np.float64)
+    s = np.asarray(sigma_px, np.float64) * z / fx
+    g = {"mean": np.column_stack([np.zeros(n), np.zeros(n), z]).astype(np.float32),
+         "quat": np.tile([1, 0, 0, 0], (n, 1)).astype(np.float32),
+         "scale": np.repeat(s[:, None], 3, axis=1).astype(np.float32),
+         "opacity": np.asarray(opac, np.float32)}
+    cam = {"R": np.eye(3), "t": np.zeros(3), "fx": fx, "fy": fx, "cx": width / 2,
+           "cy": width / 2, "width": width, "height": width}
+    return g, [cam]
+
+
+def _risk_scenes(tiny):
+    """Scenes where many decisions sit on their thresholds."""
+    scenes = {}
+    # four layers of opacity o over the whole view: T after the fourth factor
+    # is 1e-4 (1 - 2.5e-5) at the centre and rises by ~5e-5 relative towards
+    # the corners, so the stop decision of the fourth layer is marginal
+    Tc = 1e-4 * (1 - 2.5e-5)
+    o = 1 - Tc ** 0.25
+    scenes["stop_stack"] = _on_axis_scene([2.0, 2.5, 3.0, 3.5], [o] * 4, [1.0e4] * 4)
+    # one Gaussian whose alpha straddles 1/255 within 3e-5 across the view,
+    # and an opaque-ish layer behind it
+    scenes["alpha_ring"] = _on_axis_scene([2.0, 3.0], [(1 + 3e-5) / 255, 0.5], [1.55e3, 30.0])
+    # two Gaussians at exactly the same depth
+    scenes["tie"] = _on_axis_scene([2.0, 2.0, 3.0], [0.6, 0.7, 0.5], [6.0, 9.0, 20.0])
+    scenes["tiny"] = (tiny.gaussians, tiny.cams[:2])
+    return scenes
+
+
+def test_risk_bounds_the_change_when_decisions_flip(tiny):
+    """The per-entry risk is a bound: moving the 1/255 and 1e-4 thresholds by
+    0.9 of the alpha window (up and down), or walking equal depths in the
+    other order, changes no table entry by more than its risk.  Each kind of
+    move does change some entry, so the bound is exercised."""
+    eps = 1e-5
+    moves = {"alpha_up": {"alpha_min": (1 + 0.9 * eps) / 255},
+             "alpha_down": {"alpha_min": (1 - 0.9 * eps) / 255},
+             "t_up": {"t_min": 1e-4 * (1 + 0.9 * eps)},
+             "t_down": {"t_min": 1e-4 * (1 - 0.9 * eps)},
+             "ties": {"tie_reverse": True}}
+    changed = {k: 0 for k in moves}
+    for name, (g, cams) in _risk_scenes(tiny).items():
+        rng = np.random.default_rng(8)
+        masks = [rng.integers(0, 3, (c["height"], c["width"])).astype(np.int32) for c in cams]
+        base = oracle.accumulate(g, cams, masks, 3, event_rel=eps)
+        scale = np.abs(base.table).max()
+        for k, kw in moves.items():
+            alt = oracle.accumulate(g, cams, masks, 3, event_rel=eps, **kw)
+            diff = np.abs(alt.table - base.table)
+            bad = diff > base.risk * (1 + 1e-9) + 1e-14 * scale
+            assert not bad.any(), (name, k, np.argwhere(bad)[:5], diff[bad][:5], base.risk[bad][:5])
+            changed[k] += int((diff > 1e-12 * scale).sum())
+    print("entries moved per kind of decision change:", changed)
+    assert all(v > 0 for v in changed.values()), changed
+
+
+def test_risk_window_narrower_than_the_move_fails(tiny):
+    """The check above can fail: with windows narrower than the threshold
+    move, flipped decisions are no longer marked marginal and the change
+    exceeds the risk.  (The window of the stop decision is the alpha
+    precision amplified by the factors of T, about 37-fold in the stack.)"""
+    for name, er in (("alpha_ring", 1e-6), ("stop_stack", 1e-8)):
+        g, cams = _risk_scenes(tiny)[name]
+        masks = [np.ones((c["height"], c["width"]), np.int32) for c in cams]
+        base = oracle.accumulate(g, cams, masks, 2, event_rel=er)
+        kw = {"alpha_min": (1 - 9e-6) / 255} if name == "alpha_ring" else {"t_min": 1e-4 * (1 + 9e-6)}
+        alt = oracle.accumulate(g, cams, masks, 2, event_rel=er, **kw)
+        assert (np.abs(alt.table - base.table) > base.risk * (1 + 1e-9)).any(), name
 
 
 def test_risk_bounds_are_local(tiny):
