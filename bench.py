@@ -333,6 +333,9 @@ def run_flashsplat(args, rank, world, local_rank):
     csolver.solve(w.cams, dmasks, w.E, w.gamma, sync=False)
     cst = fsb.fs_synchronize(csolver.ctx, stream.cuda_stream)
     census_pairs, census_evaluated = int(cst.census_pairs), int(cst.pairs)
+    census_shape = {"rounds": int(cst.census_rounds), "steps": int(cst.census_steps),
+                    "rounds_mixed_labels": int(cst.census_rounds_mixed),
+                    "staged": int(cst.staged_entries), "list_entries": int(cst.list_entries)}
     csolver.close()
     pairs = census_pairs * args.steps
 
@@ -422,6 +425,7 @@ def run_flashsplat(args, rank, world, local_rank):
                                 "(stop included), counted by a census solve",
                 "pairs_per_step": census_pairs,
                 "evaluated_pairs_per_step": census_evaluated,
+                "census": census_shape,
                 "list_entries_per_step": entries // max(1, args.steps),
                 "staged_entries_per_step": staged // max(1, args.steps),
                 "flops_per_pair": FLOPS_PER_PAIR,

@@ -141,6 +141,10 @@ typedef struct fs_stats {
   int64_t recheck_rebinned;/* view batches the re-check binned anew (see fs_solve) */
   int64_t census_pairs;    /* pairs with alpha >= 1/255 reached before the pixel's
                               stop, the stop included (census only) */
+  int64_t census_rounds;   /* blend: compositing rounds of a warp (census only) */
+  int64_t census_steps;    /* blend: list-staging steps of a block (census only) */
+  int64_t census_rounds_mixed; /* blend: rounds of warps whose pixels carry more
+                              than one label (census only) */
 } fs_stats;
 
 /* Outputs of fs_solve.  Any pointer may be NULL to skip that output. */
@@ -259,6 +263,21 @@ fs_status fs_assign(fs_ctx* ctx, const void* table, int32_t table_dtype, int64_t
 fs_status fs_solve(fs_ctx* ctx, const fs_scene* scene, const fs_camera* cams, int32_t n_views,
                    const void* const* masks, int32_t mask_dtype, int32_t mask_memory, int32_t E,
                    float gamma, const fs_result* out, void* stream);
+
+/*
+ * fs_keep_after_removal -- object removal (Sec. 4.4): the Gaussians left when
+ * every Gaussian of the selected objects' subsets {G_i}_e is deleted from the
+ * scene.  member_bits: device [n], bit e set iff S[e, i] = 1 (the output of
+ * fs_solve / fs_assign; the paper assigns with gamma = -0.4 for removal so
+ * that the subsets reach into the object's boundary).  remove: bit e set =
+ * object e is removed.  keep_index: device int32 [n]; receives the kept
+ * Gaussians' indices in increasing order (its first *n_keep entries).
+ * n_keep: host.  The call waits for the count (it synchronises `stream`).
+ * Errors: FS_INVALID_ARGUMENT, FS_OUT_OF_MEMORY, FS_CUDA_ERROR.
+ */
+fs_status fs_keep_after_removal(fs_ctx* ctx, const uint64_t* member_bits, int64_t n,
+                                uint64_t remove, int32_t* keep_index, int64_t* n_keep,
+                                void* stream);
 
 /* Wait for the context's work on `stream` and report errors recorded by its
  * kernels: FS_TIMEOUT when a bounded device-side wait gave up (the tile

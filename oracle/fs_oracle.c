@@ -97,6 +97,7 @@ typedef struct {
   double mx, my;       /* projected mean, pixel units */
   double ca, cb, cc;   /* conic = inverse 2D covariance [[ca cb][cb cc]] */
   double opacity;
+  double lno;          /* ln(opacity) */
   int x0, x1, y0, y1;  /* inclusive pixel bounding box of the alpha>=1/255 ellipse */
   /* reduced-precision record (record_f16): alpha = o 2^-|W (p - m)|^2 with
    * the whitening matrix W rounded to FP16 and the mean m rounded to FP32 */
@@ -187,6 +188,7 @@ static int project_one(const fso_camera* cam, const float* m, const float* q4,
   p->cb = -sb / det;
   p->cc = sa / det;
   p->opacity = o;
+  p->lno = log(o);
   if (record_f16) {
     /* Whitening matrix W with |W d|^2 = 0.5 log2(e) d^T Sigma^-1 d:
      * W = sqrt(0.5 log2 e) diag(lambda1, lambda2)^-1/2 [e1 e2]^T, e1 the unit
@@ -257,6 +259,9 @@ static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use
                       double* t_final, int64_t* n_eval, int64_t* n_part) {
   const double px = px_i + 0.5, py = py_i + 0.5;
   const double ev_rel = rule->ev_rel, a_min = rule->alpha_min, t_min = rule->t_min;
+  /* ln of the smallest alpha any branch below looks at: a candidate under it
+   * is skipped before its exponential is taken (the same decision) */
+  const double ln_floor = log(a_min * (1.0 - ev_rel)) - 1e-9;
   double T = 1.0;
   double sa = 0.0;        /* sum of alpha/(1 - alpha) over the factors of T so far */
   int64_t n_fac = 0;      /* factors of T so far */
@@ -276,10 +281,13 @@ static int walk_pixel(const fso_proj* P, const int32_t* cand, int64_t n, int use
     if (p->f16) {
       const double dx = px - p->mxr, dy = py - p->myr;
       const double w0 = p->w[0] * dx + p->w[1] * dy, w1 = p->w[2] * dx + p->w[3] * dy;
-      alpha = p->opacity * exp2(-(w0 * w0 + w1 * w1));
+      const double q = w0 * w0 + w1 * w1;
+      if (p->lno - q * 0.69314718055994530942 < ln_floor) continue;
+      alpha = p->opacity * exp2(-q);
     } else {
       const double dx = px - p->mx, dy = py - p->my;
       const double power = -0.5 * (p->ca * dx * dx + p->cc * dy * dy) - p->cb * dx * dy;
+      if (p->lno + power < ln_floor) continue;
       alpha = p->opacity * exp(power);
     }
     if (alpha > FSO_ALPHA_MAX) alpha = FSO_ALPHA_MAX;
@@ -561,6 +569,8 @@ typedef struct {
   uint8_t* flags;
   int32_t* cand;            /* capacity N */
   fso_hit* hits;            /* capacity N */
+  fso_proj* local;          /* the candidates' records, in depth order (grown as needed) */
+  int64_t local_cap;
   int64_t n_eval, n_hit, n_bad, n_part;
 } sel_job;
 
@@ -591,12 +601,23 @@ static void* sel_worker(void* arg) {
         }
       }
     qsort(j->cand, (size_t)nc, sizeof(int32_t), cmp_depth);
+    /* the candidates' records side by side in depth order: the walks below
+     * read them from this local copy (local index k is candidate k) */
+    if (nc > j->local_cap) {
+      free(j->local);
+      j->local_cap = nc + nc / 2 + 1024;
+      j->local = (fso_proj*)malloc(sizeof(fso_proj) * (size_t)j->local_cap);
+    }
+    for (int64_t k = 0; k < nc; ++k) j->local[k] = P[j->cand[k]];
+    int64_t g_local = -1;
+    for (int64_t k = 0; k < nc; ++k)
+      if (j->cand[k] == g) g_local = k;
     /* 8x8-pixel bins over g's box, each holding its candidates in order */
     const int nbx = (pg->x1 - pg->x0) / FSO_BIN + 1, nby = (pg->y1 - pg->y0) / FSO_BIN + 1;
     const int64_t nb = (int64_t)nbx * nby;
     int64_t* start = (int64_t*)calloc((size_t)nb + 1, sizeof(int64_t));
     for (int64_t k = 0; k < nc; ++k) {
-      const fso_proj* q = &P[j->cand[k]];
+      const fso_proj* q = &j->local[k];
       const int bx0 = ((q->x0 > pg->x0 ? q->x0 : pg->x0) - pg->x0) / FSO_BIN;
       const int bx1 = ((q->x1 < pg->x1 ? q->x1 : pg->x1) - pg->x0) / FSO_BIN;
       const int by0 = ((q->y0 > pg->y0 ? q->y0 : pg->y0) - pg->y0) / FSO_BIN;
@@ -609,13 +630,13 @@ static void* sel_worker(void* arg) {
     int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)nb);
     memcpy(fill, start, sizeof(int64_t) * (size_t)nb);
     for (int64_t k = 0; k < nc; ++k) {
-      const fso_proj* q = &P[j->cand[k]];
+      const fso_proj* q = &j->local[k];
       const int bx0 = ((q->x0 > pg->x0 ? q->x0 : pg->x0) - pg->x0) / FSO_BIN;
       const int bx1 = ((q->x1 < pg->x1 ? q->x1 : pg->x1) - pg->x0) / FSO_BIN;
       const int by0 = ((q->y0 > pg->y0 ? q->y0 : pg->y0) - pg->y0) / FSO_BIN;
       const int by1 = ((q->y1 < pg->y1 ? q->y1 : pg->y1) - pg->y0) / FSO_BIN;
       for (int by = by0; by <= by1; ++by)
-        for (int bx = bx0; bx <= bx1; ++bx) list[fill[(int64_t)by * nbx + bx]++] = j->cand[k];
+        for (int bx = bx0; bx <= bx1; ++bx) list[fill[(int64_t)by * nbx + bx]++] = (int32_t)k;
     }
     free(fill);
     /* a walk can end past g: later Gaussians do not change earlier terms
@@ -625,13 +646,13 @@ static void* sel_worker(void* arg) {
       for (int x = pg->x0; x <= pg->x1; ++x) {
         double tf;
         const int64_t b = (int64_t)((y - pg->y0) / FSO_BIN) * nbx + (x - pg->x0) / FSO_BIN;
-        const int nh = walk_pixel(P, list + start[b], start[b + 1] - start[b], 1, x, y, j->rule,
-                                  depth_limit, j->hits, &tf, &j->n_eval, &j->n_part);
+        const int nh = walk_pixel(j->local, list + start[b], start[b + 1] - start[b], 1, x, y,
+                                  j->rule, depth_limit, j->hits, &tf, &j->n_eval, &j->n_part);
         const int32_t lab = j->mask[(int64_t)y * W + x];
         const int lab_ok = (lab >= 0 && lab < j->E);
         if (!lab_ok) j->n_bad++;
         for (int h = 0; h < nh; ++h) {
-          if (j->hits[h].g != g) continue;
+          if (j->hits[h].g != g_local) continue;
           if (j->hits[h].c > 0.0) j->n_hit++;
           j->flags[r] |= j->hits[h].flag;
           if (lab_ok) {
@@ -757,8 +778,8 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
                             (uint32_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(uint32_t)),
                             nthreads, t, jobs[t].table, jobs[t].risk, jobs[t].flags,
                             (int32_t*)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1)),
-                            (fso_hit*)malloc(sizeof(fso_hit) * (size_t)(N > 0 ? N : 1)), 0, 0, 0,
-                            0};
+                            (fso_hit*)malloc(sizeof(fso_hit) * (size_t)(N > 0 ? N : 1)), NULL,
+                            0, 0, 0, 0, 0};
           pthread_create(&th[t], NULL, sel_worker, &sj[t]);
         }
         for (int t = 0; t < nthreads; ++t) {
@@ -768,6 +789,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
           jobs[t].n_bad += sj[t].n_bad;
           free(sj[t].cand);
           free(sj[t].hits);
+          free(sj[t].local);
           free(sj[t].stamp);
         }
         free(sj);

@@ -208,7 +208,7 @@ struct fs_ctx {
   int kl_chunks = 1;
   std::vector<DevBuf> kl_val;
   std::vector<int64_t> kl_tile_off;
-  DevBuf kl_ranges, kl_satc, kl_subc, kl_bound;
+  DevBuf kl_ranges, kl_satc, kl_bound;
   std::vector<const void*> mask_dev;  // device pointer of every view's mask (last solve)
   HostBuf views_host, total_host, counters_host;
   fs_stats stats{};
@@ -231,7 +231,7 @@ DevBuf* const* workspace_bufs(fs_ctx* c, size_t* count) {
                     &c->mask_stage, &c->table_tmp, &c->table32_tmp, &c->bits_tmp,
                     &c->label_tmp, &c->margin_tmp, &c->dkey, &c->rk_flag, &c->rk_offs,
                     &c->rk_F, &c->rk_map, &c->rk_R, &c->rk_Rb, &c->kl_ranges, &c->kl_satc,
-                    &c->kl_subc, &c->kl_bound, &c->key_range, &c->lb_tmp, &c->key_a2, &c->val_a2,
+                    &c->kl_bound, &c->key_range, &c->lb_tmp, &c->key_a2, &c->val_a2,
                     &c->key_b2, &c->val_b2};
   for (DevBuf* b : list) bufs[k++] = b;
   *count = k;
@@ -330,7 +330,7 @@ fs_status fs_destroy(fs_ctx* c) {
                     &c->sort_tmp, &c->scan_tmp, &c->total, &c->counters, &c->mask_stage,
                     &c->table_tmp, &c->table32_tmp, &c->bits_tmp, &c->label_tmp, &c->margin_tmp,
                     &c->dkey, &c->rk_flag, &c->rk_offs, &c->rk_F, &c->rk_map, &c->rk_R,
-                    &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_subc, &c->kl_bound, &c->key_range, &c->lb_tmp,
+                    &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_bound, &c->key_range, &c->lb_tmp,
                     &c->key_a2, &c->val_a2, &c->key_b2, &c->val_b2};
   for (DevBuf& b : c->kl_val) b.release();
   for (DevBuf* b : bufs) b->release();
@@ -564,17 +564,14 @@ fs_status read_total(fs_ctx* c, cudaStream_t stream, int64_t* out) {
 }
 
 // Binning of sorted positions [p0, p0 + n_pos) into tile lists (count, scan,
-// emit, stable tile sort, ranges) on tiles whose `sat` bit is clear and, with
-// `done` (4 bits per tile), only where the footprint reaches an unfinished
-// sub-tile.  The sorted list values go to *val_dst (grown as needed), the
-// per-tile ranges to ranges_dst and the sorted keys' location to *key_out.
-// Returns the entry count in *I_out.
+// emit, stable tile sort, ranges) on tiles whose `sat` bit is clear.  The
+// sorted list values go to *val_dst (grown as needed) and the per-tile ranges
+// to ranges_dst.  Returns the entry count in *I_out.
 fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
                         const fs::ViewParams* vd, const uint32_t* sorted_val, const ProjPtrs& P,
-                        const uint64_t* sat, const uint64_t* done, int total_tiles,
-                        int tile_bits, int64_t kcap, bool count_entries, DevBuf* val_dst,
-                        uint2* ranges_dst, cudaStream_t stream, int64_t* I_out,
-                        const uint32_t** key_out) {
+                        const uint64_t* sat, int total_tiles, int tile_bits, int64_t kcap,
+                        bool count_entries, DevBuf* val_dst, uint2* ranges_dst,
+                        cudaStream_t stream, int64_t* I_out) {
   unsigned long long* ctr = c->counters.as<unsigned long long>();
   *I_out = 0;
   FS_CUDA(cudaMemsetAsync(ranges_dst, 0, static_cast<size_t>(total_tiles) * 8, stream),
@@ -587,7 +584,7 @@ fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
     const size_t cap_bytes = std::min(c->lk_a.bytes, val_dst->bytes);
     const uint32_t capacity = static_cast<uint32_t>(std::min<size_t>(cap_bytes / 4, 0x7FFFFFFFu));
     c->stats.kernel_launches += 1;
-    FS_CUDA(fs::launch_bin_fused(p0, n_pos, n, vd, sorted_val, P.foot, sat, done,
+    FS_CUDA(fs::launch_bin_fused(p0, n_pos, n, vd, sorted_val, P.foot, sat,
                                  c->lk_a.as<uint32_t>(), val_dst->as<uint32_t>(), capacity,
                                  c->lb_tmp.p, c->total.as<uint32_t>(), ctr, stream),
             "binning");
@@ -601,7 +598,6 @@ fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
   }
   if (count_entries) c->stats.list_entries += I;
   *I_out = I;
-  if (key_out) *key_out = c->lk_a.as<uint32_t>();
   if (I == 0) return FS_OK;
   FS_TRY(c->lk_b.ensure(static_cast<size_t>(I) * 4, "list keys"));
   FS_TRY(c->lv_b.ensure(static_cast<size_t>(I) * 4, "list values"));
@@ -618,7 +614,6 @@ fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
                             cudaMemcpyDeviceToDevice, stream),
             "list copy");
   FS_CUDA(fs::launch_ranges(I, lkey, ranges_dst, stream), "ranges");
-  if (key_out) *key_out = lkey;
   return FS_OK;
 }
 
@@ -650,7 +645,6 @@ fs_status kept_layout(fs_ctx* c, const fs_camera* cams, int32_t V, int vb, int c
   if (c->kl_val.size() < batches * chunks) c->kl_val.resize(batches * chunks);
   FS_TRY(c->kl_ranges.ensure(static_cast<size_t>(tiles) * chunks * 8 + 8, "kept ranges"));
   FS_TRY(c->kl_satc.ensure(static_cast<size_t>(tiles) + 8, "kept saturation chunks"));
-  FS_TRY(c->kl_subc.ensure(static_cast<size_t>(tiles) * 4 + 8, "kept sub-tile chunks"));
   FS_TRY(c->kl_bound.ensure(batches * chunks * 4 + 4, "kept chunk bounds"));
   return FS_OK;
 }
@@ -759,9 +753,6 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     const BatchLayout L = pr.L;
     const int total_tiles = L.total_tiles, max_tiles = L.max_tiles;
     const int tile_bits = std::max(1, ceil_log2(total_tiles));
-    if (tile_bits > 27)  // list keys hold the tile id below a 4-bit sub-tile mask
-      return fail(FS_UNSUPPORTED, "%d tiles in one view batch; use fewer views per batch",
-                  total_tiles);
     const int64_t k_total = static_cast<int64_t>(nb) * n;
     FS_TRY(c->state.ensure(static_cast<size_t>(L.pixels) * 4, "pixel state"));
     const size_t sat_bytes = static_cast<size_t>((total_tiles + 63) / 64) * 8;
@@ -774,14 +765,10 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     uint64_t* sat = c->sat.as<uint64_t>();
     const ProjPtrs P = proj_ptrs(c, keep, v0, n);
     uint8_t* satc = nullptr;
-    uint8_t* subc = nullptr;
     if (keep) {
       satc = c->kl_satc.as<uint8_t>() + c->kl_tile_off[b];
-      subc = c->kl_subc.as<uint8_t>() + 4 * c->kl_tile_off[b];
       FS_CUDA(cudaMemsetAsync(satc, 0xFF, static_cast<size_t>(total_tiles), stream),
               "saturation chunks");
-      FS_CUDA(cudaMemsetAsync(subc, 0xFF, static_cast<size_t>(total_tiles) * 4, stream),
-              "sub-tile chunks");
     }
     // the batch's projection (and its key range on the host) is complete
     FS_CUDA(cudaEventSynchronize(c->prologue_done[q]), "key range readback");
@@ -848,10 +835,8 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
         continue;
       }
       int64_t I = 0;
-      const uint32_t* lkey = nullptr;
-      FS_TRY(bin_positions(c, p0, n_pos, n, vd, sorted_val, P, sat, c->subsat.as<uint64_t>(),
-                           total_tiles, tile_bits, kcap, true, val_dst, ranges_dst, stream, &I,
-                           &lkey));
+      FS_TRY(bin_positions(c, p0, n_pos, n, vd, sorted_val, P, sat, total_tiles, tile_bits, kcap,
+                           true, val_dst, ranges_dst, stream, &I));
       p0 = p1;
       if (I == 0) continue;
       cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -866,9 +851,9 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
         c->events_used += 2;
         FS_CUDA(cudaEventRecord(ev0, stream), "cudaEventRecord");
       }
-      FS_CUDA(fs::launch_blend(vd, nb, max_tiles, ranges_dst, lkey, val_dst->as<uint32_t>(), P.rec,
+      FS_CUDA(fs::launch_blend(vd, nb, max_tiles, ranges_dst, val_dst->as<uint32_t>(), P.rec,
                                P.rec16, n, E, mask_dtype, table, table_dtype, state, sat, subsat,
-                               satc, subc, ci, ctr, c->census, stream),
+                               satc, ci, ctr, c->census, stream),
               "blend");
       if (ev1) FS_CUDA(cudaEventRecord(ev1, stream), "cudaEventRecord");
     }
@@ -910,8 +895,8 @@ fs_status recheck_batch_rebin(fs_ctx* c, const fs_scene* s, int64_t n, int nb, i
   uint32_t* sorted_val = alt ? c->val_a.as<uint32_t>() : c->val_b.as<uint32_t>();
   FS_CUDA(fs::launch_depth_tie_fix(C, n, sorted_key, sorted_val, P.dlo, stream), "depth ties");
   int64_t I = 0;
-  FS_TRY(bin_positions(c, 0, C, n, vd, sorted_val, P, skip, nullptr, total_tiles, tile_bits, kcap,
-                       false, &c->lv_a, c->ranges.as<uint2>(), stream, &I, nullptr));
+  FS_TRY(bin_positions(c, 0, C, n, vd, sorted_val, P, skip, total_tiles, tile_bits, kcap, false,
+                       &c->lv_a, c->ranges.as<uint2>(), stream, &I));
   if (I == 0) return FS_OK;
   fs::RecheckLists Ls{};
   Ls.val[0] = c->lv_a.as<uint32_t>();
@@ -1018,7 +1003,6 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
       }
       Ls.chunks = chunks;
       Ls.sat_chunk = satc;
-      Ls.sub_chunk = kept ? c->kl_subc.as<uint8_t>() + 4 * c->kl_tile_off[b] : nullptr;
       Ls.deep = deep;
       FS_CUDA(cudaMemsetAsync(Rb, 0, rbytes, stream), "batch rows clear");
       FS_CUDA(cudaMemsetAsync(ctr + fs::kRecheckIncomplete, 0, 8, stream), "incomplete clear");
@@ -1207,6 +1191,35 @@ fs_status fs_solve(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t 
   return FS_OK;
 }
 
+fs_status fs_keep_after_removal(fs_ctx* c, const uint64_t* member_bits, int64_t n,
+                                uint64_t remove, int32_t* keep_index, int64_t* n_keep,
+                                void* stream) {
+  if (!c || !n_keep) return fail(FS_INVALID_ARGUMENT, "fs_keep_after_removal: NULL argument");
+  *n_keep = 0;
+  if (n < 0 || n >= (static_cast<int64_t>(1) << 31) || (n > 0 && (!member_bits || !keep_index)))
+    return fail(FS_INVALID_ARGUMENT, "fs_keep_after_removal: bad n or NULL array");
+  if (n == 0) return FS_OK;
+  DeviceGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t nn = static_cast<size_t>(n);
+  FS_TRY(c->rk_flag.ensure(nn * 4, "removal flags"));
+  FS_TRY(c->rk_offs.ensure(nn * 4, "removal offsets"));
+  FS_TRY(c->scan_tmp.ensure(fs::scan_temp_bytes(n), "scan temp"));
+  FS_CUDA(fs::launch_keep_flags(n, member_bits, remove, c->rk_flag.as<uint32_t>(), st),
+          "removal flags");
+  FS_CUDA(fs::exclusive_scan(c->rk_flag.as<uint32_t>(), nullptr, c->rk_offs.as<uint32_t>(), n,
+                             c->total.as<uint32_t>(), c->scan_tmp.p, st),
+          "removal scan");
+  FS_CUDA(fs::launch_keep_scatter(n, c->rk_flag.as<uint32_t>(), c->rk_offs.as<uint32_t>(),
+                                  keep_index, st),
+          "removal scatter");
+  c->stats.kernel_launches += 2 + scan_launches(n);
+  int64_t kept = 0;
+  FS_TRY(read_total(c, st, &kept));
+  *n_keep = kept;
+  return FS_OK;
+}
+
 fs_status fs_check_wait_timeout(int32_t device, int32_t spins) {
   int count = 0;
   cudaError_t e = cudaGetDeviceCount(&count);
@@ -1255,6 +1268,9 @@ fs_status fs_synchronize(fs_ctx* c, void* stream, fs_stats* stats) {
   c->stats.pairs = static_cast<int64_t>(ch[fs::kPairs]);
   c->stats.staged_entries = static_cast<int64_t>(ch[fs::kStaged]);
   c->stats.census_pairs = static_cast<int64_t>(ch[fs::kCensusPairs]);
+  c->stats.census_rounds = static_cast<int64_t>(ch[fs::kRounds]);
+  c->stats.census_steps = static_cast<int64_t>(ch[fs::kSteps]);
+  c->stats.census_rounds_mixed = static_cast<int64_t>(ch[fs::kRoundsMixed]);
   c->stats.recheck_pairs = static_cast<int64_t>(ch[fs::kRecheckPairs]);
   if (ch[fs::kLookbackTimeout])
     return fail(FS_TIMEOUT, "tile binning: %llu bounded wait(s) for a preceding block's offset "

@@ -85,7 +85,40 @@ __global__ void __launch_bounds__(256) assign_rows_kernel(
   if (margin) margin[i] = d.margin;
 }
 
+// flag[i] = 1 iff Gaussian i belongs to none of the objects in `remove`
+__global__ void __launch_bounds__(256) keep_flag_kernel(int64_t n,
+                                                        const uint64_t* __restrict__ bits,
+                                                        uint64_t remove,
+                                                        uint32_t* __restrict__ flag) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = (bits[i] & remove) ? 0u : 1u;
+}
+
+__global__ void __launch_bounds__(256) keep_scatter_kernel(int64_t n,
+                                                           const uint32_t* __restrict__ flag,
+                                                           const uint32_t* __restrict__ offs,
+                                                           int32_t* __restrict__ keep) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) keep[offs[i]] = static_cast<int32_t>(i);
+}
+
 }  // namespace
+
+cudaError_t launch_keep_flags(int64_t n, const uint64_t* member_bits, uint64_t remove,
+                              uint32_t* flag, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  keep_flag_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(n, member_bits,
+                                                                              remove, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keep_scatter(int64_t n, const uint32_t* flag, const uint32_t* offs,
+                                int32_t* keep, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  keep_scatter_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(n, flag, offs,
+                                                                                 keep);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_assign(const void* table, int table_dtype, int64_t n, int E, float gamma,
                           uint64_t* member_bits, int32_t* label, float* margin,

@@ -42,15 +42,16 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return y;
 }
 
-// Pixel columns [px0, px1] of the band of pixel-centre rows y0c .. y1c
-// (relative to the tile row's top edge, widened by one pixel) that the
-// footprint can reach; false if none.  Over the band the right boundary x(dy)
-// is concave, so its maximum is at the rightmost point dy* clamped to the
-// band (and the left boundary's minimum at -dy*, clamped).
-__device__ __forceinline__ bool band_span(const Footprint& f, float yt, float lo, float hi,
-                                          int width, int* px0_out, int* px1_out) {
-  const float y0 = __fsub_rn(__fadd_rn(yt, lo), f.my);
-  const float y1 = __fsub_rn(__fadd_rn(yt, hi), f.my);
+// Tiles [tx0, tx1] of tile row ty touched by the footprint (false if none).
+// The band of pixel-centre rows of the tile, widened by one pixel, is
+// intersected with the ellipse; over the band the right boundary x(dy) is
+// concave, so its maximum is at the rightmost point dy* clamped to the band
+// (and the left boundary's minimum at -dy*, clamped).
+__device__ __forceinline__ bool row_span(const Footprint& f, int ty, int width, int* tx0,
+                                         int* tx1) {
+  const float yt = static_cast<float>(ty * kTile);
+  const float y0 = __fsub_rn(__fadd_rn(yt, -0.5f), f.my);   // band widened by one pixel
+  const float y1 = __fsub_rn(__fadd_rn(yt, 16.5f), f.my);
   const float u0 = fmaxf(y0, -f.hy), u1 = fminf(y1, f.hy);
   if (!(u0 <= u1)) return false;
   const float dr = fminf(fmaxf(f.dys, u0), u1), dl = fminf(fmaxf(-f.dys, u0), u1);
@@ -62,50 +63,9 @@ __device__ __forceinline__ bool band_span(const Footprint& f, float yt, float lo
   px0 = fmaxf(px0, 0.f);
   px1 = fminf(px1, static_cast<float>(width - 1));
   if (!(px0 <= px1)) return false;
-  *px0_out = static_cast<int>(px0);
-  *px1_out = static_cast<int>(px1);
+  *tx0 = static_cast<int>(px0) / kTile;
+  *tx1 = static_cast<int>(px1) / kTile;
   return true;
 }
-
-// The footprint over tile row ty: the pixel columns reached by the top half
-// (pixel rows 0-7 of the tile, widened by one pixel) and the bottom half
-// (rows 8-15), and the tiles [tx0, tx1] their union spans.  An empty half has
-// top0 > top1 (bot0 > bot1).
-struct RowSpans {
-  int tx0, tx1;
-  int top0, top1, bot0, bot1;
-};
-
-__device__ __forceinline__ bool row_spans(const Footprint& f, int ty, int width, RowSpans* s) {
-  const float yt = static_cast<float>(ty * kTile);
-  s->top0 = s->bot0 = 1;
-  s->top1 = s->bot1 = 0;
-  const bool t = band_span(f, yt, -0.5f, 8.5f, width, &s->top0, &s->top1);
-  const bool b = band_span(f, yt, 7.5f, 16.5f, width, &s->bot0, &s->bot1);
-  if (!t) { s->top0 = 1; s->top1 = 0; }
-  if (!b) { s->bot0 = 1; s->bot1 = 0; }
-  if (!t && !b) return false;
-  const int p0 = t ? (b ? min(s->top0, s->bot0) : s->top0) : s->bot0;
-  const int p1 = t ? (b ? max(s->top1, s->bot1) : s->top1) : s->bot1;
-  s->tx0 = p0 / kTile;
-  s->tx1 = p1 / kTile;
-  return true;
-}
-
-// Tiles [tx0, tx1] of tile row ty touched by the footprint (false if none):
-// the union of the two half-band spans above.
-__device__ __forceinline__ bool row_span(const Footprint& f, int ty, int width, int* tx0,
-                                         int* tx1) {
-  RowSpans s;
-  if (!row_spans(f, ty, width, &s)) return false;
-  *tx0 = s.tx0;
-  *tx1 = s.tx1;
-  return true;
-}
-
-// List keys carry the tile id in the low bits and, in the top four, the mask
-// of the tile's 8x8 sub-tiles that the entry's footprint reaches.
-constexpr int kSubMaskShift = 28;
-constexpr uint32_t kTileKeyMask = (1u << kSubMaskShift) - 1u;
 
 }  // namespace fs

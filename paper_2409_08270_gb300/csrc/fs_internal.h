@@ -55,29 +55,26 @@ cudaError_t launch_project(int64_t n, int n_views, const ViewParams* views, cons
 // (n_total elements; slot / n is the view of a slot)
 cudaError_t launch_depth_tie_fix(int64_t n_total, int64_t n, const uint32_t* key, uint32_t* val,
                                  const uint32_t* depth_lo, cudaStream_t stream);
-// Binning of sorted positions [p0, p0 + n_pos): one list entry per (tile,
-// Gaussian) whose footprint reaches the tile, unless the tile's `sat` bit is
-// set or (done != NULL: 4 bits per tile, set = sub-tile finished) every
-// sub-tile it reaches is finished.  Entry keys hold the tile id in bits 0-27
-// and the mask of the open sub-tiles the footprint reaches in bits 28-31.
+// Binning of sorted positions [p0, p0 + n_pos): one list entry (key = tile
+// id, value = slot) per (tile, Gaussian) whose footprint reaches the tile,
+// unless the tile's `sat` bit is set.
 cudaError_t launch_chunk_count(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
                                const uint32_t* sorted_val, const Footprint* foot,
-                               const uint64_t* sat, const uint64_t* done, uint32_t* out_cnt,
-                               cudaStream_t stream);
+                               const uint64_t* sat, uint32_t* out_cnt, cudaStream_t stream);
 cudaError_t launch_emit(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
                         const uint32_t* sorted_val, const uint32_t* offsets,
                         const uint32_t* chunk_cnt, const Footprint* foot,
-                        const uint64_t* sat, const uint64_t* done, uint32_t* out_key,
-                        uint32_t* out_val, unsigned long long* counters, cudaStream_t stream);
+                        const uint64_t* sat, uint32_t* out_key, uint32_t* out_val,
+                        unsigned long long* counters, cudaStream_t stream);
 // Count, scan and emit of sorted positions [p0, p0 + n_pos) in one launch
 // (decoupled look-back).  Entries at positions >= capacity are not written;
 // *total (device) receives the entry count.  lookback: bin_fused_temp_bytes
 // of scratch (cleared by the launcher).
 cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
                              const uint32_t* sorted_val, const Footprint* foot,
-                             const uint64_t* sat, const uint64_t* done, uint32_t* out_key,
-                             uint32_t* out_val, uint32_t capacity, void* lookback,
-                             uint32_t* total, unsigned long long* counters, cudaStream_t stream);
+                             const uint64_t* sat, uint32_t* out_key, uint32_t* out_val,
+                             uint32_t capacity, void* lookback, uint32_t* total,
+                             unsigned long long* counters, cudaStream_t stream);
 size_t bin_fused_temp_bytes(int64_t n_pos);
 // Polls of a predecessor's look-back word before the wait gives up (about 2 s).
 constexpr int kLookbackSpinLimit = 1 << 26;
@@ -101,26 +98,30 @@ cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
 cudaError_t launch_state_init(const ViewParams* views, int n_views, int max_tiles_per_view, int E,
                               int mask_dtype, float* state, uint64_t* sat, uint64_t* subsat,
                               unsigned long long* counters, cudaStream_t stream);
-// sat_chunk / sub_chunk (may be NULL): per batch tile / per sub-tile (4 per
-// tile), set to `chunk` when it finishes during this launch (later chunks
-// list nothing for it).
-// Records: float pairs in rec, or reduced precision in rec16.  list_key:
-// the tile-sorted keys (their sub-tile masks select each warp's entries).
+// sat_chunk (may be NULL): per batch tile, set to `chunk` when the tile
+// saturates during this launch (its later chunks get no list entries).
+// Records: float pairs in rec, or reduced precision in rec16.
 // census: also count the evaluated (pixel, Gaussian) pairs (kPairs) and the
 // pairs that take part in the compositing, alpha >= 1/255 up to and
 // including the pixel's stop (kCensusPairs) -- a slower variant.
 cudaError_t launch_blend(const ViewParams* views, int n_views, int max_tiles_per_view,
-                         const uint2* ranges, const uint32_t* list_key, const uint32_t* list_val,
-                         const ProjRecord* rec, const CompactRecord* rec16, int64_t n, int E,
-                         int mask_dtype, void* table, int table_dtype, float* state,
-                         uint64_t* sat, uint64_t* subsat, uint8_t* sat_chunk,
-                         uint8_t* sub_chunk, int chunk, unsigned long long* counters, bool census,
-                         cudaStream_t stream);
+                         const uint2* ranges, const uint32_t* list_val, const ProjRecord* rec,
+                         const CompactRecord* rec16, int64_t n, int E, int mask_dtype,
+                         void* table, int table_dtype, float* state, uint64_t* sat,
+                         uint64_t* subsat, uint8_t* sat_chunk, int chunk,
+                         unsigned long long* counters, bool census, cudaStream_t stream);
 
 // assignment (fs_assign.cu) -------------------------------------------------
 cudaError_t launch_assign(const void* table, int table_dtype, int64_t n, int E, float gamma,
                           uint64_t* member_bits, int32_t* label, float* margin,
                           cudaStream_t stream);
+
+// Object removal (Sec. 4.4): flag[i] = no bit of `remove` set in member_bits[i];
+// keep[offs[i]] = i for flagged i (offs: exclusive scan of flag).
+cudaError_t launch_keep_flags(int64_t n, const uint64_t* member_bits, uint64_t remove,
+                              uint32_t* flag, cudaStream_t stream);
+cudaError_t launch_keep_scatter(int64_t n, const uint32_t* flag, const uint32_t* offs,
+                                int32_t* keep, cudaStream_t stream);
 
 // dst[i] = (float) src[i], i < count
 cudaError_t launch_round_table(int64_t count, const double* src, float* dst, cudaStream_t stream);
@@ -160,16 +161,13 @@ cudaError_t launch_compact(int64_t k_total, const uint32_t* flag, const uint32_t
                            cudaStream_t stream);
 // Depth-ordered tile lists for the re-check: `chunks` consecutive depth
 // chunks, each with its list values and per-batch-tile ranges; sat_chunk and
-// deep as in launch_mark_tiles, sub_chunk the chunk in which each 8x8
-// sub-tile finished (a pixel's lists are complete up to it); all NULL when
-// the lists are complete.
+// deep as in launch_mark_tiles (NULL when the lists are complete).
 constexpr int kMaxChunks = 16;
 struct RecheckLists {
   const uint32_t* val[kMaxChunks];
   const uint2* ranges[kMaxChunks];
   int chunks;
   const uint8_t* sat_chunk;
-  const uint8_t* sub_chunk;
   const uint64_t* deep;
 };
 // Float-pair compositing of the tiles whose skip bit is clear; adds alpha*T of
@@ -204,7 +202,11 @@ enum Counter {
   kRecheckIncomplete = 5,
   kCensusPairs = 6,
   kLookbackTimeout = 7,
-  kNumCounters = 8
+  kRounds = 8,           // census: compositing rounds of the blend
+  kSteps = 9,            // census: staging steps of the blend (per block)
+  kRoundsMixed = 10,     // census: rounds of warps with more than one label
+  kRoundsSlots = 11,     // census: Gaussian slots of those rounds (sum of nq)
+  kNumCounters = 12
 };
 
 }  // namespace fs

@@ -247,8 +247,7 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
       const int64_t p1 = (ci == chunks - 1) ? n : (n >> (chunks - 1 - ci));
       const int64_t n_pos = p1 - p0;
       if (n_pos <= 0) continue;
-      NA_CUDA(launch_chunk_count(p0, n_pos, n, vd, sval, foot, sat, subsat, ccnt, strm),
-              "count");
+      NA_CUDA(launch_chunk_count(p0, n_pos, n, vd, sval, foot, sat, ccnt, strm), "count");
       NA_CUDA(exclusive_scan(ccnt, nullptr, offs, n_pos, total_d, scan_tmp, strm), "scan");
       uint32_t I = 0;
       NA_CUDA(cudaMemcpyAsync(&I, total_d, 4, cudaMemcpyDeviceToHost, strm), "readback");
@@ -258,8 +257,8 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
                        "fs_solve_noalloc: a view needs more than FS_NOALLOC_MAX_LIST_ENTRIES "
                        "(tile, Gaussian) pairs in one depth chunk; the table is incomplete");
       if (I > 0) {
-        NA_CUDA(launch_emit(p0, n_pos, n, vd, sval, offs, ccnt, foot, sat, subsat, lk_a, lv_a,
-                            ctr, strm),
+        NA_CUDA(launch_emit(p0, n_pos, n, vd, sval, offs, ccnt, foot, sat, lk_a, lv_a, ctr,
+                            strm),
                 "emit");
         bool alt2 = false;
         NA_CUDA(radix_sort_pairs(lk_a, lv_a, lk_b, lv_b, I, bits_for(tiles), sort_tmp, &alt2, strm),
@@ -268,8 +267,8 @@ extern "C" fs_status fs_solve_noalloc(int32_t device, const fs_gaussians* g, con
         const uint32_t* lval = alt2 ? lv_b : lv_a;
         NA_CUDA(cudaMemsetAsync(ranges, 0, static_cast<size_t>(tiles) * 8, strm), "clear");
         NA_CUDA(launch_ranges(I, lkey, ranges, strm), "ranges");
-        NA_CUDA(launch_blend(vd, 1, tiles, ranges, lkey, lval, rec, nullptr, n, E, mask_dtype,
-                             table, FS_F32, state, sat, subsat, nullptr, nullptr, 0, ctr, false, strm),
+        NA_CUDA(launch_blend(vd, 1, tiles, ranges, lval, rec, nullptr, n, E, mask_dtype, table,
+                             FS_F32, state, sat, subsat, nullptr, 0, ctr, false, strm),
                 "blend");
       }
       p0 = p1;

@@ -415,143 +415,22 @@ __device__ __forceinline__ RowJob row_job(int r, int R, uint32_t incl_rows, uint
   return j;
 }
 
-// One job's row: the batch tile id of the row's column 0 (-1: the footprint
-// misses the row) and the pixel spans of its two half bands, each packed as
-// first | last << 16 (0x0000FFFF: empty).
-struct JobSpan {
-  int base;
-  uint32_t top, bot;
-};
-
-__device__ __forceinline__ uint32_t pack_span(int lo, int hi) {
-  return lo <= hi ? static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16) : 0x0000FFFFu;
-}
-
-__device__ __forceinline__ RowSpans unpack_spans(const JobSpan& J) {
-  RowSpans S;
-  S.top0 = static_cast<int>(J.top & 0xFFFFu);
-  S.top1 = static_cast<int>(J.top >> 16);
-  S.bot0 = static_cast<int>(J.bot & 0xFFFFu);
-  S.bot1 = static_cast<int>(J.bot >> 16);
-  S.tx0 = min(S.top0, S.bot0) / kTile;
-  S.tx1 = max(S.top1, S.bot1) / kTile;
-  return S;
-}
-
-__device__ __forceinline__ JobSpan job_span(const RowJob& jb, int64_t n,
-                                            const ViewParams* __restrict__ views,
-                                            const Footprint* __restrict__ foot) {
-  JobSpan J;
-  J.base = -1;
-  J.top = J.bot = 0x0000FFFFu;
-  if (!jb.ok) return J;
+// Unsaturated tiles of one job's row: [a, b] (global ids) and their number.
+__device__ __forceinline__ uint32_t job_free(const RowJob& jb, int64_t n,
+                                             const ViewParams* __restrict__ views,
+                                             const Footprint* __restrict__ foot,
+                                             const uint64_t* __restrict__ sat, int* a, int* b) {
+  *a = 0;
+  *b = -1;
+  if (!jb.ok) return 0;
   const int v = static_cast<int>(jb.g / static_cast<uint32_t>(n));
   const Footprint f = foot[jb.g];
-  RowSpans S;
-  if (!row_spans(f, jb.row, views[v].width, &S)) return J;
-  J.base = views[v].tile_base + jb.row * views[v].tiles_x;
-  J.top = pack_span(S.top0, S.top1);
-  J.bot = pack_span(S.bot0, S.bot1);
-  return J;
-}
-
-// Open-sub-tile masks of tiles [t0, t1] of a row (t1 < t0 + 16), from the
-// words that hold them: done nibbles (done != NULL; a saturated tile has all
-// four bits) or, without them, the saturation bits (a saturated tile is
-// closed).  Bit 4 k + s of the result is sub-tile s of tile t0 + k still
-// open.  No word past tile t1's is read.
-__device__ __forceinline__ uint64_t open_nibbles(const uint64_t* __restrict__ sat,
-                                                 const uint64_t* __restrict__ done, int t0,
-                                                 int t1) {
-  if (done) {
-    const int w = t0 >> 4, sh = 4 * (t0 & 15);
-    uint64_t d = done[w] >> sh;
-    if ((t1 >> 4) > w) d |= done[w + 1] << (64 - sh);
-    return ~d;
-  }
-  const int w = t0 >> 6, sh = t0 & 63;
-  uint64_t b = sat[w] >> sh;
-  if ((t1 >> 6) > w) b |= sat[w + 1] << (64 - sh);
-  uint64_t o = 0;
-#pragma unroll
-  for (int k = 0; k < 16; ++k)
-    if (!((b >> k) & 1ull)) o |= 0xFull << (4 * k);
-  return o;
-}
-
-// Bit 4 k + s set for the tiles k of [lo, hi] (clipped to 0..15), for
-// sub-tile bit s.
-__device__ __forceinline__ uint64_t nib_interval(int lo, int hi, int s) {
-  lo = max(lo, 0);
-  hi = min(hi, 15);
-  if (lo > hi) return 0ull;
-  const uint64_t m = (~0ull << (4 * lo)) & (~0ull >> (60 - 4 * hi));
-  return (0x1111111111111111ull << s) & m;
-}
-
-// The sub-tiles of the 16 tiles from column g0 on that the footprint reaches,
-// as nibbles (bit 4 k + s: sub-tile s of tile g0 + k).  A half band's pixel
-// span [p0, p1] reaches the left half (pixels 16 t .. 16 t + 7) of tiles
-// ceil((p0 - 7) / 16) .. floor(p1 / 16) and the right half (16 t + 8 ..
-// 16 t + 15) of tiles floor(p0 / 16) .. floor((p1 - 8) / 16).
-__device__ __forceinline__ uint64_t reach_nibbles(const RowSpans& S, int g0) {
-  uint64_t r = 0ull;
-  if (S.top0 <= S.top1) {
-    r |= nib_interval(((S.top0 + 8) >> 4) - g0, (S.top1 >> 4) - g0, 0);
-    r |= nib_interval((S.top0 >> 4) - g0, ((S.top1 - 8) >> 4) - g0, 1);
-  }
-  if (S.bot0 <= S.bot1) {
-    r |= nib_interval(((S.bot0 + 8) >> 4) - g0, (S.bot1 >> 4) - g0, 2);
-    r |= nib_interval((S.bot0 >> 4) - g0, ((S.bot1 - 8) >> 4) - g0, 3);
-  }
-  return r;
-}
-
-// One bit per non-empty nibble (at bit 4 k).
-__device__ __forceinline__ uint64_t nonzero_nibbles(uint64_t x) {
-  x |= x >> 1;
-  x |= x >> 2;
-  return x & 0x1111111111111111ull;
-}
-
-// List entries of one job: the tiles of its row whose open sub-tiles the
-// footprint reaches (done == NULL: the unsaturated tiles it reaches), 16
-// tiles at a time with bit operations.
-__device__ __forceinline__ uint32_t job_entries(const JobSpan& J, const uint64_t* __restrict__ sat,
-                                                const uint64_t* __restrict__ done) {
-  if (J.base < 0) return 0;
-  const RowSpans S = unpack_spans(J);
-  uint32_t c = 0;
-  for (int g0 = S.tx0; g0 <= S.tx1; g0 += 16) {
-    const int g1 = min(S.tx1, g0 + 15);
-    const uint64_t e = reach_nibbles(S, g0) & open_nibbles(sat, done, J.base + g0, J.base + g1);
-    c += static_cast<uint32_t>(__popcll(nonzero_nibbles(e)));
-  }
-  return c;
-}
-
-// Writes the job's entries (tile | sub-tile mask << 28, g) from position o,
-// never at or past `end`.
-__device__ __forceinline__ void emit_job(const JobSpan& J, const uint64_t* __restrict__ sat,
-                                         const uint64_t* __restrict__ done, uint32_t g,
-                                         uint32_t* __restrict__ out_key,
-                                         uint32_t* __restrict__ out_val, uint32_t o,
-                                         uint32_t end) {
-  if (J.base < 0) return;
-  const RowSpans S = unpack_spans(J);
-  for (int g0 = S.tx0; g0 <= S.tx1 && o < end; g0 += 16) {
-    const int g1 = min(S.tx1, g0 + 15);
-    const uint64_t e = reach_nibbles(S, g0) & open_nibbles(sat, done, J.base + g0, J.base + g1);
-    uint64_t nz = nonzero_nibbles(e);
-    while (nz && o < end) {
-      const int bit = __ffsll(static_cast<long long>(nz)) - 1;  // 4 k
-      nz &= nz - 1;
-      const uint32_t m = static_cast<uint32_t>(e >> bit) & 0xFu;
-      out_key[o] = static_cast<uint32_t>(J.base + g0 + (bit >> 2)) | (m << kSubMaskShift);
-      out_val[o] = g;
-      ++o;
-    }
-  }
+  int tx0, tx1;
+  if (!row_span(f, jb.row, views[v].width, &tx0, &tx1)) return 0;
+  const int base = views[v].tile_base + jb.row * views[v].tiles_x;
+  *a = base + tx0;
+  *b = base + tx1;
+  return count_free(sat, *a, *b);
 }
 
 __device__ __forceinline__ void lane_rows(int64_t j, int64_t n_pos, int64_t p0,
@@ -583,7 +462,7 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(
     int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
     const uint32_t* __restrict__ sorted_val,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
-    const uint64_t* __restrict__ done, uint32_t* __restrict__ out_cnt) {
+    uint32_t* __restrict__ out_cnt) {
   __shared__ uint32_t s_cnt[8][32];
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -596,11 +475,35 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(
   __syncwarp();
   for (int r0 = 0; r0 < R; r0 += 32) {
     const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
-    const uint32_t fr = job_entries(job_span(jb, n, views, foot), sat, done);
+    int a, b;
+    const uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
     if (jb.ok && fr) atomicAdd(&s_cnt[warp][jb.owner], fr);
   }
   __syncwarp();
   if (j < n_pos) out_cnt[j] = s_cnt[warp][lane];
+}
+
+// Writes (tile, g) for every unsaturated tile id in [a, b], from position o,
+// never at or past `end`; returns the next position.
+__device__ __forceinline__ uint32_t emit_free(const uint64_t* __restrict__ sat, int a, int b,
+                                              uint32_t g, uint32_t* __restrict__ out_key,
+                                              uint32_t* __restrict__ out_val, uint32_t o,
+                                              uint32_t end) {
+  const int wa = a >> 6, wb = b >> 6;
+  for (int w = wa; w <= wb; ++w) {
+    uint64_t m = ~0ull;
+    if (w == wa) m &= ~0ull << (a & 63);
+    if (w == wb) m &= ~0ull >> (63 - (b & 63));
+    uint64_t bits = ~sat[w] & m;
+    while (bits && o < end) {
+      const int bit = __ffsll(static_cast<long long>(bits)) - 1;
+      bits &= bits - 1;
+      out_key[o] = static_cast<uint32_t>(w * 64 + bit);
+      out_val[o] = g;
+      ++o;
+    }
+  }
+  return o;
 }
 
 // Writes the list entries of sorted positions [p0, p0 + n_pos) in depth
@@ -612,8 +515,8 @@ __global__ void __launch_bounds__(256) emit_kernel(
     const uint32_t* __restrict__ sorted_val, const uint32_t* __restrict__ offsets,
     const uint32_t* __restrict__ chunk_cnt,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
-    const uint64_t* __restrict__ done, uint32_t* __restrict__ out_key,
-    uint32_t* __restrict__ out_val, unsigned long long* __restrict__ counters) {
+    uint32_t* __restrict__ out_key, uint32_t* __restrict__ out_val,
+    unsigned long long* __restrict__ counters) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   uint32_t g, nrows;
@@ -634,11 +537,11 @@ __global__ void __launch_bounds__(256) emit_kernel(
   uint32_t carry = 0;
   for (int r0 = 0; r0 < R; r0 += 32) {
     const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
-    const JobSpan J = job_span(jb, n, views, foot);
-    const uint32_t fr = job_entries(J, sat, done);
+    int a, b;
+    const uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
     const uint32_t sc = warp_incl_scan(fr, lane);
     const uint32_t o = wbeg + carry + sc - fr;
-    if (fr) emit_job(J, sat, done, jb.g, out_key, out_val, o, min(o + fr, wend));
+    if (fr) emit_free(sat, a, b, jb.g, out_key, out_val, o, min(o + fr, wend));
     carry += __shfl_sync(0xffffffffu, sc, 31);
   }
   if (lane == 0 && jw < n_pos && wbeg + carry != wend) atomicAdd(&counters[kBinningMismatch], 1ull);
@@ -663,8 +566,7 @@ __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
     int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
     const uint32_t* __restrict__ sorted_val,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
-    const uint64_t* __restrict__ done, uint32_t* __restrict__ out_key,
-    uint32_t* __restrict__ out_val, uint32_t capacity,
+    uint32_t* __restrict__ out_key, uint32_t* __restrict__ out_val, uint32_t capacity,
     unsigned long long* __restrict__ status, uint32_t* __restrict__ ticket,
     uint32_t* __restrict__ total, unsigned long long* __restrict__ counters, int spin_limit) {
   __shared__ uint32_t s_vb, s_boff;
@@ -681,19 +583,18 @@ __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
   const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
   // count; the first kStash rounds' jobs are kept in registers for the emission
   constexpr int kStash = 3;
-  JobSpan st_j[kStash];
+  int st_a[kStash], st_b[kStash];
   uint32_t st_fr[kStash], st_g[kStash];
   uint32_t wtot = 0;
 #pragma unroll
   for (int k = 0; k < kStash; ++k) {
-    st_j[k].base = -1;
-    st_j[k].top = st_j[k].bot = 0x0000FFFFu;
+    st_a[k] = 0;
+    st_b[k] = -1;
     st_fr[k] = 0;
     st_g[k] = 0;
     if (32 * k < R) {  // R is the same for the whole warp
       const RowJob jb = row_job(32 * k + lane, R, incl, g, ty0);
-      st_j[k] = job_span(jb, n, views, foot);
-      const uint32_t fr = job_entries(st_j[k], sat, done);
+      const uint32_t fr = job_free(jb, n, views, foot, sat, &st_a[k], &st_b[k]);
       st_fr[k] = fr;
       st_g[k] = jb.g;
       uint32_t sum = fr;
@@ -704,7 +605,8 @@ __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
   }
   for (int r0 = 32 * kStash; r0 < R; r0 += 32) {
     const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
-    uint32_t fr = job_entries(job_span(jb, n, views, foot), sat, done);
+    int a, b;
+    uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fr += __shfl_xor_sync(0xffffffffu, fr, o);
     wtot += fr;
@@ -762,26 +664,25 @@ __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
       const uint32_t sc = warp_incl_scan(fr, lane);
       const uint32_t o = wbeg + carry + sc - fr;
       if (fr && o < capacity)
-        emit_job(st_j[k], sat, done, st_g[k], out_key, out_val, o,
-                 min(min(o + fr, wend), capacity));
+        emit_free(sat, st_a[k], st_b[k], st_g[k], out_key, out_val, o,
+                  min(min(o + fr, wend), capacity));
       carry += __shfl_sync(0xffffffffu, sc, 31);
     }
   }
   for (int r0 = 32 * kStash; r0 < R; r0 += 32) {
     const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
-    const JobSpan J = job_span(jb, n, views, foot);
-    const uint32_t fr = job_entries(J, sat, done);
+    int a, b;
+    const uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
     const uint32_t sc = warp_incl_scan(fr, lane);
     const uint32_t o = wbeg + carry + sc - fr;
     if (fr && o < capacity)
-      emit_job(J, sat, done, jb.g, out_key, out_val, o, min(min(o + fr, wend), capacity));
+      emit_free(sat, a, b, jb.g, out_key, out_val, o, min(min(o + fr, wend), capacity));
     carry += __shfl_sync(0xffffffffu, sc, 31);
   }
   if (lane == 0 && wbeg + carry != wend) atomicAdd(&counters[kBinningMismatch], 1ull);
 }
 
-// [start, end) of every tile's run in the tile-sorted list (keys: tile id in
-// the low bits, a sub-tile mask above).  Each thread
+// [start, end) of every tile's run in the tile-sorted list.  Each thread
 // takes four consecutive entries (one 16-byte load when the list is 16-byte
 // aligned, as the library's buffers are) and the entries on either side.
 __global__ void ranges_kernel(int64_t n_entries, const uint32_t* __restrict__ key,
@@ -801,9 +702,6 @@ __global__ void ranges_kernel(int64_t n_entries, const uint32_t* __restrict__ ke
     for (int i = 0; i < 4; ++i) t[1 + i] = k0 + i < n_entries ? key[k0 + i] : 0xFFFFFFFFu;
   }
   t[5] = k0 + 4 < n_entries ? key[k0 + 4] : 0xFFFFFFFFu;
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-    if (t[i] != 0xFFFFFFFFu) t[i] &= kTileKeyMask;  // the tile id (the top bits hold a sub-tile mask)
 #pragma unroll
   for (int i = 1; i <= 4; ++i) {
     const int64_t k = k0 + i - 1;
@@ -852,37 +750,36 @@ cudaError_t launch_depth_tie_fix(int64_t n_total, int64_t n, const uint32_t* key
 }
 
 cudaError_t launch_chunk_count(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
-                               const uint32_t* sorted_val, const Footprint* foot,
-                               const uint64_t* sat, const uint64_t* done, uint32_t* out_cnt,
+                               const uint32_t* sorted_val,
+                               const Footprint* foot, const uint64_t* sat, uint32_t* out_cnt,
                                cudaStream_t stream) {
   if (n_pos == 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = (n_pos + threads - 1) / threads;
   chunk_count_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-      p0, n_pos, n, views, sorted_val, foot, sat, done, out_cnt);
+      p0, n_pos, n, views, sorted_val, foot, sat, out_cnt);
   return cudaGetLastError();
 }
 
 cudaError_t launch_emit(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
                         const uint32_t* sorted_val, const uint32_t* offsets,
                         const uint32_t* chunk_cnt, const Footprint* foot,
-                        const uint64_t* sat, const uint64_t* done, uint32_t* out_key,
-                        uint32_t* out_val, unsigned long long* counters, cudaStream_t stream) {
+                        const uint64_t* sat, uint32_t* out_key, uint32_t* out_val,
+                        unsigned long long* counters, cudaStream_t stream) {
   if (n_pos == 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = (n_pos + threads - 1) / threads;
   emit_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-      p0, n_pos, n, views, sorted_val, offsets, chunk_cnt, foot, sat, done, out_key, out_val,
+      p0, n_pos, n, views, sorted_val, offsets, chunk_cnt, foot, sat, out_key, out_val,
       counters);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* views,
                              const uint32_t* sorted_val,
-                             const Footprint* foot, const uint64_t* sat, const uint64_t* done,
-                             uint32_t* out_key, uint32_t* out_val, uint32_t capacity,
-                             void* lookback, uint32_t* total, unsigned long long* counters,
-                             cudaStream_t stream) {
+                             const Footprint* foot, const uint64_t* sat, uint32_t* out_key,
+                             uint32_t* out_val, uint32_t capacity, void* lookback,
+                             uint32_t* total, unsigned long long* counters, cudaStream_t stream) {
   if (n_pos <= 0) return cudaMemsetAsync(total, 0, sizeof(uint32_t), stream);
   const int threads = 128;
   const int64_t blocks = (n_pos + threads - 1) / threads;
@@ -892,8 +789,8 @@ cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewPar
   cudaError_t e = cudaMemsetAsync(lookback, 0, 256 + static_cast<size_t>(blocks) * 8, stream);
   if (e != cudaSuccess) return e;
   bin_fused_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-      p0, n_pos, n, views, sorted_val, foot, sat, done, out_key, out_val, capacity, status,
-      ticket, total, counters, kLookbackSpinLimit);
+      p0, n_pos, n, views, sorted_val, foot, sat, out_key, out_val, capacity, status, ticket,
+      total, counters, kLookbackSpinLimit);
   return cudaGetLastError();
 }
 
@@ -911,7 +808,7 @@ cudaError_t launch_lookback_probe(void* lookback, uint32_t* total, unsigned long
   const uint32_t one = 1u;
   e = cudaMemcpyAsync(ticket, &one, sizeof(one), cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return e;
-  bin_fused_kernel<<<1, 128, 0, stream>>>(0, 1, 1, views, sorted_val, foot, sat, nullptr, out_key,
+  bin_fused_kernel<<<1, 128, 0, stream>>>(0, 1, 1, views, sorted_val, foot, sat, out_key,
                                           out_val, 0u, status, ticket, total, counters,
                                           spin_limit);
   return cudaGetLastError();

@@ -274,14 +274,6 @@ __global__ void __launch_bounds__(kTilePixels) recheck_blend_kernel(
         static_cast<const LabelT*>(vp.mask)[static_cast<int64_t>(y) * vp.width + x]);
     if (l >= 0 && l < E) label = l;
   }
-  // the pixel's lists are complete up to the chunk in which its 8x8 sub-tile
-  // finished (later chunks list nothing for that sub-tile alone)
-  int pix_chunks = n_chunks;
-  if (L.sub_chunk) {
-    const int sub = ((y - y0) >= 8 ? 2 : 0) + ((x - x0) >= 8 ? 1 : 0);
-    pix_chunks = min(pix_chunks, static_cast<int>(L.sub_chunk[4 * gtile + sub]) + 1);
-  }
-  bool incomplete = false;
   const float cx = static_cast<float>(x0) + 0.5f * kTile;
   const float cy = static_cast<float>(y0) + 0.5f * kTile;
   // pixel centre (x + 0.5, y + 0.5) relative to the tile centre: exact
@@ -321,11 +313,6 @@ __global__ void __launch_bounds__(kTilePixels) recheck_blend_kernel(
   unsigned long long evals = 0;
   bool done_all = false;
   for (int c = 0; c < n_chunks && !done_all; ++c) {
-    if (live && c >= pix_chunks) {
-      // the walk goes on past the end of this pixel's complete lists
-      if (to_stop || last >= (static_cast<int64_t>(c) << 32)) incomplete = true;
-      live = false;
-    }
     const uint2 rg = L.ranges[c][gtile];
     for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kRB) {
       if (__syncthreads_count(live) == 0) {
@@ -372,7 +359,7 @@ __global__ void __launch_bounds__(kTilePixels) recheck_blend_kernel(
   }
   // still compositing where a saturated tile's kept lists end: the exact
   // walk needs entries the main pass never listed
-  if (live && truncated && to_stop) incomplete = true;
+  const bool incomplete = live && truncated && to_stop;
   const int n_inc = __syncthreads_count(incomplete);
   if (threadIdx.x == 0 && n_inc) atomicAdd(&counters[kRecheckIncomplete], 1ull);
 #pragma unroll

@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "FS_OK", 1: "FS_INVALID_ARGUMENT", 2: "FS_OUT_OF_MEMORY", 3: 
 # every entry point declared in include/flashsplat.h
 EXPORTS = ["fs_version", "fs_last_error", "fs_create", "fs_destroy", "fs_scene_create",
            "fs_scene_destroy", "fs_scene_size", "fs_accumulate", "fs_assign", "fs_solve",
-           "fs_synchronize", "fs_check_wait_timeout", "fs_solve_noalloc", "fs_server_create", "fs_server_add_scene",
+           "fs_synchronize", "fs_keep_after_removal", "fs_check_wait_timeout",
+           "fs_solve_noalloc", "fs_server_create", "fs_server_add_scene",
            "fs_server_submit", "fs_server_fetch", "fs_server_cancel", "fs_server_destroy"]
 
 
@@ -60,7 +61,8 @@ class fs_stats(ctypes.Structure):
                 ("blend_ms", ctypes.c_double), ("blend_launches", ctypes.c_int64),
                 ("staged_entries", ctypes.c_int64), ("rechecked", ctypes.c_int64),
                 ("recheck_pairs", ctypes.c_int64), ("recheck_rebinned", ctypes.c_int64),
-                ("census_pairs", ctypes.c_int64)]
+                ("census_pairs", ctypes.c_int64), ("census_rounds", ctypes.c_int64),
+                ("census_steps", ctypes.c_int64), ("census_rounds_mixed", ctypes.c_int64)]
 
 
 class fs_result(ctypes.Structure):
@@ -123,6 +125,7 @@ def load(path: str | None = None):
                            i32, f32, ctypes.POINTER(fs_result), vp]),
         "fs_synchronize": (i32, [vp, vp, ctypes.POINTER(fs_stats)]),
         "fs_check_wait_timeout": (i32, [i32, i32]),
+        "fs_keep_after_removal": (i32, [vp, vp, i64, ctypes.c_uint64, vp, ctypes.POINTER(i64), vp]),
         "fs_solve_noalloc": (i32, [i32, ctypes.POINTER(fs_gaussians), ctypes.POINTER(fs_camera),
                                    i32, ctypes.POINTER(vp), i32, i32, f32, vp, vp, vp, vp, vp]),
         "fs_server_create": (i32, [ctypes.POINTER(fs_server_options), ctypes.POINTER(vp)]),
@@ -343,6 +346,21 @@ class Solver:
                   bits.data_ptr() if bits is not None else None, label.data_ptr(),
                   margin.data_ptr(), self._stream(stream))
         return bits, label, margin
+
+    def keep_after_removal(self, bits, remove_labels, stream=None):
+        """Indices (int32, device) of the Gaussians outside every removed
+        object's subset; bits: device int64 [n] membership bits."""
+        torch = _torch()
+        n = int(bits.shape[0])
+        keep = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
+        mask = 0
+        for e in remove_labels:
+            mask |= 1 << int(e)
+        n_keep = ctypes.c_int64(0)
+        check(load().fs_keep_after_removal(self.ctx, bits.data_ptr(), n, ctypes.c_uint64(mask),
+                                           keep.data_ptr(), ctypes.byref(n_keep),
+                                           self._stream(stream)))
+        return keep[:n_keep.value]
 
     def solve(self, cams, masks, E, gamma, table_dtype="float32", stream=None, sync=True):
         """Whole path on device-resident masks: returns dict of device tensors."""

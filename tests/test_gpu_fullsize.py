@@ -3,12 +3,18 @@ configuration (50 views per batch, 6 depth chunks, near-tie re-check on),
 checked on sampled Gaussians against the oracle and on properties that hold
 at any size.
 
-The oracle tracks a sample of rows (each sampled Gaussian is walked over its
-own footprint in every view), so it finishes in a minute or two even for
-3*10^6 Gaussians and 200 views.  The sample holds seen Gaussians with
-footprints of at most 96x96 pixels: those with the smallest decision margins
-(where the FP32 table, or the re-check, decides), random ones and the
-largest contributors.
+The oracle tracks a sample of rows: each sampled Gaussian is walked over its
+own footprint in every view (candidates from a coarse grid of the view).  The
+sample has at least 500 seen Gaussians:
+  * the smallest decision margins (where the FP32 table, or the re-check,
+    decides), footprints up to 150x150 pixels;
+  * large footprints, above 96x96 and up to 150x150 pixels (many tiles,
+    many sub-tiles, many list entries each);
+  * random Gaussians with footprints up to 64x64 pixels (most of the scene).
+Every sampled entry must agree within 1e-5 relative (plus the oracle's bound
+on near-threshold decisions), every entry the bound does not cover within
+1e-5 on its own, and every sampled decision whose oracle margin is at least
+1e-6 exactly.
 """
 import numpy as np
 import pytest
@@ -16,7 +22,7 @@ import pytest
 import oracle
 from oracle.assign import assign, assign_margin
 from paper_2409_08270_gb300 import synth
-from parity import MARGIN_BAR, table_errors
+from parity import MARGIN_BAR, RTOL, table_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -51,42 +57,42 @@ def _footprint_area(w, views=3):
     return area
 
 
-def _sample(gpu, w, rng, n_tie=10, n_rand=14, n_big=4, max_area=96 * 96):
-    """Seen Gaussians whose footprints stay below max_area pixels (the CPU
-    oracle walks every pixel of a sampled footprint in every view)."""
+def _sample(gpu, w, rng, n_tie=60, n_big=40, n_rand=400):
     A = gpu["table"].astype(np.float64)
-    S = A.sum(1)
-    small = _footprint_area(w) <= max_area
-    seen = np.flatnonzero((S > 0) & small)
-    m = gpu["margin"][seen]
-    ties = seen[np.argsort(m)[:n_tie]]
-    rest = np.setdiff1d(seen, ties)
-    rand = rng.choice(rest, n_rand, replace=False)
-    pool = np.setdiff1d(rest, rand)
-    big = pool[np.argsort(-S[pool])[:n_big]]
-    return np.unique(np.concatenate([ties, rand, big]))
+    seen = A.sum(1) > 0
+    area = _footprint_area(w)
+    mid = np.flatnonzero(seen & (area <= 150 * 150))
+    ties = mid[np.argsort(gpu["margin"][mid])[:n_tie]]
+    big_pool = np.setdiff1d(np.flatnonzero(seen & (area > 96 * 96) & (area <= 150 * 150)), ties)
+    big = rng.choice(big_pool, n_big, replace=False)
+    small = np.setdiff1d(np.flatnonzero(seen & (area <= 64 * 64)), np.concatenate([ties, big]))
+    rand = rng.choice(small, n_rand, replace=False)
+    sel = np.unique(np.concatenate([ties, big, rand]))
+    return sel, area
 
 
-def _check_sample(gpu, w, sel):
+def _check_sample(gpu, w, sel, area):
+    assert len(sel) >= 500 and (area[sel] > 96 * 96).sum() >= 40
     acc = oracle.accumulate(w.gaussians, w.cams, w.masks, w.E, sel=sel)
     ok, rel, summ = table_errors(gpu["table"][sel], acc.table, acc.risk)
     print(w.name, "sampled rows", len(sel), summ, flush=True)
     assert summ["violations"] == 0, summ
-    # over 100+ views nearly every row meets some decision near its threshold
-    # (risk > 0); the error itself must still be small for almost all entries
+    # entries the near-threshold bound leaves (almost) uncovered: 1e-5 on their own
     ora = acc.table
-    big = ora >= 1e-6 * ora.max()
-    rel_all = np.abs(gpu["table"][sel].astype(np.float64) - ora)[big] / ora[big]
-    print(w.name, "relative error of", int(big.sum()), "entries: median %.2e, 90%% %.2e, max %.2e"
-          % (np.median(rel_all), np.quantile(rel_all, 0.9), rel_all.max()), flush=True)
-    assert big.sum() >= len(sel) // 2
-    assert np.quantile(rel_all, 0.9) <= 1e-4
-    S = assign(acc.table, w.gamma)
-    m = assign_margin(acc.table, w.gamma).T
+    g = gpu["table"][sel].astype(np.float64)
+    free = (ora >= 1e-6 * ora.max()) & (acc.risk <= 1e-6 * ora)
+    rel_free = np.abs(g - ora)[free] / ora[free]
+    print(w.name, "risk-free entries", int(free.sum()), "of", int((ora > 0).sum()),
+          "max rel %.2e, mean %.2e" % (rel_free.max(), rel_free.mean()), flush=True)
+    assert free.sum() >= len(sel) // 2
+    assert rel_free.max() <= RTOL
+    # every decision at least MARGIN_BAR from its tie agrees exactly
+    S = assign(ora, w.gamma)
+    m = assign_margin(ora, w.gamma).T
     bits = gpu["bits"][sel].astype(np.uint64)
     Sg = np.stack([((bits >> np.uint64(e)) & np.uint64(1)).astype(bool) for e in range(w.E)])
     decided = m >= MARGIN_BAR
-    print(w.name, "sampled decisions", int(decided.sum()), "below bar", int((~decided).sum()),
+    print(w.name, "sampled decisions", int(decided.sum()), "below the bar", int((~decided).sum()),
           "smallest oracle margin", float(m.min()), flush=True)
     assert np.array_equal(Sg[decided], S[decided])
     return acc
@@ -106,21 +112,21 @@ def _check_label_independence(fsb, w, gpu):
     assert s1.sum() <= w.pixels * (1 + 1e-5)
 
 
-@pytest.mark.timeout(900, method="thread")
+@pytest.mark.timeout(1500, method="thread")
 def test_binary_full_size_sampled(fsb):
     """1,000,000 Gaussians, 100 views of 1008x756, uint8 masks, gamma 0.5."""
     w = synth.binary_scene()
     gpu = _solve(fsb, w)
     st = gpu["stats"]
     assert st.views == 100 and st.pixels == w.pixels and st.bad_labels == 0
-    print("binary full size: pairs", st.pairs, "list entries", st.list_entries,
+    print("binary full size: list entries", st.list_entries, "staged", st.staged_entries,
           "re-checked", st.rechecked, "rebinned batches", st.recheck_rebinned, flush=True)
-    sel = _sample(gpu, w, np.random.default_rng(11))
-    _check_sample(gpu, w, sel)
+    sel, area = _sample(gpu, w, np.random.default_rng(11))
+    _check_sample(gpu, w, sel, area)
     _check_label_independence(fsb, w, gpu)
 
 
-@pytest.mark.timeout(1200, method="thread")
+@pytest.mark.timeout(2400, method="thread")
 def test_multi_full_size_sampled(fsb):
     """3,000,000 Gaussians in 32 instances, 200 views of 1256x828, int32 id
     masks with 33 labels, FP32 [3M x 33] table, gamma 0.5."""
@@ -128,10 +134,10 @@ def test_multi_full_size_sampled(fsb):
     gpu = _solve(fsb, w)
     st = gpu["stats"]
     assert st.views == 200 and st.pixels == w.pixels and st.bad_labels == 0
-    print("multi full size: pairs", st.pairs, "list entries", st.list_entries,
+    print("multi full size: list entries", st.list_entries, "staged", st.staged_entries,
           "re-checked", st.rechecked, "rebinned batches", st.recheck_rebinned, flush=True)
-    sel = _sample(gpu, w, np.random.default_rng(12), n_tie=8, n_rand=12, n_big=3)
-    _check_sample(gpu, w, sel)
+    sel, area = _sample(gpu, w, np.random.default_rng(12))
+    _check_sample(gpu, w, sel, area)
     # every instance label that has Gaussians gets some members
     lab = gpu["label"]
     assert len(np.unique(lab[lab > 0])) >= 16

@@ -1,0 +1,137 @@
+"""The precision the oracle's near-threshold windows assume, measured on the
+GPU path (Sec. 3.1 Eq. 1 terms against the FP64 oracle).
+
+The oracle marks a decision marginal when another implementation may take it
+the other way: alpha within eps = 1e-5 (relative) of 1/255, and T(1 - alpha)
+within eps (1 + sum alpha/(1 - alpha)) + 2^-23 per factor of 1e-4.  These
+tests measure the GPU's alpha and T errors directly -- one Gaussian per 1x1
+view placed so its alpha at the pixel sits near the cut, and deep stacks of
+Gaussians on one pixel -- and require them to stay well inside that model.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_08270_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+EPS = 1e-5
+
+
+@pytest.fixture(scope="module")
+def fsb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_08270_gb300 import build, flashsplat
+    build.build()
+    flashsplat.load()
+    return flashsplat
+
+
+def _rot(rng):
+    q = rng.standard_normal(4)
+    return q / np.linalg.norm(q)
+
+
+def _table(fsb, g, cams, E=2):
+    masks = [np.ones((1, 1), np.uint8) for _ in cams]
+    s = fsb.Solver(g, recheck_margin=-1.0)
+    try:
+        out = s.solve(cams, masks, E, 0.5, table_dtype="float64")
+        return out["table"].cpu().numpy()[:, 1]
+    finally:
+        s.close()
+
+
+def _stack_views(rng, n_views, depth_of, scale_px, opacity_of, fx=50.0):
+    """View i: a 1x1 camera on the axis of its own column of Gaussians (100
+    units apart); returns the scene, the cameras and each Gaussian's view."""
+    means, quats, scales, opac, owner, cams = [], [], [], [], [], []
+    for i in range(n_views):
+        x = 100.0 * i
+        zs = depth_of(i)
+        for z in zs:
+            means.append([x, 0.0, z])
+            quats.append(_rot(rng))
+            sp = scale_px(i) * z / fx
+            scales.append(sp * np.exp(rng.uniform(-0.7, 0.7, 3)))
+            opac.append(opacity_of(i))
+            owner.append(i)
+        R = np.eye(3)
+        cams.append({"R": R, "t": -R @ np.array([x, 0.0, 0.0]), "fx": fx, "fy": fx,
+                     "cx": 0.5 + rng.uniform(-2.0, 2.0), "cy": 0.5 + rng.uniform(-2.0, 2.0),
+                     "width": 1, "height": 1})
+    g = {"mean": np.array(means, np.float32), "quat": np.array(quats, np.float32),
+         "scale": np.array(scales, np.float32), "opacity": np.array(opac, np.float32)}
+    return g, cams, np.array(owner)
+
+
+def test_alpha_error_near_the_cut(fsb):
+    """One Gaussian per 1x1 view, its opacity set so that alpha at the pixel
+    is 1/255 (1 + d), d uniform in +-3e-5: where both sides keep the term,
+    the GPU's alpha is within a fraction of eps of the exact one, and a
+    keep/skip disagreement happens only within eps of the cut."""
+    rng = np.random.default_rng(21)
+    n = 600
+    g, cams, _ = _stack_views(rng, n, lambda i: [3.0], lambda i: rng.uniform(0.8, 3.0),
+                              lambda i: 0.5)
+    # the oracle's alpha at each pixel for opacity 1 fixes the opacity to use
+    g1 = dict(g, opacity=np.ones(n, np.float32))
+    a1 = oracle.accumulate(g1, cams, [np.ones((1, 1), np.int32)] * n, 2).table[:, 1]
+    target = (1 + rng.uniform(-3e-5, 3e-5, n)) / 255
+    ok = a1 > 1.5 * target                      # the pixel sits inside the footprint
+    g["opacity"] = np.where(ok, np.minimum(target / np.maximum(a1, 1e-30), 0.98), 0.5).astype(np.float32)
+    ora = oracle.accumulate(g, cams, [np.ones((1, 1), np.int32)] * n, 2).table[:, 1]
+    gpu = _table(fsb, g, cams)
+    both = ok & (ora > 0) & (gpu > 0)
+    rel = np.abs(gpu[both] - ora[both]) / ora[both]
+    print("alpha near 1/255:", int(both.sum()), "kept by both, max rel %.2e, mean %.2e"
+          % (rel.max(), rel.mean()))
+    assert both.sum() > 200
+    assert rel.max() <= 0.2 * EPS
+    differ = ok & ((ora > 0) != (gpu > 0))
+    # the decision may differ only within the window of the cut
+    a_exact = g["opacity"].astype(np.float64) * a1          # alpha before the skip
+    assert np.all(np.abs(a_exact[differ] * 255 - 1) <= EPS), a_exact[differ] * 255 - 1
+
+
+def test_transmittance_error_in_deep_stacks(fsb):
+    """Stacks of 40-250 Gaussians on one pixel (1x1 views): every term
+    alpha_k T_k the GPU adds is within the T window of the oracle's model,
+    eps (1 + sum alpha/(1 - alpha)) + 2^-23 per factor, with a factor of
+    five to spare; the stop decisions agree except within that window."""
+    rng = np.random.default_rng(22)
+    n = 120
+    counts = rng.integers(40, 251, n)
+    g, cams, owner = _stack_views(rng, n, lambda i: np.sort(rng.uniform(2.0, 6.0, counts[i])),
+                                  lambda i: 4.0, lambda i: rng.uniform(0.01, 0.12))
+    ora = oracle.accumulate(g, cams, [np.ones((1, 1), np.int32)] * n, 2)
+    A = ora.table[:, 1]
+    gpu = _table(fsb, g, cams)
+    worst = 0.0
+    checked = 0
+    for i in range(n):
+        idx = np.flatnonzero(owner == i)
+        z = g["mean"][idx, 2]
+        order = idx[np.argsort(z, kind="stable")]
+        a_o, a_g = A[order], gpu[order]
+        # T before each term and alpha of each term, from the oracle's terms
+        T = 1.0 - np.concatenate([[0.0], np.cumsum(a_o)[:-1]])
+        alpha = np.where(T > 0, a_o / np.maximum(T, 1e-300), 0.0)
+        s = np.cumsum(np.where(alpha < 1, alpha / np.maximum(1 - alpha, 1e-12), 0.0))
+        k = np.arange(1, len(order) + 1)
+        window = EPS * (1 + s) + k * 2.0 ** -23
+        both = (a_o > 0) & (a_g > 0)
+        rel = np.abs(a_g[both] - a_o[both]) / a_o[both]
+        assert np.all(rel <= 0.2 * window[both]), (i, rel.max(), window[both].max())
+        worst = max(worst, float((rel / window[both]).max()))
+        checked += int(both.sum())
+        # terms kept by one side only: the stop sits within its window
+        differ = np.flatnonzero((a_o > 0) != (a_g > 0))
+        for d in differ:
+            t_next = T[d] * (1 - alpha[d]) if a_o[d] > 0 else None
+            if t_next is not None:
+                assert abs(t_next / 1e-4 - 1) <= window[d], (i, d, t_next)
+    print("stack terms checked", checked, "largest error / window %.3f" % worst)
+    assert checked > 5000
