@@ -31,6 +31,8 @@ FLAG_ALPHA_EDGE = 1
 FLAG_T_EDGE = 2
 FLAG_DEPTH_TIE = 4
 FLAG_DOWNSTREAM = 8
+COVERAGE_EXACT = 0
+COVERAGE_3SIGMA = 1
 
 
 class Camera(ctypes.Structure):
@@ -71,7 +73,7 @@ def _load():
     lib.fso_accumulate.restype = ctypes.c_int
     lib.fso_accumulate.argtypes = [i64, vp, vp, vp, vp, i32, vp, vp, vp, i32, vp, i64, i32, i32,
                                    vp, vp, vp, vp, vp, ctypes.c_double, i32, ctypes.c_double,
-                                   ctypes.c_double, i32]
+                                   ctypes.c_double, i32, i32]
     lib.fso_pixel_lists.restype = ctypes.c_int64
     lib.fso_pixel_lists.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, i64, vp, vp, vp, vp]
     lib.fso_project_view.restype = ctypes.c_int
@@ -122,7 +124,8 @@ class Accumulation:
 def accumulate(gaussians, cams, masks, E: int, sel=None, cull_mode: int = 0,
                nthreads: int | None = None, want_t_final: bool = False,
                event_rel: float = 1e-5, record_f16: bool = False, alpha_min: float = 0.0,
-               t_min: float = 0.0, tie_reverse: bool = False) -> Accumulation:
+               t_min: float = 0.0, tie_reverse: bool = False,
+               coverage: int = 0) -> Accumulation:
     """Contribution table of Eq. 6 / Eq. 7 in FP64.
 
     gaussians: dict with mean [N,3], quat [N,4] (w,x,y,z), scale [N,3] (linear),
@@ -136,6 +139,9 @@ def accumulate(gaussians, cams, masks, E: int, sel=None, cull_mode: int = 0,
     far narrower window).
     alpha_min, t_min (0: 1/255 and 1e-4) and tie_reverse (equal depths by
     higher index first) move the rule's decisions, for tests of the bound.
+    coverage: 0 = every pixel the alpha >= 1/255 ellipse reaches; 1 = only
+    pixels in the 16x16 tiles of the 3-sigma square (the standard 3D-GS
+    rasteriser's coverage, COVERAGE_3SIGMA).
     record_f16: alpha from the reduced-precision record of each (view,
     Gaussian) -- the whitening matrix rounded to FP16 and the mean to FP32 --
     evaluated in FP64 (the oracle of the reduced-precision form).
@@ -179,7 +185,7 @@ def accumulate(gaussians, cams, masks, E: int, sel=None, cull_mode: int = 0,
                             0 if sel is None else sel.size, cull_mode, nthreads,
                             _ptr(table), _ptr(risk), _ptr(flags), _ptr(tf), _ptr(stats),
                             float(event_rel), 1 if record_f16 else 0, float(alpha_min),
-                            float(t_min), 1 if tie_reverse else 0)
+                            float(t_min), 1 if tie_reverse else 0, int(coverage))
     if rc != 0:
         raise ValueError(f"fso_accumulate failed with code {rc}")
     return Accumulation(table, risk, flags[:rows], None if tf is None else tf[:acc],

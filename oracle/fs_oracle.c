@@ -46,6 +46,8 @@
 #define FSO_NEAR_PLANE 0.2
 #define FSO_LOWPASS 0.3
 #define FSO_BIN 8
+#define FSO_TILE 16          /* the rasteriser's tile side (Sec. 3.1) */
+#define FSO_COVERAGE_3SIGMA 1
 #define FSO_CELL 32 /* coarse grid of the tracked-row mode */
 #define FSO_HALF_LOG2E 0.72134752044448170368 /* 0.5 log2(e) */
 
@@ -112,7 +114,7 @@ typedef struct {
 /* ------------------------------------------------------------------------ */
 
 static int project_one(const fso_camera* cam, const float* m, const float* q4,
-                       const float* s3, float opac, int record_f16, fso_proj* p) {
+                       const float* s3, float opac, int record_f16, int coverage, fso_proj* p) {
   p->valid = 0;
   p->f16 = 0;
   const double mx = m[0], my = m[1], mz = m[2];
@@ -225,6 +227,21 @@ static int project_one(const fso_camera* cam, const float* m, const float* q4,
   if (fy0 < 0) fy0 = 0;
   if (fx1 > cam->width - 1) fx1 = cam->width - 1;
   if (fy1 > cam->height - 1) fy1 = cam->height - 1;
+  if (coverage == FSO_COVERAGE_3SIGMA) {
+    /* the standard 3D-GS rasteriser's coverage: the 16x16 tiles that the
+     * square of half side r = ceil(3 sqrt(lambda_max(Sigma2D))) around the
+     * projected mean overlaps (continuous x in [mx - r, mx + r] against tile
+     * t's [16 t, 16 t + 16)); no pixel outside those tiles sees the Gaussian */
+    const double hh = 0.5 * (sa - sc);
+    const double lmax = 0.5 * (sa + sc) + sqrt(hh * hh + sb * sb);
+    const double r = ceil(3.0 * sqrt(lmax));
+    const double tx0 = floor((p->mx - r) / FSO_TILE), tx1 = ceil((p->mx + r) / FSO_TILE) - 1.0;
+    const double ty0 = floor((p->my - r) / FSO_TILE), ty1 = ceil((p->my + r) / FSO_TILE) - 1.0;
+    if (fx0 < tx0 * FSO_TILE) fx0 = tx0 * FSO_TILE;
+    if (fx1 > tx1 * FSO_TILE + (FSO_TILE - 1)) fx1 = tx1 * FSO_TILE + (FSO_TILE - 1);
+    if (fy0 < ty0 * FSO_TILE) fy0 = ty0 * FSO_TILE;
+    if (fy1 > ty1 * FSO_TILE + (FSO_TILE - 1)) fy1 = ty1 * FSO_TILE + (FSO_TILE - 1);
+  }
   if (fx0 > fx1 || fy0 > fy1) return 0;
   p->x0 = (int)fx0; p->x1 = (int)fx1; p->y0 = (int)fy0; p->y1 = (int)fy1;
   p->valid = 1;
@@ -384,6 +401,7 @@ typedef struct {
   fso_proj* P;
   int64_t begin, end;
   int record_f16;
+  int coverage;
   int status;
 } proj_job;
 
@@ -391,7 +409,7 @@ static void* proj_worker(void* arg) {
   proj_job* j = (proj_job*)arg;
   for (int64_t i = j->begin; i < j->end; ++i) {
     if (project_one(j->cam, j->mean + 3 * i, j->quat + 4 * i, j->scale + 3 * i, j->opacity[i],
-                    j->record_f16, &j->P[i]) < 0)
+                    j->record_f16, j->coverage, &j->P[i]) < 0)
       j->status = -1;
   }
   return NULL;
@@ -408,13 +426,13 @@ typedef struct {
 /* Projects all N Gaussians into the view (threads over index ranges). */
 static int project_all(int64_t N, const float* mean, const float* quat, const float* scale,
                        const float* opacity, const fso_camera* cam, int nthreads, int record_f16,
-                       fso_proj* P) {
+                       int coverage, fso_proj* P) {
   if (nthreads < 1) nthreads = 1;
   proj_job* jobs = (proj_job*)calloc((size_t)nthreads, sizeof(proj_job));
   pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
   for (int t = 0; t < nthreads; ++t) {
     jobs[t] = (proj_job){N, mean, quat, scale, opacity, cam, P, N * t / nthreads,
-                         N * (t + 1) / nthreads, record_f16, 0};
+                         N * (t + 1) / nthreads, record_f16, coverage, 0};
     pthread_create(&th[t], NULL, proj_worker, &jobs[t]);
   }
   int status = 0;
@@ -493,6 +511,7 @@ typedef struct {
   const uint8_t* pix_sel;   /* NULL or per-pixel "walk this pixel" */
   int32_t E;
   int cull_mode;
+  int coverage;
   const fso_rule* rule;     /* thresholds and near-threshold window */
   double depth_limit;       /* walks end beyond this depth (tracked rows only) */
   int nthreads, tid;
@@ -523,7 +542,7 @@ static void* acc_worker(void* arg) {
         n = j->vi->bin_start[b + 1] - j->vi->bin_start[b];
       }
       double tf;
-      const int nh = walk_pixel(j->P, cand, n, j->cull_mode != 1, x, y, j->rule,
+      const int nh = walk_pixel(j->P, cand, n, j->cull_mode != 1 || j->coverage != 0, x, y, j->rule,
                                 j->depth_limit, j->hits, &tf, &j->n_eval, &j->n_part);
       if (j->t_final) j->t_final[pix] = tf;
       const int32_t lab = j->mask[pix];
@@ -693,6 +712,9 @@ static void* sel_worker(void* arg) {
  *   alpha_min, t_min: the rule's thresholds (<= 0: 1/255 and 1e-4); tests
  *        move them inside their windows
  *   tie_reverse: non-zero -> equal depths are walked by higher index first
+ *   coverage: 0 = every pixel the alpha >= 1/255 ellipse reaches (exact);
+ *        FSO_COVERAGE_3SIGMA = only pixels in the 16x16 tiles of the 3-sigma
+ *        square (the standard rasteriser's tile coverage)
  * Returns 0, or -1 on a zero quaternion, -2 on bad arguments.
  */
 int fso_accumulate(int64_t N, const float* mean, const float* quat, const float* scale,
@@ -701,7 +723,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
                    const int64_t* sel, int64_t n_sel, int32_t cull_mode, int32_t nthreads,
                    double* table, double* risk, uint8_t* flags, double* t_final,
                    int64_t* stats, double event_rel, int32_t record_f16, double alpha_min,
-                   double t_min, int32_t tie_reverse) {
+                   double t_min, int32_t tie_reverse, int32_t coverage) {
   if (N < 0 || V < 0 || E < 1 || (sel && n_sel < 0)) return -2;
   if (sel && t_final) return -2;
   fso_rule rule;
@@ -740,7 +762,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
     const fso_camera* cam = &cams[v];
     const int64_t npix = (int64_t)cam->width * cam->height;
     view_index vi;
-    status = project_all(N, mean, quat, scale, opacity, cam, nthreads, record_f16, P);
+    status = project_all(N, mean, quat, scale, opacity, cam, nthreads, record_f16, coverage, P);
     if (status) break;
     if (sel) {
       int any = 0;
@@ -821,6 +843,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
       acc_job* j = &jobs[t];
       j->P = P; j->vi = &vi; j->cam = cam; j->mask = masks + mask_offsets[v];
       j->slot = slot; j->pix_sel = pix_sel; j->E = E; j->cull_mode = cull_mode;
+      j->coverage = coverage;
       j->rule = &rule;
       j->depth_limit = INFINITY;
       j->nthreads = nthreads; j->tid = t;
@@ -881,7 +904,7 @@ int64_t fso_pixel_lists(int64_t N, const float* mean, const float* quat, const f
   for (int32_t v = 0; v < V; ++v) {
     const fso_camera* cam = &cams[v];
     view_index vi;
-    int st = project_all(N, mean, quat, scale, opacity, cam, 1, 0, P);
+    int st = project_all(N, mean, quat, scale, opacity, cam, 1, 0, 0, P);
     if (st == 0) st = index_view(N, cam, P, cull_mode != 1, NULL, &vi);
     if (st) { free_view(&vi); free(P); free(hits); return -1; }
     for (int y = 0; y < cam->height; ++y)
@@ -928,7 +951,7 @@ int fso_project_view(int64_t N, const float* mean, const float* quat, const floa
   for (int64_t i = 0; i < N; ++i) {
     fso_proj p;
     memset(&p, 0, sizeof(p));
-    if (project_one(cam, mean + 3 * i, quat + 4 * i, scale + 3 * i, opacity[i], 0, &p) < 0)
+    if (project_one(cam, mean + 3 * i, quat + 4 * i, scale + 3 * i, opacity[i], 0, 0, &p) < 0)
       return -1;
     double* o = out + 10 * i;
     o[0] = p.valid;

@@ -704,11 +704,14 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     const uint32_t* krh = nullptr;  // depth-key range read back to the host
   };
   Prologue pro[2];
+  // The buffer set of batch b: the two sets alternate only when the batches
+  // overlap (the second set is allocated only then).
+  auto parity = [overlap](int bb) { return overlap ? (bb & 1) : 0; };
   // Batch b's views go up, every Gaussian is projected into them and the
-  // visible depth-key range is read back, all on `strm`; prologue_done[b & 1]
-  // marks the end.
+  // visible depth-key range is read back, all on `strm`;
+  // prologue_done[parity(b)] marks the end.
   auto launch_prologue = [&](int bb, cudaStream_t strm) -> fs_status {
-    const int q = bb & 1;
+    const int q = parity(bb);
     const int32_t w0 = bb * vb;
     const int nbb = std::min(vb, V - w0);
     fs::ViewParams* vhq = c->views_host.as<fs::ViewParams>() + q * fs::kMaxViewsPerBatch;
@@ -747,7 +750,7 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
   if (overlap) FS_TRY(launch_prologue(0, stream));
   for (int32_t v0 = 0, b = 0; v0 < V; v0 += vb, ++b) {
     const int nb = std::min(vb, V - v0);
-    const int q = b & 1;
+    const int q = parity(b);
     if (!overlap) FS_TRY(launch_prologue(b, stream));
     const Prologue& pr = pro[q];
     const BatchLayout L = pr.L;

@@ -68,13 +68,17 @@ def test_tiny_scene_fp64_table_and_batching(fsb, tiny):
     _check(gpu, acc, tiny.gamma)
 
 
-def test_view_batches_do_not_change_results(fsb, tiny):
-    """One view per batch (the next batch's projection overlaps the current
-    batch's binning and blending on a side stream, in alternating buffers)
-    gives the table of a single batch of all views: the per-view terms are the
-    same, only the order of the FP64 atomic sums differs."""
-    one = _solve(fsb, tiny, table_dtype="float64", views_per_batch=len(tiny.cams))
-    many = _solve(fsb, tiny, table_dtype="float64", views_per_batch=1)
+@pytest.mark.parametrize("recheck_margin", [0.0, -1.0])
+def test_view_batches_do_not_change_results(fsb, tiny, recheck_margin):
+    """One view per batch gives the table of a single batch of all views: the
+    per-view terms are the same, only the order of the FP64 atomic sums
+    differs.  With the re-check on, the next batch's projection overlaps the
+    current batch's binning and blending on a side stream, in alternating
+    buffers; with it off the batches run one after another in one set."""
+    one = _solve(fsb, tiny, table_dtype="float64", views_per_batch=len(tiny.cams),
+                 recheck_margin=recheck_margin)
+    many = _solve(fsb, tiny, table_dtype="float64", views_per_batch=1,
+                  recheck_margin=recheck_margin)
     np.testing.assert_allclose(many["table"], one["table"], rtol=1e-12, atol=1e-15)
     np.testing.assert_array_equal(many["bits"], one["bits"])
     assert many["stats"].views == one["stats"].views == len(tiny.cams)

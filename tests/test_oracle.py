@@ -603,3 +603,81 @@ def test_record_f16_close_to_plain(tiny):
     assert not np.array_equal(a.table, b.table)
     agree = (assign(a.table, tiny.gamma) == assign(b.table, tiny.gamma)).mean()
     assert agree > 0.99
+
+
+# --------------------------------------------------------------------------
+# 3-sigma tile coverage (the standard rasteriser's, reused by the paper, Sec. 4.2)
+# --------------------------------------------------------------------------
+
+def _brute_render_3sigma(g, cam, mask, E):
+    """Every pixel against every Gaussian in (depth, index) order, Eq. 1 with
+    the skip and stop rules; a Gaussian is seen only in the 16x16 tiles that
+    the square of half side ceil(3 sqrt(lambda_max(Sigma2D))) around its
+    projected mean overlaps."""
+    pv = oracle.project_view(g, cam)
+    N = pv.shape[0]
+    table = np.zeros((N, E))
+    valid = np.flatnonzero(pv[:, 0] > 0)
+    order = valid[np.lexsort((valid, pv[valid, 1]))]
+    rect = {}
+    for i in order:
+        a, b, c = pv[i, 4], pv[i, 5], pv[i, 6]
+        S = np.linalg.inv(np.array([[a, b], [b, c]]))
+        r = np.ceil(3 * np.sqrt(np.linalg.eigvalsh(S).max()))
+        mx, my = pv[i, 2], pv[i, 3]
+        rect[i] = (np.floor((mx - r) / 16), np.ceil((mx + r) / 16) - 1,
+                   np.floor((my - r) / 16), np.ceil((my + r) / 16) - 1)
+    for v in range(cam["height"]):
+        for u in range(cam["width"]):
+            T = 1.0
+            for i in order:
+                tx0, tx1, ty0, ty1 = rect[i]
+                if not (tx0 <= u // 16 <= tx1 and ty0 <= v // 16 <= ty1):
+                    continue
+                dx, dy = u + 0.5 - pv[i, 2], v + 0.5 - pv[i, 3]
+                power = -0.5 * (pv[i, 4] * dx * dx + pv[i, 6] * dy * dy) - pv[i, 5] * dx * dy
+                alpha = min(0.99, pv[i, 7] * np.exp(power))
+                if alpha < 1 / 255:
+                    continue
+                if T * (1 - alpha) < 1e-4:
+                    break
+                table[i, mask[v, u]] += alpha * T
+                T *= 1 - alpha
+    return table
+
+
+def test_3sigma_coverage_matches_brute_force():
+    """Opaque Gaussians elongated along the image x axis (their alpha >= 1/255
+    ellipse reaches 3.3 sigma there, past the 3-sigma square) on a 64x48 view:
+    the oracle's 3-sigma mode equals the brute-force renderer, and it differs
+    from the exact coverage on several Gaussians."""
+    rng = np.random.default_rng(5)
+    n = 16
+    quat = np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1))
+    quat[:, 3] = rng.uniform(-0.05, 0.05, n)
+    g = {"mean": np.column_stack([rng.uniform(-0.6, 0.6, n), rng.uniform(-0.5, 0.5, n),
+                                  rng.uniform(-0.3, 0.3, n)]).astype(np.float32),
+         "quat": quat,
+         "scale": np.column_stack([rng.uniform(0.15, 0.3, n), rng.uniform(0.02, 0.06, n),
+                                   rng.uniform(0.02, 0.06, n)]).astype(np.float32),
+         "opacity": rng.uniform(0.95, 0.99, n).astype(np.float32)}
+    cam = synth.camera((0.0, 0.0, -3.0), 64, 48, 120.0)
+    mask = rng.integers(0, 2, (48, 64)).astype(np.int32)
+    ora = oracle.accumulate(g, [cam], [mask], 2, coverage=oracle.COVERAGE_3SIGMA)
+    ref = _brute_render_3sigma(g, cam, mask, 2)
+    np.testing.assert_allclose(ora.table, ref, rtol=1e-10, atol=1e-14)
+    exact = oracle.accumulate(g, [cam], [mask], 2)
+    moved = np.abs(exact.table - ora.table).sum(1)
+    assert (moved > 1e-3).sum() >= 5
+
+
+def test_3sigma_coverage_equals_exact_for_faint_gaussians(tiny):
+    """With every opacity at most 0.3 the alpha >= 1/255 ellipse,
+    d^T Sigma^-1 d <= 2 ln(255 o) <= 8.7, lies inside the 3-sigma square, so
+    both coverages give the same table."""
+    g = dict(tiny.gaussians)
+    g["opacity"] = np.minimum(g["opacity"], 0.3).astype(np.float32)
+    a = oracle.accumulate(g, tiny.cams[:3], tiny.masks[:3], 2)
+    b = oracle.accumulate(g, tiny.cams[:3], tiny.masks[:3], 2, coverage=oracle.COVERAGE_3SIGMA)
+    np.testing.assert_array_equal(a.table, b.table)
+    assert a.table.sum() > 0
