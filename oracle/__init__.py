@@ -8,7 +8,8 @@ numpy (``assign.py``).
 Paper: FlashSplat (arXiv 2409.08270).  Sec. 3.1 Eq. 1 (alpha blending),
 Sec. 3.2 Eq. 2-6 (binary ILP and its closed form), Sec. 3.2 "Regularized ILP"
 (background bias), Sec. 3.3 Eq. 7 (multi-instance), Supp. Sec. 6 (contribution
-table A in R^{E x N} and segmentation matrix S).
+table A in R^{E x N} and segmentation matrix S), Sec. 3.4 and Supp. Sec. 8.2
+(novel-view mask rendering, ``render_masks``).
 """
 from __future__ import annotations
 
@@ -52,13 +53,16 @@ class Camera(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/libfs_oracle.so`` (gcc, -O2)."""
+    """Compile the oracle into ``oracle/_build/libfs_oracle.so`` (gcc, -O2,
+    no floating-point contraction, so every step rounds as written on every
+    host)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-pthread", "-o",
+           tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -76,6 +80,9 @@ def _load():
                                    ctypes.c_double, i32, i32]
     lib.fso_pixel_lists.restype = ctypes.c_int64
     lib.fso_pixel_lists.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, i64, vp, vp, vp, vp]
+    lib.fso_render_masks.restype = ctypes.c_int
+    lib.fso_render_masks.argtypes = [i64, vp, vp, vp, vp, vp, i32, vp, i32, ctypes.c_double, i32,
+                                     i32, vp, vp, vp, vp, vp]
     lib.fso_project_view.restype = ctypes.c_int
     lib.fso_project_view.argtypes = [i64, vp, vp, vp, vp, vp, vp]
     _lib = lib
@@ -237,3 +244,60 @@ def project_view(gaussians, cam):
     if rc != 0:
         raise ValueError("fso_project_view failed (zero quaternion?)")
     return out[:N]
+
+
+@dataclass
+class MaskRender:
+    label: list         # per view [H, W] int32: the mask value (0: no object passes)
+    rho: list           # per view [E-1, H, W]: rho^e, the accumulated alpha of object e
+    depth: list         # per view [E-1, H, W]: D^e = sum alpha T z / rho^e (0 where rho^e = 0)
+    rho_risk: list      # per view [E-1, H, W]: bound on |change of rho^e| (marginal decisions)
+    z_sum: list         # per view [E-1, H, W]: sum alpha T z
+    z_risk: list        # per view [E-1, H, W]: bound on |change of sum alpha T z|
+
+
+def render_masks(gaussians, cams, member_bits, E: int, tau: float = 0.1, coverage: int = 0,
+                 nthreads: int | None = None) -> MaskRender:
+    """Masks for (novel) views from a segmentation (Sec. 3.4; Supp. Sec. 8.2):
+    object e = 1 .. E-1 (the Gaussians with bit e of member_bits set) is
+    rendered alone; rho^e > tau passes, and among the objects that pass the
+    smallest depth D^e wins (E = 2: the binary mask [rho^1 > tau]).  tau = 0.1
+    is the paper's choice (Sec. 4.6).  FP64, the accumulation's rules."""
+    lib = _load()
+    mean = _f32(gaussians["mean"], 3)
+    quat = _f32(gaussians["quat"], 4)
+    scale = _f32(gaussians["scale"], 3)
+    opac = np.ascontiguousarray(np.asarray(gaussians["opacity"], dtype=np.float32).reshape(-1))
+    N = mean.shape[0]
+    bits = np.ascontiguousarray(np.asarray(member_bits).astype(np.uint64).reshape(-1))
+    if bits.size != N:
+        raise ValueError("member_bits needs one word per Gaussian")
+    if not 2 <= E <= 64:
+        raise ValueError("E must be in [2, 64]")
+    cams = list(cams)
+    npix = [int(c["width"]) * int(c["height"]) for c in cams]
+    total = sum(npix)
+    K = E - 1
+    label = np.zeros(max(total, 1), dtype=np.int32)
+    planes = [np.zeros(max(total * K, 1), dtype=np.float64) for _ in range(4)]
+    if nthreads is None:
+        nthreads = max(1, len(os.sched_getaffinity(0)))
+    rc = lib.fso_render_masks(N, _ptr(mean), _ptr(quat), _ptr(scale), _ptr(opac), _ptr(bits),
+                              len(cams), make_cameras(cams), E, float(tau), int(coverage),
+                              nthreads, _ptr(label), *[_ptr(a) for a in planes])
+    if rc != 0:
+        raise ValueError(f"fso_render_masks failed with code {rc}")
+    out = MaskRender([], [], [], [], [], [])
+    off = 0
+    for c, n in zip(cams, npix):
+        H, W = int(c["height"]), int(c["width"])
+        out.label.append(label[off:off + n].reshape(H, W).copy())
+        rho, z, rr, zr = (a[off * K:(off + n) * K].reshape(K, H, W).copy() for a in planes)
+        out.rho.append(rho)
+        out.z_sum.append(z)
+        out.rho_risk.append(rr)
+        out.z_risk.append(zr)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            out.depth.append(np.where(rho > 0, z / np.where(rho > 0, rho, 1.0), 0.0))
+        off += n
+    return out

@@ -12,6 +12,11 @@
  *   Sec. 4.2 / Supp. Sec. 6   the table is filled by walking every mask pixel
  *                     with the rasteriser's alpha compositing, adding
  *                     alpha_i*T_i into the column of the pixel's label.
+ *   Sec. 3.4          novel-view masks: each object's Gaussians rendered
+ *                     alone, accumulated alpha quantised at tau, the nearest
+ *                     passing object chosen by depth (fso_render_masks).
+ *   Sec. 4.2          optionally the standard rasteriser's 3-sigma tile
+ *                     coverage instead of the exact one (coverage = 1).
  *
  * Everything is double precision.  Conventions the paper leaves open are fixed
  * here and listed, with the reasons, in the repository's design notes:
@@ -231,12 +236,20 @@ static int project_one(const fso_camera* cam, const float* m, const float* q4,
     /* the standard 3D-GS rasteriser's coverage: the 16x16 tiles that the
      * square of half side r = ceil(3 sqrt(lambda_max(Sigma2D))) around the
      * projected mean overlaps (continuous x in [mx - r, mx + r] against tile
-     * t's [16 t, 16 t + 16)); no pixel outside those tiles sees the Gaussian */
-    const double hh = 0.5 * (sa - sc);
-    const double lmax = 0.5 * (sa + sc) + sqrt(hh * hh + sb * sb);
-    const double r = ceil(3.0 * sqrt(lmax));
-    const double tx0 = floor((p->mx - r) / FSO_TILE), tx1 = ceil((p->mx + r) / FSO_TILE) - 1.0;
-    const double ty0 = floor((p->my - r) / FSO_TILE), ty1 = ceil((p->my + r) / FSO_TILE) - 1.0;
+     * t's [16 t, 16 t + 16)); no pixel outside those tiles sees the Gaussian.
+     * r and the tiles are integers decided by floating point, so they are
+     * decided in the kernel's precision: FP32 from the FP32-rounded 2D
+     * covariance and mean, each step rounded to nearest (the library is built
+     * without contraction) */
+    const float fa = (float)sa, fb = (float)sb, fc = (float)sc;
+    const float fmx = (float)p->mx, fmy = (float)p->my;
+    const float mid = 0.5f * (fa + fc);
+    const float hd = 0.5f * (fa - fc);
+    const float lmax = mid + sqrtf(hd * hd + fb * fb);
+    const float r = ceilf(3.0f * sqrtf(lmax));
+    const float inv = 1.0f / FSO_TILE;
+    const double tx0 = floorf((fmx - r) * inv), tx1 = ceilf((fmx + r) * inv) - 1.0f;
+    const double ty0 = floorf((fmy - r) * inv), ty1 = ceilf((fmy + r) * inv) - 1.0f;
     if (fx0 < tx0 * FSO_TILE) fx0 = tx0 * FSO_TILE;
     if (fx1 > tx1 * FSO_TILE + (FSO_TILE - 1)) fx1 = tx1 * FSO_TILE + (FSO_TILE - 1);
     if (fy0 < ty0 * FSO_TILE) fy0 = ty0 * FSO_TILE;
@@ -447,9 +460,11 @@ static int project_all(int64_t N, const float* mean, const float* quat, const fl
 
 /* Depth order and spatial bins of the projected Gaussians P.  rect
  * (x0, x1, y0, y1) or NULL: only Gaussians whose pixel bounding box meets the
- * rect are indexed (the others cannot reach a pixel inside it). */
+ * rect are indexed (the others cannot reach a pixel inside it).  member or
+ * NULL: only Gaussians i with member[i] & member_bit are indexed. */
 static int index_view(int64_t N, const fso_camera* cam, const fso_proj* P, int build_bins,
-                      const int* rect, view_index* vi) {
+                      const int* rect, const uint64_t* member, uint64_t member_bit,
+                      view_index* vi) {
   memset(vi, 0, sizeof(*vi));
   int64_t nv = 0;
   for (int64_t i = 0; i < N; ++i) nv += P[i].valid;
@@ -457,6 +472,7 @@ static int index_view(int64_t N, const fso_camera* cam, const fso_proj* P, int b
   nv = 0;
   for (int64_t i = 0; i < N; ++i) {
     if (!P[i].valid) continue;
+    if (member && !(member[i] & member_bit)) continue;
     if (rect && (P[i].x1 < rect[0] || P[i].x0 > rect[1] || P[i].y1 < rect[2] || P[i].y0 > rect[3]))
       continue;
     vi->order[nv++] = (int32_t)i;
@@ -821,7 +837,7 @@ int fso_accumulate(int64_t N, const float* mean, const float* quat, const float*
       pix_base += npix;
       continue;
     }
-    status = index_view(N, cam, P, cull_mode != 1, NULL, &vi);
+    status = index_view(N, cam, P, cull_mode != 1, NULL, NULL, 0, &vi);
     if (status) { free_view(&vi); break; }
     for (int64_t i = 0; i < N; ++i)
       if (P[i].valid) seen[i] = 1;
@@ -905,7 +921,7 @@ int64_t fso_pixel_lists(int64_t N, const float* mean, const float* quat, const f
     const fso_camera* cam = &cams[v];
     view_index vi;
     int st = project_all(N, mean, quat, scale, opacity, cam, 1, 0, 0, P);
-    if (st == 0) st = index_view(N, cam, P, cull_mode != 1, NULL, &vi);
+    if (st == 0) st = index_view(N, cam, P, cull_mode != 1, NULL, NULL, 0, &vi);
     if (st) { free_view(&vi); free(P); free(hits); return -1; }
     for (int y = 0; y < cam->height; ++y)
       for (int x = 0; x < cam->width; ++x) {
@@ -961,4 +977,129 @@ int fso_project_view(int64_t N, const float* mean, const float* quat, const floa
     o[9] = p.valid ? (double)(p.y1 - p.y0 + 1) : 0.0;
   }
   return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Novel-view mask rendering (Sec. 3.4; Supp. Sec. 8.2)                      */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  const fso_proj* P;
+  const view_index* vi;     /* the object's Gaussians only */
+  const fso_camera* cam;
+  int coverage;
+  const fso_rule* rule;
+  int nthreads, tid;
+  double *rho, *z, *rho_risk, *z_risk; /* this object's planes of the view, H*W each */
+  fso_hit* hits;
+} render_job;
+
+static void* render_worker(void* arg) {
+  render_job* j = (render_job*)arg;
+  const int W = j->cam->width, H = j->cam->height;
+  for (int y = j->tid; y < H; y += j->nthreads) {
+    for (int x = 0; x < W; ++x) {
+      const int64_t b = (int64_t)(y / FSO_BIN) * j->vi->bins_x + x / FSO_BIN;
+      const int32_t* cand = j->vi->bin_list + j->vi->bin_start[b];
+      const int64_t n = j->vi->bin_start[b + 1] - j->vi->bin_start[b];
+      double tf;
+      int64_t n_eval = 0, n_part = 0;
+      const int nh = walk_pixel(j->P, cand, n, 1, x, y, j->rule, INFINITY, j->hits, &tf,
+                                &n_eval, &n_part);
+      double rho = 0.0, z = 0.0, rr = 0.0, zr = 0.0;
+      for (int h = 0; h < nh; ++h) {
+        const double d = j->P[j->hits[h].g].depth;
+        rho += j->hits[h].c;
+        z += j->hits[h].c * d;
+        rr += j->hits[h].risk;
+        zr += j->hits[h].risk * d;
+      }
+      const int64_t pix = (int64_t)y * W + x;
+      j->rho[pix] = rho;
+      j->z[pix] = z;
+      j->rho_risk[pix] = rr;
+      j->z_risk[pix] = zr;
+    }
+  }
+  return NULL;
+}
+
+/*
+ * fso_render_masks: 2D masks for (novel) views from a segmentation.  Object
+ * e = 1 .. E-1 is the subset {G_i}_e = {i : bit e of member[i] set}; each is
+ * rendered on its own (Eq. 1 over its Gaussians only, same rules as the
+ * accumulation): rho^e = sum alpha T at every pixel, and its depth
+ * D^e = sum alpha T z / rho^e, z the view-space depth of the Gaussian's mean
+ * (the alpha-weighted depth of Eq. 1 with x_i = z_i, divided by rho^e so it
+ * is a depth; 0 where rho^e = 0).  A pixel's mask value is the object with
+ * rho^e > tau of smallest D^e (equal depths: the smaller e), else 0 (Sec.
+ * 3.4: quantisation at tau, then depth guidance).  With E = 2 this is the
+ * binary rule M = [rho^1 > tau].
+ *   member[N]: membership bits (bit e: object e); E in [2, 64]
+ *   per view v, pixel block at off[v] (sum of earlier views' H*W):
+ *     label[off + p]                              int32 mask value
+ *     rho/z/rho_risk/z_risk[(off * (E-1)) + (e-1) * H*W + p]
+ *   z is the sum alpha T z (not yet divided); rho_risk and z_risk bound how
+ *   much rho^e and that sum move if a marginal decision flips (walk_pixel).
+ * Returns 0, -1 on a zero quaternion, -2 on bad arguments.
+ */
+int fso_render_masks(int64_t N, const float* mean, const float* quat, const float* scale,
+                     const float* opacity, const uint64_t* member, int32_t V,
+                     const fso_camera* cams, int32_t E, double tau, int32_t coverage,
+                     int32_t nthreads, int32_t* label, double* rho, double* z, double* rho_risk,
+                     double* z_risk) {
+  if (N < 0 || V < 0 || E < 2 || E > 64) return -2;
+  if (nthreads < 1) nthreads = 1;
+  const fso_rule rule = {FSO_ALPHA_MIN, FSO_T_MIN, FSO_EVENT_REL};
+  const int objects = E - 1;
+  fso_proj* P = (fso_proj*)malloc(sizeof(fso_proj) * (size_t)(N > 0 ? N : 1));
+  render_job* jobs = (render_job*)calloc((size_t)nthreads, sizeof(render_job));
+  pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+  int status = 0;
+  int64_t off = 0;
+  for (int32_t v = 0; v < V && !status; ++v) {
+    const fso_camera* cam = &cams[v];
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    status = project_all(N, mean, quat, scale, opacity, cam, nthreads, 0, coverage, P);
+    if (status) break;
+    for (int e = 1; e <= objects; ++e) {
+      view_index vi;
+      index_view(N, cam, P, 1, NULL, member, 1ull << e, &vi);
+      int64_t max_cand = 0;
+      const int64_t nb = (int64_t)vi.bins_x * vi.bins_y;
+      for (int64_t b = 0; b < nb; ++b) {
+        const int64_t c = vi.bin_start[b + 1] - vi.bin_start[b];
+        if (c > max_cand) max_cand = c;
+      }
+      const int64_t plane = off * objects + (int64_t)(e - 1) * npix;
+      for (int t = 0; t < nthreads; ++t) {
+        jobs[t] = (render_job){P, &vi, cam, coverage, &rule, nthreads, t,
+                               rho + plane, z + plane, rho_risk + plane, z_risk + plane,
+                               (fso_hit*)malloc(sizeof(fso_hit) * (size_t)(max_cand > 0 ? max_cand : 1))};
+        pthread_create(&th[t], NULL, render_worker, &jobs[t]);
+      }
+      for (int t = 0; t < nthreads; ++t) {
+        pthread_join(th[t], NULL);
+        free(jobs[t].hits);
+      }
+      free_view(&vi);
+    }
+    /* quantisation at tau, then the smallest depth among the objects that pass */
+    for (int64_t p = 0; p < npix; ++p) {
+      int32_t best = 0;
+      double best_d = INFINITY;
+      for (int e = 1; e <= objects; ++e) {
+        const int64_t k = off * objects + (int64_t)(e - 1) * npix + p;
+        if (!(rho[k] > tau)) continue;
+        const double d = z[k] / rho[k];
+        if (d < best_d) { best_d = d; best = e; }
+      }
+      label[off + p] = best;
+    }
+    off += npix;
+  }
+  free(jobs);
+  free(th);
+  free(P);
+  return status;
 }

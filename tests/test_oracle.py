@@ -681,3 +681,122 @@ def test_3sigma_coverage_equals_exact_for_faint_gaussians(tiny):
     b = oracle.accumulate(g, tiny.cams[:3], tiny.masks[:3], 2, coverage=oracle.COVERAGE_3SIGMA)
     np.testing.assert_array_equal(a.table, b.table)
     assert a.table.sum() > 0
+
+
+# --------------------------------------------------------------------------
+# Novel-view mask rendering (Sec. 3.4; Supp. Sec. 8.2; tau = 0.1, Sec. 4.6)
+# --------------------------------------------------------------------------
+
+def _alpha_on_axis(o, sigma_px, width, x, y, z=None, fx=20.0):
+    """Closed form: isotropic Gaussian on the axis, Sigma2D = (s^2 + 0.3) I,
+    mean at the view centre, pixel (x, y) sampled at its centre.  The scene
+    stores FP32 values: o and the scale fx^-1 sigma z are taken as rounded."""
+    o = float(np.float32(o))
+    if z is not None:
+        z32 = float(np.float32(z))
+        sigma_px = fx * float(np.float32(sigma_px * z / fx)) / z32
+    var = sigma_px ** 2 + 0.3
+    dx, dy = x + 0.5 - width / 2, y + 0.5 - width / 2
+    a = o * np.exp(-0.5 * (dx * dx + dy * dy) / var)
+    return np.where(a >= 1 / 255, np.minimum(a, 0.99), 0.0)
+
+
+def test_render_one_gaussian_rho_is_alpha_and_binary_mask_is_threshold():
+    """One Gaussian in the foreground: rho = alpha at every pixel, D = its
+    depth, and the binary mask (E = 2) is [alpha > 0.1]."""
+    width, sigma, o, z = 24, 3.0, 0.8, 2.5
+    g, cams = _on_axis_scene([z], [o], [sigma], width=width)
+    r = oracle.render_masks(g, cams, np.array([0b10], np.uint64), 2, tau=0.1)
+    yy, xx = np.mgrid[0:width, 0:width]
+    a = _alpha_on_axis(o, sigma, width, xx, yy, z=z)
+    np.testing.assert_allclose(r.rho[0][0], a, rtol=1e-12, atol=0)
+    assert np.all(r.rho_risk[0][0] == 0)
+    np.testing.assert_allclose(r.depth[0][0][a > 0], z, rtol=1e-6)  # the mean's depth (f32 input)
+    np.testing.assert_array_equal(r.label[0], (a > 0.1).astype(np.int32))
+    assert 0 < (a > 0.1).sum() < (a > 0).sum()
+    # not a member: nothing is rendered
+    r0 = oracle.render_masks(g, cams, np.array([0b01], np.uint64), 2)
+    assert np.all(r0.rho[0] == 0) and np.all(r0.label[0] == 0)
+
+
+def test_render_each_object_alone_and_front_depth_wins():
+    """Two opaque layers in different objects: each object is rendered on its
+    own (rho^e = its own alpha, not attenuated by the other layer), both pass
+    tau, and the object in front wins; swapping the memberships swaps the
+    winner.  A third object behind a transparent layer passes only where its
+    own alpha does."""
+    width = 16
+    g, cams = _on_axis_scene([2.0, 3.0, 4.0], [0.9, 0.95, 0.3], [4.0, 6.0, 3.0], width=width)
+    yy, xx = np.mgrid[0:width, 0:width]
+    a = [_alpha_on_axis(o, s, width, xx, yy, z=z)
+         for o, s, z in ((0.9, 4.0, 2.0), (0.95, 6.0, 3.0), (0.3, 3.0, 4.0))]
+    r = oracle.render_masks(g, cams, np.array([1 << 1, 1 << 2, 1 << 3], np.uint64), 4)
+    for e in range(3):
+        np.testing.assert_allclose(r.rho[0][e], a[e], rtol=1e-12, atol=0)
+    want = np.zeros((width, width), np.int32)
+    for e, zdep in sorted(((e, d) for e, d in enumerate([2.0, 3.0, 4.0])), key=lambda t: -t[1]):
+        want = np.where(a[e] > 0.1, e + 1, want)     # the nearest passing object last
+    np.testing.assert_array_equal(r.label[0], want)
+    assert {1, 2}.issubset(set(np.unique(r.label[0]).tolist()))
+    r2 = oracle.render_masks(g, cams, np.array([1 << 2, 1 << 1, 1 << 3], np.uint64), 4)
+    centre = width // 2
+    assert r.label[0][centre, centre] == 1 and r2.label[0][centre, centre] == 2
+
+
+def _brute_subset_render(g, cam, member, e):
+    """Per pixel, the Gaussians of object e in (depth, index) order with the
+    skip and stop rules: rho = sum alpha T and sum alpha T z."""
+    pv = oracle.project_view(g, cam)
+    valid = np.flatnonzero((pv[:, 0] > 0) & ((member >> np.uint64(e)) & np.uint64(1) == 1))
+    order = valid[np.lexsort((valid, pv[valid, 1]))]
+    H, W = cam["height"], cam["width"]
+    rho, zs = np.zeros((H, W)), np.zeros((H, W))
+    for v in range(H):
+        for u in range(W):
+            T = 1.0
+            for i in order:
+                dx, dy = u + 0.5 - pv[i, 2], v + 0.5 - pv[i, 3]
+                power = -0.5 * (pv[i, 4] * dx * dx + pv[i, 6] * dy * dy) - pv[i, 5] * dx * dy
+                alpha = min(0.99, pv[i, 7] * np.exp(power))
+                if alpha < 1 / 255:
+                    continue
+                if T * (1 - alpha) < 1e-4:
+                    break
+                rho[v, u] += alpha * T
+                zs[v, u] += alpha * T * pv[i, 1]
+                T *= 1 - alpha
+    return rho, zs
+
+
+def test_render_matches_brute_force_and_the_rule():
+    """A random scene split into three overlapping objects (a Gaussian may
+    belong to several): rho^e and sum alpha T z equal a brute-force walk of
+    each subset, and every mask value follows the rule -- it passes tau and
+    has the smallest depth among the objects that pass, or no object passes."""
+    rng = np.random.default_rng(17)
+    n = 40
+    g = {"mean": np.column_stack([rng.uniform(-0.5, 0.5, n), rng.uniform(-0.4, 0.4, n),
+                                  rng.uniform(-0.5, 0.5, n)]).astype(np.float32),
+         "quat": rng.standard_normal((n, 4)).astype(np.float32),
+         "scale": rng.uniform(0.03, 0.15, (n, 3)).astype(np.float32),
+         "opacity": rng.uniform(0.05, 0.99, n).astype(np.float32)}
+    cam = synth.camera((0.3, 0.2, -3.0), 28, 20, 40.0)
+    member = np.zeros(n, np.uint64)
+    for e in (1, 2, 3):
+        member |= (rng.random(n) < 0.45).astype(np.uint64) << np.uint64(e)
+    r = oracle.render_masks(g, [cam], member, 4, tau=0.1)
+    for e in (1, 2, 3):
+        rho, zs = _brute_subset_render(g, cam, member, e)
+        np.testing.assert_allclose(r.rho[0][e - 1], rho, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(r.z_sum[0][e - 1], zs, rtol=1e-12, atol=1e-15)
+    rho, depth, lab = r.rho[0], r.depth[0], r.label[0]
+    passing = rho > 0.1
+    for y in range(cam["height"]):
+        for x in range(cam["width"]):
+            es = [e for e in range(3) if passing[e, y, x]]
+            if not es:
+                assert lab[y, x] == 0
+            else:
+                best = min(es, key=lambda e: (depth[e, y, x], e))
+                assert lab[y, x] == best + 1
+    assert len(np.unique(lab)) == 4               # every object wins somewhere, and 0 too
