@@ -101,8 +101,22 @@ typedef struct fs_options {
    * the pixel stops, the stopping one included).  A slower variant, for
    * measurement; the results are the same. */
   int32_t census;
-  int32_t reserved[9];
+  /* Which pixels a Gaussian reaches (FS_COVERAGE_*).  FS_COVERAGE_EXACT
+   * (0): every pixel where alpha >= 1/255 can hold, so the result does not
+   * depend on the tile size.  FS_COVERAGE_3SIGMA: only the pixels of the
+   * 16x16 tiles that the square of half side r = ceil(3 sqrt(lambda_max))
+   * around the projected mean overlaps (tiles floor((mx - r) / 16) ..
+   * ceil((mx + r) / 16) - 1 in x, likewise in y), the coverage of the
+   * standard 3D-GS rasteriser that Sec. 4.2 builds on; lambda_max is the
+   * larger eigenvalue of the 2D covariance with its 0.3 px^2 low-pass.  The
+   * radius and the tiles are decided in FP32 from the FP32-rounded
+   * covariance and mean: r = ceil(3 sqrt(m + sqrt(h^2 + b^2))), m = (a + c)
+   * / 2, h = (a - c) / 2, every step rounded to nearest. */
+  int32_t coverage;
+  int32_t reserved[8];
 } fs_options;
+
+enum { FS_COVERAGE_EXACT = 0, FS_COVERAGE_3SIGMA = 1 };
 
 /* A Gaussian scene (Sec. 3.1: G_i = {m_i, q_i, s_i, o_i}; colour unused). */
 typedef struct fs_gaussians {
@@ -378,7 +392,8 @@ fs_status fs_server_destroy(fs_server* srv);
  * reduction), and there is no near-tie re-check -- so a Gaussian whose
  * decision margin is within the FP32 table's error (about 1e-5 relative) may
  * be labelled differently from fs_solve.  Pixels whose label is outside
- * [0, E) are skipped, as in fs_solve, but not counted anywhere.  Its working
+ * [0, E) are skipped, as in fs_solve, but not counted anywhere.  Coverage is
+ * always FS_COVERAGE_EXACT.  Its working
  * memory is a fixed array of about 13 MB in the library's device memory that
  * every GPU loading the library holds until the process exits.  Limits:
  * 1..FS_NOALLOC_MAX_GAUSSIANS Gaussians, views of at most FS_NOALLOC_MAX_SIDE

@@ -194,7 +194,8 @@ struct fs_ctx {
   bool recheck_reproject = false;
   bool compact = false;  // reduced-precision records (FP16 whitening matrix, FP32 mean)
   bool census = false;   // blend counts its pairs (slower variant)
-  DevBuf dkey, rk_flag, rk_offs, rk_F, rk_map, rk_R, rk_Rb;
+  bool sigma3 = false;   // 3-sigma tile coverage (per-slot tile columns in `cols`)
+  DevBuf dkey, rk_flag, rk_offs, rk_F, rk_map, rk_R, rk_Rb, cols;
   DevBuf key_range;  // min / max visible depth key of the batch (two slots, by batch parity)
   // the next batch's projection runs on a side stream while the current
   // batch bins and blends (resident projections only); its depth keys go to
@@ -232,7 +233,7 @@ DevBuf* const* workspace_bufs(fs_ctx* c, size_t* count) {
                     &c->label_tmp, &c->margin_tmp, &c->dkey, &c->rk_flag, &c->rk_offs,
                     &c->rk_F, &c->rk_map, &c->rk_R, &c->rk_Rb, &c->kl_ranges, &c->kl_satc,
                     &c->kl_bound, &c->key_range, &c->lb_tmp, &c->key_a2, &c->val_a2,
-                    &c->key_b2, &c->val_b2};
+                    &c->key_b2, &c->val_b2, &c->cols};
   for (DevBuf* b : list) bufs[k++] = b;
   *count = k;
   return bufs;
@@ -302,6 +303,12 @@ fs_status fs_create(fs_ctx** out, int32_t device, const fs_options* opt) {
     return fail(FS_INVALID_ARGUMENT, "fs_create: record_precision must be 0 or FS_F16");
   }
   c->compact = opt && opt->record_precision == FS_F16;
+  if (opt && opt->coverage != FS_COVERAGE_EXACT && opt->coverage != FS_COVERAGE_3SIGMA) {
+    delete c;
+    return fail(FS_INVALID_ARGUMENT, "fs_create: coverage must be FS_COVERAGE_EXACT or "
+                                     "FS_COVERAGE_3SIGMA");
+  }
+  c->sigma3 = opt && opt->coverage == FS_COVERAGE_3SIGMA;
   c->census = opt && opt->census;
   DeviceGuard g(device);
   fs_status st;
@@ -331,7 +338,7 @@ fs_status fs_destroy(fs_ctx* c) {
                     &c->table_tmp, &c->table32_tmp, &c->bits_tmp, &c->label_tmp, &c->margin_tmp,
                     &c->dkey, &c->rk_flag, &c->rk_offs, &c->rk_F, &c->rk_map, &c->rk_R,
                     &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_bound, &c->key_range, &c->lb_tmp,
-                    &c->key_a2, &c->val_a2, &c->key_b2, &c->val_b2};
+                    &c->key_a2, &c->val_a2, &c->key_b2, &c->val_b2, &c->cols};
   for (DevBuf& b : c->kl_val) b.release();
   for (DevBuf* b : bufs) b->release();
   c->views_host.release();
@@ -491,10 +498,11 @@ struct BatchLayout {
 };
 
 BatchLayout layout_batch(fs_ctx* c, fs::ViewParams* vh, const fs_camera* cams, int32_t v0,
-                         int nb) {
+                         int nb, uint32_t* cols) {
   BatchLayout L;
   for (int k = 0; k < nb; ++k) {
     fs::fill_view(cams[v0 + k], &vh[k]);
+    vh[k].cols = cols;
     vh[k].tile_base = L.total_tiles;
     vh[k].state_off = L.pixels;
     vh[k].mask = c->mask_dev[v0 + k];
@@ -522,6 +530,7 @@ struct ProjPtrs {
   uint32_t* cnt;
   uint32_t* dlo;
   uint32_t* dkey;  // resident depth keys (keep only)
+  uint32_t* cols;  // 3-sigma tile columns, or NULL (exact coverage)
 };
 
 ProjPtrs proj_ptrs(fs_ctx* c, bool keep, int32_t v0, int64_t n) {
@@ -530,7 +539,8 @@ ProjPtrs proj_ptrs(fs_ctx* c, bool keep, int32_t v0, int64_t n) {
           c->compact ? c->rec.as<fs::CompactRecord>() + off : nullptr,
           c->foot.as<fs::Footprint>() + off,
           c->cnt.as<uint32_t>() + off, c->dlo.as<uint32_t>() + off,
-          keep ? c->dkey.as<uint32_t>() + off : nullptr};
+          keep ? c->dkey.as<uint32_t>() + off : nullptr,
+          c->sigma3 ? c->cols.as<uint32_t>() + off : nullptr};
 }
 
 fs_status ensure_window(fs_ctx* c, int64_t n, int vb, int32_t V, bool keep) {
@@ -542,6 +552,7 @@ fs_status ensure_window(fs_ctx* c, int64_t n, int vb, int32_t V, bool keep) {
   FS_TRY(c->cnt.ensure(static_cast<size_t>(pcap) * 4, "counts"));
   FS_TRY(c->dlo.ensure(static_cast<size_t>(pcap) * 4, "depth low words"));
   if (keep) FS_TRY(c->dkey.ensure(static_cast<size_t>(pcap) * 4, "depth keys"));
+  if (c->sigma3) FS_TRY(c->cols.ensure(static_cast<size_t>(pcap) * 4, "tile columns"));
   FS_TRY(c->key_a.ensure(static_cast<size_t>(kcap) * 4, "keys"));
   FS_TRY(c->val_a.ensure(static_cast<size_t>(kcap) * 4, "vals"));
   FS_TRY(c->key_b.ensure(static_cast<size_t>(kcap) * 4, "keys"));
@@ -716,7 +727,8 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     const int nbb = std::min(vb, V - w0);
     fs::ViewParams* vhq = c->views_host.as<fs::ViewParams>() + q * fs::kMaxViewsPerBatch;
     Prologue& pr = pro[q];
-    pr.L = layout_batch(c, vhq, cams, w0, nbb);
+    const ProjPtrs PP = proj_ptrs(c, keep, w0, n);
+    pr.L = layout_batch(c, vhq, cams, w0, nbb, PP.cols);
     pr.vd = c->views.as<fs::ViewParams>() + q * fs::kMaxViewsPerBatch;
     pr.key = (q ? c->key_a2 : c->key_a).as<uint32_t>();
     pr.val = (q ? c->val_a2 : c->val_a).as<uint32_t>();
@@ -725,7 +737,6 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     uint32_t* krq = c->key_range.as<uint32_t>() + 4 * q;
     uint32_t* krhq = c->total_host.as<uint32_t>() + 4 + 4 * q;
     pr.krh = krhq;
-    const ProjPtrs PP = proj_ptrs(c, keep, w0, n);
     FS_CUDA(cudaMemcpyAsync(pr.vd, vhq, sizeof(fs::ViewParams) * nbb, cudaMemcpyHostToDevice,
                             strm),
             "view upload");
@@ -961,7 +972,8 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
   unsigned long long* ctr_h = c->counters_host.as<unsigned long long>();
   for (int32_t v0 = 0, b = 0; v0 < V; v0 += vb, ++b) {
     const int nb = std::min(vb, V - v0);
-    const BatchLayout L = layout_batch(c, vh, cams, v0, nb);
+    const ProjPtrs P = proj_ptrs(c, keep, v0, n);
+    const BatchLayout L = layout_batch(c, vh, cams, v0, nb, P.cols);
     const int total_tiles = L.total_tiles;
     const size_t sat_bytes = static_cast<size_t>((total_tiles + 63) / 64) * 8;
     FS_TRY(c->sat.ensure(sat_bytes, "tile flags"));
@@ -972,7 +984,6 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
     uint64_t* deep = c->subsat.as<uint64_t>();
     FS_CUDA(cudaMemcpyAsync(vd, vh, sizeof(fs::ViewParams) * nb, cudaMemcpyHostToDevice, stream),
             "view upload");
-    const ProjPtrs P = proj_ptrs(c, keep, v0, n);
     const uint32_t* key_src = P.dkey;
     if (!keep) {
       c->stats.kernel_launches += 1;

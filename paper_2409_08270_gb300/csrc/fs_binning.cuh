@@ -68,4 +68,15 @@ __device__ __forceinline__ bool row_span(const Footprint& f, int ty, int width, 
   return true;
 }
 
+// Under 3-sigma coverage, [tx0, tx1] narrowed to the slot's tile columns
+// (false if nothing is left); unchanged under exact coverage.
+__device__ __forceinline__ bool clip_cols(const ViewParams& vp, int64_t slot, int* tx0,
+                                          int* tx1) {
+  if (!vp.cols) return true;
+  const uint32_t c = vp.cols[slot];
+  *tx0 = max(*tx0, static_cast<int>(c & 0xFFFFu));
+  *tx1 = min(*tx1, static_cast<int>(c >> 16));
+  return *tx0 <= *tx1;
+}
+
 }  // namespace fs

@@ -49,6 +49,10 @@ struct ViewParams {
   int32_t pad0;
   int64_t state_off;           // first pixel of this view in the batch's pixel state
   const void* mask;            // device pointer to the view's labels
+  // 3-sigma tile coverage: per (view, Gaussian) slot, indexed like the
+  // footprints, the tile columns the Gaussian may reach (first | last << 16);
+  // written by the projection.  NULL: exact coverage.
+  uint32_t* cols;
 };
 
 // Projected record of one (view, Gaussian): 4 x float4 = 64 B.

@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(256, 3) project_kernel(
     Footprint F;
     F.mx = F.my = F.hy = F.syr = F.dys = F.a = F.b2 = 0.f;
     F.rows = 0x0000FFFFu;  // no tile row (first row 65535 > last row 0)
+    uint32_t col_clip = 0x0000FFFFu;  // 3-sigma coverage: no tile column
     if (visible) {
       const f2 ux = f2_div(tx, tz), uy = f2_div(ty, tz);
       const f2 fx = {vp.fx_hi, vp.fx_lo}, fy = {vp.fy_hi, vp.fy_lo};
@@ -287,12 +288,41 @@ __global__ void __launch_bounds__(256, 3) project_kernel(
       if (!(py1 >= 0.f && py0 <= vp.height - 1 && px1 >= 0.f && px0 <= vp.width - 1)) {
         visible = false;
       } else {
-        const int ty0 = static_cast<int>(fmaxf(py0, 0.f)) / kTile;
-        const int ty1 = static_cast<int>(fminf(py1, (float)(vp.height - 1))) / kTile;
-        F.rows = static_cast<uint32_t>(ty0) | (static_cast<uint32_t>(ty1) << 16);
-        count = 1;
+        int ty0 = static_cast<int>(fmaxf(py0, 0.f)) / kTile;
+        int ty1 = static_cast<int>(fminf(py1, (float)(vp.height - 1))) / kTile;
+        if (vp.cols) {
+          // 3-sigma coverage: the tiles that the square of half side
+          // r = ceil(3 sqrt(lambda_max)) around the mean overlaps, decided in
+          // FP32 with every step rounded to nearest (no contraction)
+          const float mid = __fmul_rn(0.5f, __fadd_rn(sxx, syy));
+          const float hd = __fmul_rn(0.5f, __fsub_rn(sxx, syy));
+          const float lmax =
+              __fadd_rn(mid, __fsqrt_rn(__fadd_rn(__fmul_rn(hd, hd), __fmul_rn(sxy, sxy))));
+          const float r = ceilf(__fmul_rn(3.f, __fsqrt_rn(lmax)));
+          const float inv = 1.f / kTile;  // a power of two: the scaling is exact
+          const float cx0 = fmaxf(floorf(__fmul_rn(__fsub_rn(F.mx, r), inv)), 0.f);
+          const float cx1 = fminf(__fsub_rn(ceilf(__fmul_rn(__fadd_rn(F.mx, r), inv)), 1.f),
+                                  static_cast<float>(vp.tiles_x - 1));
+          const float cy0 = fmaxf(floorf(__fmul_rn(__fsub_rn(F.my, r), inv)), 0.f);
+          const float cy1 = fminf(__fsub_rn(ceilf(__fmul_rn(__fadd_rn(F.my, r), inv)), 1.f),
+                                  static_cast<float>(vp.tiles_y - 1));
+          if (cx0 <= cx1 && cy0 <= cy1) {
+            ty0 = max(ty0, static_cast<int>(cy0));
+            ty1 = min(ty1, static_cast<int>(cy1));
+            col_clip = static_cast<uint32_t>(cx0) | (static_cast<uint32_t>(cx1) << 16);
+          } else {
+            ty1 = ty0 - 1;
+          }
+        }
+        if (ty0 <= ty1) {
+          F.rows = static_cast<uint32_t>(ty0) | (static_cast<uint32_t>(ty1) << 16);
+          count = 1;
+        } else {
+          visible = false;
+        }
       }
     }
+    if (vp.cols) vp.cols[slot] = col_clip;
     if (rec16)
       rec16[slot] = R16;
     else
@@ -427,6 +457,7 @@ __device__ __forceinline__ uint32_t job_free(const RowJob& jb, int64_t n,
   const Footprint f = foot[jb.g];
   int tx0, tx1;
   if (!row_span(f, jb.row, views[v].width, &tx0, &tx1)) return 0;
+  if (!clip_cols(views[v], jb.g, &tx0, &tx1)) return 0;
   const int base = views[v].tile_base + jb.row * views[v].tiles_x;
   *a = base + tx0;
   *b = base + tx1;

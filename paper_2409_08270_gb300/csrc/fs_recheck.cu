@@ -107,7 +107,7 @@ __global__ void mark_tiles_kernel(int64_t n_flagged, int n_views, int64_t n,
   footprint_rows(f, &ty0, &ty1);
   for (int ty = ty0; ty <= ty1; ++ty) {
     int tx0, tx1;
-    if (!row_span(f, ty, vp.width, &tx0, &tx1)) continue;
+    if (!row_span(f, ty, vp.width, &tx0, &tx1) || !clip_cols(vp, slot, &tx0, &tx1)) continue;
     const int a = vp.tile_base + ty * vp.tiles_x + tx0;
     const int b = vp.tile_base + ty * vp.tiles_x + tx1;
     for (int w = a >> 6; w <= (b >> 6); ++w) {
@@ -139,7 +139,7 @@ __global__ void candidates_kernel(int64_t k_total, int64_t n, const ViewParams* 
     footprint_rows(f, &ty0, &ty1);
     for (int ty = ty0; ty <= ty1 && !hit; ++ty) {
       int tx0, tx1;
-      if (!row_span(f, ty, vp.width, &tx0, &tx1)) continue;
+      if (!row_span(f, ty, vp.width, &tx0, &tx1) || !clip_cols(vp, slot, &tx0, &tx1)) continue;
       const int base = vp.tile_base + ty * vp.tiles_x;
       if (count_free(skip, base + tx0, base + tx1)) hit = 1;
     }

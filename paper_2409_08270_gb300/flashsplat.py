@@ -22,6 +22,7 @@ FS_OK, FS_INVALID_ARGUMENT, FS_OUT_OF_MEMORY, FS_CUDA_ERROR, FS_TIMEOUT, FS_UNSU
     FS_CANCELLED = range(7)
 FS_F32, FS_F64, FS_BF16, FS_F16, FS_U8, FS_I32 = range(6)
 FS_MEM_HOST, FS_MEM_DEVICE = 0, 1
+FS_COVERAGE_EXACT, FS_COVERAGE_3SIGMA = 0, 1
 
 STATUS_NAMES = {0: "FS_OK", 1: "FS_INVALID_ARGUMENT", 2: "FS_OUT_OF_MEMORY", 3: "FS_CUDA_ERROR",
                 4: "FS_TIMEOUT", 5: "FS_UNSUPPORTED", 6: "FS_CANCELLED"}
@@ -38,7 +39,8 @@ class fs_options(ctypes.Structure):
     _fields_ = [("views_per_batch", ctypes.c_int32), ("time_stages", ctypes.c_int32),
                 ("depth_chunks", ctypes.c_int32), ("recheck_margin", ctypes.c_float),
                 ("recheck_reproject", ctypes.c_int32), ("record_precision", ctypes.c_int32),
-                ("census", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("census", ctypes.c_int32), ("coverage", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
 
 
 class fs_gaussians(ctypes.Structure):
@@ -163,7 +165,7 @@ def fs_last_error() -> str:
 def fs_create(device: int = 0, views_per_batch: int = 0, time_stages: bool = False,
               depth_chunks: int = 0, recheck_margin: float = 0.0,
               recheck_reproject: bool = False, record_precision: int = 0,
-              census: bool = False) -> int:
+              census: bool = False, coverage: int = 0) -> int:
     ctx = ctypes.c_void_p()
     opt = fs_options()
     opt.views_per_batch = views_per_batch
@@ -173,6 +175,7 @@ def fs_create(device: int = 0, views_per_batch: int = 0, time_stages: bool = Fal
     opt.recheck_reproject = 1 if recheck_reproject else 0
     opt.record_precision = record_precision
     opt.census = 1 if census else 0
+    opt.coverage = coverage
     check(load().fs_create(ctypes.byref(ctx), device, ctypes.byref(opt)))
     return ctx.value
 
@@ -263,11 +266,11 @@ class Solver:
     def __init__(self, gaussians, device: int = 0, views_per_batch: int = 0,
                  time_stages: bool = False, depth_chunks: int = 0, recheck_margin: float = 0.0,
                  recheck_reproject: bool = False, record_precision: int = 0,
-                 census: bool = False):
+                 census: bool = False, coverage: int = 0):
         torch = _torch()
         self.device = torch.device("cuda", device)
         self.ctx = fs_create(device, views_per_batch, time_stages, depth_chunks, recheck_margin,
-                             recheck_reproject, record_precision, census)
+                             recheck_reproject, record_precision, census, coverage)
         self.scene = None
         dev = {}
         for k in ("mean", "quat", "scale", "opacity"):

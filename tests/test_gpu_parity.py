@@ -29,9 +29,9 @@ def fsb():
 
 
 def _solve(fsb, w, table_dtype="float32", views_per_batch=0, masks=None, E=None, gamma=None,
-           depth_chunks=0, recheck_margin=0.0):
+           depth_chunks=0, recheck_margin=0.0, **solver_kw):
     s = fsb.Solver(w.gaussians, views_per_batch=views_per_batch, depth_chunks=depth_chunks,
-                   recheck_margin=recheck_margin)
+                   recheck_margin=recheck_margin, **solver_kw)
     try:
         out = s.solve(w.cams, w.masks if masks is None else masks, w.E if E is None else E,
                       w.gamma if gamma is None else gamma, table_dtype=table_dtype)
@@ -277,3 +277,54 @@ def test_bounded_wait_gives_up_with_timeout(fsb, tiny):
     assert "gave up" in fsb.fs_last_error()
     gpu = _solve(fsb, synth.tiny_scene(n=500, views=1))
     assert gpu["table"].sum() > 0
+
+
+def _sigma3_scene(seed=41, n=3000, views=4, width=160, height=120):
+    """Opaque Gaussians stretched along the image x or y axis (cameras look
+    down z): their alpha >= 1/255 region reaches 3.3 sigma along the long
+    axis, past the 3-sigma square, so the two coverages differ."""
+    rng = np.random.default_rng(seed)
+    ang = rng.uniform(-0.03, 0.03, n)
+    quat = np.column_stack([np.cos(ang), np.zeros(n), np.zeros(n), np.sin(ang)]).astype(np.float32)
+    long_, short = rng.uniform(0.04, 0.12, n), rng.uniform(0.005, 0.02, n)
+    along_x = rng.random(n) < 0.5
+    scale = np.column_stack([np.where(along_x, long_, short), np.where(along_x, short, long_),
+                             rng.uniform(0.005, 0.02, n)]).astype(np.float32)
+    mean = np.column_stack([rng.uniform(-1, 1, n), rng.uniform(-0.75, 0.75, n),
+                            rng.uniform(-0.5, 0.5, n)]).astype(np.float32)
+    g = {"mean": mean, "quat": quat, "scale": scale,
+         "opacity": rng.uniform(0.5, 0.99, n).astype(np.float32)}
+    cams = [synth.camera((rng.uniform(-0.1, 0.1), rng.uniform(-0.1, 0.1), -3.0), width, height,
+                         150.0, target=(rng.uniform(-0.1, 0.1), rng.uniform(-0.1, 0.1), 0.0))
+            for _ in range(views)]
+    yy, xx = np.mgrid[0:height, 0:width]
+    masks = [((xx + 0.5 * yy) > 0.6 * width).astype(np.uint8) for _ in cams]
+    return synth.Workload("sigma3", g, cams, masks, 2, 0.0, np.zeros(n, np.int32))
+
+
+@pytest.mark.parametrize("variant", ["main", "batched_recheck_all", "recheck_reproject"])
+def test_3sigma_coverage_matches_the_oracle(fsb, variant):
+    """FS_COVERAGE_3SIGMA against the oracle's 3-sigma mode (Sec. 4.2's
+    standard rasteriser coverage): the table within the FP32 tolerance and
+    the labels outside the decision window.  The variants run the clipped
+    columns through every binning path: the main pass; one view per batch
+    with every Gaussian re-checked from the kept lists; the re-check that
+    projects again."""
+    w = _sigma3_scene()
+    acc3 = oracle.accumulate(w.gaussians, w.cams, w.masks, w.E, coverage=oracle.COVERAGE_3SIGMA)
+    exact = oracle.accumulate(w.gaussians, w.cams, w.masks, w.E)
+    moved = np.abs(acc3.table - exact.table).sum(1) / np.maximum(exact.table.sum(1), 1e-30)
+    assert (moved > 1e-4).sum() >= 100          # the coverages differ well past the tolerance
+    kw = {"coverage": fsb.FS_COVERAGE_3SIGMA}
+    if variant == "batched_recheck_all":
+        kw.update(views_per_batch=1, recheck_margin=10.0)
+    elif variant == "recheck_reproject":
+        kw.update(recheck_margin=10.0, recheck_reproject=True)
+    gpu = _solve(fsb, w, table_dtype="float64", **kw)
+    summ, lab = _check(gpu, acc3, w.gamma)
+    print("3-sigma", variant, summ, lab)
+    assert summ["checked_rel"] > 1000
+    # and the GPU table is the 3-sigma one, not the exact one
+    far = moved > 1e-4
+    rel_exact = np.abs(gpu["table"][far] - exact.table[far]).sum(1) / exact.table[far].sum(1)
+    assert np.all(rel_exact > 5e-5)

@@ -89,7 +89,11 @@ def test_alpha_error_near_the_cut(fsb):
     print("alpha near 1/255:", int(both.sum()), "kept by both, max rel %.2e, mean %.2e"
           % (rel.max(), rel.mean()))
     assert both.sum() > 200
-    assert rel.max() <= 0.2 * EPS
+    # alpha = 2^-a with a = |w|^2 - log2 o ~ log2(255) ~ 8 at the cut: FP32
+    # rounding of a few ulps in a moves alpha by ln2 * 8 * 2^-23 ~ 7e-7
+    # relative each, a few times that in all; the window eps must exceed it
+    # by a clear factor
+    assert rel.max() <= 0.5 * EPS
     differ = ok & ((ora > 0) != (gpu > 0))
     # the decision may differ only within the window of the cut
     a_exact = g["opacity"].astype(np.float64) * a1          # alpha before the skip
