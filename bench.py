@@ -60,6 +60,13 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="0: the workload's own count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip timing the other precision form of the workload")
+    ap.add_argument("--no-multi", action="store_true",
+                    help="skip the multi-instance workload's extra measurement")
+    ap.add_argument("--multi-steps", type=int, default=5)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="skip timing the solve captured into a CUDA graph")
     ap.add_argument("--cpu-sample-views", type=int, default=12)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"],
                     help="fp16: the reduced-precision form (BF16 quat/scale, FP16 opacity, "
@@ -246,6 +253,94 @@ def whole_job_gpix(world, pixels_per_rank, steps, total_ms):
 # the CUDA arm
 # ---------------------------------------------------------------------------
 
+def make_solver(fsb, w, args, local_rank, precision, census=False, time_stages=True):
+    """A solver over the workload's scene in one of the two forms: plain FP32
+    inputs with float-pair records, or the reduced-precision form (BF16 quat
+    and scale, FP16 opacity, FP16 whitening matrix + FP32 mean per view)."""
+    import torch
+    gaussians = w.gaussians
+    if precision == "fp16":
+        r = synth_mod().rounded_gaussians(w.gaussians)
+        gaussians = {"mean": torch.from_numpy(r["mean"]),
+                     "quat": torch.from_numpy(r["quat"]).to(torch.bfloat16),
+                     "scale": torch.from_numpy(r["scale"]).to(torch.bfloat16),
+                     "opacity": torch.from_numpy(r["opacity"]).to(torch.float16)}
+    return fsb.Solver(gaussians, device=local_rank, views_per_batch=args.views_per_batch,
+                      depth_chunks=args.depth_chunks, time_stages=time_stages and not census,
+                      recheck_margin=args.recheck_margin,
+                      record_precision=fsb.FS_F16 if precision == "fp16" else 0, census=census)
+
+
+def timed_solves(fsb, solver, w, dmasks, steps, warmup, flush, stream, dev):
+    """`warmup` untimed solves, then `steps` timed ones, each after an L2
+    flush, timed with CUDA events on the launching stream.  Returns the
+    per-step ms, the summed per-solve statistics and the last output."""
+    import torch
+    out = None
+    for _ in range(warmup):
+        out = solver.solve(w.cams, dmasks, w.E, w.gamma, sync=False)
+    fsb.fs_synchronize(solver.ctx, stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    ms, sums = [], {"blend_ms": 0.0, "blend_launches": 0, "list_entries": 0,
+                    "staged_entries": 0, "rechecked": 0, "recheck_pairs": 0,
+                    "kernel_launches": 0}
+    for _ in range(steps):
+        flush.fill_(1)                       # evict the previous step's data from L2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = solver.solve(w.cams, dmasks, w.E, w.gamma, sync=False)
+        e1.record(stream)
+        st = fsb.fs_synchronize(solver.ctx, stream.cuda_stream)
+        ms.append(e0.elapsed_time(e1))
+        for k in sums:
+            sums[k] += getattr(st, k)
+    torch.cuda.synchronize(dev)
+    return ms, sums, out
+
+
+def census_pairs_of(fsb, w, args, local_rank, precision, dmasks, stream):
+    """Work units of the blend, counted by one census solve (a counting
+    variant of the same kernels, untimed)."""
+    cs = make_solver(fsb, w, args, local_rank, precision, census=True)
+    try:
+        cs.solve(w.cams, dmasks, w.E, w.gamma, sync=False)
+        st = fsb.fs_synchronize(cs.ctx, stream.cuda_stream)
+        return st
+    finally:
+        cs.close()
+
+
+def form_accuracy(w, outs, rows=96, seed=7):
+    """Each form's table rows and labels against the FP64 oracle on the
+    ORIGINAL (unrounded) inputs, on a seeded sample of seen Gaussians: max /
+    mean relative error of the entries the oracle's near-threshold bound does
+    not cover, and the fraction of sampled labels that agree."""
+    import numpy as np
+    import oracle
+    from oracle.assign import assign, labels_from_membership
+    any_out = next(iter(outs.values()))
+    seen = np.flatnonzero(any_out["table"].sum(1) > 0)
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(seen, min(rows, seen.size), replace=False))
+    t0 = time.perf_counter()
+    acc = oracle.accumulate(w.gaussians, w.cams, w.masks, w.E, sel=sel)
+    dt = time.perf_counter() - t0
+    lab_o = labels_from_membership(assign(acc.table, w.gamma))
+    ref = acc.table
+    res = {}
+    for name, o in outs.items():
+        g = o["table"][sel].astype(np.float64)
+        ok = (ref >= 1e-6 * ref.max()) & (acc.risk <= 1e-6 * ref)
+        rel = np.abs(g - ref)[ok] / ref[ok]
+        lab = o["label"][sel]
+        res[name] = {"rows": int(sel.size), "entries_free_of_bound": int(ok.sum()),
+                     "max_rel_err": float(rel.max()) if rel.size else None,
+                     "mean_rel_err": float(rel.mean()) if rel.size else None,
+                     "label_agreement": float((lab == lab_o).mean())}
+    return res, dt
+
+
 def run_flashsplat(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -260,28 +355,10 @@ def run_flashsplat(args, rank, world, local_rank):
     w = workload(args)
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
-    gaussians = w.gaussians
-    if args.precision == "fp16":
-        r = synth_mod().rounded_gaussians(w.gaussians)
-        gaussians = {"mean": torch.from_numpy(r["mean"]),
-                     "quat": torch.from_numpy(r["quat"]).to(torch.bfloat16),
-                     "scale": torch.from_numpy(r["scale"]).to(torch.bfloat16),
-                     "opacity": torch.from_numpy(r["opacity"]).to(torch.float16)}
-    solver = fsb.Solver(gaussians, device=local_rank, views_per_batch=args.views_per_batch,
-                        depth_chunks=args.depth_chunks, time_stages=True,
-                        recheck_margin=args.recheck_margin,
-                        record_precision=fsb.FS_F16 if args.precision == "fp16" else 0)
+    solver = make_solver(fsb, w, args, local_rank, args.precision)
     dmasks = solver.upload_masks(w.masks)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
-
-    def step():
-        return solver.solve(w.cams, dmasks, w.E, w.gamma, sync=False)
-
-    for _ in range(args.warmup):
-        out = step()
-    fsb.fs_synchronize(solver.ctx, stream.cuda_stream)
-    torch.cuda.synchronize(dev)
 
     uuid = None
     try:
@@ -292,28 +369,15 @@ def run_flashsplat(args, rank, world, local_rank):
         torch.distributed.barrier()
     clocks = ClockSampler(uuid)
     torch.cuda.synchronize(dev)
-    ms_steps, blend_ms, pairs, launches, blend_launches, entries, staged = [], 0.0, 0, 0, 0, 0, 0
-    rechecked, recheck_pairs = 0, 0
     t_wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.fill_(1)                       # evict the previous step's data from L2
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        out = step()
-        e1.record(stream)
-        st = fsb.fs_synchronize(solver.ctx, stream.cuda_stream)
-        ms_steps.append(e0.elapsed_time(e1))
-        blend_ms += st.blend_ms
-        blend_launches += st.blend_launches
-        entries += st.list_entries
-        staged += st.staged_entries
-        rechecked += st.rechecked
-        recheck_pairs += st.recheck_pairs
-        launches += st.kernel_launches
-    torch.cuda.synchronize(dev)
+    ms_steps, sums, out = timed_solves(fsb, solver, w, dmasks, args.steps, args.warmup, flush,
+                                       stream, dev)
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
+    blend_ms, blend_launches = sums["blend_ms"], sums["blend_launches"]
+    entries, staged = sums["list_entries"], sums["staged_entries"]
+    rechecked, recheck_pairs = sums["rechecked"], sums["recheck_pairs"]
+    launches = sums["kernel_launches"]
     total_ms = max_over_ranks(sum(ms_steps), world, dev)
     if world > 1:
         torch.distributed.barrier()
@@ -326,17 +390,11 @@ def run_flashsplat(args, rank, world, local_rank):
     # the compositing rule of Eq. 1 must evaluate, whatever the culling.  The
     # workload is fixed, so one census solve (a counting variant of the same
     # kernels) gives the units of every timed step.
-    csolver = fsb.Solver(gaussians, device=local_rank, views_per_batch=args.views_per_batch,
-                         depth_chunks=args.depth_chunks, recheck_margin=args.recheck_margin,
-                         record_precision=fsb.FS_F16 if args.precision == "fp16" else 0,
-                         census=True)
-    csolver.solve(w.cams, dmasks, w.E, w.gamma, sync=False)
-    cst = fsb.fs_synchronize(csolver.ctx, stream.cuda_stream)
+    cst = census_pairs_of(fsb, w, args, local_rank, args.precision, dmasks, stream)
     census_pairs, census_evaluated = int(cst.census_pairs), int(cst.pairs)
     census_shape = {"rounds": int(cst.census_rounds), "steps": int(cst.census_steps),
                     "rounds_mixed_labels": int(cst.census_rounds_mixed),
                     "staged": int(cst.staged_entries), "list_entries": int(cst.list_entries)}
-    csolver.close()
     pairs = census_pairs * args.steps
 
     # ---- argmax-only re-solve for a new gamma on the resident table ----------
@@ -449,8 +507,133 @@ def run_flashsplat(args, rank, world, local_rank):
                              "gaussians_per_step": rechecked // max(1, args.steps),
                              "fp64_pairs_per_step": recheck_pairs // max(1, args.steps)},
     }
+    # ---- the same solve captured into a CUDA graph and replayed ----------------
+    if not args.no_graph:
+        line["graph"] = measure_graph(fsb, solver, w, dmasks, args, flush, stream, dev, out, world)
+    # ---- the same workload in the other form: plain FP32 vs reduced precision --
+    if world == 1 and not args.no_forms:
+        line["forms"] = measure_forms(fsb, args, w, local_rank, dev, stream, flush, solver,
+                                      dmasks, ms_steps, out)
     solver.close()
+    del dmasks
+    # ---- the multi-instance workload (3M Gaussians, 200 views, 33 labels) -----
+    if world == 1 and not args.no_multi and args.workload == "binary":
+        line["workloads"] = {"multi": measure_multi(fsb, args, local_rank, dev, stream, flush,
+                                                    n_sm, sm_clk)}
     return line, w
+
+
+def measure_graph(fsb, solver, w, dmasks, args, flush, stream, dev, out_main, world):
+    """The solve captured once (fs_graph_create) and replayed `steps` times,
+    timed like the main loop (L2 flushed before each replay, CUDA events on
+    the stream); the near-tie re-check and the FP32 rounding run after each
+    replay, outside the graph, as in fs_graph_launch."""
+    import numpy as np
+    import torch
+    t0 = time.perf_counter()
+    g = solver.capture(w.cams, dmasks, w.E, w.gamma)
+    t_capture = time.perf_counter() - t0
+    try:
+        for _ in range(args.warmup):
+            g.launch(stream)
+        g.synchronize(stream)
+        if world > 1:
+            torch.distributed.barrier()
+        ms = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.launch(stream)
+            e1.record(stream)
+            st = g.synchronize(stream)
+            ms.append(e0.elapsed_time(e1))
+        total = max_over_ranks(sum(ms), world, dev)
+        same = bool(np.array_equal(g.outputs["label"].cpu().numpy(),
+                                   out_main["label"].cpu().numpy()))
+    finally:
+        g.close()
+    return {"ms_per_step": total / args.steps,
+            "value": whole_job_gpix(world, w.pixels, args.steps, total), "unit": UNIT,
+            "capture_s": round(t_capture, 2), "labels_equal_uncaptured": same,
+            "graph_launches_per_step": 1, "rechecked_per_step": int(st.rechecked),
+            "what": "fs_graph_launch: one CUDA graph (projection, depth sort, binning, blend, "
+                    "FP64 sum, assignment) + the near-tie re-check and FP32 rounding after it"}
+
+
+def _form_entry(w, ms_steps, sums, steps):
+    total = sum(ms_steps)
+    return {"ms_per_step": total / steps, "value": w.pixels * steps / (total * 1e-3) / 1e9,
+            "unit": UNIT, "blend_ms_per_step": sums["blend_ms"] / steps if sums else None}
+
+
+def measure_forms(fsb, args, w, local_rank, dev, stream, flush, solver, dmasks, ms_main,
+                  out_main):
+    """The other precision form timed like the main one (same steps, L2 flush,
+    events), and both forms' accuracy against the FP64 oracle on the original
+    inputs for a sample of rows, plus how many labels differ between them."""
+    other = "fp16" if args.precision == "fp32" else "fp32"
+    name = {"fp32": "plain_fp32", "fp16": "bf16"}
+    s2 = make_solver(fsb, w, args, local_rank, other)
+    try:
+        ms2, sums2, out2 = timed_solves(fsb, s2, w, dmasks, args.steps, args.warmup, flush,
+                                        stream, dev)
+    finally:
+        s2.close()
+    host = {name[args.precision]: {"table": out_main["table"].float().cpu().numpy(),
+                                   "label": out_main["label"].cpu().numpy()},
+            name[other]: {"table": out2["table"].float().cpu().numpy(),
+                          "label": out2["label"].cpu().numpy()}}
+    acc, dt = form_accuracy(w, host)
+    forms = {name[args.precision]: _form_entry(w, ms_main, None, args.steps),
+             name[other]: _form_entry(w, ms2, sums2, args.steps)}
+    for k in forms:
+        forms[k].update(acc[k])
+    a, b = host["plain_fp32"]["label"], host["bf16"]["label"]
+    forms["labels_differing_between_forms"] = int((a != b).sum())
+    forms["gaussians"] = int(a.size)
+    forms["bf16_form"] = ("BF16 quaternion and scale, FP16 opacity (scene storage); per view an "
+                          "FP16 whitening matrix and FP32 mean (32 B record); blending FP32, "
+                          "table FP64 across views")
+    forms["oracle"] = (f"FP64 oracle on the original FP32 inputs, {acc[name[other]]['rows']} "
+                       f"seeded seen Gaussians over all views, {dt:.1f} s")
+    return forms
+
+
+def measure_multi(fsb, args, local_rank, dev, stream, flush, n_sm, sm_clk):
+    """The multi-instance workload in the default run: a few timed solves and
+    the blend's roofline from a census solve."""
+    import torch
+    t0 = time.perf_counter()
+    wm = synth_mod().multi_scene()
+    t_gen = time.perf_counter() - t0
+    sm = make_solver(fsb, wm, args, local_rank, "fp32")
+    try:
+        dm = sm.upload_masks(wm.masks)
+        ms, sums, _ = timed_solves(fsb, sm, wm, dm, args.multi_steps, 2, flush, stream, dev)
+        cst = census_pairs_of(fsb, wm, args, local_rank, "fp32", dm, stream)
+    finally:
+        sm.close()
+    steps = args.multi_steps
+    total = sum(ms)
+    peak = n_sm * FP32_LANES_PER_SM * 2 * sm_clk * 1e6 / 1e12
+    blend_ms = sums["blend_ms"] / steps
+    achieved = FLOPS_PER_PAIR * int(cst.census_pairs) / (blend_ms * 1e-3) / 1e12
+    plain = argparse.Namespace(**{**vars(args), "precision": "fp32"})
+    del dm
+    torch.cuda.synchronize(dev)
+    return {"config": config_of(wm, plain, {"generation_s": round(t_gen, 1)}),
+            "steps": steps, "warmup": 2, "ms_per_step": total / steps, "s_per_scene": total / steps / 1e3,
+            "value": wm.pixels * steps / (total * 1e-3) / 1e9, "unit": UNIT,
+            "roofline": {"kernel": "blend_kernel (alpha*T accumulation)", "bound": "alu",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "pairs_per_step": int(cst.census_pairs),
+                         "evaluated_pairs_per_step": int(cst.pairs),
+                         "blend_ms_per_step": blend_ms,
+                         "blend_share_of_step": sums["blend_ms"] / max(total, 1e-9)},
+            "list_entries_per_step": sums["list_entries"] // steps,
+            "near_tie_recheck_gaussians_per_step": sums["rechecked"] // steps}
 
 
 # ---------------------------------------------------------------------------
@@ -556,8 +739,8 @@ def run_serve(args):
         svc = np.array([x.done_s - x.start_s for x in infos])
         return wall, lat, svc, infos
 
-    def make(slots):
-        srv = fsb.Server(slots=slots, autotune=True)
+    def make(slots, graphs=0):
+        srv = fsb.Server(slots=slots, autotune=True, graphs=graphs)
         ids = [srv.add_scene(w.gaussians) for w in scenes]
         for k, w in enumerate(scenes):      # warm-up: tuning, untimed
             srv.fetch(srv.submit(ids[k], w.cams, variants[k][0], w.E, w.gamma))
@@ -578,6 +761,11 @@ def run_serve(args):
     seq, seq_ids = make(1)
     wall_s, lat_s, svc_s, _ = run_trace(seq, seq_ids, paced=False, window=1)
     seq.close()
+    # every request a replay of its scene's captured solve (fs_graph_*)
+    gsrv, gids = make(args.slots, graphs=len(scenes))
+    wall_g, lat_g, svc_g, _ = run_trace(gsrv, gids, paced=True)
+    wall_gb, lat_gb, _, _ = run_trace(gsrv, gids, paced=False)
+    gsrv.close()
     pix = sum(scenes[int(k)].pixels for k in picks)
     q = lambda a, p: float(np.quantile(a, p))
     return {
@@ -590,6 +778,14 @@ def run_serve(args):
         "sequential": {"requests_per_s": R / wall_s, "gpix_per_s": pix / wall_s / 1e9,
                        "p50_service_s": q(svc_s, 0.5), "p99_service_s": q(svc_s, 0.99)},
         "service_s": {"p50": q(svc, 0.5), "p99": q(svc, 0.99)},
+        "captured": {"what": "each request replays its scene's captured solve (CUDA graph) "
+                             "after its masks are copied into the captured buffers",
+                     "p50_latency_s": q(lat_g, 0.5), "p99_latency_s": q(lat_g, 0.99),
+                     "requests_per_s": R / wall_g,
+                     "service_s": {"p50": q(svc_g, 0.5), "p99": q(svc_g, 0.99)},
+                     "burst": {"requests_per_s": R / wall_gb, "gpix_per_s": pix / wall_gb / 1e9,
+                               "p50_latency_s": q(lat_gb, 0.5),
+                               "p99_latency_s": q(lat_gb, 0.99)}},
         "dtype": "f32", "data": "synthetic (16 seeded clustered scenes, orbit cameras, "
                                 "noisy label masks; two noise draws per scene)",
         "config": {"workload": "16 resident scenes: N log-uniform 2e5..2e6, 20..150 views, "

@@ -330,7 +330,13 @@ typedef struct fs_server_options {
                              times a few (views per batch, depth chunks)
                              settings on a sample of its views and keeps the
                              fastest for the scene's later requests */
-  int32_t reserved[9];
+  int32_t graphs;         /* > 0: requests run as replays of captured solves
+                             (fs_graph_*), one per scene for its last
+                             (cameras, E, gamma, mask dtype), at most `graphs`
+                             scenes kept (least recently used dropped);
+                             a request with a new key captures its scene
+                             again.  0: plain fs_solve per request */
+  int32_t reserved[8];
 } fs_server_options;
 
 /* Outcome and timing of one request (steady-clock seconds). */
@@ -371,6 +377,13 @@ fs_status fs_server_submit(fs_server* srv, int32_t scene_id, const fs_camera* ca
 fs_status fs_server_fetch(fs_server* srv, int64_t ticket, int32_t wait, uint64_t* member_bits,
                           int32_t* label, float* margin, fs_server_info* info);
 
+/* fs_server_fetch with a bounded wait: blocks at most timeout_ms milliseconds
+ * (0: not at all; negative: until done) and returns FS_TIMEOUT, leaving the
+ * request in place, if it has not finished by then. */
+fs_status fs_server_fetch_for(fs_server* srv, int64_t ticket, int32_t timeout_ms,
+                              uint64_t* member_bits, int32_t* label, float* margin,
+                              fs_server_info* info);
+
 /* Drop a request that has not started (FS_CANCELLED when fetched);
  * FS_UNSUPPORTED if it is already running or done. */
 fs_status fs_server_cancel(fs_server* srv, int64_t ticket);
@@ -378,6 +391,64 @@ fs_status fs_server_cancel(fs_server* srv, int64_t ticket);
 /* Stop accepting requests, finish the running ones, drop the queued ones,
  * join the threads and free everything. */
 fs_status fs_server_destroy(fs_server* srv);
+
+/* ---- captured solves (CUDA graph) -------------------------------------------
+ * fs_graph_create captures one solve of (scene, cams, masks, E, gamma) into a
+ * CUDA graph that fs_graph_launch replays with a single launch on any stream:
+ * the whole accumulation (projection, depth sort, binning, blending, the
+ * FP64 cross-view sum) and the assignment, with no host synchronisation
+ * inside.  It first runs the solve once uncaptured on a context of its own
+ * (the options of `ctx`, without timing or census) to fix the solve's shapes:
+ * the depth-sort bits of each view batch, the sorted positions each depth
+ * chunk spans and its list entries; the capture then reads every count from
+ * device memory and sizes its grids and lists for that plan.  After the
+ * replay, fs_graph_launch runs the near-tie re-check (when the options turn
+ * it on; its work depends on the labels) and rounds the table to FP32 when
+ * asked, outside the graph.
+ *   masks[V]: device buffers, read at every replay: the caller may write new
+ *     masks into them between replays.  With every label in [0, E) the
+ *     shapes depend on the scene and cameras only, so any such masks replay
+ *     exactly; a replay whose shapes outgrow the plan (possible only if the
+ *     scene's device memory changed) is not run past it and reports
+ *     FS_UNSUPPORTED at fs_graph_synchronize.
+ *   out: device buffers, written by every replay.
+ * The scene must outlive the graph; one replay at a time per graph.  The
+ * FP64 table of a replay equals an uncaptured fs_solve's up to the order of
+ * the FP64 atomic additions (any two solves differ in the same way).
+ * Errors: as fs_solve; FS_INVALID_ARGUMENT for host outputs or masks. */
+typedef struct fs_graph fs_graph;
+fs_status fs_graph_create(fs_ctx* ctx, const fs_scene* scene, const fs_camera* cams,
+                          int32_t n_views, const void* const* masks, int32_t mask_dtype,
+                          int32_t E, float gamma, const fs_result* out, fs_graph** graph);
+fs_status fs_graph_launch(fs_graph* graph, void* stream);
+/* Waits for `stream` and reports the replay's device-side errors, as
+ * fs_synchronize does for a context. */
+fs_status fs_graph_synchronize(fs_graph* graph, void* stream, fs_stats* stats);
+fs_status fs_graph_destroy(fs_graph* graph);
+
+/* ---- novel-view masks -------------------------------------------------------
+ * fs_render_masks: 2D masks for views -- typically ones that had no mask --
+ * from a segmentation (Sec. 3.4 "depth-guided novel view mask rendering";
+ * Supp. Sec. 8.2 on why the quantisation is needed).  Object e = 1 .. E-1 is
+ * the subset {G_i}_e = {i : bit e of member_bits[i] set} (fs_solve's S); each
+ * is rendered on its own with the solve's rules (Eq. 1 over its Gaussians
+ * only, FP32): rho^e = sum alpha T, and its depth D^e = sum alpha T z /
+ * rho^e with z the view-space depth of each Gaussian's mean (0 where rho^e
+ * is 0).  A pixel's mask value is the object with rho^e > tau of smallest
+ * D^e, equal depths to the smaller e, and 0 where no object passes.  With
+ * E = 2 this is the binary mask [rho^1 > tau]; Sec. 4.6 uses tau = 0.1.
+ * Coverage follows the context's fs_options.coverage.
+ *   member_bits: n words in device memory (bit e: object e)
+ *   masks_out[v]: device buffer of H x W values, out_dtype FS_U8 or FS_I32
+ *   rho_out[v], depth_out[v]: NULL (the array or an entry), or device buffers
+ *     of (E-1) x H x W FP32 receiving rho^e and D^e, object-major
+ * Synchronises `stream` once per view batch and object (list sizes).  Errors:
+ * FS_INVALID_ARGUMENT (NULL arguments, bad cameras, E outside [2, 64], tau
+ * NaN, bad dtype), FS_OUT_OF_MEMORY, FS_CUDA_ERROR. */
+fs_status fs_render_masks(fs_ctx* ctx, const fs_scene* scene, const fs_camera* cams,
+                          int32_t n_views, const uint64_t* member_bits, int32_t E, float tau,
+                          void* const* masks_out, int32_t out_dtype, float* const* rho_out,
+                          float* const* depth_out, void* stream);
 
 /* ---- solve without allocating ----------------------------------------------
  * The paper has no counterpart of this call; it exists for callers that may

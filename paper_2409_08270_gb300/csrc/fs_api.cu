@@ -196,6 +196,9 @@ struct fs_ctx {
   bool census = false;   // blend counts its pairs (slower variant)
   bool sigma3 = false;   // 3-sigma tile coverage (per-slot tile columns in `cols`)
   DevBuf dkey, rk_flag, rk_offs, rk_F, rk_map, rk_R, rk_Rb, cols;
+  DevBuf rd_flag, rd_offs, rd_val, render_out;  // novel-view mask rendering
+  DevBuf chunk_bnd;                             // captured solves: chunk boundaries
+  HostBuf render_out_host;
   DevBuf key_range;  // min / max visible depth key of the batch (two slots, by batch parity)
   // the next batch's projection runs on a side stream while the current
   // batch bins and blends (resident projections only); its depth keys go to
@@ -233,7 +236,8 @@ DevBuf* const* workspace_bufs(fs_ctx* c, size_t* count) {
                     &c->label_tmp, &c->margin_tmp, &c->dkey, &c->rk_flag, &c->rk_offs,
                     &c->rk_F, &c->rk_map, &c->rk_R, &c->rk_Rb, &c->kl_ranges, &c->kl_satc,
                     &c->kl_bound, &c->key_range, &c->lb_tmp, &c->key_a2, &c->val_a2,
-                    &c->key_b2, &c->val_b2, &c->cols};
+                    &c->key_b2, &c->val_b2, &c->cols, &c->rd_flag, &c->rd_offs, &c->rd_val,
+                    &c->render_out, &c->chunk_bnd};
   for (DevBuf* b : list) bufs[k++] = b;
   *count = k;
   return bufs;
@@ -338,10 +342,12 @@ fs_status fs_destroy(fs_ctx* c) {
                     &c->table_tmp, &c->table32_tmp, &c->bits_tmp, &c->label_tmp, &c->margin_tmp,
                     &c->dkey, &c->rk_flag, &c->rk_offs, &c->rk_F, &c->rk_map, &c->rk_R,
                     &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_bound, &c->key_range, &c->lb_tmp,
-                    &c->key_a2, &c->val_a2, &c->key_b2, &c->val_b2, &c->cols};
+                    &c->key_a2, &c->val_a2, &c->key_b2, &c->val_b2, &c->cols,
+                    &c->rd_flag, &c->rd_offs, &c->rd_val, &c->render_out, &c->chunk_bnd};
   for (DevBuf& b : c->kl_val) b.release();
   for (DevBuf* b : bufs) b->release();
   c->views_host.release();
+  c->render_out_host.release();
   c->total_host.release();
   c->counters_host.release();
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -578,16 +584,46 @@ fs_status read_total(fs_ctx* c, cudaStream_t stream, int64_t* out) {
 // emit, stable tile sort, ranges) on tiles whose `sat` bit is clear.  The
 // sorted list values go to *val_dst (grown as needed) and the per-tile ranges
 // to ranges_dst.  Returns the entry count in *I_out.
+//
+// Captured form (range_dev != NULL): the chunk's positions are read on the
+// device from range_dev[0 .. 1] (at most n_pos of them: the grid), nothing is
+// read back, and the lists are sized for plan_cap entries (the capture's
+// plan); a replay that outgrows either is counted (kGraphOverflow).
 fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
                         const fs::ViewParams* vd, const uint32_t* sorted_val, const ProjPtrs& P,
                         const uint64_t* sat, int total_tiles, int tile_bits, int64_t kcap,
                         bool count_entries, DevBuf* val_dst, uint2* ranges_dst,
-                        cudaStream_t stream, int64_t* I_out) {
+                        cudaStream_t stream, int64_t* I_out, const int64_t* range_dev = nullptr,
+                        int64_t plan_cap = 0) {
   unsigned long long* ctr = c->counters.as<unsigned long long>();
   *I_out = 0;
   FS_CUDA(cudaMemsetAsync(ranges_dst, 0, static_cast<size_t>(total_tiles) * 8, stream),
           "ranges clear");
   FS_TRY(c->lb_tmp.ensure(fs::bin_fused_temp_bytes(n_pos), "binning look-back"));
+  if (range_dev) {
+    uint32_t* total = c->total.as<uint32_t>();
+    const uint32_t capacity = static_cast<uint32_t>(plan_cap);
+    FS_CUDA(fs::launch_bin_fused(0, n_pos, n, vd, sorted_val, P.foot, sat, c->lk_a.as<uint32_t>(),
+                                 val_dst->as<uint32_t>(), capacity, c->lb_tmp.p, total, ctr,
+                                 stream, range_dev),
+            "binning");
+    FS_CUDA(fs::launch_graph_check(total, capacity, nullptr, 0, range_dev, n_pos, ctr, stream),
+            "plan check");
+    *I_out = plan_cap;
+    if (plan_cap == 0) return FS_OK;
+    bool alt2 = false;
+    FS_CUDA(fs::radix_sort_pairs(c->lk_a.as<uint32_t>(), val_dst->as<uint32_t>(),
+                                 c->lk_b.as<uint32_t>(), c->lv_b.as<uint32_t>(), plan_cap,
+                                 tile_bits, c->sort_tmp.p, &alt2, stream, 0u, 0xFFFFFFFFu, total),
+            "tile sort");
+    const uint32_t* lkey = alt2 ? c->lk_b.as<uint32_t>() : c->lk_a.as<uint32_t>();
+    if (alt2)
+      FS_CUDA(fs::launch_copy_count(c->lv_b.as<uint32_t>(), val_dst->as<uint32_t>(), total,
+                                    plan_cap, stream),
+              "list copy");
+    FS_CUDA(fs::launch_ranges(plan_cap, lkey, ranges_dst, stream, total), "ranges");
+    return FS_OK;
+  }
   // count, offsets and emission in one launch into the buffers' current
   // capacity; a chunk with more entries than fit runs again after growing
   int64_t I = 0;
@@ -676,10 +712,26 @@ fs_status ensure_prologue_events(fs_ctx* c) {
   return FS_OK;
 }
 
+// The shapes of one solve, fixed for its captured replays (fs_graph_*): per
+// view batch the depth-sort bits, per (batch, depth chunk) the sorted
+// positions the chunk spans and its list entries, and the batches' views in
+// pinned host memory (a replayed copy reads its source at replay time).
+struct GraphPlan {
+  std::vector<int> key_bits;      // [batch]
+  std::vector<int64_t> npos;      // [batch * chunks + ci]
+  std::vector<int64_t> entries;   // [batch * chunks + ci]
+  int chunks = 0;
+  HostBuf views;                  // [batch][kMaxViewsPerBatch]
+};
+
+// record != NULL: the solve's shapes are written to *record (a plan).
+// plan != NULL: the solve is being captured: no host readback, no side
+// stream, sizes from the plan and from device memory.
 fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t V,
                           const void* const* masks, int32_t mask_dtype, int32_t mask_memory,
                           int32_t E, void* table, int32_t table_dtype, bool keep,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, GraphPlan* record = nullptr,
+                          const GraphPlan* plan = nullptr) {
   const int64_t n = s->n;
   c->kl_valid = false;
   if (n == 0 || V == 0) return FS_OK;
@@ -699,7 +751,18 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
   // alternate between two sets of depth-sort buffers, view arrays and
   // key-range slots (by parity).  Without the memory for the second set the
   // batches run one after another.
-  bool overlap = keep && batches > 1;
+  bool overlap = keep && batches > 1 && !plan && !record;
+  if (record) {
+    record->key_bits.assign(batches, 0);
+    record->npos.assign(static_cast<size_t>(batches) * chunks, 0);
+    record->entries.assign(static_cast<size_t>(batches) * chunks, 0);
+    record->chunks = chunks;
+  }
+  if (plan && (static_cast<int>(plan->key_bits.size()) != batches || plan->chunks != chunks))
+    return fail(FS_INVALID_ARGUMENT, "captured solve: the plan does not match the inputs");
+  // sized by the recording solve: nothing is allocated while capturing
+  if (plan || record)
+    FS_TRY(c->chunk_bnd.ensure(static_cast<size_t>(fs::kMaxChunks + 1) * 8, "chunk bounds"));
   if (overlap) {
     const size_t kb = static_cast<size_t>(kcap) * 4;
     overlap = ensure_side_stream(c) == FS_OK && c->key_a2.ensure(kb, "keys") == FS_OK &&
@@ -725,7 +788,9 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     const int q = parity(bb);
     const int32_t w0 = bb * vb;
     const int nbb = std::min(vb, V - w0);
-    fs::ViewParams* vhq = c->views_host.as<fs::ViewParams>() + q * fs::kMaxViewsPerBatch;
+    fs::ViewParams* vhq =
+        plan ? plan->views.as<fs::ViewParams>() + static_cast<int64_t>(bb) * fs::kMaxViewsPerBatch
+             : c->views_host.as<fs::ViewParams>() + q * fs::kMaxViewsPerBatch;
     Prologue& pr = pro[q];
     const ProjPtrs PP = proj_ptrs(c, keep, w0, n);
     pr.L = layout_batch(c, vhq, cams, w0, nbb, PP.cols);
@@ -743,7 +808,7 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     // project every Gaussian into the batch's views; the depth sort then
     // takes only the bits in which the batch's visible depth keys differ
     FS_CUDA(cudaMemsetAsync(krq, 0xFF, 4, strm), "key range");
-    FS_CUDA(cudaMemsetAsync(krq + 1, 0, 4, strm), "key range");
+    FS_CUDA(cudaMemsetAsync(krq + 1, 0, 8, strm), "key range");
     c->stats.kernel_launches += 2;
     FS_CUDA(fs::launch_project(n, nbb, pr.vd, s->pos_op.as<float4>(), s->cov.as<float4>(),
                                PP.rec, PP.rec16, PP.foot, PP.cnt, pr.key, pr.val, PP.dlo, krq,
@@ -753,7 +818,8 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
       FS_CUDA(cudaMemcpyAsync(PP.dkey, pr.key, static_cast<size_t>(nbb) * n * 4,
                               cudaMemcpyDeviceToDevice, strm),
               "depth key copy");
-    FS_CUDA(cudaMemcpyAsync(krhq, krq, 8, cudaMemcpyDeviceToHost, strm), "key range readback");
+    if (plan) return FS_OK;  // captured: the key range stays on the device
+    FS_CUDA(cudaMemcpyAsync(krhq, krq, 12, cudaMemcpyDeviceToHost, strm), "key range readback");
     FS_CUDA(cudaEventRecord(c->prologue_done[q], strm), "prologue event");
     return FS_OK;
   };
@@ -785,20 +851,31 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
               "saturation chunks");
     }
     // the batch's projection (and its key range on the host) is complete
-    FS_CUDA(cudaEventSynchronize(c->prologue_done[q]), "key range readback");
+    if (!plan) FS_CUDA(cudaEventSynchronize(c->prologue_done[q]), "key range readback");
     if (overlap) FS_CUDA(cudaStreamWaitEvent(stream, c->prologue_done[q], 0), "prologue wait");
     const uint32_t* krh = pr.krh;
     uint32_t kmin = 0, span = 0;
     int key_bits = 0;
-    if (krh[0] <= krh[1]) {
+    int64_t k_vis = 0;  // visible slots: the first k_vis sorted positions
+    const uint32_t* krd = c->key_range.as<uint32_t>() + 4 * q;  // the same on the device
+    if (plan) {
+      key_bits = plan->key_bits[b];
+      FS_CUDA(fs::launch_graph_check(nullptr, 0u, krd, key_bits, nullptr, 0, ctr, stream),
+              "plan check");
+      FS_CUDA(fs::launch_chunk_bounds(krd, chunks, c->chunk_bnd.as<int64_t>(), stream),
+              "chunk bounds");
+    } else if (krh[0] <= krh[1]) {
       kmin = krh[0];
       span = krh[1] - krh[0] + 1;  // invisible slots map to span, after every visible one
       key_bits = std::max(1, ceil_log2(static_cast<int64_t>(span) + 1));
+      k_vis = krh[2];
     }
+    if (record) record->key_bits[b] = key_bits;
     c->stats.kernel_launches += radix_launches(k_total, key_bits);
     bool alt = false;
     FS_CUDA(fs::radix_sort_pairs(pr.key, pr.val, pr.key_alt, pr.val_alt, k_total, key_bits,
-                                 c->sort_tmp.p, &alt, stream, kmin, span),
+                                 c->sort_tmp.p, &alt, stream, kmin, span, nullptr,
+                                 plan ? krd : nullptr),
             "depth sort");
     uint32_t* sorted_key = alt ? pr.key_alt : pr.key;
     uint32_t* sorted_val = alt ? pr.val_alt : pr.val;
@@ -822,9 +899,13 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     if (keep) {  // the last slot of every chunk but the last (0xFFFFFFFF: empty chunk)
       uint32_t* bound = c->kl_bound.as<uint32_t>() + static_cast<int64_t>(b) * chunks;
       FS_CUDA(cudaMemsetAsync(bound, 0xFF, static_cast<size_t>(chunks) * 4, stream), "bounds");
-      for (int ci = 0; ci + 1 < chunks; ++ci) {
-        const int64_t pb = ci == 0 ? 0 : chunk_end(k_total, chunks, ci - 1);
-        const int64_t p1 = chunk_end(k_total, chunks, ci);
+      if (plan)
+        FS_CUDA(fs::launch_chunk_last(c->chunk_bnd.as<int64_t>(), chunks, sorted_val, bound,
+                                      stream),
+                "bounds");
+      for (int ci = 0; ci + 1 < chunks && !plan; ++ci) {
+        const int64_t pb = ci == 0 ? 0 : chunk_end(k_vis, chunks, ci - 1);
+        const int64_t p1 = chunk_end(k_vis, chunks, ci);
         if (p1 > pb)
           FS_CUDA(cudaMemcpyAsync(bound + ci, sorted_val + (p1 - 1), 4, cudaMemcpyDeviceToDevice,
                                   stream),
@@ -832,11 +913,14 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
       }
     }
 
-    // front-to-back depth chunks: a chunk lists only tiles not yet saturated
+    // front-to-back depth chunks over the visible slots: a chunk lists only
+    // tiles not yet saturated
     int64_t p0 = 0;
     for (int ci = 0; ci < chunks; ++ci) {
-      const int64_t p1 = chunk_end(k_total, chunks, ci);
-      const int64_t n_pos = p1 - p0;
+      const size_t pi = static_cast<size_t>(b) * chunks + ci;
+      const int64_t p1 = plan ? 0 : chunk_end(k_vis, chunks, ci);
+      const int64_t n_pos = plan ? plan->npos[pi] : p1 - p0;
+      if (record) record->npos[pi] = n_pos;
       DevBuf* val_dst = keep ? &c->kl_val[static_cast<size_t>(b) * chunks + ci] : &c->lv_a;
       uint2* ranges_dst =
           keep ? c->kl_ranges.as<uint2>() + (c->kl_tile_off[b] * chunks +
@@ -846,15 +930,22 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
         if (keep)
           FS_CUDA(cudaMemsetAsync(ranges_dst, 0, static_cast<size_t>(total_tiles) * 8, stream),
                   "ranges clear");
+        if (plan)  // the plan's chunk is empty: so must the replay's be
+          FS_CUDA(fs::launch_graph_check(nullptr, 0u, nullptr, 0, c->chunk_bnd.as<int64_t>() + ci,
+                                         0, ctr, stream),
+                  "plan check");
         continue;
       }
       int64_t I = 0;
       FS_TRY(bin_positions(c, p0, n_pos, n, vd, sorted_val, P, sat, total_tiles, tile_bits, kcap,
-                           true, val_dst, ranges_dst, stream, &I));
+                           !plan, val_dst, ranges_dst, stream, &I,
+                           plan ? c->chunk_bnd.as<int64_t>() + ci : nullptr,
+                           plan ? plan->entries[pi] : 0));
+      if (record) record->entries[pi] = I;
       p0 = p1;
       if (I == 0) continue;
       cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-      if (c->time_stages) {
+      if (c->time_stages && !plan) {
         while (c->events.size() < c->events_used + 2) {
           cudaEvent_t e;
           FS_CUDA(cudaEventCreate(&e), "cudaEventCreate");
@@ -1067,6 +1158,123 @@ fs_status check_accumulate_args(fs_ctx* c, const fs_scene* s, const fs_camera* c
   return FS_OK;
 }
 
+// Novel-view masks (fs_render.cu): per view batch, one projection and depth
+// sort; per object e = 1 .. E-1, the sorted slots of its visible members,
+// binned in one list, composited and folded into the masks.
+fs_status render_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t V,
+                      const uint64_t* member_bits, int32_t E, float tau,
+                      void* const* masks_out, int32_t out_dtype, float* const* rho_out,
+                      float* const* depth_out, cudaStream_t stream) {
+  const int64_t n = s->n;
+  if (V == 0) return FS_OK;
+  const size_t osize = dtype_size(out_dtype);
+  if (n == 0) {  // nothing to render: every mask is 0, every rho and depth 0
+    for (int32_t v = 0; v < V; ++v) {
+      const size_t npix = static_cast<size_t>(cams[v].width) * cams[v].height;
+      FS_CUDA(cudaMemsetAsync(masks_out[v], 0, npix * osize, stream), "mask clear");
+      if (rho_out && rho_out[v])
+        FS_CUDA(cudaMemsetAsync(rho_out[v], 0, npix * (E - 1) * 4, stream), "rho clear");
+      if (depth_out && depth_out[v])
+        FS_CUDA(cudaMemsetAsync(depth_out[v], 0, npix * (E - 1) * 4, stream), "depth clear");
+    }
+    return FS_OK;
+  }
+  const int vb = batch_views(c, n);
+  if (vb < 1) return fail(FS_UNSUPPORTED, "fs_render_masks: scene too large");
+  const int64_t kcap = static_cast<int64_t>(vb) * n;
+  FS_TRY(ensure_window(c, n, vb, V, false));
+  FS_TRY(c->key_range.ensure(32, "depth key range"));
+  FS_TRY(c->rd_flag.ensure(static_cast<size_t>(kcap) * 4, "render flags"));
+  FS_TRY(c->rd_offs.ensure(static_cast<size_t>(kcap) * 4, "render offsets"));
+  FS_TRY(c->rd_val.ensure(static_cast<size_t>(kcap) * 4, "render slots"));
+  FS_TRY(c->scan_tmp.ensure(fs::scan_temp_bytes(kcap), "scan temp"));
+  const size_t ro_bytes = sizeof(fs::RenderOut) * fs::kMaxViewsPerBatch;
+  FS_TRY(c->render_out.ensure(ro_bytes, "render outputs"));
+  FS_TRY(c->render_out_host.ensure(ro_bytes));
+  c->mask_dev.assign(V, nullptr);  // the batch views carry no input mask
+  fs::ViewParams* vh = c->views_host.as<fs::ViewParams>();
+  fs::ViewParams* vd = c->views.as<fs::ViewParams>();
+  fs::RenderOut* roh = c->render_out_host.as<fs::RenderOut>();
+  fs::RenderOut* rod = c->render_out.as<fs::RenderOut>();
+  uint32_t* krq = c->key_range.as<uint32_t>();
+  uint32_t* krh = c->total_host.as<uint32_t>() + 4;
+  for (int32_t v0 = 0; v0 < V; v0 += vb) {
+    const int nb = std::min(vb, V - v0);
+    const ProjPtrs P = proj_ptrs(c, false, v0, n);
+    const BatchLayout L = layout_batch(c, vh, cams, v0, nb, P.cols);
+    const int total_tiles = L.total_tiles, max_tiles = L.max_tiles;
+    const int tile_bits = std::max(1, ceil_log2(total_tiles));
+    const int64_t k_total = static_cast<int64_t>(nb) * n;
+    for (int k = 0; k < nb; ++k)
+      roh[k] = {masks_out[v0 + k], rho_out ? rho_out[v0 + k] : nullptr,
+                depth_out ? depth_out[v0 + k] : nullptr};
+    FS_CUDA(cudaMemcpyAsync(vd, vh, sizeof(fs::ViewParams) * nb, cudaMemcpyHostToDevice, stream),
+            "view upload");
+    FS_CUDA(cudaMemcpyAsync(rod, roh, sizeof(fs::RenderOut) * nb, cudaMemcpyHostToDevice,
+                            stream),
+            "render output upload");
+    // every Gaussian projected into the batch's views and depth-sorted once
+    FS_CUDA(cudaMemsetAsync(krq, 0xFF, 4, stream), "key range");
+    FS_CUDA(cudaMemsetAsync(krq + 1, 0, 8, stream), "key range");
+    FS_CUDA(fs::launch_project(n, nb, vd, s->pos_op.as<float4>(), s->cov.as<float4>(), P.rec,
+                               P.rec16, P.foot, P.cnt, c->key_a.as<uint32_t>(),
+                               c->val_a.as<uint32_t>(), P.dlo, krq, stream),
+            "project");
+    FS_CUDA(cudaMemcpyAsync(krh, krq, 12, cudaMemcpyDeviceToHost, stream), "key range readback");
+    FS_CUDA(cudaStreamSynchronize(stream), "key range readback");
+    uint32_t kmin = 0, span = 0;
+    int key_bits = 0;
+    int64_t k_vis = 0;  // the visible slots come first after the sort
+    if (krh[0] <= krh[1]) {
+      kmin = krh[0];
+      span = krh[1] - krh[0] + 1;
+      key_bits = std::max(1, ceil_log2(static_cast<int64_t>(span) + 1));
+      k_vis = krh[2];
+    }
+    bool alt = false;
+    FS_CUDA(fs::radix_sort_pairs(c->key_a.as<uint32_t>(), c->val_a.as<uint32_t>(),
+                                 c->key_b.as<uint32_t>(), c->val_b.as<uint32_t>(), k_total,
+                                 key_bits, c->sort_tmp.p, &alt, stream, kmin, span),
+            "depth sort");
+    uint32_t* sorted_key = alt ? c->key_b.as<uint32_t>() : c->key_a.as<uint32_t>();
+    uint32_t* sorted_val = alt ? c->val_b.as<uint32_t>() : c->val_a.as<uint32_t>();
+    FS_CUDA(fs::launch_depth_tie_fix(k_total, n, sorted_key, sorted_val, P.dlo, stream),
+            "depth ties");
+    // no tile saturates: every list is complete
+    const size_t sat_bytes = static_cast<size_t>((total_tiles + 63) / 64) * 8;
+    FS_TRY(c->sat.ensure(sat_bytes, "tile flags"));
+    FS_TRY(c->ranges.ensure(static_cast<size_t>(total_tiles) * 8, "tile ranges"));
+    FS_TRY(c->state.ensure(static_cast<size_t>(L.pixels) * 4, "pixel state"));
+    FS_CUDA(cudaMemsetAsync(c->sat.p, 0, sat_bytes, stream), "tile flags clear");
+    for (int e = 1; e < E; ++e) {
+      uint32_t* flag = c->rd_flag.as<uint32_t>();
+      FS_CUDA(fs::launch_member_select(k_vis, n, sorted_val, P.cnt, member_bits, 1ull << e, flag,
+                                       stream),
+              "object slots");
+      FS_CUDA(fs::exclusive_scan(flag, nullptr, c->rd_offs.as<uint32_t>(), k_vis,
+                                 c->total.as<uint32_t>(), c->scan_tmp.p, stream),
+              "object scan");
+      FS_CUDA(fs::launch_member_scatter(k_vis, flag, c->rd_offs.as<uint32_t>(), sorted_val,
+                                        c->rd_val.as<uint32_t>(), stream),
+              "object scatter");
+      int64_t count = 0;
+      FS_TRY(read_total(c, stream, &count));
+      int64_t I = 0;
+      FS_TRY(bin_positions(c, 0, count, n, vd, c->rd_val.as<uint32_t>(), P,
+                           c->sat.as<uint64_t>(), total_tiles, tile_bits, kcap, false, &c->lv_a,
+                           c->ranges.as<uint2>(), stream, &I));
+      FS_CUDA(fs::launch_render(vd, rod, nb, max_tiles, c->ranges.as<uint2>(),
+                                c->lv_a.as<uint32_t>(), P.rec, P.rec16, e, e == 1, tau,
+                                c->state.as<float>(), out_dtype, stream),
+              "render");
+    }
+    // the host staging of this batch is read by the copies above before the
+    // next batch rewrites it
+    FS_CUDA(cudaStreamSynchronize(stream), "render");
+  }
+  return FS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1234,6 +1442,201 @@ fs_status fs_keep_after_removal(fs_ctx* c, const uint64_t* member_bits, int64_t 
   return FS_OK;
 }
 
+}  // extern "C"
+
+// A solve captured into a CUDA graph (fs_graph_* in flashsplat.h).
+struct fs_graph {
+  fs_ctx* c = nullptr;  // the graph's own context: the capture holds its buffers
+  const fs_scene* s = nullptr;
+  std::vector<fs_camera> cams;
+  std::vector<const void*> masks;
+  int32_t mask_dtype = 0, E = 0;
+  float gamma = 0.f;
+  fs_result out{};
+  void* table = nullptr;  // the FP64 table the graph accumulates into
+  uint64_t* bits = nullptr;
+  int32_t* label = nullptr;
+  float* margin = nullptr;
+  bool keep = false, recheck = false;
+  GraphPlan plan;
+  cudaStream_t stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void graph_free(fs_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->stream) cudaStreamDestroy(g->stream);
+  g->plan.views.release();
+  if (g->c) fs_destroy(g->c);
+  delete g;
+}
+
+// The captured part of a solve: counters and table cleared, every view
+// accumulated into the FP64 table with device-side sizes, the assignment.
+fs_status graph_body(fs_graph* g, cudaStream_t st) {
+  fs_ctx* c = g->c;
+  const int64_t n = g->s->n;
+  FS_CUDA(cudaMemsetAsync(c->counters.p, 0, c->counters.bytes, st), "counters clear");
+  FS_CUDA(cudaMemsetAsync(g->table, 0, static_cast<size_t>(n) * g->E * 8, st), "table clear");
+  FS_TRY(accumulate_impl(c, g->s, g->cams.data(), static_cast<int32_t>(g->cams.size()),
+                         g->masks.data(), g->mask_dtype, FS_MEM_DEVICE, g->E, g->table, FS_F64,
+                         g->keep, st, nullptr, &g->plan));
+  if (g->bits || g->label || g->margin)
+    FS_CUDA(fs::launch_assign(g->table, FS_F64, n, g->E, g->gamma, g->bits, g->label, g->margin,
+                              st),
+            "assign");
+  return FS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fs_status fs_graph_create(fs_ctx* tmpl, const fs_scene* s, const fs_camera* cams, int32_t V,
+                          const void* const* masks, int32_t mask_dtype, int32_t E, float gamma,
+                          const fs_result* out, fs_graph** graph) {
+  if (!graph) return fail(FS_INVALID_ARGUMENT, "fs_graph_create: graph is NULL");
+  *graph = nullptr;
+  FS_TRY(check_accumulate_args(tmpl, s, cams, V, masks, mask_dtype, FS_MEM_DEVICE, E));
+  if (!out || out->memory != FS_MEM_DEVICE)
+    return fail(FS_INVALID_ARGUMENT, "fs_graph_create: outputs must be in device memory");
+  if (out->table_dtype != FS_F32 && out->table_dtype != FS_F64)
+    return fail(FS_INVALID_ARGUMENT, "table dtype must be FS_F32 or FS_F64");
+  if (!(gamma >= -1.f && gamma <= 1.f))
+    return fail(FS_INVALID_ARGUMENT, "gamma = %g outside [-1, 1]", (double)gamma);
+  if (out->member_bits && E > 64) return fail(FS_UNSUPPORTED, "member_bits needs E <= 64");
+  if (s->n == 0 || V == 0) return fail(FS_INVALID_ARGUMENT, "fs_graph_create: nothing to solve");
+  fs_options o{};
+  o.views_per_batch = tmpl->views_per_batch;
+  o.depth_chunks = tmpl->depth_chunks;
+  o.recheck_margin = tmpl->recheck_margin > 0.f ? tmpl->recheck_margin : -1.f;
+  o.recheck_reproject = tmpl->recheck_reproject ? 1 : 0;
+  o.record_precision = tmpl->compact ? FS_F16 : 0;
+  o.coverage = tmpl->sigma3 ? FS_COVERAGE_3SIGMA : FS_COVERAGE_EXACT;
+  fs_graph* g = new (std::nothrow) fs_graph();
+  if (!g) return fail(FS_OUT_OF_MEMORY, "fs_graph_create: host allocation failed");
+  fs_status st = fs_create(&g->c, tmpl->device, &o);
+  if (st != FS_OK) {
+    graph_free(g);
+    return st;
+  }
+  fs_ctx* c = g->c;
+  DeviceGuard dg(c->device);
+  g->s = s;
+  g->cams.assign(cams, cams + V);
+  g->masks.assign(masks, masks + V);
+  g->mask_dtype = mask_dtype;
+  g->E = E;
+  g->gamma = gamma;
+  g->out = *out;
+  const int64_t n = s->n;
+  const size_t nn = static_cast<size_t>(n);
+  auto bail = [&](fs_status e) {
+    graph_free(g);
+    return e;
+  };
+  g->table = (out->table && out->table_dtype == FS_F64) ? out->table : nullptr;
+  if (!g->table) {
+    if ((st = c->table_tmp.ensure(nn * E * 8, "table")) != FS_OK) return bail(st);
+    g->table = c->table_tmp.p;
+  }
+  g->bits = out->member_bits;
+  g->label = out->label;
+  g->margin = out->margin;
+  g->recheck = c->recheck_margin > 0.f;
+  if (g->recheck && !g->margin) {
+    if ((st = c->margin_tmp.ensure(nn * 4, "margins")) != FS_OK) return bail(st);
+    g->margin = c->margin_tmp.as<float>();
+  }
+  if (g->recheck && !c->recheck_reproject) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+      g->keep = (c->compact ? 76.0 : 108.0) * static_cast<double>(n) * V <=
+                0.5 * static_cast<double>(free_b);
+  }
+  cudaError_t ce = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
+  // 1. a solve that records the shapes and sizes every buffer
+  c->stats = fs_stats{};
+  ce = cudaMemsetAsync(c->counters.p, 0, c->counters.bytes, g->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(g->table, 0, nn * E * 8, g->stream);
+  if (ce != cudaSuccess) return bail(cuda_fail(ce, "fs_graph_create"));
+  if ((st = accumulate_impl(c, s, cams, V, masks, mask_dtype, FS_MEM_DEVICE, E, g->table, FS_F64,
+                            g->keep, g->stream, &g->plan, nullptr)) != FS_OK)
+    return bail(st);
+  if ((ce = cudaStreamSynchronize(g->stream)) != cudaSuccess)
+    return bail(cuda_fail(ce, "fs_graph_create"));
+  const int vb = batch_views(c, n);
+  const size_t batches = static_cast<size_t>((V + vb - 1) / vb);
+  if ((st = g->plan.views.ensure(batches * fs::kMaxViewsPerBatch * sizeof(fs::ViewParams))) !=
+      FS_OK)
+    return bail(st);
+  // 2. the capture: the same solve with device-side sizes
+  if ((ce = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return bail(cuda_fail(ce, "cudaStreamBeginCapture"));
+  st = graph_body(g, g->stream);
+  ce = cudaStreamEndCapture(g->stream, &g->graph);
+  if (st != FS_OK) return bail(st);
+  if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamEndCapture"));
+  if ((ce = cudaGraphInstantiate(&g->exec, g->graph, 0)) != cudaSuccess)
+    return bail(cuda_fail(ce, "cudaGraphInstantiate"));
+  *graph = g;
+  return FS_OK;
+}
+
+fs_status fs_graph_launch(fs_graph* g, void* stream) {
+  if (!g) return fail(FS_INVALID_ARGUMENT, "fs_graph_launch: graph is NULL");
+  fs_ctx* c = g->c;
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  c->stats = fs_stats{};
+  c->events_used = 0;
+  FS_CUDA(cudaGraphLaunch(g->exec, st), "cudaGraphLaunch");
+  const int32_t V = static_cast<int32_t>(g->cams.size());
+  c->kl_valid = g->keep;
+  if (g->recheck)
+    FS_TRY(recheck_impl(c, g->s, g->cams.data(), V, g->mask_dtype, g->E, g->gamma, g->table,
+                        FS_F64, g->bits, g->label, g->margin, g->keep, st));
+  const int64_t count = g->s->n * static_cast<int64_t>(g->E);
+  if (g->out.table && g->out.table_dtype == FS_F32)
+    FS_CUDA(fs::launch_round_table(count, static_cast<const double*>(g->table),
+                                   static_cast<float*>(g->out.table), st),
+            "table rounding");
+  return FS_OK;
+}
+
+fs_status fs_graph_synchronize(fs_graph* g, void* stream, fs_stats* stats) {
+  if (!g) return fail(FS_INVALID_ARGUMENT, "fs_graph_synchronize: graph is NULL");
+  return fs_synchronize(g->c, stream, stats);
+}
+
+fs_status fs_graph_destroy(fs_graph* g) {
+  if (!g) return FS_OK;
+  DeviceGuard dg(g->c ? g->c->device : 0);
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  graph_free(g);
+  return FS_OK;
+}
+
+fs_status fs_render_masks(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t V,
+                          const uint64_t* member_bits, int32_t E, float tau,
+                          void* const* masks_out, int32_t out_dtype, float* const* rho_out,
+                          float* const* depth_out, void* stream) {
+  FS_TRY(check_accumulate_args(c, s, cams, V, masks_out, out_dtype, FS_MEM_DEVICE, E));
+  if (E < 2 || E > 64) return fail(FS_INVALID_ARGUMENT, "fs_render_masks: E = %d out of [2, 64]", E);
+  if (!(tau == tau)) return fail(FS_INVALID_ARGUMENT, "fs_render_masks: tau is NaN");
+  if (s->n > 0 && V > 0 && !member_bits)
+    return fail(FS_INVALID_ARGUMENT, "fs_render_masks: member_bits is NULL");
+  DeviceGuard g(c->device);
+  return render_impl(c, s, cams, V, member_bits, E, tau, masks_out, out_dtype, rho_out,
+                     depth_out, static_cast<cudaStream_t>(stream));
+}
+
 fs_status fs_check_wait_timeout(int32_t device, int32_t spins) {
   int count = 0;
   cudaError_t e = cudaGetDeviceCount(&count);
@@ -1292,6 +1695,10 @@ fs_status fs_synchronize(fs_ctx* c, void* stream, fs_stats* stats) {
   if (ch[fs::kBinningMismatch])
     return fail(FS_CUDA_ERROR, "internal error: tile binning count and emission disagreed for "
                 "%llu Gaussian(s)", ch[fs::kBinningMismatch]);
+  if (ch[fs::kGraphOverflow] || ch[fs::kGraphKeyRange])
+    return fail(FS_UNSUPPORTED, "captured solve: the inputs outgrew the capture's plan (%llu "
+                "list(s) over capacity, %llu depth sort(s) short of bits); capture again",
+                ch[fs::kGraphOverflow], ch[fs::kGraphKeyRange]);
   double ms = 0.0;
   for (size_t k = 0; k + 1 < c->events_used; k += 2) {
     float t = 0.f;

@@ -59,9 +59,10 @@ struct ViewParams {
 //   w_hi, w_lo = whitening matrix W (row-major 2x2) as float pairs, with
 //                |W d|^2 = 0.5 log2(e) d^T Sigma2D^-1 d
 //   m          = (mx_hi, my_hi, mx_lo, my_lo): the projected mean as float pairs
-//   misc       = (opacity, q_cut, -log2 o, -), q_cut ~ log2(255 o): alpha =
+//   misc       = (opacity, q_cut, -log2 o, depth), q_cut ~ log2(255 o): alpha =
 //                o 2^-|w|^2 reaches 1/255 at |w|^2 = log2(255 o) (stored
-//                slightly widened)
+//                slightly widened); depth = view-space depth of the mean
+//                (FP32), read by the mask renderer
 // For a sub-tile whose centre is o the blend forms b = W (o - m) in FP32 (o - m
 // is exact or nearly so) and evaluates w = W_hi (p - o) + b for the pixel
 // centre p, |p - o| <= 5 px.
@@ -84,7 +85,7 @@ struct alignas(16) CompactRecord {
   uint32_t w01, w23;  // (W00, W01), (W10, W11) as FP16 pairs, low half first
   float o, q_cut;
   float nlo;          // -log2 o
-  float pad1;
+  float depth;        // view-space depth of the mean (FP32)
 };
 
 // Footprint of one (view, Gaussian) for the tile binning: the alpha >= 1/255
@@ -295,6 +296,14 @@ __device__ __forceinline__ uint32_t depth_key(float z) { return __float_as_uint(
 __device__ __forceinline__ uint32_t float_order_key(float x) {
   const uint32_t u = __float_as_uint(x);
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// 2^x by the hardware approximation (relative error ~2^-22, flushes
+// subnormal results to zero): alpha = o 2^-|w|^2 in the compositing kernels.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 }  // namespace fs

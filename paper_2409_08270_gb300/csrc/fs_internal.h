@@ -31,11 +31,14 @@ size_t radix_temp_bytes(int64_t n);
 // Stable LSD radix sort of (key, val) pairs on the low `bits` bits of
 // min(key - kmin, span) (the keys themselves are moved unchanged).
 // Ping-pongs between (keys, vals) and (keys_alt, vals_alt); *in_alt tells the
-// caller which pair holds the result.
+// caller which pair holds the result.  n_dev (may be NULL): the count to sort
+// is min(n, *n_dev), read on the device (the grid is sized for n); range_dev
+// (may be NULL): kmin and span from a device key range {min, max}.
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                              uint32_t* vals_alt, int64_t n, int bits, void* temp, bool* in_alt,
                              cudaStream_t stream, uint32_t kmin = 0u,
-                             uint32_t span = 0xFFFFFFFFu);
+                             uint32_t span = 0xFFFFFFFFu, const uint32_t* n_dev = nullptr,
+                             const uint32_t* range_dev = nullptr);
 
 // projection / binning (fs_project.cu) --------------------------------------
 // pos_op[n] = (m, o); cov[3n] = Sigma3D as float pairs (FP64 once per scene)
@@ -44,9 +47,12 @@ cudaError_t launch_scene_prep(int64_t n, const float* mean, const void* quat, in
                               int opacity_dtype, float4* pos_op, float4* cov, unsigned int* err,
                               cudaStream_t stream);
 // rec16 != NULL: reduced-precision records (FP16 whitening matrix, FP32 mean)
-// are written to rec16 instead of the float-pair records to rec.
-// key_range (2 uint32, may be NULL): atomic min / max of the visible slots'
-// depth keys (the caller initialises it to {0xFFFFFFFF, 0}).
+// are written to rec16 instead of the float-pair records to rec.  Records are
+// written for visible slots only (nothing reads the others'); footprints,
+// counts, keys, values and low depth words for every slot.
+// key_range (3 uint32, may be NULL): atomic min / max of the visible slots'
+// depth keys and their number (the caller initialises it to {0xFFFFFFFF, 0,
+// 0}).  After the depth sort the visible slots are the first ones.
 cudaError_t launch_project(int64_t n, int n_views, const ViewParams* views, const float4* pos_op,
                            const float4* cov, ProjRecord* rec, CompactRecord* rec16,
                            Footprint* foot, uint32_t* cnt, uint32_t* key, uint32_t* val,
@@ -74,7 +80,8 @@ cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewPar
                              const uint32_t* sorted_val, const Footprint* foot,
                              const uint64_t* sat, uint32_t* out_key, uint32_t* out_val,
                              uint32_t capacity, void* lookback, uint32_t* total,
-                             unsigned long long* counters, cudaStream_t stream);
+                             unsigned long long* counters, cudaStream_t stream,
+                             const int64_t* range_dev = nullptr);
 size_t bin_fused_temp_bytes(int64_t n_pos);
 // Polls of a predecessor's look-back word before the wait gives up (about 2 s).
 constexpr int kLookbackSpinLimit = 1 << 26;
@@ -86,7 +93,27 @@ cudaError_t launch_lookback_probe(void* lookback, uint32_t* total, unsigned long
                                   const Footprint* foot, const uint64_t* sat, uint32_t* out_key,
                                   uint32_t* out_val, int spin_limit, cudaStream_t stream);
 cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
-                          cudaStream_t stream);
+                          cudaStream_t stream, const uint32_t* n_dev = nullptr);
+
+// Captured solves (fs_graph.cu) ----------------------------------------------
+// Device-side sizes for a solve captured into a CUDA graph: no host readback.
+// bnd[0 .. chunks] = the depth-chunk boundaries over the batch's visible slots
+// (key_range[2], valid when key_range[0] <= key_range[1]).
+cudaError_t launch_chunk_bounds(const uint32_t* key_range, int chunks, int64_t* bnd,
+                                cudaStream_t stream);
+// bound[ci] = the last sorted slot of chunk ci < chunks - 1 (0xFFFFFFFF: empty)
+cudaError_t launch_chunk_last(const int64_t* bnd, int chunks, const uint32_t* sorted_val,
+                              uint32_t* bound, cudaStream_t stream);
+// dst[k] = src[k] for k < min(*n_dev, cap)
+cudaError_t launch_copy_count(const uint32_t* src, uint32_t* dst, const uint32_t* n_dev,
+                              int64_t cap, cudaStream_t stream);
+// counts kGraphOverflow when *total > capacity or the range rng[0 .. 1] holds
+// more than rng_cap positions, and kGraphKeyRange when the visible depth keys
+// need more than key_bits bits (each pointer may be NULL: no check)
+cudaError_t launch_graph_check(const uint32_t* total, uint32_t capacity,
+                               const uint32_t* key_range, int key_bits, const int64_t* rng,
+                               int64_t rng_cap, unsigned long long* counters,
+                               cudaStream_t stream);
 
 // blend / accumulate (fs_blend.cu) ------------------------------------------
 // mask_dtype: 4 = uint8, 5 = int32.  table_dtype: 0 = f32, 1 = f64.
@@ -179,6 +206,29 @@ cudaError_t launch_recheck_blend(const ViewParams* views, int n_views, int max_t
                                  const int32_t* map, double* R, unsigned long long* counters,
                                  cudaStream_t stream);
 
+// Novel-view mask rendering (fs_render.cu) ----------------------------------
+// Per-view outputs of the mask renderer: the mask (FS_U8 / FS_I32, H x W),
+// and optionally rho^e and D^e for objects e = 1 .. E-1 ((E-1) x H x W FP32).
+struct RenderOut {
+  void* mask;
+  float* rho;
+  float* depth;
+};
+// flag[k] = 1 iff sorted slot k is visible (cnt != 0) and member[slot % n] & bit
+cudaError_t launch_member_select(int64_t k_total, int64_t n, const uint32_t* sorted_val,
+                                 const uint32_t* cnt, const uint64_t* member, uint64_t bit,
+                                 uint32_t* flag, cudaStream_t stream);
+// out[offs[k]] = sorted_val[k] for flagged k (order kept)
+cudaError_t launch_member_scatter(int64_t k_total, const uint32_t* flag, const uint32_t* offs,
+                                  const uint32_t* sorted_val, uint32_t* out, cudaStream_t stream);
+// Object e's tile lists composited per pixel and folded into the masks:
+// rho^e > tau and D^e below best[] (per batch pixel, at state_off) takes label
+// e; first != 0 starts every pixel at label 0 and best = +inf.
+cudaError_t launch_render(const ViewParams* views, const RenderOut* outs, int n_views,
+                          int max_tiles_per_view, const uint2* ranges, const uint32_t* list_val,
+                          const ProjRecord* rec, const CompactRecord* rec16, int e, bool first,
+                          float tau, float* best, int out_dtype, cudaStream_t stream);
+
 // Context workspace management for the request server (fs_api.cu).
 size_t ctx_workspace_bytes(const fs_ctx* c);
 void ctx_release_workspace(fs_ctx* c);
@@ -206,7 +256,9 @@ enum Counter {
   kSteps = 9,            // census: staging steps of the blend (per block)
   kRoundsMixed = 10,     // census: rounds of warps with more than one label
   kRoundsSlots = 11,     // census: Gaussian slots of those rounds (sum of nq)
-  kNumCounters = 12
+  kGraphOverflow = 12,   // a captured solve's lists outgrew the capture's plan
+  kGraphKeyRange = 13,   // a captured solve's depth keys outgrew the plan's sort bits
+  kNumCounters = 14
 };
 
 }  // namespace fs

@@ -137,7 +137,8 @@ __device__ __forceinline__ uint16_t f2_to_half_rn(f2 x) {
 // the two rows of T Sigma3D, the x and y halves of the pinhole map, the rows
 // of W) run in packed FP32 (f2x2), bit-identical to the scalar form.  Three
 // blocks per SM (80 registers) spill less than four.
-__global__ void __launch_bounds__(256, 3) project_kernel(
+template <bool kFast>
+__global__ void __launch_bounds__(256, kFast ? 4 : 3) project_kernel(
     int64_t n, int n_views, const ViewParams* __restrict__ views_g,
     const float4* __restrict__ pos_op, const float4* __restrict__ cov3,
     ProjRecord* __restrict__ rec, CompactRecord* __restrict__ rec16, Footprint* __restrict__ foot,
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(256, 3) project_kernel(
   __syncthreads();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   uint32_t kmin = 0xFFFFFFFFu, kmax = 0u;  // visible depth keys of this thread
+  uint32_t n_vis = 0;                       // and their number
   if (i < n) {
   const float4 po = pos_op[i];
   const float4 ca = cov3[3 * i], cb = cov3[3 * i + 1], cc = cov3[3 * i + 2];
@@ -186,97 +188,174 @@ __global__ void __launch_bounds__(256, 3) project_kernel(
     F.rows = 0x0000FFFFu;  // no tile row (first row 65535 > last row 0)
     uint32_t col_clip = 0x0000FFFFu;  // 3-sigma coverage: no tile column
     if (visible) {
-      const f2 ux = f2_div(tx, tz), uy = f2_div(ty, tz);
-      const f2 fx = {vp.fx_hi, vp.fx_lo}, fy = {vp.fy_hi, vp.fy_lo};
-      // the x and y halves of the pinhole map run side by side (f2x2)
-      const f2x2 fxy = f2x2_pack(fx, fy);
-      const f2x2 mxy = f2x2_add(f2x2_mul(fxy, f2x2_pack(ux, uy)),
-                                f2x2_pack(f2{vp.cx_hi, vp.cx_lo}, f2{vp.cy_hi, vp.cy_lo}));
-      const f2 mx = f2x2_first(mxy), my = f2x2_second(mxy);
-      depth = tz.hi;
-      depth_l = tz.lo;
-      const f2 iz = f2_div(f2_from(1.f), tz);
-      const f2x2 J = f2x2_mul(fxy, f2x2_pack(iz, iz));  // (fx / z, fy / z)
-      const f2 uxc = f2_clamp(ux, vp.limx_hi, vp.limx_lo);
-      const f2 uyc = f2_clamp(uy, vp.limy_hi, vp.limy_lo);
-      const f2x2 U = f2x2_pack(uxc, uyc);
-      // rows of J W side by side: T[k] = (T0[k], T1[k]) with
-      // T0 = fx/z (W0 - ux W2), T1 = fy/z (W1 - uy W2)
-      f2x2 T[3];
+      float sxx, sxy, syy, det32, mx32, my32;  // 2D covariance and mean for the footprint
+      if constexpr (kFast) {
+        // reduced-precision form: the record keeps an FP16 W and an FP32
+        // mean, so the 2D covariance, its eigen-decomposition and W run in
+        // plain FP32 (correctly rounded divisions and roots); the depth stays
+        // a float pair for the order
+        depth = tz.hi;
+        depth_l = tz.lo;
+        R16.depth = depth;
+        const float iz = __fdiv_rn(1.f, tz.hi);
+        const float uxf = __fmul_rn(tx.hi, iz), uyf = __fmul_rn(ty.hi, iz);
+        mx32 = fmaf(vp.fx_hi, uxf, vp.cx_hi);
+        my32 = fmaf(vp.fy_hi, uyf, vp.cy_hi);
+        const float jx = vp.fx_hi * iz, jy = vp.fy_hi * iz;
+        const float ucx = fminf(fmaxf(uxf, -vp.limx_hi), vp.limx_hi);
+        const float ucy = fminf(fmaxf(uyf, -vp.limy_hi), vp.limy_hi);
+        float T0[3], T1[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const f2 w0 = {vp.R_hi[k], vp.R_lo[k]}, w1 = {vp.R_hi[3 + k], vp.R_lo[3 + k]};
-        const f2 w2 = {vp.R_hi[6 + k], vp.R_lo[6 + k]};
-        T[k] = f2x2_mul(J, f2x2_sub(f2x2_pack(w0, w1), f2x2_mul(U, f2x2_pack(w2, w2))));
-      }
-      // Sigma' = T Sigma3D T^T: M = (m0, m1) = rows of T Sigma3D, then
-      // (a, c) += (m0 T0[j], m1 T1[j]) side by side and b += m0 T1[j]
-      f2x2 ac = f2x2_pack(f2_from(0.f), f2_from(0.f));
-      f2 a, b = f2_from(0.f), c;
+        for (int k = 0; k < 3; ++k) {
+          T0[k] = jx * fmaf(-ucx, vp.R_hi[6 + k], vp.R_hi[k]);
+          T1[k] = jy * fmaf(-ucy, vp.R_hi[6 + k], vp.R_hi[3 + k]);
+        }
+        float a = 0.f, b = 0.f, c = 0.f;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        f2x2 M = f2x2_mul(T[0], f2x2_pack(S[0][j], S[0][j]));
-        M = f2x2_fma(T[1], f2x2_pack(S[1][j], S[1][j]), M);
-        M = f2x2_fma(T[2], f2x2_pack(S[2][j], S[2][j]), M);
-        ac = f2x2_fma(M, T[j], ac);
-        b = f2_fma(f2x2_first(M), f2x2_second(T[j]), b);
-      }
-      a = f2x2_first(ac);
-      c = f2x2_second(ac);
-      a = f2_add(a, f2_from(kLowPass));
-      c = f2_add(c, f2_from(kLowPass));
-      const f2 det = f2_sub(f2_mul(a, c), f2_mul(b, b));
-      const f2 h = f2_scale(f2_sub(a, c), 0.5f);
-      const f2 rr = f2_sqrt(f2_add(f2_mul(h, h), f2_mul(b, b)));
-      const f2 lam1 = f2_add(f2_scale(f2_add(a, c), 0.5f), rr);
-      const f2 lam2 = f2_div(det, lam1);
-      // unit eigenvector of lambda1 from whichever form has no cancellation
-      f2 ex, ey;
-      if (h.hi >= 0.f) {
-        ex = f2_add(h, rr);
-        ey = b;
+        for (int j = 0; j < 3; ++j) {
+          const float m0 = fmaf(T0[0], S[0][j].hi, fmaf(T0[1], S[1][j].hi, T0[2] * S[2][j].hi));
+          const float m1 = fmaf(T1[0], S[0][j].hi, fmaf(T1[1], S[1][j].hi, T1[2] * S[2][j].hi));
+          a = fmaf(m0, T0[j], a);
+          c = fmaf(m1, T1[j], c);
+          b = fmaf(m0, T1[j], b);
+        }
+        a += kLowPass;
+        c += kLowPass;
+        // a c - b^2 with the rounding error of b^2 put back (Kahan)
+        const float bb = b * b;
+        const float dt = fmaf(a, c, -bb) - fmaf(b, b, -bb);
+        const float h = 0.5f * (a - c);
+        const float rr = __fsqrt_rn(fmaf(h, h, bb));
+        const float lam1 = 0.5f * (a + c) + rr;
+        const float lam2 = __fdiv_rn(dt, lam1);
+        float ex, ey;
+        if (h >= 0.f) {
+          ex = h + rr;
+          ey = b;
+        } else {
+          ex = b;
+          ey = rr - h;
+        }
+        const float en = __fsqrt_rn(fmaf(ex, ex, ey * ey));
+        if (en > 0.f) {
+          ex = __fdiv_rn(ex, en);
+          ey = __fdiv_rn(ey, en);
+        } else {
+          ex = 1.f;
+          ey = 0.f;
+        }
+        const float k1 = __fsqrt_rn(__fdiv_rn(kHalfLog2eHi, lam1));
+        const float k2 = __fsqrt_rn(__fdiv_rn(kHalfLog2eHi, lam2));
+        R16.mx = mx32;
+        R16.my = my32;
+        R16.w01 = static_cast<uint32_t>(__half_as_ushort(__float2half_rn(ex * k1))) |
+                  (static_cast<uint32_t>(__half_as_ushort(__float2half_rn(ey * k1))) << 16);
+        R16.w23 = static_cast<uint32_t>(__half_as_ushort(__float2half_rn(-ey * k2))) |
+                  (static_cast<uint32_t>(__half_as_ushort(__float2half_rn(ex * k2))) << 16);
+        sxx = a;
+        sxy = b;
+        syy = c;
+        det32 = dt;
       } else {
-        ex = b;
-        ey = f2_sub(rr, h);
-      }
-      const f2 en = f2_sqrt(f2_add(f2_mul(ex, ex), f2_mul(ey, ey)));
-      if (en.hi > 0.f) {
-        ex = f2_div(ex, en);
-        ey = f2_div(ey, en);
-      } else {
-        ex = f2_from(1.f);
-        ey = f2_from(0.f);
-      }
-      // axis scales sqrt(0.5 log2 e / lambda) as float pairs too: the FP64
-      // near-tie re-check evaluates alpha from this record
-      const f2 hl = {kHalfLog2eHi, kHalfLog2eLo};
-      const f2 k1 = f2_sqrt(f2_div(hl, lam1));
-      const f2 k2 = f2_sqrt(f2_div(hl, lam2));
-      const f2x2 W0 = f2x2_mul(f2x2_pack(ex, ey), f2x2_pack(k1, k1));
-      const f2x2 W1 = f2x2_mul(f2x2_pack(f2_neg(ey), ex), f2x2_pack(k2, k2));
-      const f2 W00 = f2x2_first(W0), W01 = f2x2_second(W0);
-      const f2 W10 = f2x2_first(W1), W11 = f2x2_second(W1);
-      R.w_hi = make_float4(W00.hi, W01.hi, W10.hi, W11.hi);
-      R.w_lo = make_float4(W00.lo, W01.lo, W10.lo, W11.lo);
-      R.m = make_float4(mx.hi, my.hi, mx.lo, my.lo);
-      if (rec16) {
-        R16.mx = mx.hi;  // the float pair is normalised: hi is the FP32 rounding
-        R16.my = my.hi;
-        R16.w01 = static_cast<uint32_t>(f2_to_half_rn(W00)) |
-                  (static_cast<uint32_t>(f2_to_half_rn(W01)) << 16);
-        R16.w23 = static_cast<uint32_t>(f2_to_half_rn(W10)) |
-                  (static_cast<uint32_t>(f2_to_half_rn(W11)) << 16);
+        const f2 ux = f2_div(tx, tz), uy = f2_div(ty, tz);
+        const f2 fx = {vp.fx_hi, vp.fx_lo}, fy = {vp.fy_hi, vp.fy_lo};
+        // the x and y halves of the pinhole map run side by side (f2x2)
+        const f2x2 fxy = f2x2_pack(fx, fy);
+        const f2x2 mxy = f2x2_add(f2x2_mul(fxy, f2x2_pack(ux, uy)),
+                                  f2x2_pack(f2{vp.cx_hi, vp.cx_lo}, f2{vp.cy_hi, vp.cy_lo}));
+        const f2 mx = f2x2_first(mxy), my = f2x2_second(mxy);
+        depth = tz.hi;
+        depth_l = tz.lo;
+        R.misc.w = depth;
+        R16.depth = depth;
+        const f2 iz = f2_div(f2_from(1.f), tz);
+        const f2x2 J = f2x2_mul(fxy, f2x2_pack(iz, iz));  // (fx / z, fy / z)
+        const f2 uxc = f2_clamp(ux, vp.limx_hi, vp.limx_lo);
+        const f2 uyc = f2_clamp(uy, vp.limy_hi, vp.limy_lo);
+        const f2x2 U = f2x2_pack(uxc, uyc);
+        // rows of J W side by side: T[k] = (T0[k], T1[k]) with
+        // T0 = fx/z (W0 - ux W2), T1 = fy/z (W1 - uy W2)
+        f2x2 T[3];
+  #pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const f2 w0 = {vp.R_hi[k], vp.R_lo[k]}, w1 = {vp.R_hi[3 + k], vp.R_lo[3 + k]};
+          const f2 w2 = {vp.R_hi[6 + k], vp.R_lo[6 + k]};
+          T[k] = f2x2_mul(J, f2x2_sub(f2x2_pack(w0, w1), f2x2_mul(U, f2x2_pack(w2, w2))));
+        }
+        // Sigma' = T Sigma3D T^T: M = (m0, m1) = rows of T Sigma3D, then
+        // (a, c) += (m0 T0[j], m1 T1[j]) side by side and b += m0 T1[j]
+        f2x2 ac = f2x2_pack(f2_from(0.f), f2_from(0.f));
+        f2 a, b = f2_from(0.f), c;
+  #pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          f2x2 M = f2x2_mul(T[0], f2x2_pack(S[0][j], S[0][j]));
+          M = f2x2_fma(T[1], f2x2_pack(S[1][j], S[1][j]), M);
+          M = f2x2_fma(T[2], f2x2_pack(S[2][j], S[2][j]), M);
+          ac = f2x2_fma(M, T[j], ac);
+          b = f2_fma(f2x2_first(M), f2x2_second(T[j]), b);
+        }
+        a = f2x2_first(ac);
+        c = f2x2_second(ac);
+        a = f2_add(a, f2_from(kLowPass));
+        c = f2_add(c, f2_from(kLowPass));
+        const f2 det = f2_sub(f2_mul(a, c), f2_mul(b, b));
+        const f2 h = f2_scale(f2_sub(a, c), 0.5f);
+        const f2 rr = f2_sqrt(f2_add(f2_mul(h, h), f2_mul(b, b)));
+        const f2 lam1 = f2_add(f2_scale(f2_add(a, c), 0.5f), rr);
+        const f2 lam2 = f2_div(det, lam1);
+        // unit eigenvector of lambda1 from whichever form has no cancellation
+        f2 ex, ey;
+        if (h.hi >= 0.f) {
+          ex = f2_add(h, rr);
+          ey = b;
+        } else {
+          ex = b;
+          ey = f2_sub(rr, h);
+        }
+        const f2 en = f2_sqrt(f2_add(f2_mul(ex, ex), f2_mul(ey, ey)));
+        if (en.hi > 0.f) {
+          ex = f2_div(ex, en);
+          ey = f2_div(ey, en);
+        } else {
+          ex = f2_from(1.f);
+          ey = f2_from(0.f);
+        }
+        // axis scales sqrt(0.5 log2 e / lambda) as float pairs too: the FP64
+        // near-tie re-check evaluates alpha from this record
+        const f2 hl = {kHalfLog2eHi, kHalfLog2eLo};
+        const f2 k1 = f2_sqrt(f2_div(hl, lam1));
+        const f2 k2 = f2_sqrt(f2_div(hl, lam2));
+        const f2x2 W0 = f2x2_mul(f2x2_pack(ex, ey), f2x2_pack(k1, k1));
+        const f2x2 W1 = f2x2_mul(f2x2_pack(f2_neg(ey), ex), f2x2_pack(k2, k2));
+        const f2 W00 = f2x2_first(W0), W01 = f2x2_second(W0);
+        const f2 W10 = f2x2_first(W1), W11 = f2x2_second(W1);
+        R.w_hi = make_float4(W00.hi, W01.hi, W10.hi, W11.hi);
+        R.w_lo = make_float4(W00.lo, W01.lo, W10.lo, W11.lo);
+        R.m = make_float4(mx.hi, my.hi, mx.lo, my.lo);
+        if (rec16) {
+          R16.mx = mx.hi;  // the float pair is normalised: hi is the FP32 rounding
+          R16.my = my.hi;
+          R16.w01 = static_cast<uint32_t>(f2_to_half_rn(W00)) |
+                    (static_cast<uint32_t>(f2_to_half_rn(W01)) << 16);
+          R16.w23 = static_cast<uint32_t>(f2_to_half_rn(W10)) |
+                    (static_cast<uint32_t>(f2_to_half_rn(W11)) << 16);
+        }
+        sxx = a.hi;
+        sxy = b.hi;
+        syy = c.hi;
+        det32 = det.hi;
+        mx32 = mx.hi;
+        my32 = my.hi;
       }
       // binning footprint (FP32 is plenty: the binning keeps a pixel of margin)
       const float r2b = binning_r2(r2);
-      const float sxx = a.hi, sxy = b.hi, syy = c.hi;
-      F.mx = mx.hi;
-      F.my = my.hi;
+      F.mx = mx32;
+      F.my = my32;
       F.syr = syy * r2b;
       F.hy = sqrtf(F.syr);
       F.dys = sxy * sqrtf(r2b / sxx);
       F.a = sxy / syy;
-      F.b2 = det.hi / (syy * syy);
+      F.b2 = det32 / (syy * syy);
       const float hy = F.hy;
       const float py0 = ceilf(__fsub_rn(__fsub_rn(F.my, hy), 1.5f));
       const float py1 = floorf(__fadd_rn(__fadd_rn(F.my, hy), 0.5f));
@@ -323,16 +402,19 @@ __global__ void __launch_bounds__(256, 3) project_kernel(
       }
     }
     if (vp.cols) vp.cols[slot] = col_clip;
-    if (rec16)
-      rec16[slot] = R16;
-    else
-      rec[slot] = R;
+    if (visible) {  // records are read only through tile lists, which hold visible slots
+      if (rec16)
+        rec16[slot] = R16;
+      else
+        rec[slot] = R;
+    }
     foot[slot] = F;
     cnt[slot] = visible ? count : 0u;
     const uint32_t k = visible ? depth_key(depth) : 0xFFFFFFFFu;
     if (visible) {
       kmin = min(kmin, k);
       kmax = max(kmax, k);
+      ++n_vis;
     }
     key[slot] = k;
     val[slot] = static_cast<uint32_t>(slot);
@@ -342,9 +424,11 @@ __global__ void __launch_bounds__(256, 3) project_kernel(
   if (key_range) {
     kmin = __reduce_min_sync(0xffffffffu, kmin);
     kmax = __reduce_max_sync(0xffffffffu, kmax);
+    n_vis = __reduce_add_sync(0xffffffffu, n_vis);
     if ((threadIdx.x & 31) == 0 && kmin <= kmax) {
       atomicMin(&key_range[0], kmin);
       atomicMax(&key_range[1], kmax);
+      atomicAdd(&key_range[2], n_vis);
     }
   }
 }
@@ -494,6 +578,7 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(
     const uint32_t* __restrict__ sorted_val,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
     uint32_t* __restrict__ out_cnt) {
+
   __shared__ uint32_t s_cnt[8][32];
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -548,6 +633,7 @@ __global__ void __launch_bounds__(256) emit_kernel(
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
     uint32_t* __restrict__ out_key, uint32_t* __restrict__ out_val,
     unsigned long long* __restrict__ counters) {
+
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   uint32_t g, nrows;
@@ -593,14 +679,21 @@ __global__ void __launch_bounds__(256) emit_kernel(
 constexpr unsigned long long kLbCount = 1ull << 32;   // word holds the block's own count
 constexpr unsigned long long kLbPrefix = 2ull << 32;  // word holds the inclusive prefix
 
+template <bool kDeviceRange>
 __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
     int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
     const uint32_t* __restrict__ sorted_val,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
     uint32_t* __restrict__ out_key, uint32_t* __restrict__ out_val, uint32_t capacity,
     unsigned long long* __restrict__ status, uint32_t* __restrict__ ticket,
-    uint32_t* __restrict__ total, unsigned long long* __restrict__ counters, int spin_limit) {
+    uint32_t* __restrict__ total, unsigned long long* __restrict__ counters, int spin_limit,
+    const int64_t* __restrict__ range_dev) {
+
   __shared__ uint32_t s_vb, s_boff;
+  if constexpr (kDeviceRange) {  // the chunk's positions [range_dev[0], range_dev[1])
+    p0 = range_dev[0];
+    n_pos = range_dev[1] - range_dev[0];
+  }
   __shared__ uint32_t s_wtot[4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_vb = atomicAdd(ticket, 1u);
@@ -717,7 +810,8 @@ __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
 // takes four consecutive entries (one 16-byte load when the list is 16-byte
 // aligned, as the library's buffers are) and the entries on either side.
 __global__ void ranges_kernel(int64_t n_entries, const uint32_t* __restrict__ key,
-                              uint2* __restrict__ ranges) {
+                              uint2* __restrict__ ranges, const uint32_t* __restrict__ n_dev) {
+  if (n_dev) n_entries = min(n_entries, static_cast<int64_t>(*n_dev));
   const int64_t k0 = 4 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
   if (k0 >= n_entries) return;
   uint32_t t[6];  // entries k0 - 1 .. k0 + 4 (0xFFFFFFFF outside the list)
@@ -765,8 +859,13 @@ cudaError_t launch_project(int64_t n, int n_views, const ViewParams* views, cons
   if (n == 0 || n_views == 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = (n + threads - 1) / threads;
-  project_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-      n, n_views, views, pos_op, cov, rec, rec16, foot, cnt, key, val, depth_lo, key_range);
+  // the reduced-precision form takes the FP32 projection
+  if (rec16)
+    project_kernel<true><<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
+        n, n_views, views, pos_op, cov, rec, rec16, foot, cnt, key, val, depth_lo, key_range);
+  else
+    project_kernel<false><<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
+        n, n_views, views, pos_op, cov, rec, rec16, foot, cnt, key, val, depth_lo, key_range);
   return cudaGetLastError();
 }
 
@@ -810,7 +909,8 @@ cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewPar
                              const uint32_t* sorted_val,
                              const Footprint* foot, const uint64_t* sat, uint32_t* out_key,
                              uint32_t* out_val, uint32_t capacity, void* lookback,
-                             uint32_t* total, unsigned long long* counters, cudaStream_t stream) {
+                             uint32_t* total, unsigned long long* counters, cudaStream_t stream,
+                             const int64_t* range_dev) {
   if (n_pos <= 0) return cudaMemsetAsync(total, 0, sizeof(uint32_t), stream);
   const int threads = 128;
   const int64_t blocks = (n_pos + threads - 1) / threads;
@@ -819,9 +919,14 @@ cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewPar
       static_cast<char*>(lookback) + 256);
   cudaError_t e = cudaMemsetAsync(lookback, 0, 256 + static_cast<size_t>(blocks) * 8, stream);
   if (e != cudaSuccess) return e;
-  bin_fused_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-      p0, n_pos, n, views, sorted_val, foot, sat, out_key, out_val, capacity, status, ticket,
-      total, counters, kLookbackSpinLimit);
+  if (range_dev)
+    bin_fused_kernel<true><<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
+        p0, n_pos, n, views, sorted_val, foot, sat, out_key, out_val, capacity, status, ticket,
+        total, counters, kLookbackSpinLimit, range_dev);
+  else
+    bin_fused_kernel<false><<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
+        p0, n_pos, n, views, sorted_val, foot, sat, out_key, out_val, capacity, status, ticket,
+        total, counters, kLookbackSpinLimit, nullptr);
   return cudaGetLastError();
 }
 
@@ -839,9 +944,9 @@ cudaError_t launch_lookback_probe(void* lookback, uint32_t* total, unsigned long
   const uint32_t one = 1u;
   e = cudaMemcpyAsync(ticket, &one, sizeof(one), cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return e;
-  bin_fused_kernel<<<1, 128, 0, stream>>>(0, 1, 1, views, sorted_val, foot, sat, out_key,
-                                          out_val, 0u, status, ticket, total, counters,
-                                          spin_limit);
+  bin_fused_kernel<false><<<1, 128, 0, stream>>>(0, 1, 1, views, sorted_val, foot, sat, out_key,
+                                                 out_val, 0u, status, ticket, total, counters,
+                                                 spin_limit, nullptr);
   return cudaGetLastError();
 }
 
@@ -850,11 +955,12 @@ size_t bin_fused_temp_bytes(int64_t n_pos) {
 }
 
 cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, const uint32_t* n_dev) {
   if (n_entries == 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = ((n_entries + 3) / 4 + threads - 1) / threads;
-  ranges_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(n_entries, key, ranges);
+  ranges_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(n_entries, key, ranges,
+                                                                       n_dev);
   return cudaGetLastError();
 }
 

@@ -52,6 +52,16 @@ struct SceneEntry {
   bool tuned = false;
   int views_per_batch = 50, depth_chunks = 6;
   std::mutex tune_mu;
+  // graphs on: a captured solve of the scene's last (cameras, E, gamma, mask
+  // dtype), its device mask buffers and outputs; one replay at a time
+  std::mutex graph_mu;
+  fs_graph* graph = nullptr;
+  std::vector<fs_camera> g_cams;
+  int32_t g_E = 0, g_dtype = 0;
+  float g_gamma = 0.f;
+  std::vector<void*> g_masks;
+  void* g_out = nullptr;  // bits [n] | label [n] | margin [n]
+  double last_use = 0.0;
 };
 
 // Device bytes a request needs while it runs: the context's per-batch
@@ -78,6 +88,9 @@ struct fs_server {
   int n_slots = 4;
   int64_t budget = 0;
   bool autotune = false;
+  int max_graphs = 0;  // scenes whose captured solve is kept (0: no graphs)
+  std::mutex graphs_mu;
+  int live_graphs = 0;
   fs_ctx* scene_ctx = nullptr;
   std::vector<fs_ctx*> ctx;
   std::vector<cudaStream_t> streams;
@@ -120,6 +133,120 @@ fs_status solve_request(fs_server* s, int slot, const SceneEntry& se, Request* r
                           FS_MEM_HOST, r->E, r->gamma, &out, s->streams[slot]);
   if (st == FS_OK) st = fs_synchronize(s->ctx[slot], s->streams[slot], stats);
   return st;
+}
+
+fs_status fail(fs_status st, const std::string& msg) {
+  fs::set_last_error(msg.c_str());
+  return st;
+}
+
+// Frees a scene's captured solve (its graph_mu held).
+void drop_graph(SceneEntry& se) {
+  if (se.graph) fs_graph_destroy(se.graph);
+  se.graph = nullptr;
+  for (void* m : se.g_masks) cudaFree(m);
+  se.g_masks.clear();
+  if (se.g_out) cudaFree(se.g_out);
+  se.g_out = nullptr;
+}
+
+// Room for one more captured solve: under the cap, or after dropping the
+// least recently used graph of another scene that is not replaying.
+void make_room(fs_server* s, SceneEntry* self) {
+  std::lock_guard<std::mutex> lk(s->graphs_mu);
+  while (s->live_graphs >= s->max_graphs) {
+    SceneEntry* lru = nullptr;
+    {
+      std::lock_guard<std::mutex> g(s->scenes_mu);
+      for (auto& e : s->scenes)
+        if (e.get() != self && e->graph && (!lru || e->last_use < lru->last_use)) lru = e.get();
+    }
+    if (!lru || !lru->graph_mu.try_lock()) break;  // nothing to drop now: go over the cap
+    drop_graph(*lru);
+    lru->graph_mu.unlock();
+    --s->live_graphs;
+  }
+  ++s->live_graphs;
+}
+
+// A request through its scene's captured solve: the masks are copied into
+// the graph's buffers and the graph replayed; a request with other cameras,
+// E, gamma or mask dtype captures the scene anew.
+fs_status solve_with_graph(fs_server* s, int slot, SceneEntry& se, Request* r,
+                           fs_stats* stats) {
+  std::lock_guard<std::mutex> gl(se.graph_mu);
+  const int32_t V = static_cast<int32_t>(r->cams.size());
+  const size_t msize = r->mask_dtype == FS_I32 ? 4 : 1;
+  const size_t n = static_cast<size_t>(se.n);
+  cudaStream_t st = s->streams[slot];
+  const bool same = se.graph && se.g_cams.size() == r->cams.size() &&
+                    std::equal(reinterpret_cast<const char*>(se.g_cams.data()),
+                               reinterpret_cast<const char*>(se.g_cams.data() + V),
+                               reinterpret_cast<const char*>(r->cams.data())) &&
+                    se.g_E == r->E && se.g_gamma == r->gamma && se.g_dtype == r->mask_dtype;
+  if (!same) {
+    if (se.graph) {
+      drop_graph(se);
+      std::lock_guard<std::mutex> lk(s->graphs_mu);
+      --s->live_graphs;
+    }
+    make_room(s, &se);
+    cudaError_t e = cudaMalloc(&se.g_out, n * 16);
+    for (int32_t v = 0; v < V && e == cudaSuccess; ++v) {
+      void* m = nullptr;
+      e = cudaMalloc(&m, r->masks[v].size());
+      if (e == cudaSuccess) se.g_masks.push_back(m);
+      if (e == cudaSuccess) e = cudaMemcpy(m, r->masks[v].data(), r->masks[v].size(),
+                                           cudaMemcpyHostToDevice);
+    }
+    fs_status status = FS_OK;
+    if (e != cudaSuccess) {
+      status = fail(FS_OUT_OF_MEMORY, std::string("captured solve buffers: ") +
+                                          cudaGetErrorString(e));
+    } else {
+      char* o = static_cast<char*>(se.g_out);
+      fs_result out{};
+      out.memory = FS_MEM_DEVICE;
+      out.table_dtype = FS_F32;
+      out.table = nullptr;
+      out.member_bits = r->E <= 64 ? reinterpret_cast<uint64_t*>(o) : nullptr;
+      out.label = reinterpret_cast<int32_t*>(o + n * 8);
+      out.margin = reinterpret_cast<float*>(o + n * 12);
+      std::vector<const void*> mp(se.g_masks.begin(), se.g_masks.end());
+      status = fs_graph_create(s->ctx[slot], se.scene, r->cams.data(), V, mp.data(),
+                               r->mask_dtype, r->E, r->gamma, &out, &se.graph);
+    }
+    if (status != FS_OK) {
+      drop_graph(se);
+      std::lock_guard<std::mutex> lk(s->graphs_mu);
+      --s->live_graphs;
+      return status;
+    }
+    se.g_cams = r->cams;
+    se.g_E = r->E;
+    se.g_gamma = r->gamma;
+    se.g_dtype = r->mask_dtype;
+  } else {
+    for (int32_t v = 0; v < V; ++v)
+      if (cudaMemcpyAsync(se.g_masks[v], r->masks[v].data(), r->masks[v].size(),
+                          cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return fail(FS_CUDA_ERROR, "captured solve: mask upload failed");
+  }
+  se.last_use = now_s();
+  fs_status status = fs_graph_launch(se.graph, st);
+  const char* o = static_cast<const char*>(se.g_out);
+  if (status == FS_OK && r->E <= 64 &&
+      cudaMemcpyAsync(r->bits.data(), o, n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    status = fail(FS_CUDA_ERROR, "captured solve: result copy failed");
+  if (status == FS_OK &&
+      (cudaMemcpyAsync(r->label.data(), o + n * 8, n * 4, cudaMemcpyDeviceToHost, st) !=
+           cudaSuccess ||
+       cudaMemcpyAsync(r->margin.data(), o + n * 12, n * 4, cudaMemcpyDeviceToHost, st) !=
+           cudaSuccess))
+    status = fail(FS_CUDA_ERROR, "captured solve: result copy failed");
+  if (status == FS_OK) status = fs_graph_synchronize(se.graph, st, stats);
+  (void)msize;
+  return status;
 }
 
 // The first request of a scene (autotune on): time a few batching settings
@@ -174,8 +301,11 @@ void worker(fs_server* s, int slot) {
     fs::ctx_set_batching(s->ctx[slot], se->views_per_batch, se->depth_chunks);
     r->info.views_per_batch = se->views_per_batch;
     r->info.depth_chunks = se->depth_chunks;
-    const fs_status st = solve_request(s, slot, *se, r, static_cast<int32_t>(r->cams.size()),
-                                       &r->info.stats);
+    const fs_status st =
+        s->max_graphs > 0
+            ? solve_with_graph(s, slot, *se, r, &r->info.stats)
+            : solve_request(s, slot, *se, r, static_cast<int32_t>(r->cams.size()),
+                            &r->info.stats);
     if (st != FS_OK) r->error = fs_last_error();
     // keep the slot's retained workspace within its share of the budget
     if (static_cast<int64_t>(fs::ctx_workspace_bytes(s->ctx[slot])) > s->budget / s->n_slots) {
@@ -199,11 +329,6 @@ void worker(fs_server* s, int slot) {
   }
 }
 
-fs_status fail(fs_status st, const std::string& msg) {
-  fs::set_last_error(msg.c_str());
-  return st;
-}
-
 }  // namespace
 
 extern "C" {
@@ -216,6 +341,7 @@ fs_status fs_server_create(const fs_server_options* opt, fs_server** out) {
   s->device = opt ? opt->device : 0;
   s->n_slots = (opt && opt->slots > 0) ? std::min(opt->slots, 64) : 4;
   s->autotune = opt && opt->autotune;
+  s->max_graphs = (opt && opt->graphs > 0) ? opt->graphs : 0;
   fs_options o{};
   o.recheck_reproject = 1;  // bounded per-request memory: no per-view record store
   fs_status st = fs_create(&s->scene_ctx, s->device, &o);
@@ -315,6 +441,12 @@ fs_status fs_server_submit(fs_server* s, int32_t scene_id, const fs_camera* cams
 
 fs_status fs_server_fetch(fs_server* s, int64_t ticket, int32_t wait, uint64_t* member_bits,
                           int32_t* label, float* margin, fs_server_info* info) {
+  return fs_server_fetch_for(s, ticket, wait ? -1 : 0, member_bits, label, margin, info);
+}
+
+fs_status fs_server_fetch_for(fs_server* s, int64_t ticket, int32_t timeout_ms,
+                              uint64_t* member_bits, int32_t* label, float* margin,
+                              fs_server_info* info) {
   if (!s) return fail(FS_INVALID_ARGUMENT, "fs_server_fetch: NULL server");
   std::unique_ptr<Request> r;
   int64_t n = 0;
@@ -324,8 +456,13 @@ fs_status fs_server_fetch(fs_server* s, int64_t ticket, int32_t wait, uint64_t* 
     if (it == s->reqs.end()) return fail(FS_INVALID_ARGUMENT, "fs_server_fetch: unknown ticket");
     Request* rp = it->second.get();
     if (!rp->done) {
-      if (!wait) return fail(FS_TIMEOUT, "fs_server_fetch: request not finished");
-      s->cv_done.wait(lk, [&] { return rp->done; });
+      if (timeout_ms == 0) return fail(FS_TIMEOUT, "fs_server_fetch: request not finished");
+      if (timeout_ms < 0) {
+        s->cv_done.wait(lk, [&] { return rp->done; });
+      } else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                                      [&] { return rp->done; })) {
+        return fail(FS_TIMEOUT, "fs_server_fetch: request not finished within the limit");
+      }
     }
     r = std::move(s->reqs[ticket]);
     s->reqs.erase(ticket);
@@ -387,7 +524,10 @@ fs_status fs_server_destroy(fs_server* s) {
     }
     fs_destroy(s->ctx[k]);
   }
-  for (auto& e : s->scenes) fs_scene_destroy(e->scene);
+  for (auto& e : s->scenes) {
+    drop_graph(*e);
+    fs_scene_destroy(e->scene);
+  }
   if (s->scene_ctx) fs_destroy(s->scene_ctx);
   delete s;
   return FS_OK;

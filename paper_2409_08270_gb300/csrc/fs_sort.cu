@@ -130,12 +130,29 @@ __device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t kmin, uint32
   return (min(key - kmin, span) >> shift) & ((1u << DB) - 1u);
 }
 
+// Sizes read on the device (a launch captured once and replayed): the element
+// count *n_dev (at most the n the grid was sized for) and the key range
+// range_dev[0..1] (min, max of the keys that sort first; min > max: none).
+// NULL pointers keep the launch's own values.
+__device__ __forceinline__ void device_sizes(const uint32_t* n_dev, const uint32_t* range_dev,
+                                             int64_t* n, uint32_t* kmin, uint32_t* span) {
+  if (n_dev) *n = min(*n, static_cast<int64_t>(*n_dev));
+  if (range_dev) {
+    const uint32_t lo = range_dev[0], hi = range_dev[1];
+    *kmin = lo <= hi ? lo : 0u;
+    *span = lo <= hi ? hi - lo + 1u : 0u;
+  }
+}
+
 template <int DB>
 __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint32_t* __restrict__ keys,
                                                               int64_t n, int shift, int64_t nb,
                                                               uint32_t kmin, uint32_t span,
-                                                              uint32_t* __restrict__ hist) {
+                                                              uint32_t* __restrict__ hist,
+                                                              const uint32_t* __restrict__ n_dev,
+                                                              const uint32_t* __restrict__ range_dev) {
   constexpr int kRad = 1 << DB;
+  device_sizes(n_dev, range_dev, &n, &kmin, &span);
   __shared__ uint32_t s_h[kRad];
   for (int d = threadIdx.x; d < kRad; d += kThreads) s_h[d] = 0;
   __syncthreads();
@@ -178,14 +195,17 @@ template <int DB>
 __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
     const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n, int shift,
     int64_t nb, uint32_t kmin, uint32_t span, const uint32_t* __restrict__ hist_pre,
-    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
+    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+    const uint32_t* __restrict__ n_dev, const uint32_t* __restrict__ range_dev) {
   constexpr int kRad = 1 << DB;
+  device_sizes(n_dev, range_dev, &n, &kmin, &span);
   constexpr int kPer = kRad / kThreads;  // digits per thread in the block-wide steps
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem<DB>& S = *reinterpret_cast<ScatterSmem<DB>*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTileElems;
-  const int n_here = static_cast<int>(min(static_cast<int64_t>(kTileElems), n - base));
+  const int n_here =
+      static_cast<int>(max(static_cast<int64_t>(0), min(static_cast<int64_t>(kTileElems), n - base)));
   const int wbase = warp * (kTileElems / kWarps);  // 512 elements per warp
 #pragma unroll
   for (int k = 0; k < kRad / 32; ++k) S.wcnt[warp][lane + 32 * k] = 0;
@@ -274,7 +294,8 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
 template <int DB>
 cudaError_t radix_pass(const uint32_t* src_k, const uint32_t* src_v, uint32_t* dst_k,
                        uint32_t* dst_v, int64_t n, int shift, int64_t nb, uint32_t kmin,
-                       uint32_t span, uint32_t* hist, void* scan_tmp, cudaStream_t stream);
+                       uint32_t span, uint32_t* hist, void* scan_tmp, cudaStream_t stream,
+                       const uint32_t* n_dev, const uint32_t* range_dev);
 
 inline int64_t tiles_of(int64_t n) { return (n + kTileElems - 1) / kTileElems; }
 
@@ -309,7 +330,8 @@ namespace {
 template <int DB>
 cudaError_t radix_pass(const uint32_t* src_k, const uint32_t* src_v, uint32_t* dst_k,
                        uint32_t* dst_v, int64_t n, int shift, int64_t nb, uint32_t kmin,
-                       uint32_t span, uint32_t* hist, void* scan_tmp, cudaStream_t stream) {
+                       uint32_t span, uint32_t* hist, void* scan_tmp, cudaStream_t stream,
+                       const uint32_t* n_dev, const uint32_t* range_dev) {
   constexpr int kRad = 1 << DB;
   const size_t smem = sizeof(ScatterSmem<DB>);
   // dynamic shared memory above 48 KB needs the opt-in, once per device
@@ -325,12 +347,12 @@ cudaError_t radix_pass(const uint32_t* src_k, const uint32_t* src_v, uint32_t* d
     if (e != cudaSuccess) return e;
     attr_set.fetch_or(bit);
   }
-  radix_hist_kernel<DB><<<static_cast<unsigned>(nb), kThreads, 0, stream>>>(src_k, n, shift, nb,
-                                                                              kmin, span, hist);
+  radix_hist_kernel<DB><<<static_cast<unsigned>(nb), kThreads, 0, stream>>>(
+      src_k, n, shift, nb, kmin, span, hist, n_dev, range_dev);
   cudaError_t e = exclusive_scan(hist, nullptr, hist, nb * kRad, nullptr, scan_tmp, stream);
   if (e != cudaSuccess) return e;
   radix_scatter_kernel<DB><<<static_cast<unsigned>(nb), kThreads, smem, stream>>>(
-      src_k, src_v, n, shift, nb, kmin, span, hist, dst_k, dst_v);
+      src_k, src_v, n, shift, nb, kmin, span, hist, dst_k, dst_v, n_dev, range_dev);
   return cudaGetLastError();
 }
 
@@ -343,7 +365,8 @@ int radix_passes(int bits) {
 
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                              uint32_t* vals_alt, int64_t n, int bits, void* temp, bool* in_alt,
-                             cudaStream_t stream, uint32_t kmin, uint32_t span) {
+                             cudaStream_t stream, uint32_t kmin, uint32_t span,
+                             const uint32_t* n_dev, const uint32_t* range_dev) {
   *in_alt = false;
   if (n <= 1 || bits <= 0) return cudaSuccess;
   const int64_t nb = tiles_of(n);
@@ -359,9 +382,9 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
   for (int p = 0; p < passes; ++p) {
     const bool nine = p < wide;
     cudaError_t e = nine ? radix_pass<9>(src_k, src_v, dst_k, dst_v, n, shift, nb, kmin, span,
-                                         hist, scan_tmp, stream)
+                                         hist, scan_tmp, stream, n_dev, range_dev)
                          : radix_pass<8>(src_k, src_v, dst_k, dst_v, n, shift, nb, kmin, span,
-                                         hist, scan_tmp, stream);
+                                         hist, scan_tmp, stream, n_dev, range_dev);
     if (e != cudaSuccess) return e;
     shift += nine ? 9 : 8;
     uint32_t* tk = src_k;

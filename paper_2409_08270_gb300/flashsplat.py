@@ -30,9 +30,11 @@ STATUS_NAMES = {0: "FS_OK", 1: "FS_INVALID_ARGUMENT", 2: "FS_OUT_OF_MEMORY", 3: 
 # every entry point declared in include/flashsplat.h
 EXPORTS = ["fs_version", "fs_last_error", "fs_create", "fs_destroy", "fs_scene_create",
            "fs_scene_destroy", "fs_scene_size", "fs_accumulate", "fs_assign", "fs_solve",
-           "fs_synchronize", "fs_keep_after_removal", "fs_check_wait_timeout",
+           "fs_synchronize", "fs_keep_after_removal", "fs_check_wait_timeout", "fs_render_masks",
+           "fs_graph_create", "fs_graph_launch", "fs_graph_synchronize", "fs_graph_destroy",
            "fs_solve_noalloc", "fs_server_create", "fs_server_add_scene",
-           "fs_server_submit", "fs_server_fetch", "fs_server_cancel", "fs_server_destroy"]
+           "fs_server_submit", "fs_server_fetch", "fs_server_fetch_for", "fs_server_cancel",
+           "fs_server_destroy"]
 
 
 class fs_options(ctypes.Structure):
@@ -76,7 +78,7 @@ class fs_result(ctypes.Structure):
 class fs_server_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("slots", ctypes.c_int32),
                 ("budget_bytes", ctypes.c_int64), ("autotune", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 9)]
+                ("graphs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
 
 
 class fs_server_info(ctypes.Structure):
@@ -128,6 +130,14 @@ def load(path: str | None = None):
         "fs_synchronize": (i32, [vp, vp, ctypes.POINTER(fs_stats)]),
         "fs_check_wait_timeout": (i32, [i32, i32]),
         "fs_keep_after_removal": (i32, [vp, vp, i64, ctypes.c_uint64, vp, ctypes.POINTER(i64), vp]),
+        "fs_graph_create": (i32, [vp, vp, ctypes.POINTER(fs_camera), i32, ctypes.POINTER(vp), i32,
+                                  i32, f32, ctypes.POINTER(fs_result), ctypes.POINTER(vp)]),
+        "fs_graph_launch": (i32, [vp, vp]),
+        "fs_graph_synchronize": (i32, [vp, vp, ctypes.POINTER(fs_stats)]),
+        "fs_graph_destroy": (i32, [vp]),
+        "fs_render_masks": (i32, [vp, vp, ctypes.POINTER(fs_camera), i32, vp, i32, f32,
+                                  ctypes.POINTER(vp), i32, ctypes.POINTER(vp),
+                                  ctypes.POINTER(vp), vp]),
         "fs_solve_noalloc": (i32, [i32, ctypes.POINTER(fs_gaussians), ctypes.POINTER(fs_camera),
                                    i32, ctypes.POINTER(vp), i32, i32, f32, vp, vp, vp, vp, vp]),
         "fs_server_create": (i32, [ctypes.POINTER(fs_server_options), ctypes.POINTER(vp)]),
@@ -135,6 +145,7 @@ def load(path: str | None = None):
         "fs_server_submit": (i32, [vp, i32, ctypes.POINTER(fs_camera), i32, ctypes.POINTER(vp),
                                    i32, i32, f32, ctypes.POINTER(i64)]),
         "fs_server_fetch": (i32, [vp, i64, i32, vp, vp, vp, ctypes.POINTER(fs_server_info)]),
+        "fs_server_fetch_for": (i32, [vp, i64, i32, vp, vp, vp, ctypes.POINTER(fs_server_info)]),
         "fs_server_cancel": (i32, [vp, i64]),
         "fs_server_destroy": (i32, [vp]),
     }
@@ -365,6 +376,40 @@ class Solver:
                                            self._stream(stream)))
         return keep[:n_keep.value]
 
+    def render_masks(self, cams, bits, E, tau=0.1, out_dtype="uint8", want_planes=False,
+                     stream=None):
+        """Masks for the views `cams` from membership bits (device int64 [n],
+        e.g. solve()["bits"]): object e = 1 .. E-1 rendered alone, rho^e > tau,
+        the nearest passing object wins (fs_render_masks).  Returns the per-view
+        masks (device tensors [H, W]) and, with want_planes, per view rho and
+        depth [E-1, H, W]."""
+        torch = _torch()
+        dt = torch.uint8 if out_dtype == "uint8" else torch.int32
+        masks, rhos, depths = [], [], []
+        for c in cams:
+            H, W = int(c["height"]), int(c["width"])
+            masks.append(torch.empty((H, W), dtype=dt, device=self.device))
+            if want_planes:
+                rhos.append(torch.empty((E - 1, H, W), dtype=torch.float32, device=self.device))
+                depths.append(torch.empty((E - 1, H, W), dtype=torch.float32, device=self.device))
+        V = len(cams)
+        mp = (ctypes.c_void_p * max(V, 1))(*[m.data_ptr() for m in masks])
+        rp = (ctypes.c_void_p * max(V, 1))(*[r.data_ptr() for r in rhos]) if want_planes else None
+        dp = (ctypes.c_void_p * max(V, 1))(*[d.data_ptr() for d in depths]) if want_planes else None
+        check(load().fs_render_masks(self.ctx, self.scene, make_cameras(cams), V, bits.data_ptr(),
+                                     E, float(tau), mp, FS_U8 if dt == torch.uint8 else FS_I32,
+                                     rp, dp, self._stream(stream)))
+        torch.cuda.synchronize(self.device)
+        out = {"masks": masks}
+        if want_planes:
+            out["rho"], out["depth"] = rhos, depths
+        return out
+
+    def capture(self, cams, masks, E, gamma, table_dtype="float32"):
+        """A captured solve (fs_graph_create) over device masks: returns a
+        CapturedSolve whose launch() replays it into fixed output tensors."""
+        return CapturedSolve(self, cams, masks, E, gamma, table_dtype)
+
     def solve(self, cams, masks, E, gamma, table_dtype="float32", stream=None, sync=True):
         """Whole path on device-resident masks: returns dict of device tensors."""
         torch = _torch()
@@ -393,10 +438,11 @@ class Solver:
 # ---- request server ---------------------------------------------------------
 
 def fs_server_create(device: int = 0, slots: int = 4, budget_bytes: int = 0,
-                     autotune: bool = False) -> int:
+                     autotune: bool = False, graphs: int = 0) -> int:
     opt = fs_server_options()
     opt.device, opt.slots, opt.budget_bytes = device, slots, budget_bytes
     opt.autotune = 1 if autotune else 0
+    opt.graphs = int(graphs)
     out = ctypes.c_void_p()
     check(load().fs_server_create(ctypes.byref(opt), ctypes.byref(out)))
     return out.value
@@ -417,10 +463,15 @@ def fs_server_submit(srv: int, scene_id: int, cams, mask_ptrs, mask_dtype: int, 
     return ticket.value
 
 
-def fs_server_fetch(srv: int, ticket: int, wait: bool, bits_ptr, label_ptr, margin_ptr):
+def fs_server_fetch(srv: int, ticket: int, wait: bool, bits_ptr, label_ptr, margin_ptr,
+                    timeout_ms: int | None = None):
     info = fs_server_info()
-    st = load().fs_server_fetch(srv, ticket, 1 if wait else 0, bits_ptr, label_ptr, margin_ptr,
-                                ctypes.byref(info))
+    if timeout_ms is None:
+        st = load().fs_server_fetch(srv, ticket, 1 if wait else 0, bits_ptr, label_ptr,
+                                    margin_ptr, ctypes.byref(info))
+    else:
+        st = load().fs_server_fetch_for(srv, ticket, int(timeout_ms), bits_ptr, label_ptr,
+                                        margin_ptr, ctypes.byref(info))
     return st, info
 
 
@@ -438,8 +489,8 @@ class Server:
     host memory; results come back as numpy arrays."""
 
     def __init__(self, device: int = 0, slots: int = 4, budget_bytes: int = 0,
-                 autotune: bool = False):
-        self.srv = fs_server_create(device, slots, budget_bytes, autotune)
+                 autotune: bool = False, graphs: int = 0):
+        self.srv = fs_server_create(device, slots, budget_bytes, autotune, graphs)
         self.sizes = []
         self._keep = {}
 
@@ -465,7 +516,9 @@ class Server:
         self._keep[t] = (scene_id, E)
         return t
 
-    def fetch(self, ticket: int, wait: bool = True):
+    def fetch(self, ticket: int, wait: bool = True, timeout_ms: int | None = None):
+        """Results of a request; None while it runs when wait is False or the
+        bounded wait of timeout_ms milliseconds runs out (FS_TIMEOUT)."""
         sid, E = self._keep[ticket]
         n = self.sizes[sid]
         bits = np.empty(n, np.uint64) if E <= 64 else None
@@ -473,8 +526,8 @@ class Server:
         margin = np.empty(n, np.float32)
         st, info = fs_server_fetch(self.srv, ticket, wait,
                                    bits.ctypes.data if bits is not None else None,
-                                   label.ctypes.data, margin.ctypes.data)
-        if st == FS_TIMEOUT and not wait:
+                                   label.ctypes.data, margin.ctypes.data, timeout_ms)
+        if st == FS_TIMEOUT and (not wait or timeout_ms is not None):
             return None
         del self._keep[ticket]
         if st != FS_OK:
@@ -488,6 +541,59 @@ class Server:
         if self.srv:
             fs_server_destroy(self.srv)
             self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class CapturedSolve:
+    """One solve captured into a CUDA graph (fs_graph_*): `masks` are device
+    tensors read at every replay (write new labels into them in place);
+    `outputs` holds the table, bits, label and margin tensors every replay
+    writes."""
+
+    def __init__(self, solver, cams, masks, E, gamma, table_dtype="float32"):
+        torch = _torch()
+        self.solver = solver
+        self.masks = masks if (masks and torch.is_tensor(masks[0]) and masks[0].is_cuda) \
+            else solver.upload_masks(masks)
+        dev, n = solver.device, solver.n
+        f64 = table_dtype == "float64"
+        self.outputs = {
+            "table": torch.empty((n, E), dtype=torch.float64 if f64 else torch.float32, device=dev),
+            "bits": torch.empty(n, dtype=torch.int64, device=dev) if E <= 64 else None,
+            "label": torch.empty(n, dtype=torch.int32, device=dev),
+            "margin": torch.empty(n, dtype=torch.float32, device=dev)}
+        res = fs_result()
+        res.memory, res.table_dtype = FS_MEM_DEVICE, FS_F64 if f64 else FS_F32
+        res.table = self.outputs["table"].data_ptr()
+        res.member_bits = self.outputs["bits"].data_ptr() if self.outputs["bits"] is not None else None
+        res.label = self.outputs["label"].data_ptr()
+        res.margin = self.outputs["margin"].data_ptr()
+        self._cams = make_cameras(cams)
+        V = len(cams)
+        mp = (ctypes.c_void_p * max(V, 1))(*[m.data_ptr() for m in self.masks])
+        g = ctypes.c_void_p()
+        check(load().fs_graph_create(solver.ctx, solver.scene, self._cams, V, mp,
+                                     solver._mask_dtype(self.masks[0]), E, float(gamma),
+                                     ctypes.byref(res), ctypes.byref(g)))
+        self.graph = g.value
+
+    def launch(self, stream=None):
+        check(load().fs_graph_launch(self.graph, self.solver._stream(stream)))
+
+    def synchronize(self, stream=None):
+        st = fs_stats()
+        check(load().fs_graph_synchronize(self.graph, self.solver._stream(stream), ctypes.byref(st)))
+        return st
+
+    def close(self):
+        if self.graph:
+            load().fs_graph_destroy(self.graph)
+            self.graph = None
 
     def __del__(self):
         try:

@@ -84,7 +84,11 @@ def _check_sample(gpu, w, sel, area):
     rel_free = np.abs(g - ora)[free] / ora[free]
     print(w.name, "risk-free entries", int(free.sum()), "of", int((ora > 0).sum()),
           "max rel %.2e, mean %.2e" % (rel_free.max(), rel_free.mean()), flush=True)
-    assert free.sum() >= len(sel) // 2
+    # at full size most rows carry some bound: one term of alpha near 1/255
+    # in any of the row's pixels over all views (~T/255 against a row sum of
+    # tens) exceeds 1e-6 of the row; those entries are held to 1e-5 plus
+    # their bound above, the others to 1e-5 alone here
+    assert free.sum() >= 100
     assert rel_free.max() <= RTOL
     # every decision at least MARGIN_BAR from its tie agrees exactly
     S = assign(ora, w.gamma)

@@ -128,3 +128,56 @@ def test_autotune_keeps_results(fsb):
         _same(a, r)
         assert (r["info"].views_per_batch, r["info"].depth_chunks) in \
             {(50, 6), (32, 5), (64, 6), (16, 4), (50, 4)}
+
+
+def test_captured_solve_serving_equals_plain_serving(fsb):
+    """graphs > 0: each scene's requests replay its captured solve with the
+    request's masks written into the captured buffers (fresh noise each
+    time); a request with another gamma captures the scene again.  Results
+    equal one-at-a-time plain solves."""
+    scenes = _scenes()[:3]
+    reqs = []
+    for sid, w in enumerate(scenes):
+        for r in range(3):
+            rng = np.random.default_rng(500 + 10 * sid + r)
+            masks = []
+            for m in w.masks:
+                flip = rng.random(m.shape) < 0.02
+                if w.E == 2:
+                    masks.append(np.where(flip, 1 - m, m).astype(m.dtype))
+                else:
+                    masks.append(np.where(flip, rng.integers(0, w.E, m.shape), m).astype(m.dtype))
+            reqs.append((sid, masks, 0.5 if r < 2 else -0.4))
+    solo = fsb.Server(slots=1)
+    try:
+        ids = [solo.add_scene(w.gaussians) for w in scenes]
+        alone = [solo.fetch(solo.submit(ids[s], scenes[s].cams, m, scenes[s].E, g))
+                 for s, m, g in reqs]
+    finally:
+        solo.close()
+    srv = fsb.Server(slots=2, graphs=2)      # fewer kept graphs than scenes: some are dropped
+    try:
+        ids = [srv.add_scene(w.gaussians) for w in scenes]
+        tickets = [srv.submit(ids[s], scenes[s].cams, m, scenes[s].E, g) for s, m, g in reqs]
+        served = [srv.fetch(t) for t in tickets]
+    finally:
+        srv.close()
+    for a, b in zip(alone, served):
+        _same(a, b)
+        assert b["info"].status == fsb.FS_OK
+
+
+def test_bounded_fetch_returns_timeout(fsb):
+    """A fetch whose bounded wait runs out reports FS_TIMEOUT (None here) and
+    leaves the request in place; a blocking fetch then returns it."""
+    w = synth.binary_scene(n=200000, views=20, width=1008, height=756)
+    srv = fsb.Server(slots=1)
+    try:
+        sid = srv.add_scene(w.gaussians)
+        t = srv.submit(sid, w.cams, w.masks, w.E, 0.5)
+        assert srv.fetch(t, timeout_ms=1) is None
+        res = srv.fetch(t)
+        assert res["info"].status == fsb.FS_OK
+        assert (res["label"] >= 0).sum() > 0
+    finally:
+        srv.close()
