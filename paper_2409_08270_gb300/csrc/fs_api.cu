@@ -1109,6 +1109,9 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
       Ls.chunks = chunks;
       Ls.sat_chunk = satc;
       Ls.deep = deep;
+      Ls.flagged = F;
+      Ls.n_flagged = static_cast<int>(std::min<int64_t>(nF, 0x7FFFFFFF));
+      Ls.cnt = P.cnt;
       FS_CUDA(cudaMemsetAsync(Rb, 0, rbytes, stream), "batch rows clear");
       FS_CUDA(cudaMemsetAsync(ctr + fs::kRecheckIncomplete, 0, 8, stream), "incomplete clear");
       c->stats.kernel_launches += 1;

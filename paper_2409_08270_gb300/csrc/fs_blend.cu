@@ -477,8 +477,13 @@ __global__ void __launch_bounds__(128, 6) blend_kernel(
   unsigned long long n_eval = 0, n_part = 0;
   unsigned long long n_rounds = 0, n_steps = 0, n_mixed = 0;
 
+  // the stager's list entry of the next step, loaded a step ahead so that
+  // the record gather does not wait behind it
+  uint32_t g_next = (stager && rg.x + threadIdx.x < rg.y) ? list_val[rg.x + threadIdx.x] : 0u;
   for (uint32_t base = rg.x;; base += kStep) {
     const bool more = base < rg.y;
+    const uint32_t g_here = g_next;
+    if (stager && base + kStep + threadIdx.x < rg.y) g_next = list_val[base + kStep + threadIdx.x];
     // ---- stage (warps 0 and 1): entry base + threadIdx.x against all four
     // sub-tiles; bit s of keep: the entry goes to sub-tile s's queue
     uint32_t keep = 0u;
@@ -486,7 +491,7 @@ __global__ void __launch_bounds__(128, 6) blend_kernel(
     float bt0 = 0.f, bt1 = 0.f, nlo = 0.f, clampf = 0.f;
     int32_t gi = 0;
     if (stager && more && base + threadIdx.x < rg.y) {
-      const uint32_t g = list_val[base + threadIdx.x];
+      const uint32_t g = g_here;
       gi = static_cast<int32_t>(g - gbase);
       float o, qc;
       if (rec16) {

@@ -60,7 +60,8 @@ cudaError_t launch_project(int64_t n, int n_views, const ViewParams* views, cons
 // re-orders runs of equal 32-bit depth keys by the depth's low word, then slot
 // (n_total elements; slot / n is the view of a slot)
 cudaError_t launch_depth_tie_fix(int64_t n_total, int64_t n, const uint32_t* key, uint32_t* val,
-                                 const uint32_t* depth_lo, cudaStream_t stream);
+                                 const uint32_t* depth_lo, cudaStream_t stream,
+                                 const uint32_t* n_dev = nullptr);
 // Binning of sorted positions [p0, p0 + n_pos): one list entry (key = tile
 // id, value = slot) per (tile, Gaussian) whose footprint reaches the tile,
 // unless the tile's `sat` bit is set.
@@ -196,6 +197,12 @@ struct RecheckLists {
   int chunks;
   const uint8_t* sat_chunk;
   const uint64_t* deep;
+  // the re-checked Gaussians (n_flagged of them) and the batch's per-slot
+  // visibility: a deep tile walks only the pixels one of them can reach
+  // (NULL: every labelled pixel of a deep tile)
+  const uint32_t* flagged;
+  int n_flagged;
+  const uint32_t* cnt;
 };
 // Float-pair compositing of the tiles whose skip bit is clear; adds alpha*T of
 // Gaussian i (map[i] >= 0) at a pixel of label e into R[map[i] * E + e].

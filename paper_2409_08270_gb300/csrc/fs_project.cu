@@ -468,7 +468,9 @@ __device__ __forceinline__ void fix_tie_run(int64_t k, int64_t n_total, const Sl
 // the keys are 16-byte aligned) for the start of an equal-key run.
 __global__ void depth_tie_fix_kernel(int64_t n_total, int64_t n, const uint32_t* __restrict__ key,
                                      uint32_t* __restrict__ val,
-                                     const uint32_t* __restrict__ depth_lo) {
+                                     const uint32_t* __restrict__ depth_lo,
+                                     const uint32_t* __restrict__ n_dev) {
+  if (n_dev) n_total = min(n_total, static_cast<int64_t>(*n_dev));
   const int64_t k0 = 4 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
   if (k0 + 1 >= n_total) return;
   uint32_t t[5];  // keys k0 .. k0 + 4 (0xFFFFFFFF past the end: never a run)
@@ -870,12 +872,13 @@ cudaError_t launch_project(int64_t n, int n_views, const ViewParams* views, cons
 }
 
 cudaError_t launch_depth_tie_fix(int64_t n_total, int64_t n, const uint32_t* key, uint32_t* val,
-                                 const uint32_t* depth_lo, cudaStream_t stream) {
+                                 const uint32_t* depth_lo, cudaStream_t stream,
+                                 const uint32_t* n_dev) {
   if (n_total < 2) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = ((n_total + 3) / 4 + threads - 1) / threads;
   depth_tie_fix_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(n_total, n, key, val,
-                                                                              depth_lo);
+                                                                              depth_lo, n_dev);
   return cudaGetLastError();
 }
 

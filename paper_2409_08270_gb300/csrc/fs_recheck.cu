@@ -159,6 +159,7 @@ __global__ void compact_kernel(int64_t k_total, const uint32_t* __restrict__ fla
 }
 
 constexpr int kRB = 64;  // list entries staged per round
+constexpr int kDeepTest = 256;  // re-checked Gaussians a deep tile tests per pixel at most
 
 // Float-pair constants of the compositing rule (Sec. 3.1 Eq. 1 conventions).
 constexpr double kAlphaMinD = 1.0 / 255.0, kAlphaMaxD = 0.99, kTMinD = 1e-4;
@@ -304,12 +305,35 @@ __global__ void __launch_bounds__(kTilePixels) recheck_blend_kernel(
     }
   }
 
+  // deep tiles: a pixel is walked to its stop only where a re-checked
+  // Gaussian visible in this view can reach it (the others hold nothing to
+  // re-check); with many re-checked Gaussians every labelled pixel is
+  bool deep_px = deep;
+  if (deep && L.flagged && L.n_flagged <= kDeepTest) {
+    bool reached = false;
+    for (int k0 = 0; k0 < L.n_flagged; k0 += kRB) {
+      const int cnt = min(kRB, L.n_flagged - k0);
+      __syncthreads();
+      if (threadIdx.x < cnt) {
+        const uint32_t gi = L.flagged[k0 + threadIdx.x];
+        const int64_t slot = static_cast<int64_t>(blockIdx.y) * n + gi;
+        s_e[threadIdx.x].j = -1;
+        if (L.cnt[slot])
+          s_e[threadIdx.x] = rec16 ? stage_compact(rec16[slot], pos_op[gi].w, cx, cy, 0)
+                                   : stage_entry(rec[slot], cx, cy, 0);
+      }
+      __syncthreads();
+      for (int e = 0; e < cnt; ++e)
+        if (s_e[e].j >= 0 && reaches(s_e[e], lx, ly)) reached = true;
+    }
+    deep_px = reached;
+  }
+
   // pass 2: float-pair compositing
   const f2 a_min = FS_F2C(kAlphaMinD), a_max = FS_F2C(kAlphaMaxD), t_min = FS_F2C(kTMinD);
   f2 T = f2_from(1.f);
-  // deep tiles: every labelled pixel is walked to its stop
-  bool live = label >= 0 && (deep || last >= 0);
-  const bool to_stop = deep;
+  bool live = label >= 0 && (deep_px || last >= 0);
+  const bool to_stop = deep_px;
   unsigned long long evals = 0;
   bool done_all = false;
   for (int c = 0; c < n_chunks && !done_all; ++c) {
