@@ -403,8 +403,9 @@ fs_status fs_server_destroy(fs_server* srv);
  * chunk spans and its list entries; the capture then reads every count from
  * device memory and sizes its grids and lists for that plan.  After the
  * replay, fs_graph_launch runs the near-tie re-check (when the options turn
- * it on; its work depends on the labels) and rounds the table to FP32 when
- * asked, outside the graph.
+ * it on; its work depends on the labels) on a second context of the graph's
+ * own, projecting the views again (nothing may move the captured buffers),
+ * and rounds the table to FP32 when asked, outside the graph.
  *   masks[V]: device buffers, read at every replay: the caller may write new
  *     masks into them between replays.  With every label in [0, E) the
  *     shapes depend on the scene and cameras only, so any such masks replay

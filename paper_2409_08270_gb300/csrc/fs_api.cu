@@ -1450,6 +1450,9 @@ fs_status fs_keep_after_removal(fs_ctx* c, const uint64_t* member_bits, int64_t 
 // A solve captured into a CUDA graph (fs_graph_* in flashsplat.h).
 struct fs_graph {
   fs_ctx* c = nullptr;  // the graph's own context: the capture holds its buffers
+  // the near-tie re-check after a replay runs on a context of its own: its
+  // buffers may grow, and nothing may move the captured ones
+  fs_ctx* rc = nullptr;
   const fs_scene* s = nullptr;
   std::vector<fs_camera> cams;
   std::vector<const void*> masks;
@@ -1475,6 +1478,7 @@ void graph_free(fs_graph* g) {
   if (g->graph) cudaGraphDestroy(g->graph);
   if (g->stream) cudaStreamDestroy(g->stream);
   g->plan.views.release();
+  if (g->rc) fs_destroy(g->rc);
   if (g->c) fs_destroy(g->c);
   delete g;
 }
@@ -1556,11 +1560,14 @@ fs_status fs_graph_create(fs_ctx* tmpl, const fs_scene* s, const fs_camera* cams
     if ((st = c->margin_tmp.ensure(nn * 4, "margins")) != FS_OK) return bail(st);
     g->margin = c->margin_tmp.as<float>();
   }
-  if (g->recheck && !c->recheck_reproject) {
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
-      g->keep = (c->compact ? 76.0 : 108.0) * static_cast<double>(n) * V <=
-                0.5 * static_cast<double>(free_b);
+  // the re-check projects again on its own context (kept lists would live in
+  // the captured one): g->keep stays false
+  if (g->recheck) {
+    if ((st = fs_create(&g->rc, tmpl->device, &o)) != FS_OK) return bail(st);
+    const int vbr = batch_views(g->rc, n);
+    if ((st = ensure_window(g->rc, n, vbr, V, false)) != FS_OK) return bail(st);
+    if ((st = stage_masks(g->rc, cams, V, masks, mask_dtype, FS_MEM_DEVICE, nullptr)) != FS_OK)
+      return bail(st);
   }
   cudaError_t ce = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
@@ -1601,10 +1608,13 @@ fs_status fs_graph_launch(fs_graph* g, void* stream) {
   c->events_used = 0;
   FS_CUDA(cudaGraphLaunch(g->exec, st), "cudaGraphLaunch");
   const int32_t V = static_cast<int32_t>(g->cams.size());
-  c->kl_valid = g->keep;
-  if (g->recheck)
-    FS_TRY(recheck_impl(c, g->s, g->cams.data(), V, g->mask_dtype, g->E, g->gamma, g->table,
-                        FS_F64, g->bits, g->label, g->margin, g->keep, st));
+  if (g->recheck) {
+    fs_ctx* rc = g->rc;
+    rc->stats = fs_stats{};
+    FS_CUDA(cudaMemsetAsync(rc->counters.p, 0, rc->counters.bytes, st), "counters clear");
+    FS_TRY(recheck_impl(rc, g->s, g->cams.data(), V, g->mask_dtype, g->E, g->gamma, g->table,
+                        FS_F64, g->bits, g->label, g->margin, false, st));
+  }
   const int64_t count = g->s->n * static_cast<int64_t>(g->E);
   if (g->out.table && g->out.table_dtype == FS_F32)
     FS_CUDA(fs::launch_round_table(count, static_cast<const double*>(g->table),
@@ -1615,7 +1625,15 @@ fs_status fs_graph_launch(fs_graph* g, void* stream) {
 
 fs_status fs_graph_synchronize(fs_graph* g, void* stream, fs_stats* stats) {
   if (!g) return fail(FS_INVALID_ARGUMENT, "fs_graph_synchronize: graph is NULL");
-  return fs_synchronize(g->c, stream, stats);
+  fs_stats rs{};
+  if (g->rc) FS_TRY(fs_synchronize(g->rc, stream, &rs));
+  FS_TRY(fs_synchronize(g->c, stream, stats));
+  if (stats) {
+    stats->rechecked = rs.rechecked;
+    stats->recheck_pairs = rs.recheck_pairs;
+    stats->recheck_rebinned = rs.recheck_rebinned;
+  }
+  return FS_OK;
 }
 
 fs_status fs_graph_destroy(fs_graph* g) {

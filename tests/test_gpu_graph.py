@@ -46,11 +46,14 @@ def _same_solve(a, b, rtol=1e-12):
 
 
 @pytest.mark.parametrize("opts", [
-    {},                                                 # one batch, re-check on (kept lists)
+    {},                                                 # one batch, re-check on
     {"views_per_batch": 3},                             # three batches
     {"views_per_batch": 2, "recheck_margin": -1.0},     # no re-check
     {"views_per_batch": 3, "coverage": 1},              # 3-sigma coverage
     {"record_precision": 3},                            # reduced-precision records (FS_F16)
+    # every Gaussian re-checked after each replay: the re-check's full-depth
+    # lists outgrow the main pass's, on a context of their own
+    {"views_per_batch": 3, "recheck_margin": 10.0},
 ])
 def test_captured_solve_replays_the_solve(fsb, tiny, opts):
     import torch
