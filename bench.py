@@ -283,7 +283,7 @@ def timed_solves(fsb, solver, w, dmasks, steps, warmup, flush, stream, dev):
     torch.cuda.synchronize(dev)
     ms, sums = [], {"blend_ms": 0.0, "blend_launches": 0, "list_entries": 0,
                     "staged_entries": 0, "rechecked": 0, "recheck_pairs": 0,
-                    "kernel_launches": 0}
+                    "kernel_launches": 0, "stage_ms": [0.0] * len(fsb.STAGES)}
     for _ in range(steps):
         flush.fill_(1)                       # evict the previous step's data from L2
         e0 = torch.cuda.Event(enable_timing=True)
@@ -294,9 +294,23 @@ def timed_solves(fsb, solver, w, dmasks, steps, warmup, flush, stream, dev):
         st = fsb.fs_synchronize(solver.ctx, stream.cuda_stream)
         ms.append(e0.elapsed_time(e1))
         for k in sums:
-            sums[k] += getattr(st, k)
+            if k == "stage_ms":
+                for i in range(len(sums[k])):
+                    sums[k][i] += st.stage_ms[i]
+            else:
+                sums[k] += getattr(st, k)
     torch.cuda.synchronize(dev)
     return ms, sums, out
+
+
+def stages_of(fsb, sums, steps):
+    """Device time per stage and step (CUDA events on the stream each stage
+    runs on; the next view batch's projection overlaps the current batch on a
+    side stream, so the stages can add up to more than the step)."""
+    out = {name: round(sums["stage_ms"][i] / max(1, steps), 4)
+           for i, name in enumerate(fsb.STAGES)}
+    out["note"] = "per-stage device time; overlapping stages make the sum exceed the step"
+    return out
 
 
 def census_pairs_of(fsb, w, args, local_rank, precision, dmasks, stream):
@@ -501,6 +515,7 @@ def run_flashsplat(args, rank, world, local_rank):
                                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                       "wall_s_timed": t_wall}),
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "clocks": clk,
+        "stages_ms_per_step": stages_of(fsb, sums, args.steps),
         "gamma_resolve": gamma_resolve,
         "near_tie_recheck": {"margin_below": (args.recheck_margin if args.recheck_margin > 0 else
                                               1e-4 if args.recheck_margin == 0 else None),
@@ -632,6 +647,7 @@ def measure_multi(fsb, args, local_rank, dev, stream, flush, n_sm, sm_clk):
                          "evaluated_pairs_per_step": int(cst.pairs),
                          "blend_ms_per_step": blend_ms,
                          "blend_share_of_step": sums["blend_ms"] / max(total, 1e-9)},
+            "stages_ms_per_step": stages_of(fsb, sums, steps),
             "list_entries_per_step": sums["list_entries"] // steps,
             "near_tie_recheck_gaussians_per_step": sums["rechecked"] // steps}
 

@@ -75,7 +75,7 @@ typedef struct fs_scene fs_scene;
 /* Context options.  Zero-initialise and set what you need; 0 = default. */
 typedef struct fs_options {
   int32_t views_per_batch;  /* views binned and blended per launch group (default 50, at most 64) */
-  int32_t time_stages;      /* non-zero: time every blend launch with CUDA events */
+  int32_t time_stages;      /* non-zero: time every stage (FS_STAGE_*) with CUDA events */
   int32_t depth_chunks;     /* front-to-back binning chunks per batch (default 6, 1 = off) */
   /* fs_solve re-evaluates in FP64 every Gaussian whose FP32 decision margin
    * (see fs_assign) is below this value (default 1e-4 when 0; negative = off).
@@ -147,7 +147,7 @@ typedef struct fs_stats {
   int64_t bad_labels;      /* pixels whose label was outside [0, E) (skipped) */
   int64_t pairs;           /* (pixel, Gaussian) pairs evaluated by the blend (census only) */
   int64_t kernel_launches; /* kernels launched by the library */
-  double blend_ms;         /* summed blend time (fs_options.time_stages), else 0 */
+  double blend_ms;         /* summed blend time (= stage_ms[FS_STAGE_BLEND]) */
   int64_t blend_launches;  /* blend launches timed */
   int64_t staged_entries;  /* list entries the blend staged before its tiles saturated */
   int64_t rechecked;       /* Gaussians re-evaluated in FP64 by fs_solve */
@@ -159,7 +159,28 @@ typedef struct fs_stats {
   int64_t census_steps;    /* blend: list-staging steps of a block (census only) */
   int64_t census_rounds_mixed; /* blend: rounds of warps whose pixels carry more
                               than one label (census only) */
+  double stage_ms[8];      /* summed device time per stage, indexed by FS_STAGE_*
+                              (fs_options.time_stages, uncaptured work), else 0 */
 } fs_stats;
+
+/* Stages of a solve timed under fs_options.time_stages (fs_stats.stage_ms):
+ * the projection of every Gaussian into a view batch, the batch's depth
+ * sort with its tie fix, the pixel-state set-up, the tile binning of each
+ * depth chunk, its tile sort and ranges, the blend, the near-tie re-check,
+ * and the assignment with the table's rounding.  A batch projected on the
+ * side stream while the previous batch blends is timed on that stream, so
+ * the stages can add up to more than the solve. */
+enum {
+  FS_STAGE_PROJECT = 0,
+  FS_STAGE_DEPTH_SORT = 1,
+  FS_STAGE_PIXEL_STATE = 2,
+  FS_STAGE_BINNING = 3,
+  FS_STAGE_TILE_SORT = 4,
+  FS_STAGE_BLEND = 5,
+  FS_STAGE_RECHECK = 6,
+  FS_STAGE_ASSIGN = 7,
+  FS_NUM_STAGES = 8
+};
 
 /* Outputs of fs_solve.  Any pointer may be NULL to skip that output. */
 typedef struct fs_result {

@@ -183,8 +183,10 @@ struct fs_ctx {
   int depth_chunks = 6;  // front-to-back chunks per batch (sizes 1/32, 1/32, 1/16, ..., 1/2)
   int n_sm = 0;
   bool time_stages = false;
-  std::vector<cudaEvent_t> events;  // (start, stop) pairs around blend launches
+  std::vector<cudaEvent_t> events;  // (start, stop) pairs around timed stages
+  std::vector<int> event_stage;     // the stage (FS_STAGE_*) of each pair
   size_t events_used = 0;
+  bool stage_outer = false;         // a stage holding others (the re-check) is open
   // workspace
   DevBuf views, rec, foot, cnt, key_a, val_a, key_b, val_b, offs, ccnt, dlo, state, sat, subsat;
   DevBuf lk_a, lv_a, lk_b, lv_b, ranges, sort_tmp, scan_tmp, total, counters;
@@ -497,6 +499,31 @@ fs_status stage_masks(fs_ctx* c, const fs_camera* cams, int32_t V, const void* c
 }
 
 // The view parameters of views [v0, v0 + nb), written to the host array vh.
+// fs_options.time_stages (work that is not being captured): an event pair
+// around one stage's launches on `strm`.  stage_begin gives the pair's index
+// (-1 when not timing); stage_end closes the pair on the same stream.
+fs_status stage_begin(fs_ctx* c, int stage, cudaStream_t strm, bool capturing, int* idx) {
+  *idx = -1;
+  if (!c->time_stages || capturing || c->stage_outer) return FS_OK;
+  while (c->events.size() < c->events_used + 2) {
+    cudaEvent_t e;
+    FS_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+    c->events.push_back(e);
+  }
+  const size_t pair = c->events_used / 2;
+  if (c->event_stage.size() <= pair) c->event_stage.resize(pair + 1);
+  c->event_stage[pair] = stage;
+  *idx = static_cast<int>(c->events_used);
+  c->events_used += 2;
+  FS_CUDA(cudaEventRecord(c->events[*idx], strm), "cudaEventRecord");
+  return FS_OK;
+}
+
+fs_status stage_end(fs_ctx* c, int idx, cudaStream_t strm) {
+  if (idx >= 0) FS_CUDA(cudaEventRecord(c->events[idx + 1], strm), "cudaEventRecord");
+  return FS_OK;
+}
+
 struct BatchLayout {
   int total_tiles = 0;
   int max_tiles = 0;
@@ -631,10 +658,13 @@ fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
     const size_t cap_bytes = std::min(c->lk_a.bytes, val_dst->bytes);
     const uint32_t capacity = static_cast<uint32_t>(std::min<size_t>(cap_bytes / 4, 0x7FFFFFFFu));
     c->stats.kernel_launches += 1;
+    int tb = -1;
+    FS_TRY(stage_begin(c, FS_STAGE_BINNING, stream, false, &tb));
     FS_CUDA(fs::launch_bin_fused(p0, n_pos, n, vd, sorted_val, P.foot, sat,
                                  c->lk_a.as<uint32_t>(), val_dst->as<uint32_t>(), capacity,
                                  c->lb_tmp.p, c->total.as<uint32_t>(), ctr, stream),
             "binning");
+    FS_TRY(stage_end(c, tb, stream));
     FS_TRY(read_total(c, stream, &I));
     if (I >= (static_cast<int64_t>(1) << 31))
       return fail(FS_UNSUPPORTED, "%lld list entries in one chunk; use fewer views per batch",
@@ -651,6 +681,8 @@ fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
   FS_TRY(c->sort_tmp.ensure(fs::radix_temp_bytes(std::max<int64_t>(I, kcap)), "sort temp"));
   c->stats.kernel_launches += 1 + radix_launches(I, tile_bits);
   bool alt2 = false;
+  int tt = -1;
+  FS_TRY(stage_begin(c, FS_STAGE_TILE_SORT, stream, false, &tt));
   FS_CUDA(fs::radix_sort_pairs(c->lk_a.as<uint32_t>(), val_dst->as<uint32_t>(),
                                c->lk_b.as<uint32_t>(), c->lv_b.as<uint32_t>(), I, tile_bits,
                                c->sort_tmp.p, &alt2, stream),
@@ -661,6 +693,7 @@ fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
                             cudaMemcpyDeviceToDevice, stream),
             "list copy");
   FS_CUDA(fs::launch_ranges(I, lkey, ranges_dst, stream), "ranges");
+  FS_TRY(stage_end(c, tt, stream));
   return FS_OK;
 }
 
@@ -810,10 +843,13 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     FS_CUDA(cudaMemsetAsync(krq, 0xFF, 4, strm), "key range");
     FS_CUDA(cudaMemsetAsync(krq + 1, 0, 8, strm), "key range");
     c->stats.kernel_launches += 2;
+    int tp = -1;
+    FS_TRY(stage_begin(c, FS_STAGE_PROJECT, strm, plan != nullptr, &tp));
     FS_CUDA(fs::launch_project(n, nbb, pr.vd, s->pos_op.as<float4>(), s->cov.as<float4>(),
                                PP.rec, PP.rec16, PP.foot, PP.cnt, pr.key, pr.val, PP.dlo, krq,
                                strm),
             "project");
+    FS_TRY(stage_end(c, tp, strm));
     if (PP.dkey)
       FS_CUDA(cudaMemcpyAsync(PP.dkey, pr.key, static_cast<size_t>(nbb) * n * 4,
                               cudaMemcpyDeviceToDevice, strm),
@@ -873,6 +909,8 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     if (record) record->key_bits[b] = key_bits;
     c->stats.kernel_launches += radix_launches(k_total, key_bits);
     bool alt = false;
+    int td = -1;
+    FS_TRY(stage_begin(c, FS_STAGE_DEPTH_SORT, stream, plan != nullptr, &td));
     FS_CUDA(fs::radix_sort_pairs(pr.key, pr.val, pr.key_alt, pr.val_alt, k_total, key_bits,
                                  c->sort_tmp.p, &alt, stream, kmin, span, nullptr,
                                  plan ? krd : nullptr),
@@ -881,6 +919,7 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
     uint32_t* sorted_val = alt ? pr.val_alt : pr.val;
     FS_CUDA(fs::launch_depth_tie_fix(k_total, n, sorted_key, sorted_val, P.dlo, stream),
             "depth ties");
+    FS_TRY(stage_end(c, td, stream));
     if (overlap && b + 1 < batches) {
       // batch b + 1's buffers (the other parity) were last read by batch
       // b - 1's chunks, which `stream` has passed here
@@ -889,11 +928,14 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
       FS_TRY(launch_prologue(b + 1, c->side));
     }
     uint64_t* subsat = c->subsat.as<uint64_t>();
+    int ts = -1;
+    FS_TRY(stage_begin(c, FS_STAGE_PIXEL_STATE, stream, plan != nullptr, &ts));
     FS_CUDA(cudaMemsetAsync(sat, 0, sat_bytes, stream), "tile flags clear");
     FS_CUDA(cudaMemsetAsync(subsat, 0, subsat_bytes, stream), "sub-tile flags clear");
     FS_CUDA(fs::launch_state_init(vd, nb, max_tiles, E, mask_dtype, state, sat, subsat, ctr,
                                   stream),
             "pixel state");
+    FS_TRY(stage_end(c, ts, stream));
     c->stats.views += nb;
     c->stats.pixels += L.pixels;
     if (keep) {  // the last slot of every chunk but the last (0xFFFFFFFF: empty chunk)
@@ -944,23 +986,13 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
       if (record) record->entries[pi] = I;
       p0 = p1;
       if (I == 0) continue;
-      cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-      if (c->time_stages && !plan) {
-        while (c->events.size() < c->events_used + 2) {
-          cudaEvent_t e;
-          FS_CUDA(cudaEventCreate(&e), "cudaEventCreate");
-          c->events.push_back(e);
-        }
-        ev0 = c->events[c->events_used];
-        ev1 = c->events[c->events_used + 1];
-        c->events_used += 2;
-        FS_CUDA(cudaEventRecord(ev0, stream), "cudaEventRecord");
-      }
+      int tb = -1;
+      FS_TRY(stage_begin(c, FS_STAGE_BLEND, stream, plan != nullptr, &tb));
       FS_CUDA(fs::launch_blend(vd, nb, max_tiles, ranges_dst, val_dst->as<uint32_t>(), P.rec,
                                P.rec16, n, E, mask_dtype, table, table_dtype, state, sat, subsat,
                                satc, ci, ctr, c->census, stream),
               "blend");
-      if (ev1) FS_CUDA(cudaEventRecord(ev1, stream), "cudaEventRecord");
+      FS_TRY(stage_end(c, tb, stream));
     }
   }
   c->kl_valid = keep;
@@ -1377,13 +1409,23 @@ fs_status fs_solve(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t 
     FS_TRY(c->margin_tmp.ensure(nn * 4, "margins"));
     margin = c->margin_tmp.as<float>();
   }
+  int ta = -1;
+  FS_TRY(stage_begin(c, FS_STAGE_ASSIGN, st, false, &ta));
   if (bits || label || margin) {
     FS_CUDA(fs::launch_assign(table, FS_F64, n, E, gamma, bits, label, margin, st), "assign");
     if (n > 0) c->stats.kernel_launches += 1;
   }
-  if (recheck)
-    FS_TRY(recheck_impl(c, s, cams, V, mask_dtype, E, gamma, table, FS_F64, bits, label, margin,
-                        keep, st));
+  FS_TRY(stage_end(c, ta, st));
+  if (recheck) {
+    int tr = -1;
+    FS_TRY(stage_begin(c, FS_STAGE_RECHECK, st, false, &tr));
+    c->stage_outer = tr >= 0;  // its binning and sorts count as re-check time
+    const fs_status rs = recheck_impl(c, s, cams, V, mask_dtype, E, gamma, table, FS_F64, bits,
+                                      label, margin, keep, st);
+    c->stage_outer = false;
+    FS_TRY(rs);
+    FS_TRY(stage_end(c, tr, st));
+  }
   // the caller's table: rounded once to FP32, or the FP64 sums themselves
   const int64_t count = n * static_cast<int64_t>(E);
   const void* result = table;
@@ -1394,8 +1436,11 @@ fs_status fs_solve(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t 
       dst = c->table32_tmp.as<float>();
     }
     c->stats.kernel_launches += count > 0 ? 1 : 0;
+    int tr = -1;
+    FS_TRY(stage_begin(c, FS_STAGE_ASSIGN, st, false, &tr));
     FS_CUDA(fs::launch_round_table(count, static_cast<const double*>(table), dst, st),
             "table rounding");
+    FS_TRY(stage_end(c, tr, st));
     result = dst;
   } else if (out->table && dev_out && table != out->table) {
     FS_CUDA(cudaMemcpyAsync(out->table, table, tbytes, cudaMemcpyDeviceToDevice, st),
@@ -1611,6 +1656,7 @@ fs_status fs_graph_launch(fs_graph* g, void* stream) {
   if (g->recheck) {
     fs_ctx* rc = g->rc;
     rc->stats = fs_stats{};
+    rc->events_used = 0;
     FS_CUDA(cudaMemsetAsync(rc->counters.p, 0, rc->counters.bytes, st), "counters clear");
     FS_TRY(recheck_impl(rc, g->s, g->cams.data(), V, g->mask_dtype, g->E, g->gamma, g->table,
                         FS_F64, g->bits, g->label, g->margin, false, st));
@@ -1720,14 +1766,17 @@ fs_status fs_synchronize(fs_ctx* c, void* stream, fs_stats* stats) {
     return fail(FS_UNSUPPORTED, "captured solve: the inputs outgrew the capture's plan (%llu "
                 "list(s) over capacity, %llu depth sort(s) short of bits); capture again",
                 ch[fs::kGraphOverflow], ch[fs::kGraphKeyRange]);
-  double ms = 0.0;
+  int64_t blends = 0;
+  for (int k = 0; k < FS_NUM_STAGES; ++k) c->stats.stage_ms[k] = 0.0;
   for (size_t k = 0; k + 1 < c->events_used; k += 2) {
     float t = 0.f;
     FS_CUDA(cudaEventElapsedTime(&t, c->events[k], c->events[k + 1]), "cudaEventElapsedTime");
-    ms += t;
+    const int stage = c->event_stage[k / 2];
+    c->stats.stage_ms[stage] += t;
+    if (stage == FS_STAGE_BLEND) ++blends;
   }
-  c->stats.blend_ms = ms;
-  c->stats.blend_launches = static_cast<int64_t>(c->events_used / 2);
+  c->stats.blend_ms = c->stats.stage_ms[FS_STAGE_BLEND];
+  c->stats.blend_launches = blends;
   if (stats) *stats = c->stats;
   return FS_OK;
 }

@@ -464,8 +464,11 @@ __device__ __forceinline__ void fix_tie_run(int64_t k, int64_t n_total, const Sl
   }
 }
 
-// Each thread screens four consecutive positions (one 16-byte key load when
-// the keys are 16-byte aligned) for the start of an equal-key run.
+// Each thread screens four consecutive positions for the start of a run of
+// equal keys within one view.  Equal keys of different views are common (a
+// batch holds many views of the same depths), so the screen compares the
+// views of neighbours from one 16-byte key load and one 16-byte value load
+// (when both arrays are 16-byte aligned) before a run is walked.
 __global__ void depth_tie_fix_kernel(int64_t n_total, int64_t n, const uint32_t* __restrict__ key,
                                      uint32_t* __restrict__ val,
                                      const uint32_t* __restrict__ depth_lo,
@@ -474,7 +477,10 @@ __global__ void depth_tie_fix_kernel(int64_t n_total, int64_t n, const uint32_t*
   const int64_t k0 = 4 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
   if (k0 + 1 >= n_total) return;
   uint32_t t[5];  // keys k0 .. k0 + 4 (0xFFFFFFFF past the end: never a run)
-  if (k0 + 4 <= n_total && (reinterpret_cast<uintptr_t>(key) & 15u) == 0) {
+  uint32_t w[5];  // their values (slots), where a key is present
+  const bool full = k0 + 4 <= n_total &&
+                    ((reinterpret_cast<uintptr_t>(key) | reinterpret_cast<uintptr_t>(val)) & 15u) == 0;
+  if (full) {
     const uint4 q = *reinterpret_cast<const uint4*>(key + k0);
     t[0] = q.x;
     t[1] = q.y;
@@ -485,10 +491,28 @@ __global__ void depth_tie_fix_kernel(int64_t n_total, int64_t n, const uint32_t*
     for (int i = 0; i < 4; ++i) t[i] = k0 + i < n_total ? key[k0 + i] : 0xFFFFFFFFu;
   }
   t[4] = k0 + 4 < n_total ? key[k0 + 4] : 0xFFFFFFFFu;
+  bool any = false;  // an equal neighbour somewhere among the four
+#pragma unroll
+  for (int i = 0; i < 4; ++i) any = any || (t[i] != 0xFFFFFFFFu && t[i + 1] == t[i]);
+  if (!any) return;
+  if (full) {
+    const uint4 q = *reinterpret_cast<const uint4*>(val + k0);
+    w[0] = q.x;
+    w[1] = q.y;
+    w[2] = q.z;
+    w[3] = q.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = k0 + i < n_total ? val[k0 + i] : 0u;
+  }
+  w[4] = k0 + 4 < n_total ? val[k0 + 4] : 0u;
   const SlotView view_of(n);
+  uint32_t vw[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) vw[i] = view_of(w[i]);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    if (t[i] != 0xFFFFFFFFu && t[i + 1] == t[i] && k0 + i + 1 < n_total)
+    if (t[i] != 0xFFFFFFFFu && t[i + 1] == t[i] && vw[i + 1] == vw[i] && k0 + i + 1 < n_total)
       fix_tie_run(k0 + i, n_total, view_of, t[i], key, val, depth_lo);
   }
 }

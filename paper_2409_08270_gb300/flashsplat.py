@@ -66,7 +66,13 @@ class fs_stats(ctypes.Structure):
                 ("staged_entries", ctypes.c_int64), ("rechecked", ctypes.c_int64),
                 ("recheck_pairs", ctypes.c_int64), ("recheck_rebinned", ctypes.c_int64),
                 ("census_pairs", ctypes.c_int64), ("census_rounds", ctypes.c_int64),
-                ("census_steps", ctypes.c_int64), ("census_rounds_mixed", ctypes.c_int64)]
+                ("census_steps", ctypes.c_int64), ("census_rounds_mixed", ctypes.c_int64),
+                ("stage_ms", ctypes.c_double * 8)]
+
+
+# indices of fs_stats.stage_ms (FS_STAGE_*)
+STAGES = ("project", "depth_sort", "pixel_state", "binning", "tile_sort", "blend", "recheck",
+          "assign")
 
 
 class fs_result(ctypes.Structure):
