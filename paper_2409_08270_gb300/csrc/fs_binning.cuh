@@ -33,6 +33,18 @@ __device__ __forceinline__ uint32_t count_free(const uint64_t* __restrict__ sat,
   return c;
 }
 
+// Whether any tile id in [a, b] is unsaturated.
+__device__ __forceinline__ bool any_free(const uint64_t* __restrict__ sat, int a, int b) {
+  const int wa = a >> 6, wb = b >> 6;
+  for (int w = wa; w <= wb; ++w) {
+    uint64_t m = ~0ull;
+    if (w == wa) m &= ~0ull << (a & 63);
+    if (w == wb) m &= ~0ull >> (63 - (b & 63));
+    if (~sat[w] & m) return true;
+  }
+  return false;
+}
+
 // Hardware square root (relative error ~2^-23): far inside the one-pixel
 // margin of the spans below, and the same instruction wherever a span is
 // evaluated, so every kernel that bins gets identical spans.

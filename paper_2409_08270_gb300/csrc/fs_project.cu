@@ -574,19 +574,47 @@ __device__ __forceinline__ uint32_t job_free(const RowJob& jb, int64_t n,
   return count_free(sat, *a, *b);
 }
 
-__device__ __forceinline__ void lane_rows(int64_t j, int64_t n_pos, int64_t p0,
+// The lane's sorted position j (if < n_pos): its slot g, first tile row ty0
+// and number of tile rows -- none when every tile of its footprint's
+// bounding box is already saturated, as is the case for most slots of later
+// depth chunks.  Over the footprint x(dy) - mx stays within +-hx, hx^2 =
+// syr (a^2 + b2); the box takes one more pixel on each side than the rows'
+// spans, so it holds every span whatever their rounding.
+__device__ __forceinline__ void lane_rows(int64_t j, int64_t n_pos, int64_t p0, int64_t n,
+                                          const ViewParams* __restrict__ views,
                                           const uint32_t* __restrict__ sorted_val,
-                                          const Footprint* __restrict__ foot, uint32_t* g,
+                                          const Footprint* __restrict__ foot,
+                                          const uint64_t* __restrict__ sat, uint32_t* g,
                                           int* ty0, uint32_t* nrows) {
   *g = 0;
   *ty0 = 0;
   *nrows = 0;
-  if (j < n_pos) {
-    *g = sorted_val[p0 + j];
-    int t0, t1;
-    footprint_rows(foot[*g], &t0, &t1);
-    *ty0 = t0;
-    *nrows = static_cast<uint32_t>(max(0, t1 - t0 + 1));
+  if (j >= n_pos) return;
+  const uint32_t gg = sorted_val[p0 + j];
+  *g = gg;
+  const Footprint f = foot[gg];
+  int t0, t1;
+  footprint_rows(f, &t0, &t1);
+  *ty0 = t0;
+  if (t1 < t0) return;
+  const ViewParams& vp = views[gg / static_cast<uint32_t>(n)];
+  const float hx = sqrtf(f.syr * fmaf(f.a, f.a, f.b2));
+  const float x0 = fmaxf(ceilf(f.mx - hx - 2.5f), 0.f);
+  const float x1 = fminf(floorf(f.mx + hx + 1.5f), static_cast<float>(vp.width - 1));
+  if (!(x0 <= x1)) return;
+  int c0 = static_cast<int>(x0) / kTile, c1 = static_cast<int>(x1) / kTile;
+  if (vp.cols) {  // 3-sigma coverage
+    const uint32_t c = vp.cols[gg];
+    c0 = max(c0, static_cast<int>(c & 0xFFFFu));
+    c1 = min(c1, static_cast<int>(c >> 16));
+    if (c0 > c1) return;
+  }
+  for (int ty = t0; ty <= t1; ++ty) {
+    const int base = vp.tile_base + ty * vp.tiles_x;
+    if (any_free(sat, base + c0, base + c1)) {
+      *nrows = static_cast<uint32_t>(t1 - t0 + 1);
+      return;
+    }
   }
 }
 
@@ -610,7 +638,7 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t g, nrows;
   int ty0;
-  lane_rows(j, n_pos, p0, sorted_val, foot, &g, &ty0, &nrows);
+  lane_rows(j, n_pos, p0, n, views, sorted_val, foot, sat, &g, &ty0, &nrows);
   const uint32_t incl = warp_incl_scan(nrows, lane);
   const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
   s_cnt[warp][lane] = 0;
@@ -664,7 +692,7 @@ __global__ void __launch_bounds__(256) emit_kernel(
   const int lane = threadIdx.x & 31;
   uint32_t g, nrows;
   int ty0;
-  lane_rows(j, n_pos, p0, sorted_val, foot, &g, &ty0, &nrows);
+  lane_rows(j, n_pos, p0, n, views, sorted_val, foot, sat, &g, &ty0, &nrows);
   const uint32_t incl = warp_incl_scan(nrows, lane);
   const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
   // the warp's output range [wbeg, wend)
@@ -728,7 +756,7 @@ __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
   const int64_t j = static_cast<int64_t>(vb) * blockDim.x + threadIdx.x;
   uint32_t g, nrows;
   int ty0;
-  lane_rows(j, n_pos, p0, sorted_val, foot, &g, &ty0, &nrows);
+  lane_rows(j, n_pos, p0, n, views, sorted_val, foot, sat, &g, &ty0, &nrows);
   const uint32_t incl = warp_incl_scan(nrows, lane);
   const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
   // count; the first kStash rounds' jobs are kept in registers for the emission
