@@ -25,7 +25,7 @@ constexpr float kHalfLog2eLo = static_cast<float>(kHalfLog2e - static_cast<doubl
 // with m = floor((2^32 - 1) / n), umulhi(g, m) is floor(g / n) or one less.
 struct SlotView {
   uint32_t n, m;
-  __device__ __forceinline__ explicit SlotView(int64_t n_)
+  __host__ __device__ __forceinline__ explicit SlotView(int64_t n_)
       : n(static_cast<uint32_t>(n_)), m(0xFFFFFFFFu / static_cast<uint32_t>(n_)) {}
   __device__ __forceinline__ uint32_t operator()(uint32_t g) const {
     uint32_t q = __umulhi(g, m);

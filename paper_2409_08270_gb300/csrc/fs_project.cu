@@ -556,14 +556,14 @@ __device__ __forceinline__ RowJob row_job(int r, int R, uint32_t incl_rows, uint
 }
 
 // Unsaturated tiles of one job's row: [a, b] (global ids) and their number.
-__device__ __forceinline__ uint32_t job_free(const RowJob& jb, int64_t n,
+__device__ __forceinline__ uint32_t job_free(const RowJob& jb, SlotView sv,
                                              const ViewParams* __restrict__ views,
                                              const Footprint* __restrict__ foot,
                                              const uint64_t* __restrict__ sat, int* a, int* b) {
   *a = 0;
   *b = -1;
   if (!jb.ok) return 0;
-  const int v = static_cast<int>(jb.g / static_cast<uint32_t>(n));
+  const int v = static_cast<int>(sv(jb.g));
   const Footprint f = foot[jb.g];
   int tx0, tx1;
   if (!row_span(f, jb.row, views[v].width, &tx0, &tx1)) return 0;
@@ -580,7 +580,7 @@ __device__ __forceinline__ uint32_t job_free(const RowJob& jb, int64_t n,
 // depth chunks.  Over the footprint x(dy) - mx stays within +-hx, hx^2 =
 // syr (a^2 + b2); the box takes one more pixel on each side than the rows'
 // spans, so it holds every span whatever their rounding.
-__device__ __forceinline__ void lane_rows(int64_t j, int64_t n_pos, int64_t p0, int64_t n,
+__device__ __forceinline__ void lane_rows(int64_t j, int64_t n_pos, int64_t p0, SlotView sv,
                                           const ViewParams* __restrict__ views,
                                           const uint32_t* __restrict__ sorted_val,
                                           const Footprint* __restrict__ foot,
@@ -597,7 +597,7 @@ __device__ __forceinline__ void lane_rows(int64_t j, int64_t n_pos, int64_t p0, 
   footprint_rows(f, &t0, &t1);
   *ty0 = t0;
   if (t1 < t0) return;
-  const ViewParams& vp = views[gg / static_cast<uint32_t>(n)];
+  const ViewParams& vp = views[sv(gg)];
   const float hx = sqrtf(f.syr * fmaf(f.a, f.a, f.b2));
   const float x0 = fmaxf(ceilf(f.mx - hx - 2.5f), 0.f);
   const float x1 = fminf(floorf(f.mx + hx + 1.5f), static_cast<float>(vp.width - 1));
@@ -628,7 +628,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 }
 
 __global__ void __launch_bounds__(256) chunk_count_kernel(
-    int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
+    int64_t p0, int64_t n_pos, SlotView sv, const ViewParams* __restrict__ views,
     const uint32_t* __restrict__ sorted_val,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
     uint32_t* __restrict__ out_cnt) {
@@ -638,7 +638,7 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t g, nrows;
   int ty0;
-  lane_rows(j, n_pos, p0, n, views, sorted_val, foot, sat, &g, &ty0, &nrows);
+  lane_rows(j, n_pos, p0, sv, views, sorted_val, foot, sat, &g, &ty0, &nrows);
   const uint32_t incl = warp_incl_scan(nrows, lane);
   const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
   s_cnt[warp][lane] = 0;
@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(
   for (int r0 = 0; r0 < R; r0 += 32) {
     const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
     int a, b;
-    const uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
+    const uint32_t fr = job_free(jb, sv, views, foot, sat, &a, &b);
     if (jb.ok && fr) atomicAdd(&s_cnt[warp][jb.owner], fr);
   }
   __syncwarp();
@@ -681,7 +681,7 @@ __device__ __forceinline__ uint32_t emit_free(const uint64_t* __restrict__ sat, 
 // offsets[first] (the exclusive scan of chunk_cnt); row r's entries start at
 // that base plus the free tiles of all earlier rows of the warp.
 __global__ void __launch_bounds__(256) emit_kernel(
-    int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
+    int64_t p0, int64_t n_pos, SlotView sv, const ViewParams* __restrict__ views,
     const uint32_t* __restrict__ sorted_val, const uint32_t* __restrict__ offsets,
     const uint32_t* __restrict__ chunk_cnt,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(256) emit_kernel(
   const int lane = threadIdx.x & 31;
   uint32_t g, nrows;
   int ty0;
-  lane_rows(j, n_pos, p0, n, views, sorted_val, foot, sat, &g, &ty0, &nrows);
+  lane_rows(j, n_pos, p0, sv, views, sorted_val, foot, sat, &g, &ty0, &nrows);
   const uint32_t incl = warp_incl_scan(nrows, lane);
   const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
   // the warp's output range [wbeg, wend)
@@ -709,7 +709,7 @@ __global__ void __launch_bounds__(256) emit_kernel(
   for (int r0 = 0; r0 < R; r0 += 32) {
     const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
     int a, b;
-    const uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
+    const uint32_t fr = job_free(jb, sv, views, foot, sat, &a, &b);
     const uint32_t sc = warp_incl_scan(fr, lane);
     const uint32_t o = wbeg + carry + sc - fr;
     if (fr) emit_free(sat, a, b, jb.g, out_key, out_val, o, min(o + fr, wend));
@@ -735,7 +735,7 @@ constexpr unsigned long long kLbPrefix = 2ull << 32;  // word holds the inclusiv
 
 template <bool kDeviceRange>
 __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
-    int64_t p0, int64_t n_pos, int64_t n, const ViewParams* __restrict__ views,
+    int64_t p0, int64_t n_pos, SlotView sv, const ViewParams* __restrict__ views,
     const uint32_t* __restrict__ sorted_val,
     const Footprint* __restrict__ foot, const uint64_t* __restrict__ sat,
     uint32_t* __restrict__ out_key, uint32_t* __restrict__ out_val, uint32_t capacity,
@@ -756,7 +756,7 @@ __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
   const int64_t j = static_cast<int64_t>(vb) * blockDim.x + threadIdx.x;
   uint32_t g, nrows;
   int ty0;
-  lane_rows(j, n_pos, p0, n, views, sorted_val, foot, sat, &g, &ty0, &nrows);
+  lane_rows(j, n_pos, p0, sv, views, sorted_val, foot, sat, &g, &ty0, &nrows);
   const uint32_t incl = warp_incl_scan(nrows, lane);
   const int R = static_cast<int>(__shfl_sync(0xffffffffu, incl, 31));
   // count; the first kStash rounds' jobs are kept in registers for the emission
@@ -772,7 +772,7 @@ __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
     st_g[k] = 0;
     if (32 * k < R) {  // R is the same for the whole warp
       const RowJob jb = row_job(32 * k + lane, R, incl, g, ty0);
-      const uint32_t fr = job_free(jb, n, views, foot, sat, &st_a[k], &st_b[k]);
+      const uint32_t fr = job_free(jb, sv, views, foot, sat, &st_a[k], &st_b[k]);
       st_fr[k] = fr;
       st_g[k] = jb.g;
       uint32_t sum = fr;
@@ -784,7 +784,7 @@ __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
   for (int r0 = 32 * kStash; r0 < R; r0 += 32) {
     const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
     int a, b;
-    uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
+    uint32_t fr = job_free(jb, sv, views, foot, sat, &a, &b);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fr += __shfl_xor_sync(0xffffffffu, fr, o);
     wtot += fr;
@@ -850,7 +850,7 @@ __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
   for (int r0 = 32 * kStash; r0 < R; r0 += 32) {
     const RowJob jb = row_job(r0 + lane, R, incl, g, ty0);
     int a, b;
-    const uint32_t fr = job_free(jb, n, views, foot, sat, &a, &b);
+    const uint32_t fr = job_free(jb, sv, views, foot, sat, &a, &b);
     const uint32_t sc = warp_incl_scan(fr, lane);
     const uint32_t o = wbeg + carry + sc - fr;
     if (fr && o < capacity)
@@ -942,7 +942,7 @@ cudaError_t launch_chunk_count(int64_t p0, int64_t n_pos, int64_t n, const ViewP
   const int threads = 256;
   const int64_t blocks = (n_pos + threads - 1) / threads;
   chunk_count_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-      p0, n_pos, n, views, sorted_val, foot, sat, out_cnt);
+      p0, n_pos, SlotView(n > 0 ? n : 1), views, sorted_val, foot, sat, out_cnt);
   return cudaGetLastError();
 }
 
@@ -955,7 +955,7 @@ cudaError_t launch_emit(int64_t p0, int64_t n_pos, int64_t n, const ViewParams* 
   const int threads = 256;
   const int64_t blocks = (n_pos + threads - 1) / threads;
   emit_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-      p0, n_pos, n, views, sorted_val, offsets, chunk_cnt, foot, sat, out_key, out_val,
+      p0, n_pos, SlotView(n > 0 ? n : 1), views, sorted_val, offsets, chunk_cnt, foot, sat, out_key, out_val,
       counters);
   return cudaGetLastError();
 }
@@ -976,11 +976,11 @@ cudaError_t launch_bin_fused(int64_t p0, int64_t n_pos, int64_t n, const ViewPar
   if (e != cudaSuccess) return e;
   if (range_dev)
     bin_fused_kernel<true><<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-        p0, n_pos, n, views, sorted_val, foot, sat, out_key, out_val, capacity, status, ticket,
+        p0, n_pos, SlotView(n > 0 ? n : 1), views, sorted_val, foot, sat, out_key, out_val, capacity, status, ticket,
         total, counters, kLookbackSpinLimit, range_dev);
   else
     bin_fused_kernel<false><<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-        p0, n_pos, n, views, sorted_val, foot, sat, out_key, out_val, capacity, status, ticket,
+        p0, n_pos, SlotView(n > 0 ? n : 1), views, sorted_val, foot, sat, out_key, out_val, capacity, status, ticket,
         total, counters, kLookbackSpinLimit, nullptr);
   return cudaGetLastError();
 }
@@ -999,7 +999,7 @@ cudaError_t launch_lookback_probe(void* lookback, uint32_t* total, unsigned long
   const uint32_t one = 1u;
   e = cudaMemcpyAsync(ticket, &one, sizeof(one), cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return e;
-  bin_fused_kernel<false><<<1, 128, 0, stream>>>(0, 1, 1, views, sorted_val, foot, sat, out_key,
+  bin_fused_kernel<false><<<1, 128, 0, stream>>>(0, 1, SlotView(1), views, sorted_val, foot, sat, out_key,
                                                  out_val, 0u, status, ticket, total, counters,
                                                  spin_limit, nullptr);
   return cudaGetLastError();
