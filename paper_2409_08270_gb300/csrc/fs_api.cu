@@ -189,6 +189,7 @@ struct fs_ctx {
   bool stage_outer = false;         // a stage holding others (the re-check) is open
   // workspace
   DevBuf views, rec, foot, cnt, key_a, val_a, key_b, val_b, offs, ccnt, dlo, state, sat, subsat;
+  DevBuf free_tab;  // the batch's per-view prefix tables of unsaturated tiles
   DevBuf lk_a, lv_a, lk_b, lv_b, ranges, sort_tmp, scan_tmp, total, counters;
   DevBuf mask_stage, table_tmp, table32_tmp, bits_tmp, label_tmp, margin_tmp;
   // near-tie re-check: resident per-view depth keys, flagged set, FP64 rows
@@ -530,12 +531,40 @@ struct BatchLayout {
   int64_t pixels = 0;
 };
 
+// Cells of the prefix tables of views [v0, v0 + nb): (tiles_x + 1) x
+// (tiles_y + 1) per view.
+int64_t free_cells(const fs_camera* cams, int32_t v0, int nb) {
+  int64_t cells = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int64_t tx = (cams[v0 + k].width + fs::kTile - 1) / fs::kTile;
+    const int64_t ty = (cams[v0 + k].height + fs::kTile - 1) / fs::kTile;
+    cells += (tx + 1) * (ty + 1);
+  }
+  return cells;
+}
+
+// Sizes the prefix tables for the largest batch of the solve once, before
+// any batch is laid out, so that no batch's tables move while another
+// batch's work is queued.
+fs_status ensure_free_tabs(fs_ctx* c, const fs_camera* cams, int32_t V, int vb) {
+  int64_t most = 1;
+  for (int32_t v0 = 0; v0 < V; v0 += vb)
+    most = std::max(most, free_cells(cams, v0, std::min(vb, V - v0)));
+  return c->free_tab.ensure(static_cast<size_t>(most) * 4, "tile prefix tables");
+}
+
 BatchLayout layout_batch(fs_ctx* c, fs::ViewParams* vh, const fs_camera* cams, int32_t v0,
                          int nb, uint32_t* cols) {
   BatchLayout L;
+  // the prefix tables, where ensure_free_tabs made room (else the binning
+  // walks the saturation bits)
+  const bool tabs = c->free_tab.bytes >= static_cast<size_t>(free_cells(cams, v0, nb)) * 4;
+  int64_t cell = 0;
   for (int k = 0; k < nb; ++k) {
     fs::fill_view(cams[v0 + k], &vh[k]);
     vh[k].cols = cols;
+    vh[k].free_tab = tabs ? c->free_tab.as<uint32_t>() + cell : nullptr;
+    cell += static_cast<int64_t>(vh[k].tiles_x + 1) * (vh[k].tiles_y + 1);
     vh[k].tile_base = L.total_tiles;
     vh[k].state_off = L.pixels;
     vh[k].mask = c->mask_dev[v0 + k];
@@ -617,7 +646,8 @@ fs_status read_total(fs_ctx* c, cudaStream_t stream, int64_t* out) {
 // read back, and the lists are sized for plan_cap entries (the capture's
 // plan); a replay that outgrows either is counted (kGraphOverflow).
 fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
-                        const fs::ViewParams* vd, const uint32_t* sorted_val, const ProjPtrs& P,
+                        const fs::ViewParams* vd, int nb, const uint32_t* sorted_val,
+                        const ProjPtrs& P,
                         const uint64_t* sat, int total_tiles, int tile_bits, int64_t kcap,
                         bool count_entries, DevBuf* val_dst, uint2* ranges_dst,
                         cudaStream_t stream, int64_t* I_out, const int64_t* range_dev = nullptr,
@@ -627,6 +657,8 @@ fs_status bin_positions(fs_ctx* c, int64_t p0, int64_t n_pos, int64_t n,
   FS_CUDA(cudaMemsetAsync(ranges_dst, 0, static_cast<size_t>(total_tiles) * 8, stream),
           "ranges clear");
   FS_TRY(c->lb_tmp.ensure(fs::bin_fused_temp_bytes(n_pos), "binning look-back"));
+  // the views' prefix tables of the tiles still unsaturated
+  FS_CUDA(fs::launch_free_tables(vd, nb, sat, stream), "tile prefix tables");
   if (range_dev) {
     uint32_t* total = c->total.as<uint32_t>();
     const uint32_t capacity = static_cast<uint32_t>(plan_cap);
@@ -769,6 +801,7 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
   c->kl_valid = false;
   if (n == 0 || V == 0) return FS_OK;
   const int vb = batch_views(c, n);
+  FS_TRY(ensure_free_tabs(c, cams, V, vb));
   if (vb < 1) return fail(FS_UNSUPPORTED, "fs_accumulate: scene too large");
   const int64_t kcap = static_cast<int64_t>(vb) * n;
   const int chunks = std::max(1, std::min(c->depth_chunks, fs::kMaxChunks));
@@ -979,7 +1012,7 @@ fs_status accumulate_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, i
         continue;
       }
       int64_t I = 0;
-      FS_TRY(bin_positions(c, p0, n_pos, n, vd, sorted_val, P, sat, total_tiles, tile_bits, kcap,
+      FS_TRY(bin_positions(c, p0, n_pos, n, vd, nb, sorted_val, P, sat, total_tiles, tile_bits, kcap,
                            !plan, val_dst, ranges_dst, stream, &I,
                            plan ? c->chunk_bnd.as<int64_t>() + ci : nullptr,
                            plan ? plan->entries[pi] : 0));
@@ -1032,7 +1065,7 @@ fs_status recheck_batch_rebin(fs_ctx* c, const fs_scene* s, int64_t n, int nb, i
   uint32_t* sorted_val = alt ? c->val_a.as<uint32_t>() : c->val_b.as<uint32_t>();
   FS_CUDA(fs::launch_depth_tie_fix(C, n, sorted_key, sorted_val, P.dlo, stream), "depth ties");
   int64_t I = 0;
-  FS_TRY(bin_positions(c, 0, C, n, vd, sorted_val, P, skip, total_tiles, tile_bits, kcap, false,
+  FS_TRY(bin_positions(c, 0, C, n, vd, nb, sorted_val, P, skip, total_tiles, tile_bits, kcap, false,
                        &c->lv_a, c->ranges.as<uint2>(), stream, &I));
   if (I == 0) return FS_OK;
   fs::RecheckLists Ls{};
@@ -1088,6 +1121,7 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
   }
 
   const int vb = batch_views(c, n);
+  FS_TRY(ensure_free_tabs(c, cams, V, vb));
   const int64_t kcap = static_cast<int64_t>(vb) * n;
   const int chunks = c->kl_chunks;
   fs::ViewParams* vh = c->views_host.as<fs::ViewParams>();
@@ -1215,6 +1249,7 @@ fs_status render_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32
     return FS_OK;
   }
   const int vb = batch_views(c, n);
+  FS_TRY(ensure_free_tabs(c, cams, V, vb));
   if (vb < 1) return fail(FS_UNSUPPORTED, "fs_render_masks: scene too large");
   const int64_t kcap = static_cast<int64_t>(vb) * n;
   FS_TRY(ensure_window(c, n, vb, V, false));
@@ -1295,7 +1330,7 @@ fs_status render_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32
       int64_t count = 0;
       FS_TRY(read_total(c, stream, &count));
       int64_t I = 0;
-      FS_TRY(bin_positions(c, 0, count, n, vd, c->rd_val.as<uint32_t>(), P,
+      FS_TRY(bin_positions(c, 0, count, n, vd, nb, c->rd_val.as<uint32_t>(), P,
                            c->sat.as<uint64_t>(), total_tiles, tile_bits, kcap, false, &c->lv_a,
                            c->ranges.as<uint2>(), stream, &I));
       FS_CUDA(fs::launch_render(vd, rod, nb, max_tiles, c->ranges.as<uint2>(),

@@ -45,6 +45,16 @@ __device__ __forceinline__ bool any_free(const uint64_t* __restrict__ sat, int a
   return false;
 }
 
+// Unsaturated tiles of rows [r0, r1] x columns [c0, c1] of a view, from its
+// prefix table (four reads).
+__device__ __forceinline__ uint32_t free_in_box(const ViewParams& vp, int r0, int r1, int c0,
+                                                int c1) {
+  const int w1 = vp.tiles_x + 1;
+  const uint32_t* t = vp.free_tab;
+  return t[(r1 + 1) * w1 + c1 + 1] - t[r0 * w1 + c1 + 1] - t[(r1 + 1) * w1 + c0] +
+         t[r0 * w1 + c0];
+}
+
 // Hardware square root (relative error ~2^-23): far inside the one-pixel
 // margin of the spans below, and the same instruction wherever a span is
 // evaluated, so every kernel that bins gets identical spans.

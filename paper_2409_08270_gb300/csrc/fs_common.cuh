@@ -53,6 +53,11 @@ struct ViewParams {
   // footprints, the tile columns the Gaussian may reach (first | last << 16);
   // written by the projection.  NULL: exact coverage.
   uint32_t* cols;
+  // Per view, the 2-D prefix sums of its unsaturated tiles for the binning's
+  // slot test: (tiles_y + 1) x (tiles_x + 1) counts, entry r * (tiles_x + 1)
+  // + c = unsaturated tiles in rows < r and columns < c, rebuilt before each
+  // binning.  NULL: the test walks the saturation bits row by row.
+  uint32_t* free_tab;
 };
 
 // Projected record of one (view, Gaussian): 4 x float4 = 64 B.

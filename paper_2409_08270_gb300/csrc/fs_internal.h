@@ -93,6 +93,10 @@ cudaError_t launch_lookback_probe(void* lookback, uint32_t* total, unsigned long
                                   const ViewParams* views, const uint32_t* sorted_val,
                                   const Footprint* foot, const uint64_t* sat, uint32_t* out_key,
                                   uint32_t* out_val, int spin_limit, cudaStream_t stream);
+// Each view's prefix table of unsaturated tiles (ViewParams::free_tab, where
+// set) from the batch's saturation bits: one block per view.
+cudaError_t launch_free_tables(const ViewParams* views, int n_views, const uint64_t* sat,
+                               cudaStream_t stream);
 cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
                           cudaStream_t stream, const uint32_t* n_dev = nullptr);
 

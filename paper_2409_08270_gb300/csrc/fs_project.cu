@@ -609,6 +609,10 @@ __device__ __forceinline__ void lane_rows(int64_t j, int64_t n_pos, int64_t p0, 
     c1 = min(c1, static_cast<int>(c >> 16));
     if (c0 > c1) return;
   }
+  if (vp.free_tab) {
+    if (free_in_box(vp, t0, t1, c0, c1)) *nrows = static_cast<uint32_t>(t1 - t0 + 1);
+    return;
+  }
   for (int ty = t0; ty <= t1; ++ty) {
     const int base = vp.tile_base + ty * vp.tiles_x;
     if (any_free(sat, base + c0, base + c1)) {
@@ -860,6 +864,39 @@ __global__ void __launch_bounds__(128, 12) bin_fused_kernel(
   if (lane == 0 && wbeg + carry != wend) atomicAdd(&counters[kBinningMismatch], 1ull);
 }
 
+// Per view of the batch (one block each), the 2-D prefix sums of its
+// unsaturated tiles: free_tab[r * (tiles_x + 1) + c] = unsaturated tiles in
+// rows < r and columns < c (row 0 and column 0 are zero).  Running sums
+// along each row, then down each column.
+__global__ void __launch_bounds__(256) free_table_kernel(const ViewParams* __restrict__ views,
+                                                         const uint64_t* __restrict__ sat) {
+  const ViewParams& vp = views[blockIdx.x];
+  uint32_t* tab = vp.free_tab;
+  if (!tab) return;
+  const int tx = vp.tiles_x, ty = vp.tiles_y, w1 = tx + 1;
+  for (int c = threadIdx.x; c < w1; c += blockDim.x) tab[c] = 0u;
+  for (int r = threadIdx.x; r < ty; r += blockDim.x) {
+    const int g0 = vp.tile_base + r * tx;
+    uint32_t* row = tab + static_cast<int64_t>(r + 1) * w1;
+    uint32_t run = 0;
+    row[0] = 0u;
+    for (int c = 0; c < tx; ++c) {
+      const int g = g0 + c;
+      run += static_cast<uint32_t>(((sat[g >> 6] >> (g & 63)) & 1ull) == 0ull);
+      row[c + 1] = run;
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x + 1; c < w1; c += blockDim.x) {
+    uint32_t acc = 0;
+    for (int r = 1; r <= ty; ++r) {
+      uint32_t* e = tab + static_cast<int64_t>(r) * w1 + c;
+      acc += *e;
+      *e = acc;
+    }
+  }
+}
+
 // [start, end) of every tile's run in the tile-sorted list.  Each thread
 // takes four consecutive entries (one 16-byte load when the list is 16-byte
 // aligned, as the library's buffers are) and the entries on either side.
@@ -1007,6 +1044,13 @@ cudaError_t launch_lookback_probe(void* lookback, uint32_t* total, unsigned long
 
 size_t bin_fused_temp_bytes(int64_t n_pos) {
   return 256 + static_cast<size_t>((n_pos + 127) / 128) * 8;
+}
+
+cudaError_t launch_free_tables(const ViewParams* views, int n_views, const uint64_t* sat,
+                               cudaStream_t stream) {
+  if (n_views <= 0) return cudaSuccess;
+  free_table_kernel<<<static_cast<unsigned>(n_views), 256, 0, stream>>>(views, sat);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ranges(int64_t n_entries, const uint32_t* key, uint2* ranges,
