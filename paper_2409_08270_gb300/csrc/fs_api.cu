@@ -595,7 +595,7 @@ struct ProjPtrs {
   uint32_t* cols;  // 3-sigma tile columns, or NULL (exact coverage)
 };
 
-ProjPtrs proj_ptrs(fs_ctx* c, bool keep, int32_t v0, int64_t n) {
+ProjPtrs proj_ptrs(const fs_ctx* c, bool keep, int32_t v0, int64_t n) {
   const int64_t off = keep ? static_cast<int64_t>(v0) * n : 0;
   return {c->compact ? nullptr : c->rec.as<fs::ProjRecord>() + off,
           c->compact ? c->rec.as<fs::CompactRecord>() + off : nullptr,
@@ -1082,11 +1082,18 @@ fs_status recheck_batch_rebin(fs_ctx* c, const fs_scene* s, int64_t n, int nb, i
 // Re-check of the Gaussians whose margin is below c->recheck_margin (see
 // fs_recheck.cu): their rows of `table` and their bits / label / margin are
 // replaced.  `margin` holds the FP32 decision's margins on entry.
+// kept_from: another context whose resident projection and kept lists the
+// re-check reads (never writes); c supplies every buffer it writes.
 fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t V,
                        int32_t mask_dtype, int32_t E, float gamma, void* table,
                        int32_t table_dtype, uint64_t* bits, int32_t* label, float* margin,
-                       bool keep, cudaStream_t stream) {
+                       bool keep, cudaStream_t stream, const fs_ctx* kept_from = nullptr) {
   const int64_t n = s->n;
+  if (kept_from && !(keep && kept_from->kl_valid)) {
+    kept_from = nullptr;  // nothing kept there: project again into c
+    keep = false;
+  }
+  const fs_ctx* K = kept_from ? kept_from : c;  // the resident projection and lists
   if (n == 0 || V == 0) return FS_OK;
   const size_t nn = static_cast<size_t>(n);
   FS_TRY(c->rk_flag.ensure(nn * 4, "re-check flags"));
@@ -1113,7 +1120,7 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
   FS_TRY(c->rk_R.ensure(rbytes, "re-check rows"));
   double* R = c->rk_R.as<double>();
   FS_CUDA(cudaMemsetAsync(R, 0, rbytes, stream), "re-check rows clear");
-  const bool kept = keep && c->kl_valid;
+  const bool kept = keep && K->kl_valid;
   double* Rb = nullptr;
   if (kept) {
     FS_TRY(c->rk_Rb.ensure(rbytes, "re-check batch rows"));
@@ -1123,13 +1130,13 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
   const int vb = batch_views(c, n);
   FS_TRY(ensure_free_tabs(c, cams, V, vb));
   const int64_t kcap = static_cast<int64_t>(vb) * n;
-  const int chunks = c->kl_chunks;
+  const int chunks = K->kl_chunks;
   fs::ViewParams* vh = c->views_host.as<fs::ViewParams>();
   unsigned long long* ctr = c->counters.as<unsigned long long>();
   unsigned long long* ctr_h = c->counters_host.as<unsigned long long>();
   for (int32_t v0 = 0, b = 0; v0 < V; v0 += vb, ++b) {
     const int nb = std::min(vb, V - v0);
-    const ProjPtrs P = proj_ptrs(c, keep, v0, n);
+    const ProjPtrs P = proj_ptrs(K, keep, v0, n);
     const BatchLayout L = layout_batch(c, vh, cams, v0, nb, P.cols);
     const int total_tiles = L.total_tiles;
     const size_t sat_bytes = static_cast<size_t>((total_tiles + 63) / 64) * 8;
@@ -1154,8 +1161,8 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
     FS_CUDA(cudaMemsetAsync(skip, 0xFF, sat_bytes, stream), "skip bits");
     FS_CUDA(cudaMemsetAsync(deep, 0, sat_bytes, stream), "deep bits");
     FS_CUDA(cudaMemsetAsync(c->total.p, 0, sizeof(uint32_t), stream), "visible clear");
-    const uint8_t* satc = kept ? c->kl_satc.as<uint8_t>() + c->kl_tile_off[b] : nullptr;
-    const uint32_t* bound = kept ? c->kl_bound.as<uint32_t>() + static_cast<int64_t>(b) * chunks
+    const uint8_t* satc = kept ? K->kl_satc.as<uint8_t>() + K->kl_tile_off[b] : nullptr;
+    const uint32_t* bound = kept ? K->kl_bound.as<uint32_t>() + static_cast<int64_t>(b) * chunks
                                  : nullptr;
     c->stats.kernel_launches += 1;
     FS_CUDA(fs::launch_mark_tiles(nF, nb, n, F, vd, P.cnt, P.foot, skip, c->total.as<uint32_t>(),
@@ -1168,9 +1175,9 @@ fs_status recheck_impl(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int3
       // walk the main pass's kept chunk lists
       fs::RecheckLists Ls{};
       for (int ci = 0; ci < chunks; ++ci) {
-        Ls.val[ci] = c->kl_val[static_cast<size_t>(b) * chunks + ci].as<uint32_t>();
-        Ls.ranges[ci] = c->kl_ranges.as<uint2>() +
-                        (c->kl_tile_off[b] * chunks + static_cast<int64_t>(ci) * total_tiles);
+        Ls.val[ci] = K->kl_val[static_cast<size_t>(b) * chunks + ci].as<uint32_t>();
+        Ls.ranges[ci] = K->kl_ranges.as<uint2>() +
+                        (K->kl_tile_off[b] * chunks + static_cast<int64_t>(ci) * total_tiles);
       }
       Ls.chunks = chunks;
       Ls.sat_chunk = satc;
@@ -1385,6 +1392,23 @@ fs_status fs_assign(fs_ctx* c, const void* table, int32_t table_dtype, int64_t n
   return FS_OK;
 }
 
+// Whether every view's projection can stay resident for the near-tie
+// re-check: it must fit in half of the free device memory (108 B per
+// Gaussian and view; 76 B with reduced-precision records), and the context
+// must not be set to project again.
+bool keep_fits(const fs_ctx* c, int64_t n, int32_t V) {
+  if (c->recheck_reproject) return false;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const double need = (c->compact ? 76.0 : 108.0) * static_cast<double>(n) * V;
+  const double have = static_cast<double>(c->rec.bytes + c->foot.bytes + c->cnt.bytes +
+                                          c->dlo.bytes + c->dkey.bytes);
+  return need <= have + 0.5 * static_cast<double>(free_b);
+}
+
 fs_status fs_solve(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t V,
                    const void* const* masks, int32_t mask_dtype, int32_t mask_memory, int32_t E,
                    float gamma, const fs_result* out, void* stream) {
@@ -1419,16 +1443,7 @@ fs_status fs_solve(fs_ctx* c, const fs_scene* s, const fs_camera* cams, int32_t 
   // keep every view's projection resident for the re-check when it fits in
   // half of the free device memory (108 B per Gaussian and view; 76 B with
   // reduced-precision records)
-  bool keep = false;
-  if (recheck && !c->recheck_reproject) {
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-      const double need = (c->compact ? 76.0 : 108.0) * static_cast<double>(n) * V;
-      const double have = static_cast<double>(c->rec.bytes + c->foot.bytes + c->cnt.bytes +
-                                              c->dlo.bytes + c->dkey.bytes);
-      keep = need <= have + 0.5 * static_cast<double>(free_b);
-    }
-  }
+  const bool keep = recheck && keep_fits(c, n, V);
   FS_TRY(accumulate_impl(c, s, cams, V, masks, mask_dtype, mask_memory, E, table, FS_F64, keep,
                          st));
   uint64_t* bits = out->member_bits;
@@ -1640,8 +1655,10 @@ fs_status fs_graph_create(fs_ctx* tmpl, const fs_scene* s, const fs_camera* cams
     if ((st = c->margin_tmp.ensure(nn * 4, "margins")) != FS_OK) return bail(st);
     g->margin = c->margin_tmp.as<float>();
   }
-  // the re-check projects again on its own context (kept lists would live in
-  // the captured one): g->keep stays false
+  // the re-check runs on a context of its own, which reads the captured
+  // solve's resident projection and kept lists when they fit (g->keep) and
+  // writes only its own buffers, so nothing the graph holds is ever resized
+  g->keep = g->recheck && keep_fits(c, n, V);
   if (g->recheck) {
     if ((st = fs_create(&g->rc, tmpl->device, &o)) != FS_OK) return bail(st);
     const int vbr = batch_views(g->rc, n);
@@ -1694,7 +1711,8 @@ fs_status fs_graph_launch(fs_graph* g, void* stream) {
     rc->events_used = 0;
     FS_CUDA(cudaMemsetAsync(rc->counters.p, 0, rc->counters.bytes, st), "counters clear");
     FS_TRY(recheck_impl(rc, g->s, g->cams.data(), V, g->mask_dtype, g->E, g->gamma, g->table,
-                        FS_F64, g->bits, g->label, g->margin, false, st));
+                        FS_F64, g->bits, g->label, g->margin, g->keep, st,
+                        g->keep ? g->c : nullptr));
   }
   const int64_t count = g->s->n * static_cast<int64_t>(g->E);
   if (g->out.table && g->out.table_dtype == FS_F32)
