@@ -329,6 +329,30 @@ fs_status fs_synchronize(fs_ctx* ctx, void* stream, fs_stats* stats);
  * bytes of device memory for the duration of the call. */
 fs_status fs_check_wait_timeout(int32_t device, int32_t spins);
 
+/* Test hooks (no counterpart in the paper): the library's own primitives on
+ * caller-owned device buffers, so that tests can check each one alone
+ * against a plain CPU result.  Synchronous on `device`; each call allocates
+ * its temporary device storage for its own duration.  FS_INVALID_ARGUMENT for
+ * a bad device, NULL array with n > 0, or a size out of range.
+ *
+ * fs_test_sort_pairs: stable sort, in place, of n (key, val) pairs (two
+ *   device arrays of n uint32, n < 2^31) by key, for keys below 2^bits
+ *   (1 <= bits <= 32; the passes take whole 8- or 9-bit digits, so bits
+ *   above `bits` must be zero): the radix sort that orders the depth keys
+ *   and the tile ids of the binning (Sec. 4.2's tile lists).
+ * fs_test_exclusive_scan: out[k] = in[0] + ... + in[k - 1] (mod 2^32) over
+ *   n device uint32 (n < 2^31); *total (host) = the sum of all n.
+ * fs_test_tile_ranges: for n keys in non-decreasing order (device uint32,
+ *   each < n_tiles, checked on the host), ranges (device, n_tiles pairs of
+ *   uint32) receives per tile t the run [first, last + 1) of key t, and
+ *   [0, 0) for a tile without an entry. */
+fs_status fs_test_sort_pairs(int32_t device, uint32_t* keys, uint32_t* vals, int64_t n,
+                             int32_t bits);
+fs_status fs_test_exclusive_scan(int32_t device, const uint32_t* in, uint32_t* out, int64_t n,
+                                 uint32_t* total);
+fs_status fs_test_tile_ranges(int32_t device, const uint32_t* keys, int64_t n, int32_t n_tiles,
+                              uint32_t* ranges);
+
 /* ---- request server (continuous batching) -----------------------------------
  * Segmentation requests against resident scenes, served by `slots` workers
  * that each own a context and a CUDA stream.  A request (scene, cameras,

@@ -1791,6 +1791,89 @@ fs_status fs_check_wait_timeout(int32_t device, int32_t spins) {
   return FS_OK;
 }
 
+namespace {
+
+fs_status test_device(int32_t device, const char* what) {
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= count) return fail(FS_INVALID_ARGUMENT, "%s: bad device %d", what, device);
+  return FS_OK;
+}
+
+}  // namespace
+
+fs_status fs_test_sort_pairs(int32_t device, uint32_t* keys, uint32_t* vals, int64_t n,
+                             int32_t bits) {
+  FS_TRY(test_device(device, "fs_test_sort_pairs"));
+  if (n < 0 || n >= (static_cast<int64_t>(1) << 31) || bits < 1 || bits > 32 ||
+      (n > 0 && (!keys || !vals)))
+    return fail(FS_INVALID_ARGUMENT, "fs_test_sort_pairs: bad arrays, n or bits");
+  if (n == 0) return FS_OK;
+  DeviceGuard g(device);
+  DevBuf ak, av, tmp;
+  FS_TRY(ak.ensure(static_cast<size_t>(n) * 4, "sort keys"));
+  FS_TRY(av.ensure(static_cast<size_t>(n) * 4, "sort vals"));
+  FS_TRY(tmp.ensure(fs::radix_temp_bytes(n), "sort temp"));
+  bool alt = false;
+  cudaError_t e = fs::radix_sort_pairs(keys, vals, ak.as<uint32_t>(), av.as<uint32_t>(), n, bits,
+                                       tmp.p, &alt, nullptr);
+  if (e == cudaSuccess && alt) {
+    e = cudaMemcpy(keys, ak.p, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(vals, av.p, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToDevice);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  ak.release();
+  av.release();
+  tmp.release();
+  if (e != cudaSuccess) return cuda_fail(e, "fs_test_sort_pairs");
+  return FS_OK;
+}
+
+fs_status fs_test_exclusive_scan(int32_t device, const uint32_t* in, uint32_t* out, int64_t n,
+                                 uint32_t* total) {
+  FS_TRY(test_device(device, "fs_test_exclusive_scan"));
+  if (n < 0 || n >= (static_cast<int64_t>(1) << 31) || !total || (n > 0 && (!in || !out)))
+    return fail(FS_INVALID_ARGUMENT, "fs_test_exclusive_scan: bad arrays or n");
+  *total = 0;
+  if (n == 0) return FS_OK;
+  DeviceGuard g(device);
+  DevBuf tmp, tot;
+  FS_TRY(tmp.ensure(fs::scan_temp_bytes(n), "scan temp"));
+  FS_TRY(tot.ensure(4, "scan total"));
+  cudaError_t e = fs::exclusive_scan(in, nullptr, out, n, tot.as<uint32_t>(), tmp.p, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(total, tot.p, 4, cudaMemcpyDeviceToHost);
+  tmp.release();
+  tot.release();
+  if (e != cudaSuccess) return cuda_fail(e, "fs_test_exclusive_scan");
+  return FS_OK;
+}
+
+fs_status fs_test_tile_ranges(int32_t device, const uint32_t* keys, int64_t n, int32_t n_tiles,
+                              uint32_t* ranges) {
+  FS_TRY(test_device(device, "fs_test_tile_ranges"));
+  if (n < 0 || n >= (static_cast<int64_t>(1) << 31) || n_tiles < 1 || !ranges ||
+      (n > 0 && !keys))
+    return fail(FS_INVALID_ARGUMENT, "fs_test_tile_ranges: bad arrays, n or n_tiles");
+  DeviceGuard g(device);
+  // every key must name a tile: the kernel writes ranges[key]
+  std::vector<uint32_t> hk(static_cast<size_t>(n));
+  cudaError_t e = n > 0 ? cudaMemcpy(hk.data(), keys, static_cast<size_t>(n) * 4,
+                                     cudaMemcpyDeviceToHost)
+                        : cudaSuccess;
+  if (e != cudaSuccess) return cuda_fail(e, "fs_test_tile_ranges");
+  for (int64_t k = 0; k < n; ++k)
+    if (hk[k] >= static_cast<uint32_t>(n_tiles) || (k > 0 && hk[k] < hk[k - 1]))
+      return fail(FS_INVALID_ARGUMENT, "fs_test_tile_ranges: key %lld out of range or order",
+                  (long long)k);
+  e = cudaMemset(ranges, 0, static_cast<size_t>(n_tiles) * 8);
+  if (e == cudaSuccess && n > 0)
+    e = fs::launch_ranges(n, keys, reinterpret_cast<uint2*>(ranges), nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "fs_test_tile_ranges");
+  return FS_OK;
+}
+
 fs_status fs_synchronize(fs_ctx* c, void* stream, fs_stats* stats) {
   if (!c) return fail(FS_INVALID_ARGUMENT, "NULL context");
   DeviceGuard g(c->device);

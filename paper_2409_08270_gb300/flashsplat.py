@@ -31,6 +31,7 @@ STATUS_NAMES = {0: "FS_OK", 1: "FS_INVALID_ARGUMENT", 2: "FS_OUT_OF_MEMORY", 3: 
 EXPORTS = ["fs_version", "fs_last_error", "fs_create", "fs_destroy", "fs_scene_create",
            "fs_scene_destroy", "fs_scene_size", "fs_accumulate", "fs_assign", "fs_solve",
            "fs_synchronize", "fs_keep_after_removal", "fs_check_wait_timeout", "fs_render_masks",
+           "fs_test_sort_pairs", "fs_test_exclusive_scan", "fs_test_tile_ranges",
            "fs_graph_create", "fs_graph_launch", "fs_graph_synchronize", "fs_graph_destroy",
            "fs_solve_noalloc", "fs_server_create", "fs_server_add_scene",
            "fs_server_submit", "fs_server_fetch", "fs_server_fetch_for", "fs_server_cancel",
@@ -135,6 +136,9 @@ def load(path: str | None = None):
                            i32, f32, ctypes.POINTER(fs_result), vp]),
         "fs_synchronize": (i32, [vp, vp, ctypes.POINTER(fs_stats)]),
         "fs_check_wait_timeout": (i32, [i32, i32]),
+        "fs_test_sort_pairs": (i32, [i32, vp, vp, i64, i32]),
+        "fs_test_exclusive_scan": (i32, [i32, vp, vp, i64, ctypes.POINTER(ctypes.c_uint32)]),
+        "fs_test_tile_ranges": (i32, [i32, vp, i64, i32, vp]),
         "fs_keep_after_removal": (i32, [vp, vp, i64, ctypes.c_uint64, vp, ctypes.POINTER(i64), vp]),
         "fs_graph_create": (i32, [vp, vp, ctypes.POINTER(fs_camera), i32, ctypes.POINTER(vp), i32,
                                   i32, f32, ctypes.POINTER(fs_result), ctypes.POINTER(vp)]),
@@ -240,6 +244,29 @@ def fs_synchronize(ctx, stream=0) -> fs_stats:
 def fs_check_wait_timeout(device: int, spins: int) -> int:
     """Status of the bounded-wait diagnostic (FS_TIMEOUT expected)."""
     return load().fs_check_wait_timeout(device, spins)
+
+
+def fs_test_sort_pairs(device: int, keys, vals, bits: int) -> None:
+    """Stable in-place sort of two uint32 device arrays by key, for keys
+    below 2^bits (the library's radix sort, for isolated tests)."""
+    check(load().fs_test_sort_pairs(device, keys.data_ptr(), vals.data_ptr(), keys.numel(),
+                                    bits))
+
+
+def fs_test_exclusive_scan(device: int, inp, out) -> int:
+    """Exclusive prefix sum (mod 2^32) of a uint32 device array into `out`;
+    returns the total."""
+    tot = ctypes.c_uint32(0)
+    check(load().fs_test_exclusive_scan(device, inp.data_ptr(), out.data_ptr(), inp.numel(),
+                                        ctypes.byref(tot)))
+    return int(tot.value)
+
+
+def fs_test_tile_ranges(device: int, keys, n_tiles: int, ranges) -> None:
+    """Per tile, the [first, last + 1) run of its key in a sorted uint32
+    device array, into `ranges` (n_tiles x 2 uint32 on the device)."""
+    check(load().fs_test_tile_ranges(device, keys.data_ptr(), keys.numel(), n_tiles,
+                                     ranges.data_ptr()))
 
 
 def fs_solve_noalloc(device, g: fs_gaussians, cams, masks, mask_dtype, E, gamma, table,
