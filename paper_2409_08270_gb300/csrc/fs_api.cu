@@ -240,7 +240,7 @@ DevBuf* const* workspace_bufs(fs_ctx* c, size_t* count) {
                     &c->rk_F, &c->rk_map, &c->rk_R, &c->rk_Rb, &c->kl_ranges, &c->kl_satc,
                     &c->kl_bound, &c->key_range, &c->lb_tmp, &c->key_a2, &c->val_a2,
                     &c->key_b2, &c->val_b2, &c->cols, &c->rd_flag, &c->rd_offs, &c->rd_val,
-                    &c->render_out, &c->chunk_bnd};
+                    &c->render_out, &c->chunk_bnd, &c->free_tab};
   for (DevBuf* b : list) bufs[k++] = b;
   *count = k;
   return bufs;
@@ -346,7 +346,8 @@ fs_status fs_destroy(fs_ctx* c) {
                     &c->dkey, &c->rk_flag, &c->rk_offs, &c->rk_F, &c->rk_map, &c->rk_R,
                     &c->rk_Rb, &c->kl_ranges, &c->kl_satc, &c->kl_bound, &c->key_range, &c->lb_tmp,
                     &c->key_a2, &c->val_a2, &c->key_b2, &c->val_b2, &c->cols,
-                    &c->rd_flag, &c->rd_offs, &c->rd_val, &c->render_out, &c->chunk_bnd};
+                    &c->rd_flag, &c->rd_offs, &c->rd_val, &c->render_out, &c->chunk_bnd,
+                    &c->free_tab};
   for (DevBuf& b : c->kl_val) b.release();
   for (DevBuf* b : bufs) b->release();
   c->views_host.release();
