@@ -119,7 +119,9 @@ __global__ void __launch_bounds__(256) state_init_kernel(
 constexpr int kRound = 32;     // Gaussians composited per round (one per lane)
 constexpr int kStep = 64;      // list entries staged per block step
 constexpr int kQCap = 96;      // per-warp queue: a partial round plus one step
-constexpr int kMinorCap = 8;   // label-boundary lanes a warp sums in shared memory
+constexpr int kMinorCap = 2;   // label-boundary lanes a warp sums in shared memory (more
+                               // add their second pixel to the table directly; the cap keeps
+                               // seven blocks' shared memory within an SM's)
 
 // Per-warp shared memory.  The queue is a ring of kQCap Gaussians, two per
 // float4 (g = first half of each component pair, h = second).
@@ -377,7 +379,7 @@ __device__ __forceinline__ int rank_by_key(int key, uint32_t lt) {
 }
 
 template <typename LabelT, typename TableT, bool kCensus>
-__global__ void __launch_bounds__(128, 6) blend_kernel(
+__global__ void __launch_bounds__(128, 7) blend_kernel(
     const ViewParams* __restrict__ views, const uint2* __restrict__ ranges,
     const uint32_t* __restrict__ list_val, const ProjRecord* __restrict__ rec,
     const CompactRecord* __restrict__ rec16, int64_t n, int E, TableT* __restrict__ table,
