@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(256) state_init_kernel(
 // ---------------------------------------------------------------------------
 constexpr int kRound = 32;     // Gaussians composited per round (one per lane)
 constexpr int kStep = 64;      // list entries staged per block step
+constexpr int kStagers = kStep / 32;  // warps that stage them, one entry per thread
 constexpr int kQCap = 96;      // per-warp queue: a partial round plus one step
 constexpr int kMinorCap = 2;   // label-boundary lanes a warp sums in shared memory (more
                                // add their second pixel to the table directly; the cap keeps
@@ -472,7 +473,7 @@ __global__ void __launch_bounds__(128, 7) blend_kernel(
   // -(1e-4 / kSkipScale rounded down to the float below) / ulp
   const float thr = 1e-4f * kTScale;
   const float neg_thr = -__uint_as_float(__float_as_uint(thr) - 1u) * kStepScale;
-  // staging: warps 0 and 1 take one list entry per thread and step
+  // staging: the first kStagers warps take one list entry per thread and step
   const bool stager = threadIdx.x < kStep;
   const float tcx = static_cast<float>(tx * kTile + 8), tcy = static_cast<float>(ty * kTile + 8);
   uint32_t head = 0, n_staged = 0;
@@ -486,7 +487,7 @@ __global__ void __launch_bounds__(128, 7) blend_kernel(
     const bool more = base < rg.y;
     const uint32_t g_here = g_next;
     if (stager && base + kStep + threadIdx.x < rg.y) g_next = list_val[base + kStep + threadIdx.x];
-    // ---- stage (warps 0 and 1): entry base + threadIdx.x against all four
+    // ---- stage (the stager warps): entry base + threadIdx.x against all four
     // sub-tiles; bit s of keep: the entry goes to sub-tile s's queue
     uint32_t keep = 0u;
     float4 wk = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -546,12 +547,18 @@ __global__ void __launch_bounds__(128, 7) blend_kernel(
     if (kCensus) ++n_steps;
     // the queue tails after this step (entries of warp 0, then of warp 1)
     const uint32_t my_tail = B.tail[sub];
-    const uint32_t new_tail = my_tail + B.cnt[0][sub] + B.cnt[1][sub];
+    uint32_t new_tail = my_tail;
+#pragma unroll
+    for (int w = 0; w < kStagers; ++w) new_tail += B.cnt[w][sub];
     // ---- append the kept entries to the sub-tiles' queues, in list order
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       if (!((keep >> s) & 1u)) continue;
-      const uint32_t qi = (B.tail[s] + (warp == 0 ? 0u : B.cnt[0][s]) + __popc(bal[s] & lt)) % kQCap;
+      uint32_t before = B.tail[s];  // entries queued ahead: earlier steps', earlier stagers'
+#pragma unroll
+      for (int w = 0; w < kStagers; ++w)
+        if (w < warp) before += B.cnt[w][s];
+      const uint32_t qi = (before + __popc(bal[s] & lt)) % kQCap;
       WarpSmem& T = B.w[s];
       const int pr = static_cast<int>(qi >> 1), c = static_cast<int>(qi & 1u);
       const float ex = (s & 1) ? 4.f : -4.f, ey = (s & 2) ? 4.f : -4.f;
