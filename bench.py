@@ -40,10 +40,10 @@ FLOPS_PER_PAIR = 19   # FP32 flops of one (pixel, Gaussian) compositing step, FM
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of blend_kernel per work unit (census pair), from
 # one ncu capture of the current kernel: the six launches of an 8-view solve
-# of the binary workload read 240.5 MB and wrote 0.63 MB for 435.7 M census
+# of the binary workload read 240.4 MB and wrote 0.62 MB for 435.7 M census
 # pairs (profiles/blend_kernel_binary_1M_8views.txt); scaled by the units of
 # the launches timed here.
-BLEND_DRAM_BYTES_PER_PAIR = 241.1e6 / 435.7e6
+BLEND_DRAM_BYTES_PER_PAIR = 241.0e6 / 435.7e6
 
 
 def parse():
