@@ -245,7 +245,7 @@ __device__ __forceinline__ bool reaches(const Staged& e, float lx, float ly) {
 // the pixel; pass 2 composites the pixel in float pairs up to that position
 // (deep tiles: up to its stop).
 template <typename LabelT>
-__global__ void __launch_bounds__(kTilePixels) recheck_blend_kernel(
+__global__ void __launch_bounds__(kTilePixels, 6) recheck_blend_kernel(
     const ViewParams* __restrict__ views, RecheckLists L, const uint64_t* __restrict__ skip,
     const ProjRecord* __restrict__ rec, const CompactRecord* __restrict__ rec16,
     const float4* __restrict__ pos_op, int64_t n, int E, const int32_t* __restrict__ map,
