@@ -257,7 +257,10 @@ __global__ void __launch_bounds__(256, kFast ? 4 : 3) project_kernel(
         syy = c;
         det32 = dt;
       } else {
-        const f2 ux = f2_div(tx, tz), uy = f2_div(ty, tz);
+        // one float-pair reciprocal of the depth, then (x, y) / z side by side
+        const f2 iz = f2_div(f2_from(1.f), tz);
+        const f2x2 uxy = f2x2_mul(f2x2_pack(tx, ty), f2x2_pack(iz, iz));
+        const f2 ux = f2x2_first(uxy), uy = f2x2_second(uxy);
         const f2 fx = {vp.fx_hi, vp.fx_lo}, fy = {vp.fy_hi, vp.fy_lo};
         // the x and y halves of the pinhole map run side by side (f2x2)
         const f2x2 fxy = f2x2_pack(fx, fy);
@@ -268,7 +271,6 @@ __global__ void __launch_bounds__(256, kFast ? 4 : 3) project_kernel(
         depth_l = tz.lo;
         R.misc.w = depth;
         R16.depth = depth;
-        const f2 iz = f2_div(f2_from(1.f), tz);
         const f2x2 J = f2x2_mul(fxy, f2x2_pack(iz, iz));  // (fx / z, fy / z)
         const f2 uxc = f2_clamp(ux, vp.limx_hi, vp.limx_lo);
         const f2 uyc = f2_clamp(uy, vp.limy_hi, vp.limy_lo);
@@ -314,8 +316,10 @@ __global__ void __launch_bounds__(256, kFast ? 4 : 3) project_kernel(
         }
         const f2 en = f2_sqrt(f2_add(f2_mul(ex, ex), f2_mul(ey, ey)));
         if (en.hi > 0.f) {
-          ex = f2_div(ex, en);
-          ey = f2_div(ey, en);
+          const f2 ien = f2_div(f2_from(1.f), en);
+          const f2x2 e = f2x2_mul(f2x2_pack(ex, ey), f2x2_pack(ien, ien));
+          ex = f2x2_first(e);
+          ey = f2x2_second(e);
         } else {
           ex = f2_from(1.f);
           ey = f2_from(0.f);
