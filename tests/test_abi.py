@@ -76,3 +76,36 @@ def test_product_path_has_no_oracle_dependency():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "fs_oracle" not in text and "fso_" not in text, f
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding passes across the ABI has the header's size
+    and field offsets (a C program compiled against include/flashsplat.h
+    prints them; gcc only, no GPU)."""
+    import shutil
+    from paper_2409_08270_gb300 import flashsplat as fsb
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = [fsb.fs_options, fsb.fs_gaussians, fsb.fs_camera, fsb.fs_stats, fsb.fs_result,
+               fsb.fs_server_options, fsb.fs_server_info]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "flashsplat.h"',
+             "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for field, *_ in st._fields_:
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    want = dict(line.rsplit(" ", 1) for line in out.strip().splitlines())
+    for st in structs:
+        name = st.__name__
+        assert int(want[name]) == ctypes.sizeof(st), name
+        for field, *_ in st._fields_:
+            assert int(want[f"{name}.{field}"]) == getattr(st, field).offset, (name, field)
