@@ -85,3 +85,28 @@ def test_object_removal_keeps_the_rest(fsb):
     assert decided.mean() > 0.9
     np.testing.assert_array_equal(gpu_keep[decided], ora_keep[decided])
     assert 0 < gpu_keep.sum() < w.n
+
+
+def test_stage_times_cover_the_solve(fsb):
+    """fs_options.time_stages: every stage of a solve is timed on its own
+    stream (fs_stats.stage_ms); the blend's share is blend_ms, and without
+    the option nothing is timed."""
+    w = synth.tiny_scene()
+    s = fsb.Solver(w.gaussians, time_stages=True, recheck_margin=1e30)
+    try:
+        st = s.solve(w.cams, w.masks, w.E, w.gamma)["stats"]
+    finally:
+        s.close()
+    ms = dict(zip(fsb.STAGES, st.stage_ms))
+    assert all(v >= 0.0 for v in ms.values()), ms
+    for name in ("project", "depth_sort", "pixel_state", "binning", "tile_sort", "blend",
+                 "recheck", "assign"):
+        assert ms[name] > 0.0, (name, ms)
+    assert st.blend_ms == ms["blend"]
+    assert st.blend_launches > 0
+    plain = fsb.Solver(w.gaussians)
+    try:
+        st0 = plain.solve(w.cams, w.masks, w.E, w.gamma)["stats"]
+    finally:
+        plain.close()
+    assert all(v == 0.0 for v in st0.stage_ms)
